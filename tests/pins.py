@@ -1,0 +1,163 @@
+"""Pin measurements of the oracle against results that do not come from it.
+
+Each function runs one family of checks on an oracle object (the shipped
+``oracle`` module, or a compiled copy of ``bs_oracle.c`` with a planted
+mistake) and returns the numbers the tests compare with their bounds.
+
+  single_tet   Eq. 1 on one tet / the star of a node, exact values from the
+               ray-free Duffy-cone integrator in ``brute_force.py``.
+  ball         uniform omega in a tetrahedralised unit ball: closed form
+               omega x (x - c)/3 inside, a^3 omega x (x - c) / (3|x - c|^3)
+               outside; convergence in h at 64 x 64 directions (Section 3.2
+               reports eps ~ h^2.15 for its ring).
+  hill         Hill's spherical vortex (Section 3.1), with the velocity
+               re-derived from the Stokes stream function (the printed
+               formula is garbled, see ``hill_velocity``).
+"""
+from __future__ import annotations
+
+import numpy as np
+from brute_force import tet_integral
+
+from workloads import ball_mesh, hill_vorticity
+from workloads.configs import jittered_grid
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def single_tet_fixture():
+    rng = np.random.default_rng(5)
+    V = np.array([[0, 0, 0], [1, 0.1, 0], [0.2, 1, 0.1], [0.1, 0.2, 1.0]])
+    om = rng.standard_normal((4, 3))
+    return V, om
+
+
+def single_tet(orc, Ns=(32, 64, 128), qs=(1, 4, 27, 64)):
+    V, om = single_tet_fixture()
+    tets = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    points = {
+        "inside": V.mean(axis=0) + 0.05,
+        "outside": np.array([1.2, 0.9, 0.8]),
+        "vertex": V[2].copy(),
+        "far": np.array([3.0, 2.0, 1.0]),
+    }
+    out = {}
+    for name, x in points.items():
+        exact = tet_integral(x, V, om, 48)
+        out[name] = {
+            "ray": [_rel(orc.velocity(V, tets, om, x[None], far_ratio=np.inf, n_theta=N, n_phi=N)[0], exact)
+                    for N in Ns],
+            "gauss": [_rel(orc.velocity(V, tets, om, x[None], far_ratio=0.0, tet_order=q)[0], exact) for q in qs],
+        }
+    return out
+
+
+def star_fixture():
+    rng = np.random.default_rng(11)
+    nodes, tets = jittered_grid(4, 0.0, 1.0, rng)
+    om = rng.standard_normal(nodes.shape)
+    c = 1 + 4 * (1 + 4 * 1)  # interior node (1, 1, 1)
+    star = tets[np.any(tets == c, axis=1)]
+    return nodes, star, om, c
+
+
+def star(orc, Ns=(16, 32, 64, 128)):
+    """Pure-ray velocity at an interior node from the 24 tets around it, against the Duffy sum."""
+    nodes, st, om, c = star_fixture()
+    x = nodes[c]
+    exact = sum(tet_integral(x, nodes[t], om[t], 48) for t in st)
+    return [_rel(orc.velocity(nodes, st, om, x[None], far_ratio=np.inf, n_theta=N, n_phi=N)[0], exact)
+            for N in Ns]
+
+
+BALL_OMEGA = np.array([0.3, -0.5, 0.8])
+
+
+def _ball_points(mesh, count, rmax, seed=0):
+    r = np.linalg.norm(mesh.nodes, axis=1)
+    idx = np.nonzero(r < rmax)[0]
+    rng = np.random.default_rng(seed)
+    return mesh.nodes[rng.choice(idx, size=min(count, len(idx)), replace=False)]
+
+
+def ball(orc, ns=(5, 9, 17), N=64, count=8):
+    """RMS error / |omega|_max at interior nodes for the pure-ray rule, and the fitted slope in h."""
+    errs = []
+    hs = []
+    for n in ns:
+        b = ball_mesh(n, lambda X: np.tile(BALL_OMEGA, (len(X), 1)))
+        X = _ball_points(b, count, 0.55)
+        v = orc.velocity(b.nodes, b.tets, b.omega, X, far_ratio=np.inf, n_theta=N, n_phi=N)
+        exact = np.cross(BALL_OMEGA, X) / 3.0
+        errs.append(float(np.sqrt(np.mean(np.sum((v - exact) ** 2, axis=1))) / np.abs(BALL_OMEGA).max()))
+        hs.append(2.0 / (n - 1))
+    slope = float(np.polyfit(np.log(hs), np.log(errs), 1)[0])
+    return errs, slope
+
+
+def ball_outside(orc, n=9, params=None):
+    params = params or dict(far_ratio=2.0, tet_order=4, n_theta=16, n_phi=16)
+    b = ball_mesh(n, lambda X: np.tile(BALL_OMEGA, (len(X), 1)))
+    X = np.array([[0.0, 0.0, 1.5], [1.3, 0.4, -0.2], [-0.9, -1.1, 0.7], [2.5, -1.0, 0.5]])
+    v = orc.velocity(b.nodes, b.tets, b.omega, X, **params)
+    R = np.linalg.norm(X, axis=1)
+    exact = np.cross(BALL_OMEGA, X) / (3.0 * R[:, None] ** 3)
+    return float(np.abs(v - exact).max() / np.abs(exact).max())
+
+
+def hill_velocity(X, A=1.0, a=1.0):
+    """Velocity of Hill's spherical vortex in the frame where the fluid is at rest far away.
+
+    From the Stokes stream function psi = (A/10) r^2 (a^2 - r^2 - z^2) inside
+    (translation speed U = 2 A a^2 / 15): u_r = A r z / 5,
+    u_z = (A/5)(5a^2/3 - 2 r^2 - z^2) inside, a point dipole
+    (U a^3 / 2 R^3)(3 (z.R^) R^ - z^) outside.  omega = A (-y, x, 0) inside.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    x, y, z = X.T
+    r = np.hypot(x, y)
+    R = np.linalg.norm(X, axis=1)
+    U = 2.0 * A * a * a / 15.0
+    ur = A * r * z / 5.0
+    uz = A / 5.0 * (5.0 * a * a / 3.0 - 2.0 * r * r - z * z)
+    safe = np.where(r > 0, r, 1.0)
+    vin = np.stack([ur * x / safe, ur * y / safe, uz], axis=1)
+    Rs = np.where(R > 0, R, 1.0)
+    rh = X / Rs[:, None]
+    vout = U * a**3 / (2.0 * Rs[:, None] ** 3) * (3.0 * rh[:, 2:3] * rh - np.array([0.0, 0.0, 1.0]))
+    return np.where((R < a)[:, None], vin, vout)
+
+
+def hill(orc, ns=(5, 9, 17), params=None, count=12):
+    params = params or dict(far_ratio=2.0, tet_order=4, n_theta=16, n_phi=16)
+    errs = []
+    for n in ns:
+        b = ball_mesh(n, hill_vorticity)
+        X = _ball_points(b, count, 0.6)
+        v = orc.velocity(b.nodes, b.tets, b.omega, X, **params)
+        ex = hill_velocity(X)
+        errs.append(float(np.sqrt(np.mean(np.sum((v - ex) ** 2, axis=1))) / np.abs(ex).max()))
+    return errs
+
+
+def divergence(orc, N=64, far_ratio=np.inf, count=4, seed=3):
+    """max |div v| / max |grad v| by central differences at off-node points of the unit-cube mesh."""
+    from workloads import config1_plain
+
+    m = config1_plain()
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0.3, 0.7, size=(count, 3))
+    d = 1e-3 / 8
+    pts = []
+    for x in X:
+        for j in range(3):
+            e = np.zeros(3)
+            e[j] = d
+            pts += [x + e, x - e]
+    v = orc.velocity(m.nodes, m.tets, m.omega, np.array(pts), far_ratio=far_ratio, n_theta=N, n_phi=N)
+    v = v.reshape(count, 3, 2, 3)
+    grad = (v[:, :, 0, :] - v[:, :, 1, :]) / (2 * d)  # [pt, j (d/dx_j), component]
+    div = np.einsum("pjj->p", grad)
+    return float(np.abs(div).max() / np.abs(grad).max())

@@ -1,0 +1,48 @@
+"""Input generators: sizes, orientation, conformity and seeding (no GPU)."""
+import numpy as np
+
+from workloads import config1_plain, config2_ring, config3_samples, kuhn_grid
+from workloads.configs import ball_mesh, config4_batch
+from workloads.mesh import tet_volumes6
+
+
+def test_kuhn_grid_counts_and_volume():
+    for n in (2, 3, 5):
+        nodes, tets = kuhn_grid(n, -1.0, 1.0)
+        assert nodes.shape == (n**3, 3) and tets.shape == (6 * (n - 1) ** 3, 4)
+        vol = tet_volumes6(nodes, tets) / 6
+        assert np.all(vol > 0)
+        assert abs(vol.sum() - 8.0) < 1e-12
+
+
+def test_kuhn_grid_is_conforming():
+    """Every interior face is shared by exactly two tets, boundary faces by one."""
+    n = 4
+    nodes, tets = kuhn_grid(n, 0.0, 1.0)
+    faces = {}
+    for t in tets:
+        for f in ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2)):
+            key = tuple(sorted(t[list(f)]))
+            faces[key] = faces.get(key, 0) + 1
+    counts = np.array(list(faces.values()))
+    assert set(counts) <= {1, 2}
+    assert (counts == 1).sum() == 6 * 2 * (n - 1) ** 2  # two triangles per boundary square
+
+
+def test_config_sizes_and_seeds():
+    a, b = config1_plain(), config1_plain()
+    assert a.n_nodes == 729 and a.n_tets == 3072
+    assert np.array_equal(a.nodes, b.nodes) and np.array_equal(a.omega, b.omega)
+    assert np.all(tet_volumes6(a.nodes, a.tets) > 0)
+    c2 = config2_ring()
+    assert c2.n_nodes == 32768 and c2.n_tets == 178746
+    s = config3_samples(64**3)
+    assert len(s) == 4096 and len(np.unique(s)) == 4096
+
+
+def test_ball_and_batch():
+    b = ball_mesh(9)
+    assert np.all(tet_volumes6(b.nodes, b.tets) > 0)
+    assert np.linalg.norm(b.nodes, axis=1).max() <= 1.0 + 1e-15
+    batch = config4_batch(count=4)
+    assert len(batch) == 4 and all(8 <= m.n_side <= 24 for m in batch)
