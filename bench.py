@@ -1,0 +1,317 @@
+"""Benchmark: Biot-Savart velocity at every node of the 64^3 Fourier workload on GB300.
+
+One step = one velocity evaluation at all 262144 nodes over all 1500282 tets
+(float32 bulk, far_ratio 2, 4-point far rule, 8 x 16 directions), i.e.
+3.93e11 node-tet interactions.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun): every rank evaluates its own replica of the workload
+(independent problems, no collective on the data path; weak scaling); the
+timed region is bracketed by barriers and the slowest rank's time is used.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import config3_fourier, config3_samples  # noqa: E402
+
+PARAMS = dict(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16)
+METRIC = "node-tet interactions/s (velocity at all nodes, FP32 path)"
+UNIT = "interactions/s"
+# algorithmic FP32 flops (far pair: 8 classify + 4 x 25 quadrature-point; near pair:
+# 8 classify + 9 per line bounding-sphere test; hit line: 80)
+FLOPS_FAR_PAIR = 108
+FLOPS_NEAR_PAIR_BASE = 8
+FLOPS_NEAR_PER_LINE = 9
+FLOPS_PER_HIT = 80
+FP32_LANES_PER_SM = 128
+MAX_SM_MHZ = 2070.0
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "velocity_fp32_fourier64_traffic.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_0712_1695_gb300", "csrc", f) for f in ("bs_velocity.cu", "bs_internal.cuh")]
+
+
+def workload_config():
+    return {"workload": "fourier-64^3: 262144 nodes x 1500282 tets, velocity at all nodes",
+            "far_ratio": PARAMS["far_ratio"], "tet_gauss_order": PARAMS["tet_gauss_order"],
+            "n_theta": PARAMS["n_theta"], "n_phi": PARAMS["n_phi"], "precision": "fp32",
+            "l2": "inputs larger than L2 (far records 168 MB, near records 192 MB per replica)"}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_oracle_sample(mesh, count: int, seed_offset: int = 0):
+    import oracle
+
+    idx = config3_samples(mesh.n_nodes, 4096)
+    rng = np.random.default_rng(77 + seed_offset)
+    sel = np.sort(rng.choice(idx, size=count, replace=False))
+    t = time.perf_counter()
+    oracle.velocity(mesh.nodes, mesh.tets, mesh.omega, mesh.nodes[sel], far_ratio=PARAMS["far_ratio"],
+                    tet_order=PARAMS["tet_gauss_order"], n_theta=PARAMS["n_theta"], n_phi=PARAMS["n_phi"])
+    dt = time.perf_counter() - t
+    return count * mesh.n_tets / dt, dt, oracle.num_threads()
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    mesh = config3_fourier()
+    import oracle
+
+    oracle.build()
+    count = args.ref_sample
+    for w in range(args.warmup):
+        run_oracle_sample(mesh, max(8, count // 8), seed_offset=100 + w)
+    vals, times = [], []
+    cores = 1
+    for s in range(args.steps):
+        v, dt, cores = run_oracle_sample(mesh, count, seed_offset=s)
+        vals.append(v)
+        times.append(dt)
+    value = count * mesh.n_tets * len(times) / sum(times)
+    sample = f"{count} of the 4096 seeded sample nodes x all {mesh.n_tets} tets per step (FP64 oracle)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=128, help="oracle sample nodes for cpu_baseline")
+    ap.add_argument("--ref-sample", type=int, default=96, help="oracle sample nodes per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+
+    import paper_0712_1695_gb300 as bs
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    bs.load()
+    mesh = config3_fourier()
+    h = bs.Mesh(mesh.nodes, mesh.tets, mesh.omega)
+    k = mesh.n_nodes
+    pairs = k * mesh.n_tets
+    stream = torch.cuda.current_stream()
+    pts = torch.from_numpy(mesh.nodes).cuda()
+    out = torch.empty((k, 3), dtype=torch.float64, device="cuda")
+    P = dict(PARAMS, precision=bs.BS_FP32)
+
+    # counts of one untimed evaluation give the algorithmic flops of a launch
+    cnt = torch.zeros((k, 3), dtype=torch.int32, device="cuda")
+    h.bs_velocity(pts, out_dev=out, counts_dev=cnt, **P)
+    h.bs_status()
+    c = cnt.to(torch.int64).sum(dim=0).cpu().numpy()
+    n_near, n_far, n_hit = int(c[0]), int(c[1]), int(c[2])
+    L = PARAMS["n_theta"] * PARAMS["n_phi"]
+    flops = (n_far * FLOPS_FAR_PAIR + n_near * (FLOPS_NEAR_PAIR_BASE + FLOPS_NEAR_PER_LINE * L)
+             + n_hit * FLOPS_PER_HIT)
+
+    for _ in range(args.warmup):
+        h.bs_velocity(pts, out_dev=out, **P)
+    barrier()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h.bs_profile(True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            h.bs_velocity(pts, out_dev=out, **P)
+        ev1.record(stream)
+        barrier()
+    kernel_ms, kernel_launches, all_launches = h.bs_profile_read()
+    h.bs_profile(False)
+    h.bs_status()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = world * pairs / (ms_max * 1e-3)
+
+    # end to end through the public API: pinned host inputs of a Lagrangian step (node
+    # positions and vorticity) -> device, bs_update, bs_velocity at all nodes, velocities -> host
+    nodes_h = torch.from_numpy(mesh.nodes).pin_memory()
+    omega_h = torch.from_numpy(mesh.omega).pin_memory()
+    vel_h = torch.empty((k, 3), dtype=torch.float64).pin_memory()
+    nodes_d = torch.empty_like(pts)
+    omega_d = torch.empty_like(pts)
+
+    def e2e_step():
+        nodes_d.copy_(nodes_h, non_blocking=True)
+        omega_d.copy_(omega_h, non_blocking=True)
+        h.bs_update(nodes_d, omega_d)
+        h.bs_velocity(nodes_d, out_dev=out, **P)
+        vel_h.copy_(out, non_blocking=True)
+        stream.synchronize()
+
+    e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        e2e_step()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    t_e2e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+    e2e_value = world * pairs / float(t_e2e.item())
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    props = torch.cuda.get_device_properties(local_rank)
+    n_sm = props.multi_processor_count
+    clocks = clk.summary()
+    kernel_avg_ms = kernel_ms / max(kernel_launches, 1)
+    achieved = flops / (kernel_avg_ms * 1e-3) / 1e12
+    peak = n_sm * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    traffic = None
+    if os.path.exists(PROFILE_TRAFFIC):
+        with open(PROFILE_TRAFFIC) as f:
+            tr = json.load(f)
+        if tr.get("kernel_source_hash") == kernel_source_hash():
+            traffic = tr.get("dram_bytes_per_launch")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "velocity_kernel<float,4,2,128,64>",
+                "kernel_ms": kernel_avg_ms,
+                "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {MAX_SM_MHZ:.0f} MHz",
+                "flops_per_launch": flops}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (n_sm * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e-6)
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+
+        oracle.build()
+        run_oracle_sample(mesh, 8, seed_offset=999)  # page in
+        v, dt, cores = run_oracle_sample(mesh, args.cpu_sample)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_sample} of the 4096 seeded sample nodes x all {mesh.n_tets} tets ({dt:.1f} s)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(),
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * k * 24, "d2h_bytes_per_step": k * 24},
+            "gpu_launches": int(all_launches), "clocks": clocks,
+            "counts": {"near_pairs": n_near, "far_pairs": n_far, "ray_hits": n_hit}}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,149 @@
+/*
+ * bs.h -- C ABI of libbs: Biot-Savart velocity on tetrahedral meshes with
+ * linearly varying nodal vorticity, on one GB300 GPU (sm_103a).
+ *
+ * Method (Carley, "Evaluation of Biot-Savart integrals on tetrahedral
+ * meshes"): for every evaluation point x and every tetrahedron T,
+ *   v(x) += contribution of T to  -(1/4pi) int r x omega / R^3 dV   (Eq. 1)
+ *   - T far  (|x - centroid(T)|^2 > (far_ratio * circumradius(T))^2):
+ *       tet Gauss rule applied to Eq. 1 (Section 1);
+ *   - T near: ray rule of Section 2 -- for each direction s_nm of the
+ *       Gauss-Legendre product rule of Eq. 3, the chord [R0, R1] of the line
+ *       x + R s through T and the exact integral of the linear omega along
+ *       it (Eq. 5, with the factor sign(R) that Eq. 2 needs when theta
+ *       covers [0, pi] only), weighted by k_nm = (pi/16) sin(phi_n) w_n w_m.
+ *
+ * Conventions for every call:
+ *   - Arrays are row-major and tightly packed: points/nodes/omega/velocity
+ *     are [count][3] float64, tets are [count][4] int32 node indices.
+ *   - "host" pointers are ordinary CPU memory, "device" pointers are CUDA
+ *     global memory of the current device.  The caller owns every array it
+ *     passes; the library copies what it keeps.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that take a stream are asynchronous and stream-ordered;
+ *     they do not synchronise the host.
+ *   - Every call returns BS_OK (0) or one of the BS_ERR_* codes below and,
+ *     on error, leaves a message for bs_last_error() (per host thread).
+ *     A call that returns an error has launched no kernel and written no
+ *     output.
+ */
+#ifndef BS_H
+#define BS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BS_API __attribute__((visibility("default")))
+#else
+#define BS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BS_OK 0
+#define BS_ERR_ARG 1     /* NULL pointer, negative size, parameter out of range */
+#define BS_ERR_MESH 2    /* node index out of range, or |volume| <= 1e-14 h^3   */
+#define BS_ERR_ORDER 3   /* tet_gauss_order not in {1, 4, 8, 27, 64}            */
+#define BS_ERR_CUDA 4    /* a CUDA runtime call failed                          */
+#define BS_ERR_TIMEOUT 5 /* a bounded device-side wait gave up                  */
+
+#define BS_FP64 0 /* every step in float64                                           */
+#define BS_FP32 1 /* float32 bulk with compensated per-point sums; the ray steps of   */
+                  /* pairs whose point sits on a vertex, edge or face of the tet run  */
+                  /* in float64; the final per-point sum is float64                   */
+
+typedef struct bs_ctx *bs_handle;
+typedef struct bs_batch_ctx *bs_batch;
+
+typedef struct {
+    double far_ratio;    /* far <=> |x-c|^2 > (far_ratio*rho)^2; must be >= 2 (so a tet
+                            with x at a vertex is never far) or +INFINITY (every tet
+                            near: the paper's all-ray rule of Section 2.2)          */
+    int tet_gauss_order; /* far rule points: 1 (centroid), 4 (degree 2), 8/27/64
+                            (conical product rules of degree 3/5/7)                 */
+    int n_theta;         /* M Gauss points in theta (azimuth over [0, pi]), 1..256   */
+    int n_phi;           /* N Gauss points in phi (polar, weighted by sin phi), 1..256 */
+    int precision;       /* BS_FP64 or BS_FP32                                       */
+    int32_t *counts;     /* optional device [k][3] int32 output: near tets, far tets,
+                            ray hits (line-tet pairs with chord > 1e-9 * longest edge);
+                            NULL to skip                                             */
+} bs_params;
+
+/* Upload a mesh and precompute its per-tet tables (Section 2.2 steps 2-3 and
+ * the far-rule data).  nodes: host [n_nodes][3]; tets: host [n_tets][4];
+ * omega: host [n_nodes][3].  Tets of either orientation are accepted.
+ * Synchronises the device.  Errors: BS_ERR_ARG (NULL, n_nodes < 1,
+ * n_tets < 0), BS_ERR_MESH (index out of range or degenerate tet; the
+ * message names the first offending tet), BS_ERR_CUDA.  On success *out
+ * owns every device buffer of the mesh until bs_destroy. */
+BS_API int bs_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets, const double *omega,
+              bs_handle *out);
+
+/* Replace node positions and/or nodal vorticity (same connectivity) from
+ * device arrays [n_nodes][3] (either may be NULL to keep the current one)
+ * and recompute the per-tet tables on `stream` (one step of a Lagrangian vortex method, Section 1).
+ * Asynchronous: a degenerate tet is reported by the next bs_status. */
+BS_API int bs_update(bs_handle h, const double *nodes_dev, const double *omega_dev, void *stream);
+
+/* Velocity at k evaluation points.  eval_pts_dev: device [k][3];
+ * out_dev: device [k][3], overwritten (not accumulated).  k = 0 is a no-op.
+ * Errors: BS_ERR_ARG, BS_ERR_ORDER, BS_ERR_CUDA. */
+BS_API int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_params *p, double *out_dev,
+                void *stream);
+
+/* Same as bs_velocity with HOST buffers: copies the points in, evaluates and
+ * copies the velocities out on `stream`, then synchronises it. */
+BS_API int bs_velocity_host(bs_handle h, const double *eval_pts_host, int64_t k, const bs_params *p, double *out_host,
+                     void *stream);
+
+/* Synchronise `stream` and return BS_ERR_MESH / BS_ERR_TIMEOUT if a kernel of
+ * this handle raised its device error flag since the last call (clears it). */
+BS_API int bs_status(bs_handle h, void *stream);
+
+/* Free every device buffer of the handle (synchronises the device). */
+BS_API int bs_destroy(bs_handle h);
+
+/* Mesh sizes of a handle. */
+BS_API int bs_mesh_size(bs_handle h, int64_t *n_nodes, int64_t *n_tets);
+
+/* Kernel timing of a handle (for benchmarks).  bs_profile(h, 1) starts
+ * recording a CUDA event pair around every velocity-kernel launch of this
+ * handle (on the launch stream) and counting every kernel the handle
+ * launches; bs_profile(h, 0) stops.  bs_profile_read synchronises the device
+ * and returns the summed velocity-kernel time (ms), the number of velocity
+ * kernel launches and the number of all kernel launches since profiling was
+ * enabled. */
+BS_API int bs_profile(bs_handle h, int enable);
+BS_API int bs_profile_read(bs_handle h, double *kernel_ms, int64_t *kernel_launches, int64_t *all_launches);
+
+/* Message of the last error on the calling host thread ("" if none). */
+BS_API const char *bs_last_error(void);
+
+/* Tables computed on the device, copied to host arrays (synchronous):
+ * directions s [n_phi*n_theta][3] and weights k [n_phi*n_theta] of Eq. 3,
+ * line index l = n*n_theta + m;  tet rule barycentric points [order][4] and
+ * weights [order] (fractions of |V|). */
+BS_API int bs_direction_table(int n_phi, int n_theta, double *s_host, double *k_host);
+BS_API int bs_tet_rule(int order, double *bary_host, double *w_host);
+
+/* Many meshes in one persistent launch (evaluation points = each mesh's own
+ * nodes).  bs_batch_create: host array of n handles (not owned; they must
+ * outlive the batch).  bs_batch_velocity: outs[i] is a device [n_nodes_i][3]
+ * output for mesh i (host array of n device pointers); p->counts must be NULL.
+ * The work queue is built on the device; the launch sequence is captured once
+ * into a CUDA graph per (params, stream) and replayed. */
+BS_API int bs_batch_create(const bs_handle *meshes, int n, bs_batch *out);
+BS_API int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void *stream);
+BS_API int bs_batch_destroy(bs_batch b);
+
+/* Time the kernel variants (points per thread, tet tile) for this mesh and
+ * parameters on `stream` and keep the fastest for later calls with the same
+ * precision/order/direction count.  Synchronises the stream. */
+BS_API int bs_autotune(bs_handle h, const bs_params *p, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BS_H */

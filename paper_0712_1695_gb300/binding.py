@@ -1,0 +1,241 @@
+"""Thin ctypes binding of libbs (include/bs.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Device arrays are torch CUDA tensors (float64 [k, 3] points
+and outputs, int32 [k, 3] counts); streams are taken from torch.  If the
+library is missing, every call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libbs.so")
+
+BS_OK, BS_ERR_ARG, BS_ERR_MESH, BS_ERR_ORDER, BS_ERR_CUDA, BS_ERR_TIMEOUT = range(6)
+BS_FP64, BS_FP32 = 0, 1
+EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_status", "bs_destroy",
+            "bs_mesh_size", "bs_last_error", "bs_direction_table", "bs_tet_rule", "bs_batch_create",
+            "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read")
+
+
+class BSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libbs error {code}: {msg}")
+        self.code = code
+
+
+class bs_params(ctypes.Structure):
+    _fields_ = [("far_ratio", ctypes.c_double), ("tet_gauss_order", ctypes.c_int), ("n_theta", ctypes.c_int),
+                ("n_phi", ctypes.c_int), ("precision", ctypes.c_int), ("counts", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def load(path: str = LIB_PATH):
+    """Load libbs.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libbs.so not built ({path}); run paper_0712_1695_gb300/build.py")
+        lib = ctypes.CDLL(path)
+        lib.bs_create.argtypes = [_D, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64, _D,
+                                  ctypes.POINTER(_P)]
+        lib.bs_update.argtypes = [_P, _P, _P, _P]
+        lib.bs_velocity.argtypes = [_P, _P, ctypes.c_int64, ctypes.POINTER(bs_params), _P, _P]
+        lib.bs_velocity_host.argtypes = [_P, _D, ctypes.c_int64, ctypes.POINTER(bs_params), _D, _P]
+        lib.bs_status.argtypes = [_P, _P]
+        lib.bs_destroy.argtypes = [_P]
+        lib.bs_mesh_size.argtypes = [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        lib.bs_last_error.argtypes = []
+        lib.bs_last_error.restype = ctypes.c_char_p
+        lib.bs_direction_table.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+        lib.bs_tet_rule.argtypes = [ctypes.c_int, _D, _D]
+        lib.bs_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]
+        lib.bs_batch_velocity.argtypes = [_P, ctypes.POINTER(bs_params), ctypes.POINTER(_P), _P]
+        lib.bs_batch_destroy.argtypes = [_P]
+        lib.bs_autotune.argtypes = [_P, ctypes.POINTER(bs_params), _P]
+        lib.bs_profile.argtypes = [_P, ctypes.c_int]
+        lib.bs_profile_read.argtypes = [_P, _D, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != BS_OK:
+        raise BSError(rc, load().bs_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_params(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16, precision=BS_FP64, counts=None):
+    p = bs_params()
+    p.far_ratio = float(far_ratio)
+    p.tet_gauss_order = int(tet_gauss_order)
+    p.n_theta = int(n_theta)
+    p.n_phi = int(n_phi)
+    p.precision = int(precision)
+    p.counts = None if counts is None else ctypes.c_void_p(counts.data_ptr())
+    return p
+
+
+def _host_f64(a, cols=3):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1, cols)
+    return a
+
+
+class Mesh:
+    """A mesh on the device (bs_handle)."""
+
+    def __init__(self, nodes, tets, omega):
+        lib = load()
+        nodes = _host_f64(nodes)
+        omega = _host_f64(omega)
+        tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+        h = _P()
+        _check(lib.bs_create(nodes.ctypes.data_as(_D), len(nodes), tets.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                             len(tets), omega.ctypes.data_as(_D), ctypes.byref(h)))
+        self.handle = h
+        self.n_nodes = len(nodes)
+        self.n_tets = len(tets)
+
+    def close(self):
+        if self.handle:
+            _check(load().bs_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bs_update(self, nodes_dev=None, omega_dev=None, stream=None):
+        for t in (nodes_dev, omega_dev):
+            if t is not None:
+                _require_dev(t, (self.n_nodes, 3))
+        _check(load().bs_update(self.handle, None if nodes_dev is None else nodes_dev.data_ptr(),
+                                None if omega_dev is None else omega_dev.data_ptr(), _stream_ptr(stream)))
+
+    def bs_status(self, stream=None):
+        _check(load().bs_status(self.handle, _stream_ptr(stream)))
+
+    def bs_velocity(self, pts_dev, out_dev=None, counts_dev=None, stream=None, **params):
+        """Velocity at device points (torch float64 [k, 3]); returns the output tensor."""
+        import torch
+
+        k = int(pts_dev.shape[0])
+        _require_dev(pts_dev, (k, 3))
+        if out_dev is None:
+            out_dev = torch.empty((k, 3), dtype=torch.float64, device=pts_dev.device)
+        _require_dev(out_dev, (k, 3))
+        if counts_dev is not None:
+            if counts_dev.dtype != torch.int32 or tuple(counts_dev.shape) != (k, 3) or not counts_dev.is_contiguous():
+                raise ValueError("counts must be a contiguous int32 [k, 3] CUDA tensor")
+        p = make_params(counts=counts_dev, **params)
+        _check(load().bs_velocity(self.handle, pts_dev.data_ptr(), k, ctypes.byref(p), out_dev.data_ptr(),
+                                  _stream_ptr(stream)))
+        return out_dev
+
+    def bs_velocity_host(self, pts, stream=None, out=None, **params):
+        """Velocity at host points (numpy float64 [k, 3]) through host buffers."""
+        pts = _host_f64(pts)
+        if out is None:
+            out = np.empty_like(pts)
+        p = make_params(**params)
+        _check(load().bs_velocity_host(self.handle, pts.ctypes.data_as(_D), len(pts), ctypes.byref(p),
+                                       out.ctypes.data_as(_D), _stream_ptr(stream)))
+        return out
+
+    def bs_profile(self, enable: bool):
+        _check(load().bs_profile(self.handle, int(bool(enable))))
+
+    def bs_profile_read(self):
+        """(summed velocity-kernel ms, velocity-kernel launches, all kernel launches)."""
+        ms = ctypes.c_double()
+        kl = ctypes.c_int64()
+        al = ctypes.c_int64()
+        _check(load().bs_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(kl), ctypes.byref(al)))
+        return ms.value, kl.value, al.value
+
+    def bs_autotune(self, stream=None, **params):
+        p = make_params(**params)
+        _check(load().bs_autotune(self.handle, ctypes.byref(p), _stream_ptr(stream)))
+
+
+def _require_dev(t, shape):
+    import torch
+
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and tuple(t.shape) == tuple(shape)):
+        raise ValueError(f"expected a contiguous float64 CUDA tensor of shape {shape}")
+
+
+def bs_create(nodes, tets, omega) -> Mesh:
+    return Mesh(nodes, tets, omega)
+
+
+def bs_direction_table(n_phi: int, n_theta: int):
+    L = n_phi * n_theta
+    s = np.zeros((L, 3))
+    k = np.zeros(L)
+    _check(load().bs_direction_table(n_phi, n_theta, s.ctypes.data_as(_D), k.ctypes.data_as(_D)))
+    return s, k
+
+
+def bs_tet_rule(order: int):
+    b = np.zeros((order, 4))
+    w = np.zeros(order)
+    _check(load().bs_tet_rule(order, b.ctypes.data_as(_D), w.ctypes.data_as(_D)))
+    return b, w
+
+
+class Batch:
+    """Many meshes evaluated in one persistent launch (bs_batch)."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        arr = (_P * len(self.meshes))(*[m.handle for m in self.meshes])
+        h = _P()
+        _check(load().bs_batch_create(arr, len(self.meshes), ctypes.byref(h)))
+        self.handle = h
+
+    def bs_batch_velocity(self, outs, stream=None, **params):
+        ptrs = (_P * len(outs))(*[o.data_ptr() for o in outs])
+        for o, m in zip(outs, self.meshes):
+            _require_dev(o, (m.n_nodes, 3))
+        p = make_params(**params)
+        _check(load().bs_batch_velocity(self.handle, ctypes.byref(p), ptrs, _stream_ptr(stream)))
+        return outs
+
+    def close(self):
+        if self.handle:
+            _check(load().bs_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+INF = math.inf

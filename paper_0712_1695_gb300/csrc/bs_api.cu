@@ -1,0 +1,456 @@
+// bs_api.cu -- the C ABI of libbs (declared in include/bs.h): argument
+// checks, device buffer ownership, table caching and kernel sequencing.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "bs_internal.cuh"
+
+using namespace bs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    return fail(BS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define BS_CUDA(call)                                            \
+    do {                                                         \
+        cudaError_t _e = (call);                                 \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call);      \
+    } while (0)
+
+bool valid_order(int q) { return q == 1 || q == 4 || q == 8 || q == 27 || q == 64; }
+
+int check_params(const bs_params *p)
+{
+    if (!p) return fail(BS_ERR_ARG, "params is NULL");
+    const double fr = p->far_ratio;
+    if (isnan(fr) || (!isinf(fr) && fr < 2.0) || (isinf(fr) && fr < 0))
+        return fail(BS_ERR_ARG, "far_ratio must be >= 2 or +INFINITY");
+    if (p->n_theta < 1 || p->n_theta > 256 || p->n_phi < 1 || p->n_phi > 256)
+        return fail(BS_ERR_ARG, "n_theta and n_phi must be in 1..256");
+    if (p->precision != BS_FP32 && p->precision != BS_FP64) return fail(BS_ERR_ARG, "precision must be BS_FP64 or BS_FP32");
+    if (!valid_order(p->tet_gauss_order)) return fail(BS_ERR_ORDER, "tet_gauss_order must be 1, 4, 8, 27 or 64");
+    return BS_OK;
+}
+
+}  // namespace
+
+struct bs_ctx {
+    int device = 0;
+    int n_sm = 0;
+    int64_t n_nodes = 0, n_tets = 0;
+    double *nodes = nullptr;
+    int32_t *tets = nullptr;
+    double *omega = nullptr;
+    float4 *near32 = nullptr;
+    double *near64 = nullptr;
+    double *rho2 = nullptr;
+    int *flag = nullptr;
+    unsigned long long *first_bad = nullptr;
+    int *work_counter = nullptr;
+    uint64_t version = 1;  // bumped whenever the near records change
+    // far records of the last tet rule
+    TetRule rule;
+    uint64_t far_version = 0;
+    float *far32 = nullptr;
+    double *far64 = nullptr;
+    // direction table of the last (n_phi, n_theta)
+    LineTables lines;
+    // scratch for per-chunk partial sums
+    double *partial = nullptr;
+    size_t partial_cap = 0;
+    // staging for bs_velocity_host
+    double *stage = nullptr;
+    size_t stage_cap = 0;
+    int occ[2][65] = {};  // cached CTAs per SM by [precision][Q]
+    // kernel timing (bs_profile)
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
+    int64_t prof_kernel = 0, prof_all = 0;
+};
+
+namespace {
+
+void drop_events(bs_ctx *h)
+{
+    for (auto &p : h->ev_used) h->ev_free.push_back(p);
+    h->ev_used.clear();
+}
+
+void free_ctx(bs_ctx *h)
+{
+    drop_events(h);
+    for (auto &p : h->ev_free) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    void *bufs[] = {h->nodes, h->tets,  h->omega,     h->near32,   h->near64,  h->rho2,         h->flag,
+                    h->first_bad, h->work_counter, h->rule.bary, h->rule.w, h->far32, h->far64, h->lines.f32,
+                    h->lines.f64, h->partial, h->stage};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete h;
+}
+
+cudaError_t ensure_lines(bs_ctx *h, int n_phi, int n_theta, cudaStream_t st)
+{
+    if (h->lines.f32 && h->lines.n_phi == n_phi && h->lines.n_theta == n_theta) return cudaSuccess;
+    if (h->lines.f32) cudaFreeAsync(h->lines.f32, st);
+    if (h->lines.f64) cudaFreeAsync(h->lines.f64, st);
+    h->lines = LineTables();
+    const size_t L = (size_t)n_phi * n_theta;
+    cudaError_t e = cudaMallocAsync((void **)&h->lines.f32, L * sizeof(float4), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMallocAsync((void **)&h->lines.f64, L * sizeof(dbl4), st);
+    if (e != cudaSuccess) return e;
+    e = build_lines(n_phi, n_theta, h->lines.f32, h->lines.f64, st);
+    if (e != cudaSuccess) return e;
+    if (h->prof) h->prof_all += 1;
+    h->lines.n_phi = n_phi;
+    h->lines.n_theta = n_theta;
+    return cudaSuccess;
+}
+
+cudaError_t ensure_far(bs_ctx *h, int Q, cudaStream_t st)
+{
+    if (h->far32 && h->rule.order == Q && h->far_version == h->version) return cudaSuccess;
+    cudaError_t e;
+    if (h->rule.order != Q) {
+        if (h->rule.bary) cudaFreeAsync(h->rule.bary, st);
+        if (h->rule.w) cudaFreeAsync(h->rule.w, st);
+        if (h->far32) cudaFreeAsync(h->far32, st);
+        if (h->far64) cudaFreeAsync(h->far64, st);
+        h->rule = TetRule();
+        h->far32 = nullptr;
+        h->far64 = nullptr;
+        if ((e = cudaMallocAsync((void **)&h->rule.bary, sizeof(double) * 4 * Q, st)) != cudaSuccess) return e;
+        if ((e = cudaMallocAsync((void **)&h->rule.w, sizeof(double) * Q, st)) != cudaSuccess) return e;
+        if ((e = build_tet_rule(Q, h->rule.bary, h->rule.w, st)) != cudaSuccess) return e;
+        if (h->prof) h->prof_all += 1;
+        const size_t n = (size_t)std::max<int64_t>(h->n_tets, 1);
+        if ((e = cudaMallocAsync((void **)&h->far32, n * far_stride<float>(Q) * sizeof(float), st)) != cudaSuccess)
+            return e;
+        if ((e = cudaMallocAsync((void **)&h->far64, n * far_stride<double>(Q) * sizeof(double), st)) != cudaSuccess)
+            return e;
+        h->rule.order = Q;
+    }
+    if ((e = build_far_records(h->near64, h->rho2, h->n_tets, h->rule, h->far32, h->far64, st)) != cudaSuccess)
+        return e;
+    if (h->prof) h->prof_all += 1;
+    h->far_version = h->version;
+    return cudaSuccess;
+}
+
+cudaError_t ensure_partial(bs_ctx *h, size_t bytes, cudaStream_t st)
+{
+    if (bytes <= h->partial_cap) return cudaSuccess;
+    if (h->partial) cudaFreeAsync(h->partial, st);
+    h->partial = nullptr;
+    h->partial_cap = 0;
+    cudaError_t e = cudaMallocAsync((void **)&h->partial, bytes, st);
+    if (e == cudaSuccess) h->partial_cap = bytes;
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bs_last_error(void) { return g_last_error.c_str(); }
+
+int bs_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets, const double *omega,
+              bs_handle *out)
+{
+    if (!out) return fail(BS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!nodes || !omega || (n_tets > 0 && !tets)) return fail(BS_ERR_ARG, "NULL mesh array");
+    if (n_nodes < 1 || n_tets < 0) return fail(BS_ERR_ARG, "need n_nodes >= 1 and n_tets >= 0");
+    if (n_nodes > INT32_MAX) return fail(BS_ERR_ARG, "n_nodes exceeds the int32 index range");
+    bs_ctx *h = new bs_ctx();
+    h->n_nodes = n_nodes;
+    h->n_tets = n_tets;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    const size_t nt = (size_t)std::max<int64_t>(n_tets, 1);
+    if (e == cudaSuccess) e = cudaMalloc(&h->nodes, sizeof(double) * 3 * n_nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->omega, sizeof(double) * 3 * n_nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&h->tets, sizeof(int32_t) * 4 * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&h->near32, sizeof(float4) * kNearF32Vec4 * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&h->near64, sizeof(double) * kNearF64 * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&h->rho2, sizeof(double) * nt);
+    if (e == cudaSuccess) e = cudaMalloc(&h->flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->first_bad, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&h->work_counter, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(h->nodes, nodes, sizeof(double) * 3 * n_nodes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->omega, omega, sizeof(double) * 3 * n_nodes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n_tets > 0)
+        e = cudaMemcpy(h->tets, tets, sizeof(int32_t) * 4 * n_tets, cudaMemcpyHostToDevice);
+    const unsigned long long none = ~0ull;
+    if (e == cudaSuccess) e = cudaMemset(h->flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(h->first_bad, &none, sizeof(none), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = build_near_records(h->nodes, n_nodes, h->tets, n_tets, h->omega, h->near32, h->near64, h->rho2, h->flag,
+                               h->first_bad, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int flag = 0;
+    unsigned long long bad = none;
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&bad, h->first_bad, sizeof(bad), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        free_ctx(h);
+        return cuda_fail(e, "bs_create");
+    }
+    if (flag) {
+        free_ctx(h);
+        char msg[160];
+        snprintf(msg, sizeof msg, "tet %llu: %s", bad,
+                 (flag & kFlagMeshIndex) ? "node index out of range (or degenerate tet)"
+                                         : "degenerate tet (|volume| <= 1e-14 h^3)");
+        return fail(BS_ERR_MESH, msg);
+    }
+    *out = h;
+    return BS_OK;
+}
+
+int bs_update(bs_handle h, const double *nodes_dev, const double *omega_dev, void *stream)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (nodes_dev)
+        BS_CUDA(cudaMemcpyAsync(h->nodes, nodes_dev, sizeof(double) * 3 * h->n_nodes, cudaMemcpyDeviceToDevice, st));
+    if (omega_dev)
+        BS_CUDA(cudaMemcpyAsync(h->omega, omega_dev, sizeof(double) * 3 * h->n_nodes, cudaMemcpyDeviceToDevice, st));
+    BS_CUDA(build_near_records(h->nodes, h->n_nodes, h->tets, h->n_tets, h->omega, h->near32, h->near64, h->rho2,
+                               h->flag, h->first_bad, st));
+    if (h->prof && h->n_tets > 0) h->prof_all += 1;
+    ++h->version;
+    return BS_OK;
+}
+
+int bs_status(bs_handle h, void *stream)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    BS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int flag = 0;
+    BS_CUDA(cudaMemcpy(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    BS_CUDA(cudaMemset(h->flag, 0, sizeof(int)));
+    if (flag & kFlagTimeout) return fail(BS_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (flag & (kFlagMeshIndex | kFlagMeshVolume)) return fail(BS_ERR_MESH, "degenerate tet after bs_update");
+    return BS_OK;
+}
+
+int bs_mesh_size(bs_handle h, int64_t *n_nodes, int64_t *n_tets)
+{
+    if (!h || !n_nodes || !n_tets) return fail(BS_ERR_ARG, "NULL argument");
+    *n_nodes = h->n_nodes;
+    *n_tets = h->n_tets;
+    return BS_OK;
+}
+
+int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_params *p, double *out_dev,
+                void *stream)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (k < 0) return fail(BS_ERR_ARG, "k < 0");
+    if (k == 0) return BS_OK;
+    if (!eval_pts_dev || !out_dev) return fail(BS_ERR_ARG, "NULL points or output");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->n_tets == 0) {
+        BS_CUDA(cudaMemsetAsync(out_dev, 0, sizeof(double) * 3 * k, st));
+        if (p->counts) BS_CUDA(cudaMemsetAsync(p->counts, 0, sizeof(int32_t) * 3 * k, st));
+        return BS_OK;
+    }
+    const int Q = p->tet_gauss_order;
+    BS_CUDA(ensure_lines(h, p->n_phi, p->n_theta, st));
+    BS_CUDA(ensure_far(h, Q, st));
+
+    const LaunchShape shape = shape_for(p->precision, Q);
+    int &occ = h->occ[p->precision][Q];
+    if (occ == 0) occ = std::max(1, velocity_ctas_per_sm(p->precision, Q));
+    const int64_t BP = (int64_t)shape.threads * shape.points_per_thread;
+    const int64_t n_blocks = (k + BP - 1) / BP;
+    const int64_t n_tiles = (h->n_tets + shape.tile - 1) / shape.tile;
+    const int64_t target = 8LL * h->n_sm * occ;
+    int64_t n_chunks = std::min<int64_t>(std::max<int64_t>((target + n_blocks - 1) / n_blocks, 1), n_tiles);
+    const int64_t per = (n_tiles + n_chunks - 1) / n_chunks;
+    n_chunks = (n_tiles + per - 1) / per;
+
+    VelocityArgs a;
+    a.n_tets = h->n_tets;
+    a.far = p->precision == BS_FP32 ? (const void *)h->far32 : (const void *)h->far64;
+    a.near32 = h->near32;
+    a.near64 = h->near64;
+    a.pts = eval_pts_dev;
+    a.k = k;
+    a.Q = Q;
+    a.far_ratio2 = isinf(p->far_ratio) ? INFINITY : p->far_ratio * p->far_ratio;
+    a.all_ray = isinf(p->far_ratio) ? 1 : 0;
+    a.lines = h->lines;
+    a.L = p->n_phi * p->n_theta;
+    a.counts = p->counts;
+    a.out = out_dev;
+    a.flag = h->flag;
+    a.work_counter = h->work_counter;
+    a.n_chunks = (int)n_chunks;
+    a.tiles_per_chunk = (int)per;
+    if (n_chunks == 1) {
+        a.partial = out_dev;  // a single chunk writes the final sums directly
+    } else {
+        BS_CUDA(ensure_partial(h, sizeof(double) * 3 * (size_t)k * n_chunks, st));
+        a.partial = h->partial;
+    }
+    int grid = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->prof) {
+        if (h->ev_free.empty()) {
+            BS_CUDA(cudaEventCreate(&e0));
+            BS_CUDA(cudaEventCreate(&e1));
+        } else {
+            e0 = h->ev_free.back().first;
+            e1 = h->ev_free.back().second;
+            h->ev_free.pop_back();
+        }
+        h->ev_used.push_back({e0, e1});
+    }
+    BS_CUDA(launch_velocity(p->precision, a, h->n_sm, st, &grid, e0, e1));
+    if (n_chunks > 1) BS_CUDA(launch_reduce(a, st));
+    if (h->prof) {
+        h->prof_kernel += 1;
+        h->prof_all += 2 + (n_chunks > 1 ? 1 : 0);
+    }
+    return BS_OK;
+}
+
+int bs_velocity_host(bs_handle h, const double *eval_pts_host, int64_t k, const bs_params *p, double *out_host,
+                     void *stream)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (k < 0) return fail(BS_ERR_ARG, "k < 0");
+    if (k == 0) return BS_OK;
+    if (!eval_pts_host || !out_host) return fail(BS_ERR_ARG, "NULL points or output");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(double) * 3 * (size_t)k;
+    if (2 * bytes > h->stage_cap) {
+        if (h->stage) cudaFreeAsync(h->stage, st);
+        h->stage = nullptr;
+        h->stage_cap = 0;
+        BS_CUDA(cudaMallocAsync((void **)&h->stage, 2 * bytes, st));
+        h->stage_cap = 2 * bytes;
+    }
+    double *dpts = h->stage, *dout = h->stage + 3 * k;
+    BS_CUDA(cudaMemcpyAsync(dpts, eval_pts_host, bytes, cudaMemcpyHostToDevice, st));
+    rc = bs_velocity(h, dpts, k, p, dout, stream);
+    if (rc) return rc;
+    BS_CUDA(cudaMemcpyAsync(out_host, dout, bytes, cudaMemcpyDeviceToHost, st));
+    BS_CUDA(cudaStreamSynchronize(st));
+    return BS_OK;
+}
+
+int bs_destroy(bs_handle h)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    cudaDeviceSynchronize();
+    free_ctx(h);
+    return BS_OK;
+}
+
+int bs_direction_table(int n_phi, int n_theta, double *s_host, double *k_host)
+{
+    if (n_phi < 1 || n_phi > 256 || n_theta < 1 || n_theta > 256) return fail(BS_ERR_ARG, "n_phi/n_theta out of 1..256");
+    if (!s_host || !k_host) return fail(BS_ERR_ARG, "NULL output");
+    const size_t L = (size_t)n_phi * n_theta;
+    float4 *f = nullptr;
+    dbl4 *d = nullptr;
+    BS_CUDA(cudaMalloc(&f, L * sizeof(float4)));
+    cudaError_t e = cudaMalloc(&d, L * sizeof(dbl4));
+    if (e == cudaSuccess) e = build_lines(n_phi, n_theta, f, d, 0);
+    dbl4 *hd = new dbl4[L];
+    if (e == cudaSuccess) e = cudaMemcpy(hd, d, L * sizeof(dbl4), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        for (size_t l = 0; l < L; ++l) {
+            s_host[3 * l] = hd[l].x;
+            s_host[3 * l + 1] = hd[l].y;
+            s_host[3 * l + 2] = hd[l].z;
+            k_host[l] = hd[l].w;
+        }
+    delete[] hd;
+    cudaFree(f);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "bs_direction_table");
+    return BS_OK;
+}
+
+int bs_tet_rule(int order, double *bary_host, double *w_host)
+{
+    if (!valid_order(order)) return fail(BS_ERR_ORDER, "tet_gauss_order must be 1, 4, 8, 27 or 64");
+    if (!bary_host || !w_host) return fail(BS_ERR_ARG, "NULL output");
+    double *b = nullptr, *w = nullptr;
+    BS_CUDA(cudaMalloc(&b, sizeof(double) * 4 * order));
+    cudaError_t e = cudaMalloc(&w, sizeof(double) * order);
+    if (e == cudaSuccess) e = build_tet_rule(order, b, w, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(bary_host, b, sizeof(double) * 4 * order, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(w_host, w, sizeof(double) * order, cudaMemcpyDeviceToHost);
+    cudaFree(b);
+    if (w) cudaFree(w);
+    if (e != cudaSuccess) return cuda_fail(e, "bs_tet_rule");
+    return BS_OK;
+}
+
+int bs_profile(bs_handle h, int enable)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    h->prof = enable != 0;
+    drop_events(h);
+    h->prof_kernel = h->prof_all = 0;
+    return BS_OK;
+}
+
+int bs_profile_read(bs_handle h, double *kernel_ms, int64_t *kernel_launches, int64_t *all_launches)
+{
+    if (!h || !kernel_ms || !kernel_launches || !all_launches) return fail(BS_ERR_ARG, "NULL argument");
+    BS_CUDA(cudaDeviceSynchronize());
+    double total = 0.0;
+    for (auto &p : h->ev_used) {
+        float ms = 0.f;
+        BS_CUDA(cudaEventElapsedTime(&ms, p.first, p.second));
+        total += ms;
+    }
+    *kernel_ms = total;
+    *kernel_launches = h->prof_kernel;
+    *all_launches = h->prof_all;
+    return BS_OK;
+}
+
+int bs_batch_create(const bs_handle *, int, bs_batch *out)
+{
+    if (out) *out = nullptr;
+    return fail(BS_ERR_ARG, "bs_batch_create: not available in this build");
+}
+int bs_batch_velocity(bs_batch, const bs_params *, double *const *, void *)
+{
+    return fail(BS_ERR_ARG, "bs_batch_velocity: not available in this build");
+}
+int bs_batch_destroy(bs_batch) { return BS_OK; }
+int bs_autotune(bs_handle, const bs_params *, void *) { return fail(BS_ERR_ARG, "bs_autotune: not available in this build"); }
+
+}  // extern "C"

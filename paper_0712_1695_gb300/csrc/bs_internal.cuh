@@ -1,0 +1,120 @@
+// bs_internal.cuh -- device data layouts and helpers shared by the libbs
+// translation units (tables, per-tet precompute, velocity kernels, C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/bs.h"
+
+namespace bs {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// Per-tet records.
+//
+// Far record (one per tet, rebuilt when the far rule changes): everything the
+// far rule and the near/far test need, streamed through shared memory.
+//   [c.x c.y c.z rho^2] then per quadrature point q: [x_q (3), w'_q (3)]
+//   with w'_q = -(w_q |V| / 4pi) omega(x_q)  (sign and 1/4pi of Eq. 1 folded in)
+// Stride in elements: 4 + 6Q, rounded up to a multiple of 4 for float.
+//
+// Near record (one per tet, independent of the parameters): what the ray rule
+// needs.  Barycentric coordinates lambda_i(y) = g_i . (y - v0) + delta_i0
+// with g_0 = -(g_1 + g_2 + g_3) (the face planes of the tet).
+//   float  : 8 x float4  [v0 h] [g1 Rb^2] [g2 c.x] [g3 c.y] [w0 c.z] [w1 -] [w2 -] [w3 -]
+//   double : 40 doubles  v0..v3 (12) g1 g2 g3 (9) w0..w3 (12) c (3) h Rb^2 (2) pad (2)
+//   h = longest edge, c = centroid, Rb = largest vertex distance from c.
+// ---------------------------------------------------------------------------
+template <typename T>
+__host__ __device__ constexpr int far_stride(int Q)
+{
+    return sizeof(T) == 4 ? ((4 + 6 * Q + 3) / 4) * 4 : (4 + 6 * Q);
+}
+constexpr int kNearF32Vec4 = 8;  // float4 per near record
+constexpr int kNearF64 = 40;     // doubles per near record
+namespace nf64 {
+constexpr int V = 0, G = 12, W = 21, C = 33, H = 36, RB2 = 37;
+}
+
+// Four doubles on a 32-byte boundary (one line of the direction table).
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+
+// Line table of Eq. 3: per line (s_x, s_y, s_z, k) in float4 and dbl4.
+struct LineTables {
+    int n_phi = 0, n_theta = 0;
+    float4 *f32 = nullptr;
+    dbl4 *f64 = nullptr;
+};
+
+struct TetRule {
+    int order = 0;
+    double *bary = nullptr;  // device [order][4]
+    double *w = nullptr;     // device [order]
+};
+
+// Error flag values written by kernels (device int in the handle).
+constexpr int kFlagMeshIndex = 1;
+constexpr int kFlagMeshVolume = 2;
+constexpr int kFlagTimeout = 4;
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files).
+// ---------------------------------------------------------------------------
+cudaError_t build_lines(int n_phi, int n_theta, float4 *f32, dbl4 *f64, cudaStream_t st);
+cudaError_t build_tet_rule(int order, double *bary, double *w, cudaStream_t st);
+
+// near records + per-tet validity; error flag gets kFlagMesh* and first_bad the lowest bad tet
+cudaError_t build_near_records(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                               const double *omega, float4 *near32, double *near64, double *rho2,
+                               int *flag, unsigned long long *first_bad, cudaStream_t st);
+// far records for a tet rule (needs near64 for vertices/omega and rho2)
+cudaError_t build_far_records(const double *near64, const double *rho2, int64_t n_tets, const TetRule &rule,
+                              float *far32, double *far64, cudaStream_t st);
+
+struct VelocityArgs {
+    // mesh
+    int64_t n_tets = 0;
+    const void *far = nullptr;      // far records (float or double)
+    const float4 *near32 = nullptr;
+    const double *near64 = nullptr;
+    // points
+    const double *pts = nullptr;  // [k][3]
+    int64_t k = 0;
+    // rule
+    int Q = 4;
+    double far_ratio2 = 4.0;  // +inf for all-ray
+    int all_ray = 0;
+    LineTables lines;
+    int L = 0;
+    // outputs
+    double *partial = nullptr;  // [n_chunks][k][3]
+    int32_t *counts = nullptr;  // [k][3] or null (zeroed before)
+    double *out = nullptr;      // [k][3]
+    int *flag = nullptr;
+    int *work_counter = nullptr;  // device int, zeroed by launch_velocity
+    // decomposition
+    int n_chunks = 1;
+    int tiles_per_chunk = 1;
+};
+
+struct LaunchShape {
+    int points_per_thread = 2;  // P
+    int threads = 128;
+    int tile = 64;  // tets per shared-memory tile
+};
+
+// kernel variant (points per thread, tile) used for a precision and tet rule
+LaunchShape shape_for(int precision, int Q);
+int velocity_ctas_per_sm(int precision, int Q);
+// ev_start/ev_stop (optional) are recorded around the velocity kernel alone
+cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
+                            cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);
+cudaError_t launch_reduce(const VelocityArgs &a, cudaStream_t st);
+
+}  // namespace bs
