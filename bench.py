@@ -164,7 +164,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=128, help="oracle sample nodes for cpu_baseline")
+    ap.add_argument("--cpu-sample", type=int, default=640, help="oracle sample nodes for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=96, help="oracle sample nodes per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -39,6 +39,11 @@ constexpr float kBoundPadF = 1e-4f;  // relative safety on the bounding-sphere l
 constexpr double kBoundPadD = 1e-9;
 constexpr double kTau = 1e-9;        // chord length threshold, in units of the longest edge
 constexpr float kDegenA = 1e-5f;     // float32: |a_i| below this with x inside/on the tet -> float64 pair
+// A line with |b_i| <= eps |g_i| (|s . n_i| <= eps) is parallel to face i: that face bounds nothing
+// and the line is outside the tet when a_i < -eps (the oracle's Moller-Trumbore treats
+// |det| <= 1e-12 |e1||e2| as parallel and accepts area coordinates down to -1e-12).
+constexpr double kParD = 1e-12;
+constexpr float kParF = 1e-6f;
 constexpr long long kWaitCap = 1LL << 26;
 
 // ---------------------------------------------------------------------------
@@ -157,6 +162,9 @@ __device__ __noinline__ NearOut near_pair_f64(V3<double> x, const double *__rest
     const V3<double> rc = mk(r[nf64::C] - x.x, r[nf64::C + 1] - x.y, r[nf64::C + 2] - x.z);
     const double rc2 = dot3(rc, rc);
     const double bound = rb2 * (1.0 + kBoundPadD);
+    const V3<double> g0 = mk(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
+    const double par2[4] = {kParD * kParD * dot3(g0, g0), kParD * kParD * dot3(g1, g1),
+                            kParD * kParD * dot3(g2, g2), kParD * kParD * dot3(g3, g3)};
     double ax = 0.0, ay = 0.0, az = 0.0;
     int hits = 0;
     for (int l = lane; l < L; l += 32) {
@@ -173,9 +181,9 @@ __device__ __noinline__ NearOut near_pair_f64(V3<double> x, const double *__rest
         bool empty = false;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            if (b[i] > 0.0) lo = fmax(lo, -a[i] / b[i]);
-            else if (b[i] < 0.0) hi = fmin(hi, -a[i] / b[i]);
-            else empty = empty || (a[i] < 0.0);
+            if (b[i] * b[i] <= par2[i]) empty = empty || (a[i] < -kParD);
+            else if (b[i] > 0.0) lo = fmax(lo, -a[i] / b[i]);
+            else hi = fmin(hi, -a[i] / b[i]);
         }
         if (empty || !(hi - lo > kTau * h)) continue;
         const V3<double> Wb = mk(b[0] * w[0].x + b[1] * w[1].x + b[2] * w[2].x + b[3] * w[3].x,
@@ -239,6 +247,9 @@ __device__ __noinline__ NearOut near_pair_f32(V3<double> x, const float4 *__rest
                             (float)(r64[nf64::C + 2] - x.z));
     const float rc2 = dot3(rc, rc);
     const float bound = rb2 * (1.0f + kBoundPadF);
+    const V3<float> g0 = mk(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
+    const float par2[4] = {kParF * kParF * dot3(g0, g0), kParF * kParF * dot3(g1, g1), kParF * kParF * dot3(g2, g2),
+                           kParF * kParF * dot3(g3, g3)};
     const float tau_h = (float)kTau * h;
     float ax = 0.f, ay = 0.f, az = 0.f;
     int hits = 0;
@@ -256,9 +267,9 @@ __device__ __noinline__ NearOut near_pair_f32(V3<double> x, const float4 *__rest
         bool empty = false;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            if (b[i] > 0.f) lo = fmaxf(lo, -a[i] / b[i]);
-            else if (b[i] < 0.f) hi = fminf(hi, -a[i] / b[i]);
-            else empty = empty || (a[i] < 0.f);
+            if (b[i] * b[i] <= par2[i]) empty = empty || (a[i] < -kParF);
+            else if (b[i] > 0.f) lo = fmaxf(lo, -a[i] / b[i]);
+            else hi = fminf(hi, -a[i] / b[i]);
         }
         if (empty || !(hi - lo > tau_h)) continue;
         const V3<float> Wb = mk(b[0] * w[0].x + b[1] * w[1].x + b[2] * w[2].x + b[3] * w[3].x,
