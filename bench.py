@@ -167,6 +167,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=640, help="oracle sample nodes for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=96, help="oracle sample nodes per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--points", type=int, default=0,
+                    help="evaluate only this many seeded nodes (small case for profiler captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -196,10 +199,14 @@ def main():
     bs.load()
     mesh = config3_fourier()
     h = bs.Mesh(mesh.nodes, mesh.tets, mesh.omega)
-    k = mesh.n_nodes
+    eval_nodes = mesh.nodes
+    if args.points:
+        sel = np.sort(np.random.default_rng(4242).choice(mesh.n_nodes, size=args.points, replace=False))
+        eval_nodes = np.ascontiguousarray(mesh.nodes[sel])
+    k = len(eval_nodes)
     pairs = k * mesh.n_tets
     stream = torch.cuda.current_stream()
-    pts = torch.from_numpy(mesh.nodes).cuda()
+    pts = torch.from_numpy(eval_nodes).cuda()
     out = torch.empty((k, 3), dtype=torch.float64, device="cuda")
     P = dict(PARAMS, precision=bs.BS_FP32)
 
@@ -252,18 +259,21 @@ def main():
         vel_h.copy_(out, non_blocking=True)
         stream.synchronize()
 
-    e2e_step()
-    barrier()
-    t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 3))
-    for _ in range(e2e_steps):
+    e2e = None
+    if not args.no_e2e and not args.points:
         e2e_step()
-    barrier()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    t_e2e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_value = world * pairs / float(t_e2e.item())
+        barrier()
+        t0 = time.perf_counter()
+        e2e_steps = max(1, min(args.steps, 3))
+        for _ in range(e2e_steps):
+            e2e_step()
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        t_e2e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * pairs / float(t_e2e.item()), "unit": UNIT, "h2d_bytes_per_step": 2 * k * 24,
+               "d2h_bytes_per_step": k * 24}
 
     if rank != 0:
         if dist is not None:
@@ -291,7 +301,7 @@ def main():
         roofline["frac_at_sampled_clock"] = achieved / (n_sm * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e-6)
 
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and not args.points:
         import oracle
 
         oracle.build()
@@ -300,11 +310,14 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_sample} of the 4096 seeded sample nodes x all {mesh.n_tets} tets ({dt:.1f} s)"}
 
+    config = workload_config()
+    if args.points:
+        config["workload"] = f"fourier-64^3 mesh (1500282 tets), velocity at {k} seeded nodes (profiling case)"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
             "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * k * 24, "d2h_bytes_per_step": k * 24},
+            "e2e": e2e,
             "gpu_launches": int(all_launches), "clocks": clocks,
             "counts": {"near_pairs": n_near, "far_pairs": n_far, "ray_hits": n_hit}}
     print(json.dumps(line), flush=True)

@@ -70,6 +70,16 @@ struct bs_ctx {
     uint64_t far_version = 0;
     float *far32 = nullptr;
     double *far64 = nullptr;
+    float4 *tile_hdr = nullptr;
+    float *tile_rho = nullptr;
+    int far_tile = 0;
+    // spatial order of the evaluation points
+    int *perm = nullptr;
+    unsigned *keys = nullptr;
+    size_t order_cap = 0;  // points
+    int *cell_count = nullptr;
+    int cell_bits = 0;
+    int *box = nullptr;
     // direction table of the last (n_phi, n_theta)
     LineTables lines;
     // scratch for per-chunk partial sums
@@ -102,7 +112,8 @@ void free_ctx(bs_ctx *h)
     }
     void *bufs[] = {h->nodes, h->tets,  h->omega,     h->near32,   h->near64,  h->rho2,         h->flag,
                     h->first_bad, h->work_counter, h->rule.bary, h->rule.w, h->far32, h->far64, h->lines.f32,
-                    h->lines.f64, h->partial, h->stage};
+                    h->lines.f64, h->partial, h->stage, h->tile_hdr, h->tile_rho, h->perm, h->keys,
+                    h->cell_count, h->box};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete h;
@@ -131,29 +142,60 @@ cudaError_t ensure_far(bs_ctx *h, int Q, cudaStream_t st)
 {
     if (h->far32 && h->rule.order == Q && h->far_version == h->version) return cudaSuccess;
     cudaError_t e;
+    const int tile = shape_for(BS_FP32, Q).tile;
     if (h->rule.order != Q) {
-        if (h->rule.bary) cudaFreeAsync(h->rule.bary, st);
-        if (h->rule.w) cudaFreeAsync(h->rule.w, st);
-        if (h->far32) cudaFreeAsync(h->far32, st);
-        if (h->far64) cudaFreeAsync(h->far64, st);
+        void *old[] = {h->rule.bary, h->rule.w, h->far32, h->far64, h->tile_hdr, h->tile_rho};
+        for (void *b : old)
+            if (b) cudaFreeAsync(b, st);
         h->rule = TetRule();
         h->far32 = nullptr;
         h->far64 = nullptr;
+        h->tile_hdr = nullptr;
+        h->tile_rho = nullptr;
         if ((e = cudaMallocAsync((void **)&h->rule.bary, sizeof(double) * 4 * Q, st)) != cudaSuccess) return e;
         if ((e = cudaMallocAsync((void **)&h->rule.w, sizeof(double) * Q, st)) != cudaSuccess) return e;
         if ((e = build_tet_rule(Q, h->rule.bary, h->rule.w, st)) != cudaSuccess) return e;
         if (h->prof) h->prof_all += 1;
         const size_t n = (size_t)std::max<int64_t>(h->n_tets, 1);
+        const size_t nt = (n + tile - 1) / tile;
         if ((e = cudaMallocAsync((void **)&h->far32, n * far_stride<float>(Q) * sizeof(float), st)) != cudaSuccess)
             return e;
         if ((e = cudaMallocAsync((void **)&h->far64, n * far_stride<double>(Q) * sizeof(double), st)) != cudaSuccess)
             return e;
+        if ((e = cudaMallocAsync((void **)&h->tile_hdr, nt * sizeof(float4), st)) != cudaSuccess) return e;
+        if ((e = cudaMallocAsync((void **)&h->tile_rho, nt * sizeof(float), st)) != cudaSuccess) return e;
         h->rule.order = Q;
+        h->far_tile = tile;
     }
-    if ((e = build_far_records(h->near64, h->rho2, h->n_tets, h->rule, h->far32, h->far64, st)) != cudaSuccess)
+    if ((e = build_far_records(h->near64, h->rho2, h->n_tets, h->rule, tile, h->tile_hdr, h->tile_rho, h->far32,
+                               h->far64, st)) != cudaSuccess)
         return e;
-    if (h->prof) h->prof_all += 1;
+    if (h->prof) h->prof_all += 2;
     h->far_version = h->version;
+    return cudaSuccess;
+}
+
+cudaError_t ensure_order(bs_ctx *h, int64_t k, int bits, cudaStream_t st)
+{
+    cudaError_t e;
+    if ((size_t)k > h->order_cap) {
+        if (h->perm) cudaFreeAsync(h->perm, st);
+        if (h->keys) cudaFreeAsync(h->keys, st);
+        h->perm = nullptr;
+        h->keys = nullptr;
+        h->order_cap = 0;
+        if ((e = cudaMallocAsync((void **)&h->perm, sizeof(int) * k, st)) != cudaSuccess) return e;
+        if ((e = cudaMallocAsync((void **)&h->keys, sizeof(unsigned) * k, st)) != cudaSuccess) return e;
+        h->order_cap = (size_t)k;
+    }
+    if (bits > h->cell_bits) {
+        if (h->cell_count) cudaFreeAsync(h->cell_count, st);
+        h->cell_count = nullptr;
+        h->cell_bits = 0;
+        if ((e = cudaMallocAsync((void **)&h->cell_count, sizeof(int) << (3 * bits), st)) != cudaSuccess) return e;
+        h->cell_bits = bits;
+    }
+    if (!h->box && (e = cudaMallocAsync((void **)&h->box, sizeof(int) * 8, st)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -288,17 +330,25 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
     const int64_t BP = (int64_t)shape.threads * shape.points_per_thread;
     const int64_t n_blocks = (k + BP - 1) / BP;
     const int64_t n_tiles = (h->n_tets + shape.tile - 1) / shape.tile;
-    const int64_t target = 8LL * h->n_sm * occ;
+    const int64_t target = 16LL * h->n_sm * occ;
     int64_t n_chunks = std::min<int64_t>(std::max<int64_t>((target + n_blocks - 1) / n_blocks, 1), n_tiles);
     const int64_t per = (n_tiles + n_chunks - 1) / n_chunks;
     n_chunks = (n_tiles + per - 1) / per;
+
+    const int bits = order_grid_bits(k);
+    BS_CUDA(ensure_order(h, k, bits, st));
+    BS_CUDA(ensure_partial(h, sizeof(double) * 3 * (size_t)k * n_chunks, st));
+    BS_CUDA(spatial_order(eval_pts_dev, k, bits, h->box, h->keys, h->cell_count, h->perm, st));
 
     VelocityArgs a;
     a.n_tets = h->n_tets;
     a.far = p->precision == BS_FP32 ? (const void *)h->far32 : (const void *)h->far64;
     a.near32 = h->near32;
     a.near64 = h->near64;
+    a.tile_hdr = h->tile_hdr;
+    a.tile_rho = h->tile_rho;
     a.pts = eval_pts_dev;
+    a.perm = h->perm;
     a.k = k;
     a.Q = Q;
     a.far_ratio2 = isinf(p->far_ratio) ? INFINITY : p->far_ratio * p->far_ratio;
@@ -311,12 +361,7 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
     a.work_counter = h->work_counter;
     a.n_chunks = (int)n_chunks;
     a.tiles_per_chunk = (int)per;
-    if (n_chunks == 1) {
-        a.partial = out_dev;  // a single chunk writes the final sums directly
-    } else {
-        BS_CUDA(ensure_partial(h, sizeof(double) * 3 * (size_t)k * n_chunks, st));
-        a.partial = h->partial;
-    }
+    a.partial = h->partial;
     int grid = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->prof) {
@@ -331,10 +376,10 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
         h->ev_used.push_back({e0, e1});
     }
     BS_CUDA(launch_velocity(p->precision, a, h->n_sm, st, &grid, e0, e1));
-    if (n_chunks > 1) BS_CUDA(launch_reduce(a, st));
+    BS_CUDA(launch_reduce(a, st));
     if (h->prof) {
         h->prof_kernel += 1;
-        h->prof_all += 2 + (n_chunks > 1 ? 1 : 0);
+        h->prof_all += 5 /* ordering */ + 3 /* zero, velocity, reduce */;
     }
     return BS_OK;
 }

@@ -17,10 +17,13 @@ constexpr double kPi = 3.14159265358979323846;
 // Per-tet records.
 //
 // Far record (one per tet, rebuilt when the far rule changes): everything the
-// far rule and the near/far test need, streamed through shared memory.
-//   [c.x c.y c.z rho^2] then per quadrature point q: [x_q (3), w'_q (3)]
-//   with w'_q = -(w_q |V| / 4pi) omega(x_q)  (sign and 1/4pi of Eq. 1 folded in)
-// Stride in elements: 4 + 6Q, rounded up to a multiple of 4 for float.
+// far rule and the near/far test need, streamed through shared memory, with
+// w'_q = -(w_q |V| / 4pi) omega(x_q) (sign and 1/4pi of Eq. 1 folded in).
+//   double: [c (3), rho^2] then per quadrature point [x_q (3), w'_q (3)]  (4 + 6Q)
+//   float : tile frame (coordinates relative to the tile origin o):
+//           [c - o (3), rho^2] then per q three float4
+//           [-2 x_q' (3), |x_q'|^2] [w'_q (3), B.x] [B.y, B.z, 0, 0], B = x_q' x w'_q  (4 + 12Q)
+// Tile header (per TILE consecutive tets): float4 [o (3), rc], float rho_max.
 //
 // Near record (one per tet, independent of the parameters): what the ray rule
 // needs.  Barycentric coordinates lambda_i(y) = g_i . (y - v0) + delta_i0
@@ -32,7 +35,7 @@ constexpr double kPi = 3.14159265358979323846;
 template <typename T>
 __host__ __device__ constexpr int far_stride(int Q)
 {
-    return sizeof(T) == 4 ? ((4 + 6 * Q + 3) / 4) * 4 : (4 + 6 * Q);
+    return sizeof(T) == 4 ? (4 + 12 * Q) : (4 + 6 * Q);
 }
 constexpr int kNearF32Vec4 = 8;  // float4 per near record
 constexpr int kNearF64 = 40;     // doubles per near record
@@ -73,9 +76,13 @@ cudaError_t build_tet_rule(int order, double *bary, double *w, cudaStream_t st);
 cudaError_t build_near_records(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
                                const double *omega, float4 *near32, double *near64, double *rho2,
                                int *flag, unsigned long long *first_bad, cudaStream_t st);
-// far records for a tet rule (needs near64 for vertices/omega and rho2)
+// tile headers and far records for a tet rule and tile size (needs near64 and rho2)
 cudaError_t build_far_records(const double *near64, const double *rho2, int64_t n_tets, const TetRule &rule,
-                              float *far32, double *far64, cudaStream_t st);
+                              int tile, float4 *hdr, float *hrho, float *far32, double *far64, cudaStream_t st);
+// spatial order of the evaluation points (Morton counting sort on a 2^bits grid)
+int order_grid_bits(int64_t k);
+cudaError_t spatial_order(const double *pts, int64_t k, int bits, int *box, unsigned *keys, int *count, int *perm,
+                          cudaStream_t st);
 
 struct VelocityArgs {
     // mesh
@@ -83,8 +90,11 @@ struct VelocityArgs {
     const void *far = nullptr;      // far records (float or double)
     const float4 *near32 = nullptr;
     const double *near64 = nullptr;
+    const float4 *tile_hdr = nullptr;  // [n_tiles] origin + centroid radius
+    const float *tile_rho = nullptr;   // [n_tiles] largest circumradius
     // points
     const double *pts = nullptr;  // [k][3]
+    const int *perm = nullptr;    // [k] visiting order (spatially sorted)
     int64_t k = 0;
     // rule
     int Q = 4;

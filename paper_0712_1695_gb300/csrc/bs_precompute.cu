@@ -7,9 +7,9 @@
 // h (chord threshold and the paper's pre-check scale), the centroid c and the
 // bounding radius Rb about it (a line farther than Rb from c misses the tet).
 //
-// Far record (per tet rule): centroid, circumradius^2 (near/far test) and, per
-// quadrature point, x_q and w'_q = -(w_q |V| / 4pi) omega(x_q), so that the
-// far rule of Eq. 1 is v += sum_q (x - x_q) x w'_q / |x - x_q|^3.
+// Far record (per tet rule and tile size): centroid, circumradius^2 (near/far
+// test) and, per quadrature point, x_q and w'_q = -(w_q |V| / 4pi) omega(x_q),
+// so that the far rule of Eq. 1 is v += sum_q (x - x_q) x w'_q / |x - x_q|^3.
 #include <math.h>
 
 #include "bs_internal.cuh"
@@ -116,10 +116,47 @@ __global__ void near_records_kernel(const double *__restrict__ nodes, int64_t n_
     f[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// Tile headers, one thread per tile of `tile` consecutive tets: origin o (mean
+// of the centroids, rounded to float), radius rc of the centroids about o
+// (rounded up), and the largest circumradius.  A point x is far from every
+// tet of the tile when |x - o| - rc > far_ratio * rho_max.
+__global__ void tile_headers_kernel(const double *__restrict__ near64, const double *__restrict__ rho2,
+                                    int64_t n_tets, int tile, float4 *__restrict__ hdr, float *__restrict__ hrho)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t first = t * tile;
+    if (first >= n_tets) return;
+    const int cnt = (int)min((int64_t)tile, n_tets - first);
+    D3 o = {0, 0, 0};
+    double rmax = 0.0;
+    for (int j = 0; j < cnt; ++j) {
+        const D3 c = load3(near64 + (first + j) * kNearF64 + nf64::C);
+        o = {o.x + c.x, o.y + c.y, o.z + c.z};
+        rmax = fmax(rmax, rho2[first + j]);
+    }
+    o = scale(o, 1.0 / cnt);
+    const float ox = (float)o.x, oy = (float)o.y, oz = (float)o.z;
+    const D3 of = {(double)ox, (double)oy, (double)oz};
+    double rc = 0.0;
+    for (int j = 0; j < cnt; ++j) {
+        const D3 d = sub(load3(near64 + (first + j) * kNearF64 + nf64::C), of);
+        rc = fmax(rc, sqrt(dot(d, d)));
+    }
+    hdr[t] = make_float4(ox, oy, oz, (float)(rc * (1.0 + 1e-6) + 1e-30));
+    hrho[t] = (float)(sqrt(rmax) * (1.0 + 1e-6));
+}
+
+// float32 far record (tile frame, x' = x - o of the tet's tile):
+//   [c' (3), rho^2] then per quadrature point three float4:
+//   [-2 x_q' (3), |x_q'|^2] [w'_q (3), B_q.x] [B_q.y, B_q.z, 0, 0]
+//   with B_q = x_q' x w'_q, so that sum_q (x' - x_q') x w'_q / |x' - x_q'|^3
+//   = x' x A - B with A = sum_q w'_q / r_q^3, B = sum_q B_q / r_q^3 and
+//   r_q^2 = |x'|^2 - 2 x'.x_q' + |x_q'|^2 (small terms in the tile frame).
+// float64 far record (global frame): [c (3), rho^2] then per q [x_q (3), w'_q (3)].
 __global__ void far_records_kernel(const double *__restrict__ near64, const double *__restrict__ rho2,
-                                   int64_t n_tets, int Q, const double *__restrict__ bary,
-                                   const double *__restrict__ wq, float *__restrict__ far32,
-                                   double *__restrict__ far64)
+                                   int64_t n_tets, int Q, int tile, const double *__restrict__ bary,
+                                   const double *__restrict__ wq, const float4 *__restrict__ hdr,
+                                   float *__restrict__ far32, double *__restrict__ far64)
 {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n_tets) return;
@@ -133,14 +170,17 @@ __global__ void far_records_kernel(const double *__restrict__ near64, const doub
     const int s32 = far_stride<float>(Q), s64 = far_stride<double>(Q);
     float *f = far32 + e * s32;
     double *d = far64 + e * s64;
+    const float4 h = hdr[e / tile];
+    const D3 o = {(double)h.x, (double)h.y, (double)h.z};
     const D3 c = load3(r + nf64::C);
     d[0] = c.x;
     d[1] = c.y;
     d[2] = c.z;
     d[3] = rho2[e];
-    f[0] = (float)c.x;
-    f[1] = (float)c.y;
-    f[2] = (float)c.z;
+    const D3 cl = sub(c, o);
+    f[0] = (float)cl.x;
+    f[1] = (float)cl.y;
+    f[2] = (float)cl.z;
     f[3] = (float)rho2[e];
     const double s = -vol / (4.0 * kPi);
     for (int q = 0; q < Q; ++q) {
@@ -152,12 +192,23 @@ __global__ void far_records_kernel(const double *__restrict__ near64, const doub
         }
         wv = scale(wv, s * wq[q]);
         const double vals[6] = {xq.x, xq.y, xq.z, wv.x, wv.y, wv.z};
-        for (int j = 0; j < 6; ++j) {
-            d[4 + 6 * q + j] = vals[j];
-            f[4 + 6 * q + j] = (float)vals[j];
-        }
+        for (int j = 0; j < 6; ++j) d[4 + 6 * q + j] = vals[j];
+        const D3 xl = sub(xq, o);
+        const D3 B = cross(xl, wv);
+        float *g = f + 4 + 12 * q;
+        g[0] = (float)(-2.0 * xl.x);
+        g[1] = (float)(-2.0 * xl.y);
+        g[2] = (float)(-2.0 * xl.z);
+        g[3] = (float)dot(xl, xl);
+        g[4] = (float)wv.x;
+        g[5] = (float)wv.y;
+        g[6] = (float)wv.z;
+        g[7] = (float)B.x;
+        g[8] = (float)B.y;
+        g[9] = (float)B.z;
+        g[10] = 0.f;
+        g[11] = 0.f;
     }
-    for (int j = 4 + 6 * Q; j < s32; ++j) f[j] = 0.f;
 }
 
 }  // namespace
@@ -174,12 +225,14 @@ cudaError_t build_near_records(const double *nodes, int64_t n_nodes, const int32
 }
 
 cudaError_t build_far_records(const double *near64, const double *rho2, int64_t n_tets, const TetRule &rule,
-                              float *far32, double *far64, cudaStream_t st)
+                              int tile, float4 *hdr, float *hrho, float *far32, double *far64, cudaStream_t st)
 {
     if (n_tets == 0) return cudaSuccess;
     const int tb = 128;
-    far_records_kernel<<<(unsigned)((n_tets + tb - 1) / tb), tb, 0, st>>>(near64, rho2, n_tets, rule.order,
-                                                                         rule.bary, rule.w, far32, far64);
+    const int64_t n_tiles = (n_tets + tile - 1) / tile;
+    tile_headers_kernel<<<(unsigned)((n_tiles + tb - 1) / tb), tb, 0, st>>>(near64, rho2, n_tets, tile, hdr, hrho);
+    far_records_kernel<<<(unsigned)((n_tets + tb - 1) / tb), tb, 0, st>>>(near64, rho2, n_tets, rule.order, tile,
+                                                                         rule.bary, rule.w, hdr, far32, far64);
     return cudaGetLastError();
 }
 

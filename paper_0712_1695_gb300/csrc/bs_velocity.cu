@@ -44,6 +44,7 @@ constexpr float kDegenA = 1e-5f;     // float32: |a_i| below this with x inside/
 // |det| <= 1e-12 |e1||e2| as parallel and accepts area coordinates down to -1e-12).
 constexpr double kParD = 1e-12;
 constexpr float kParF = 1e-6f;
+constexpr float kVertexFallback = 1e-5f;
 constexpr long long kWaitCap = 1LL << 26;
 
 // ---------------------------------------------------------------------------
@@ -126,167 +127,303 @@ struct NearOut {
     int hits;
 };
 
-// float64 version: every step in double.  Used by the float64 path and by
-// degenerate pairs of the float32 path.
-__device__ __noinline__ NearOut near_pair_f64(V3<double> x, const double *__restrict__ r, const dbl4 *__restrict__ lines,
-                                 int L, int lane)
+// Everything about a pair that does not depend on the line, in float64.
+struct PairF64 {
+    double a[4];           // lambda_i(x); exactly e_k when x is vertex k
+    V3<double> g[4];       // face-plane gradients, g0 = -(g1 + g2 + g3)
+    V3<double> w[4];       // nodal vorticity
+    V3<double> Wa;         // omega interpolated (linearly extended) at x
+    V3<double> rc;         // centroid - x
+    double rc2, bound, tau_h, par2[4];
+};
+
+__device__ inline int vertex_index(V3<double> x, const double *__restrict__ r)
 {
-    V3<double> v[4];
     int vk = -1;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        v[i] = mk(r[nf64::V + 3 * i], r[nf64::V + 3 * i + 1], r[nf64::V + 3 * i + 2]);
-        if (vk < 0 && v[i].x == x.x && v[i].y == x.y && v[i].z == x.z) vk = i;
-    }
-    const V3<double> g1 = mk(r[nf64::G + 0], r[nf64::G + 1], r[nf64::G + 2]);
-    const V3<double> g2 = mk(r[nf64::G + 3], r[nf64::G + 4], r[nf64::G + 5]);
-    const V3<double> g3 = mk(r[nf64::G + 6], r[nf64::G + 7], r[nf64::G + 8]);
-    V3<double> w[4];
+    for (int i = 0; i < 4; ++i)
+        if (vk < 0 && r[nf64::V + 3 * i] == x.x && r[nf64::V + 3 * i + 1] == x.y && r[nf64::V + 3 * i + 2] == x.z)
+            vk = i;
+    return vk;
+}
+
+__device__ inline void pair_setup_f64(PairF64 &P, V3<double> x, const double *__restrict__ r, int vk)
+{
+    P.g[1] = mk(r[nf64::G + 0], r[nf64::G + 1], r[nf64::G + 2]);
+    P.g[2] = mk(r[nf64::G + 3], r[nf64::G + 4], r[nf64::G + 5]);
+    P.g[3] = mk(r[nf64::G + 6], r[nf64::G + 7], r[nf64::G + 8]);
+    P.g[0] = mk(-(P.g[1].x + P.g[2].x + P.g[3].x), -(P.g[1].y + P.g[2].y + P.g[3].y),
+                -(P.g[1].z + P.g[2].z + P.g[3].z));
 #pragma unroll
-    for (int i = 0; i < 4; ++i) w[i] = mk(r[nf64::W + 3 * i], r[nf64::W + 3 * i + 1], r[nf64::W + 3 * i + 2]);
-    const double h = r[nf64::H], rb2 = r[nf64::RB2];
-    const V3<double> d0 = mk(x.x - v[0].x, x.y - v[0].y, x.z - v[0].z);
-    double a[4];
+    for (int i = 0; i < 4; ++i) P.w[i] = mk(r[nf64::W + 3 * i], r[nf64::W + 3 * i + 1], r[nf64::W + 3 * i + 2]);
     if (vk >= 0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = (i == vk) ? 1.0 : 0.0;
+        for (int i = 0; i < 4; ++i) P.a[i] = (i == vk) ? 1.0 : 0.0;
     } else {
-        a[1] = dot3(g1, d0);
-        a[2] = dot3(g2, d0);
-        a[3] = dot3(g3, d0);
-        a[0] = 1.0 - a[1] - a[2] - a[3];
+        const V3<double> d0 = mk(x.x - r[nf64::V], x.y - r[nf64::V + 1], x.z - r[nf64::V + 2]);
+        P.a[1] = dot3(P.g[1], d0);
+        P.a[2] = dot3(P.g[2], d0);
+        P.a[3] = dot3(P.g[3], d0);
+        P.a[0] = 1.0 - P.a[1] - P.a[2] - P.a[3];
     }
-    const V3<double> Wa = mk(a[0] * w[0].x + a[1] * w[1].x + a[2] * w[2].x + a[3] * w[3].x,
-                             a[0] * w[0].y + a[1] * w[1].y + a[2] * w[2].y + a[3] * w[3].y,
-                             a[0] * w[0].z + a[1] * w[1].z + a[2] * w[2].z + a[3] * w[3].z);
-    const V3<double> rc = mk(r[nf64::C] - x.x, r[nf64::C + 1] - x.y, r[nf64::C + 2] - x.z);
-    const double rc2 = dot3(rc, rc);
-    const double bound = rb2 * (1.0 + kBoundPadD);
-    const V3<double> g0 = mk(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
-    const double par2[4] = {kParD * kParD * dot3(g0, g0), kParD * kParD * dot3(g1, g1),
-                            kParD * kParD * dot3(g2, g2), kParD * kParD * dot3(g3, g3)};
-    double ax = 0.0, ay = 0.0, az = 0.0;
-    int hits = 0;
-    for (int l = lane; l < L; l += 32) {
-        const dbl4 ln = lines[l];
-        const V3<double> s = mk(ln.x, ln.y, ln.z);
-        const double rs = dot3(rc, s);
-        if (rc2 - rs * rs > bound) continue;  // line farther than Rb from the centroid
-        double b[4];
-        b[1] = dot3(g1, s);
-        b[2] = dot3(g2, s);
-        b[3] = dot3(g3, s);
-        b[0] = -(b[1] + b[2] + b[3]);
-        double lo = -INFINITY, hi = INFINITY;
-        bool empty = false;
+    const double *a = P.a;
+    P.Wa = mk(a[0] * P.w[0].x + a[1] * P.w[1].x + a[2] * P.w[2].x + a[3] * P.w[3].x,
+              a[0] * P.w[0].y + a[1] * P.w[1].y + a[2] * P.w[2].y + a[3] * P.w[3].y,
+              a[0] * P.w[0].z + a[1] * P.w[1].z + a[2] * P.w[2].z + a[3] * P.w[3].z);
+    P.rc = mk(r[nf64::C] - x.x, r[nf64::C + 1] - x.y, r[nf64::C + 2] - x.z);
+    P.rc2 = dot3(P.rc, P.rc);
+    P.bound = r[nf64::RB2] * (1.0 + kBoundPadD);
+    P.tau_h = kTau * r[nf64::H];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (b[i] * b[i] <= par2[i]) empty = empty || (a[i] < -kParD);
-            else if (b[i] > 0.0) lo = fmax(lo, -a[i] / b[i]);
-            else hi = fmin(hi, -a[i] / b[i]);
-        }
-        if (empty || !(hi - lo > kTau * h)) continue;
-        const V3<double> Wb = mk(b[0] * w[0].x + b[1] * w[1].x + b[2] * w[2].x + b[3] * w[3].x,
-                                 b[0] * w[0].y + b[1] * w[1].y + b[2] * w[2].y + b[3] * w[3].y,
-                                 b[0] * w[0].z + b[1] * w[1].z + b[2] * w[2].z + b[3] * w[3].z);
-        const double f1 = fabs(hi) - fabs(lo);
-        const double f2 = 0.5 * (hi * fabs(hi) - lo * fabs(lo));
-        const V3<double> J = mk(f1 * Wa.x + f2 * Wb.x, f1 * Wa.y + f2 * Wb.y, f1 * Wa.z + f2 * Wb.z);
-        ax += ln.w * (s.y * J.z - s.z * J.y);
-        ay += ln.w * (s.z * J.x - s.x * J.z);
-        az += ln.w * (s.x * J.y - s.y * J.x);
-        ++hits;
+    for (int i = 0; i < 4; ++i) P.par2[i] = kParD * kParD * dot3(P.g[i], P.g[i]);
+}
+
+// One line in float64; adds k * s x J to acc and returns true on a hit.
+__device__ inline bool line_f64(const PairF64 &P, const dbl4 ln, V3<double> &acc)
+{
+    const V3<double> s = mk(ln.x, ln.y, ln.z);
+    const double rs = dot3(P.rc, s);
+    if (P.rc2 - rs * rs > P.bound) return false;  // line farther than Rb from the centroid
+    double b[4];
+    b[1] = dot3(P.g[1], s);
+    b[2] = dot3(P.g[2], s);
+    b[3] = dot3(P.g[3], s);
+    b[0] = -(b[1] + b[2] + b[3]);
+    double lo = -INFINITY, hi = INFINITY;
+    bool empty = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (b[i] * b[i] <= P.par2[i]) empty = empty || (P.a[i] < -kParD);
+        else if (b[i] > 0.0) lo = fmax(lo, -P.a[i] / b[i]);
+        else hi = fmin(hi, -P.a[i] / b[i]);
     }
+    if (empty || !(hi - lo > P.tau_h)) return false;
+    const V3<double> *w = P.w;
+    const V3<double> Wb = mk(b[0] * w[0].x + b[1] * w[1].x + b[2] * w[2].x + b[3] * w[3].x,
+                             b[0] * w[0].y + b[1] * w[1].y + b[2] * w[2].y + b[3] * w[3].y,
+                             b[0] * w[0].z + b[1] * w[1].z + b[2] * w[2].z + b[3] * w[3].z);
+    const double f1 = fabs(hi) - fabs(lo);
+    const double f2 = 0.5 * (hi * fabs(hi) - lo * fabs(lo));
+    const V3<double> J = mk(f1 * P.Wa.x + f2 * Wb.x, f1 * P.Wa.y + f2 * Wb.y, f1 * P.Wa.z + f2 * Wb.z);
+    acc.x += ln.w * (s.y * J.z - s.z * J.y);
+    acc.y += ln.w * (s.z * J.x - s.x * J.z);
+    acc.z += ln.w * (s.x * J.y - s.y * J.x);
+    return true;
+}
+
+// float64 version: every step in double.  Used by the float64 path and by
+// pairs of the float32 path whose point lies on an edge or face of the tet.
+__device__ __noinline__ NearOut near_pair_f64(V3<double> x, const double *__restrict__ r,
+                                              const dbl4 *__restrict__ lines, int L, int lane)
+{
+    PairF64 P;
+    pair_setup_f64(P, x, r, vertex_index(x, r));
+    V3<double> acc = mk(0.0, 0.0, 0.0);
+    int hits = 0;
+    for (int l = lane; l < L; l += 32) hits += line_f64(P, lines[l], acc) ? 1 : 0;
     NearOut o;
-    o.vx = warp_sum(ax);
-    o.vy = warp_sum(ay);
-    o.vz = warp_sum(az);
+    o.vx = warp_sum(acc.x);
+    o.vy = warp_sum(acc.y);
+    o.vz = warp_sum(acc.z);
     o.hits = warp_sum(hits);
     return o;
 }
 
+// One line in float64 with the record read from memory as it is needed (a
+// small register footprint: used for the rare float64 steps of the float32
+// path).  vk = vertex index of x in the tet or -1.
+__device__ __noinline__ bool line_f64_lean(V3<double> x, const double *__restrict__ r, int vk, const dbl4 ln,
+                                           V3<double> &acc)
+{
+    const V3<double> s = mk(ln.x, ln.y, ln.z);
+    {
+        const V3<double> rc = mk(r[nf64::C] - x.x, r[nf64::C + 1] - x.y, r[nf64::C + 2] - x.z);
+        const double rs = dot3(rc, s);
+        if (dot3(rc, rc) - rs * rs > r[nf64::RB2] * (1.0 + kBoundPadD)) return false;
+    }
+    double a[4], b[4];
+    {
+        const V3<double> d0 = mk(x.x - r[nf64::V], x.y - r[nf64::V + 1], x.z - r[nf64::V + 2]);
+        double sa = 0.0, sb = 0.0;
+        for (int i = 1; i < 4; ++i) {
+            const V3<double> g = mk(r[nf64::G + 3 * i - 3], r[nf64::G + 3 * i - 2], r[nf64::G + 3 * i - 1]);
+            a[i] = dot3(g, d0);
+            b[i] = dot3(g, s);
+            sa += a[i];
+            sb += b[i];
+        }
+        a[0] = 1.0 - sa;
+        b[0] = -sb;
+        if (vk >= 0)
+            for (int i = 0; i < 4; ++i) a[i] = (i == vk) ? 1.0 : 0.0;
+    }
+    double lo = -INFINITY, hi = INFINITY;
+    bool empty = false;
+    for (int i = 0; i < 4; ++i) {
+        V3<double> g;
+        if (i == 0) {
+            g = mk(0.0, 0.0, 0.0);
+            for (int j = 1; j < 4; ++j) {
+                g.x -= r[nf64::G + 3 * j - 3];
+                g.y -= r[nf64::G + 3 * j - 2];
+                g.z -= r[nf64::G + 3 * j - 1];
+            }
+        } else {
+            g = mk(r[nf64::G + 3 * i - 3], r[nf64::G + 3 * i - 2], r[nf64::G + 3 * i - 1]);
+        }
+        if (b[i] * b[i] <= kParD * kParD * dot3(g, g)) empty = empty || (a[i] < -kParD);
+        else if (b[i] > 0.0) lo = fmax(lo, -a[i] / b[i]);
+        else hi = fmin(hi, -a[i] / b[i]);
+    }
+    if (empty || !(hi - lo > kTau * r[nf64::H])) return false;
+    const double f1 = fabs(hi) - fabs(lo);
+    const double f2 = 0.5 * (hi * fabs(hi) - lo * fabs(lo));
+    V3<double> J = mk(0.0, 0.0, 0.0);
+    for (int i = 0; i < 4; ++i) {
+        const double c = f1 * a[i] + f2 * b[i];
+        J.x += c * r[nf64::W + 3 * i];
+        J.y += c * r[nf64::W + 3 * i + 1];
+        J.z += c * r[nf64::W + 3 * i + 2];
+    }
+    acc.x += ln.w * (s.y * J.z - s.z * J.y);
+    acc.y += ln.w * (s.z * J.x - s.x * J.z);
+    acc.z += ln.w * (s.x * J.y - s.y * J.x);
+    return true;
+}
+
 // float32 version.  The differences x - v0 and c - x are taken in float64
 // and rounded once, so a_i carries no error from the absolute coordinates.
-// Pairs whose point is on (or within 1e-5 in barycentric units of) the
-// boundary of the tet go to the float64 version: there the chord can jump
-// with the sign of a tiny b_i and float32 rounding would pick a side at
-// random.
-__device__ __noinline__ NearOut near_pair_f32(V3<double> x, const float4 *__restrict__ r32, const double *__restrict__ r64,
-                                 const float4 *__restrict__ lines, const dbl4 *__restrict__ lines64, int L,
-                                 int lane)
+// When x is vertex k of the tet, a = e_k exactly and the chord is decided by
+// the signs of b_i on the three faces through x; a line with
+// |b_i| <= 1e-5 |g_i| on one of them (nearly in that face plane, where the
+// chord jumps with the sign) is recomputed in float64 in a second pass, after
+// the float32 state is dead (keeps the register footprint of the pass
+// small).  Pairs whose point is within 1e-5 (barycentric) of the tet's
+// boundary without being a vertex run wholly in float64.
+__device__ __noinline__ NearOut near_pair_f32(V3<double> x, const float4 *__restrict__ r32,
+                                              const double *__restrict__ r64, const float4 *__restrict__ lines,
+                                              const dbl4 *__restrict__ lines64, int L, int lane)
 {
-    const V3<double> v0 = mk(r64[nf64::V], r64[nf64::V + 1], r64[nf64::V + 2]);
-    bool at_vertex = false;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        at_vertex = at_vertex || (r64[nf64::V + 3 * i] == x.x && r64[nf64::V + 3 * i + 1] == x.y &&
-                                  r64[nf64::V + 3 * i + 2] == x.z);
-    const float4 q0 = r32[0], q1 = r32[1], q2 = r32[2];
-    const V3<float> g1 = mk(q0.x, q0.y, q0.z), g2 = mk(q1.x, q1.y, q1.z), g3 = mk(q2.x, q2.y, q2.z);
-    const float h = q0.w, rb2 = q1.w;
-    const V3<float> d0 = mk((float)(x.x - v0.x), (float)(x.y - v0.y), (float)(x.z - v0.z));
-    float a[4];
-    a[1] = dot3(g1, d0);
-    a[2] = dot3(g2, d0);
-    a[3] = dot3(g3, d0);
-    a[0] = 1.0f - a[1] - a[2] - a[3];
-    const float amin = fminf(fminf(a[0], a[1]), fminf(a[2], a[3]));
-    const float aabs = fminf(fminf(fabsf(a[0]), fabsf(a[1])), fminf(fabsf(a[2]), fabsf(a[3])));
-    if (at_vertex || (amin > -kDegenA && aabs < kDegenA)) return near_pair_f64(x, r64, lines64, L, lane);
-
-    V3<float> w[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 t = r32[3 + i];
-        w[i] = mk(t.x, t.y, t.z);
-    }
-    const V3<float> Wa = mk(a[0] * w[0].x + a[1] * w[1].x + a[2] * w[2].x + a[3] * w[3].x,
-                            a[0] * w[0].y + a[1] * w[1].y + a[2] * w[2].y + a[3] * w[3].y,
-                            a[0] * w[0].z + a[1] * w[1].z + a[2] * w[2].z + a[3] * w[3].z);
-    const V3<float> rc = mk((float)(r64[nf64::C] - x.x), (float)(r64[nf64::C + 1] - x.y),
-                            (float)(r64[nf64::C + 2] - x.z));
-    const float rc2 = dot3(rc, rc);
-    const float bound = rb2 * (1.0f + kBoundPadF);
-    const V3<float> g0 = mk(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
-    const float par2[4] = {kParF * kParF * dot3(g0, g0), kParF * kParF * dot3(g1, g1), kParF * kParF * dot3(g2, g2),
-                           kParF * kParF * dot3(g3, g3)};
-    const float tau_h = (float)kTau * h;
+    const int vk = vertex_index(x, r64);
     float ax = 0.f, ay = 0.f, az = 0.f;
     int hits = 0;
-    for (int l = lane; l < L; l += 32) {
-        const float4 ln = lines[l];
-        const V3<float> s = mk(ln.x, ln.y, ln.z);
-        const float rs = dot3(rc, s);
-        if (rc2 - rs * rs > bound) continue;
-        float b[4];
-        b[1] = dot3(g1, s);
-        b[2] = dot3(g2, s);
-        b[3] = dot3(g3, s);
-        b[0] = -(b[1] + b[2] + b[3]);
-        float lo = -INFINITY, hi = INFINITY;
-        bool empty = false;
+    bool any_redo = false;
+    bool whole_f64 = false;
+    {
+        const float4 q0 = r32[0], q1 = r32[1], q2 = r32[2];
+        V3<float> g[4];
+        g[1] = mk(q0.x, q0.y, q0.z);
+        g[2] = mk(q1.x, q1.y, q1.z);
+        g[3] = mk(q2.x, q2.y, q2.z);
+        g[0] = mk(-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z));
+        const float h = q0.w, rb2 = q1.w;
+        float a[4];
+        if (vk >= 0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (b[i] * b[i] <= par2[i]) empty = empty || (a[i] < -kParF);
-            else if (b[i] > 0.f) lo = fmaxf(lo, -a[i] / b[i]);
-            else hi = fminf(hi, -a[i] / b[i]);
+            for (int i = 0; i < 4; ++i) a[i] = (i == vk) ? 1.0f : 0.0f;
+        } else {
+            const V3<float> d0 = mk((float)(x.x - r64[nf64::V]), (float)(x.y - r64[nf64::V + 1]),
+                                    (float)(x.z - r64[nf64::V + 2]));
+            a[1] = dot3(g[1], d0);
+            a[2] = dot3(g[2], d0);
+            a[3] = dot3(g[3], d0);
+            a[0] = 1.0f - a[1] - a[2] - a[3];
+            const float amin = fminf(fminf(a[0], a[1]), fminf(a[2], a[3]));
+            const float aabs = fminf(fminf(fabsf(a[0]), fabsf(a[1])), fminf(fabsf(a[2]), fabsf(a[3])));
+            whole_f64 = amin > -kDegenA && aabs < kDegenA;
         }
-        if (empty || !(hi - lo > tau_h)) continue;
-        const V3<float> Wb = mk(b[0] * w[0].x + b[1] * w[1].x + b[2] * w[2].x + b[3] * w[3].x,
-                                b[0] * w[0].y + b[1] * w[1].y + b[2] * w[2].y + b[3] * w[3].y,
-                                b[0] * w[0].z + b[1] * w[1].z + b[2] * w[2].z + b[3] * w[3].z);
-        const float f1 = fabsf(hi) - fabsf(lo);
-        const float f2 = 0.5f * (hi * fabsf(hi) - lo * fabsf(lo));
-        const V3<float> J = mk(f1 * Wa.x + f2 * Wb.x, f1 * Wa.y + f2 * Wb.y, f1 * Wa.z + f2 * Wb.z);
-        ax += ln.w * (s.y * J.z - s.z * J.y);
-        ay += ln.w * (s.z * J.x - s.x * J.z);
-        az += ln.w * (s.x * J.y - s.y * J.x);
-        ++hits;
+        if (!whole_f64) {
+            V3<float> w[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 t = r32[3 + i];
+                w[i] = mk(t.x, t.y, t.z);
+            }
+            const V3<float> Wa = mk(a[0] * w[0].x + a[1] * w[1].x + a[2] * w[2].x + a[3] * w[3].x,
+                                    a[0] * w[0].y + a[1] * w[1].y + a[2] * w[2].y + a[3] * w[3].y,
+                                    a[0] * w[0].z + a[1] * w[1].z + a[2] * w[2].z + a[3] * w[3].z);
+            const V3<float> rc = mk((float)(r64[nf64::C] - x.x), (float)(r64[nf64::C + 1] - x.y),
+                                    (float)(r64[nf64::C + 2] - x.z));
+            const float rc2 = dot3(rc, rc);
+            const float bound = rb2 * (1.0f + kBoundPadF);
+            const float tau_h = (float)kTau * h;
+            float par2[4], fb2[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float gg = dot3(g[i], g[i]);
+                par2[i] = kParF * kParF * gg;
+                // faces through vertex vk: below this |b_i| the sign is decided in float64
+                fb2[i] = (vk >= 0 && i != vk) ? kVertexFallback * kVertexFallback * gg : -1.0f;
+            }
+#pragma unroll 1
+            for (int l = lane; l < L; l += 32) {
+                const float4 ln = lines[l];
+                const V3<float> s = mk(ln.x, ln.y, ln.z);
+                const float rs = dot3(rc, s);
+                if (rc2 - rs * rs > bound) continue;
+                float b[4];
+                b[1] = dot3(g[1], s);
+                b[2] = dot3(g[2], s);
+                b[3] = dot3(g[3], s);
+                b[0] = -(b[1] + b[2] + b[3]);
+                bool redo = false;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) redo = redo || (b[i] * b[i] <= fb2[i]);
+                if (redo) {
+                    any_redo = true;
+                    continue;
+                }
+                float lo = -INFINITY, hi = INFINITY;
+                bool empty = false;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (b[i] * b[i] <= par2[i]) empty = empty || (a[i] < -kParF);
+                    else if (b[i] > 0.f) lo = fmaxf(lo, -a[i] / b[i]);
+                    else hi = fminf(hi, -a[i] / b[i]);
+                }
+                if (empty || !(hi - lo > tau_h)) continue;
+                const V3<float> Wb = mk(b[0] * w[0].x + b[1] * w[1].x + b[2] * w[2].x + b[3] * w[3].x,
+                                        b[0] * w[0].y + b[1] * w[1].y + b[2] * w[2].y + b[3] * w[3].y,
+                                        b[0] * w[0].z + b[1] * w[1].z + b[2] * w[2].z + b[3] * w[3].z);
+                const float f1 = fabsf(hi) - fabsf(lo);
+                const float f2 = 0.5f * (hi * fabsf(hi) - lo * fabsf(lo));
+                const V3<float> J = mk(f1 * Wa.x + f2 * Wb.x, f1 * Wa.y + f2 * Wb.y, f1 * Wa.z + f2 * Wb.z);
+                ax += ln.w * (s.y * J.z - s.z * J.y);
+                ay += ln.w * (s.z * J.x - s.x * J.z);
+                az += ln.w * (s.x * J.y - s.y * J.x);
+                ++hits;
+            }
+        }
+    }
+    V3<double> acc = mk((double)ax, (double)ay, (double)az);
+    if (whole_f64) {
+#pragma unroll 1
+        for (int l = lane; l < L; l += 32) hits += line_f64_lean(x, r64, -1, lines64[l], acc) ? 1 : 0;
+    } else if (any_redo) {
+        // second pass: find this lane's flagged lines again (same float32 test) and redo them in float64
+        const float4 q0 = r32[0], q1 = r32[1], q2 = r32[2];
+        const V3<float> g1 = mk(q0.x, q0.y, q0.z), g2 = mk(q1.x, q1.y, q1.z), g3 = mk(q2.x, q2.y, q2.z);
+        const V3<float> g0 = mk(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
+        const V3<float> rc = mk((float)(r64[nf64::C] - x.x), (float)(r64[nf64::C + 1] - x.y),
+                                (float)(r64[nf64::C + 2] - x.z));
+        const float rc2 = dot3(rc, rc), bound = q1.w * (1.0f + kBoundPadF);
+        const float f = kVertexFallback * kVertexFallback;
+#pragma unroll 1
+        for (int l = lane; l < L; l += 32) {
+            const float4 ln = lines[l];
+            const V3<float> s = mk(ln.x, ln.y, ln.z);
+            const float rs = dot3(rc, s);
+            if (rc2 - rs * rs > bound) continue;
+            const float b1 = dot3(g1, s), b2 = dot3(g2, s), b3 = dot3(g3, s), b0 = -(b1 + b2 + b3);
+            const bool redo = (vk != 0 && b0 * b0 <= f * dot3(g0, g0)) || (vk != 1 && b1 * b1 <= f * dot3(g1, g1)) ||
+                              (vk != 2 && b2 * b2 <= f * dot3(g2, g2)) || (vk != 3 && b3 * b3 <= f * dot3(g3, g3));
+            if (redo && line_f64_lean(x, r64, vk, lines64[l], acc)) ++hits;
+        }
     }
     NearOut o;
-    o.vx = warp_sum(ax);
-    o.vy = warp_sum(ay);
-    o.vz = warp_sum(az);
+    o.vx = warp_sum(acc.x);
+    o.vy = warp_sum(acc.y);
+    o.vz = warp_sum(acc.z);
     o.hits = warp_sum(hits);
     return o;
 }
@@ -305,23 +442,35 @@ struct Acc<double> {
     double s[3];
 };
 
-template <typename T, int Q, int P, int NT, int TILE>
-__global__ void __launch_bounds__(NT) velocity_kernel(const VelocityArgs a)
+template <int S>
+struct Pipe {
+    uint64_t full[S];  // bulk copy of the tile in stage s has landed
+    int done[S];       // warps finished with stage s (the last one refills it)
+};
+
+// Points: the block holds BP = NT*P consecutive points of the spatial order;
+// warp w owns the 32*P consecutive slots [w*32*P, (w+1)*32*P), lane l the
+// slots w*32*P + p*32 + l.  A warp therefore covers a compact patch of
+// points, and a tile whose tets are all far from that patch skips the
+// per-pair near/far test (culled=true below).
+template <typename T, int Q, int P, int NT, int TILE, int S, int MINB>
+__global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a)
 {
     constexpr int RS = far_stride<T>(Q);
     constexpr int BP = NT * P;
     constexpr int NW = NT / 32;
-    constexpr int QCAP = 256;
+    constexpr int QCAP = 32 * P * TILE;  // a whole tile's pairs fit: the queue is drained between tiles only
     constexpr int TILE_BYTES = TILE * RS * (int)sizeof(T);
+    constexpr bool F32 = sizeof(T) == 4;
     static_assert(TILE <= 256, "tet index in the near queue is 8 bits");
     static_assert(P * 32 <= 256, "point slot in the near queue is 8 bits");
 
     extern __shared__ __align__(128) unsigned char smem[];
-    T *tiles = reinterpret_cast<T *>(smem);                                         // [2][TILE*RS]
-    double *spts = reinterpret_cast<double *>(smem + 2 * TILE_BYTES);               // [BP][3]
-    uint16_t *queue = reinterpret_cast<uint16_t *>(spts + 3 * BP);                  // [NW][QCAP]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(queue + NW * QCAP);               // [2]
-    int *s_item = reinterpret_cast<int *>(bars + 2);
+    T *tiles = reinterpret_cast<T *>(smem);                            // [S][TILE*RS]
+    double *spts = reinterpret_cast<double *>(smem + S * TILE_BYTES);  // [BP][3]
+    uint16_t *queue = reinterpret_cast<uint16_t *>(spts + 3 * BP);     // [NW][QCAP]
+    Pipe<S> *pipe = reinterpret_cast<Pipe<S> *>(queue + NW * QCAP);
+    int *s_item = reinterpret_cast<int *>(pipe + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t k = a.k;
@@ -329,15 +478,27 @@ __global__ void __launch_bounds__(NT) velocity_kernel(const VelocityArgs a)
     const int64_t n_items = n_blocks * a.n_chunks;
     const int64_t n_tiles = (a.n_tets + TILE - 1) / TILE;
     const T fr2 = (T)a.far_ratio2;
+    const float fr = a.all_ray ? INFINITY : (float)sqrt(a.far_ratio2);
     const T *far = reinterpret_cast<const T *>(a.far);
 
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int st = 0; st < S; ++st) {
+            mbar_init(&pipe->full[st], 1);
+            pipe->done[st] = 0;
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phase = 0u;  // bit st: parity of the next completion of full[st]
+
+    auto issue = [&](int64_t t, int st) {
+        const int64_t first = t * TILE;
+        const int cnt = (int)min((int64_t)TILE, a.n_tets - first);
+        const uint32_t bytes = (uint32_t)cnt * RS * sizeof(T);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&pipe->full[st], bytes);
+        bulk_g2s(tiles + st * TILE * RS, far + first * RS, bytes, &pipe->full[st]);
+    };
 
     for (;;) {
         if (tid == 0) *s_item = atomicAdd(a.work_counter, 1);
@@ -347,23 +508,19 @@ __global__ void __launch_bounds__(NT) velocity_kernel(const VelocityArgs a)
         const int64_t pb = item % n_blocks, ck = item / n_blocks;
         const int64_t t0 = ck * a.tiles_per_chunk;
         const int64_t t1 = min(t0 + (int64_t)a.tiles_per_chunk, n_tiles);
+        const int n_local = (int)(t1 - t0);
 
-        // kick off the first tile while the points are loaded
-        auto issue = [&](int64_t t, int buf) {
-            const int64_t first = t * TILE;
-            const int cnt = (int)min((int64_t)TILE, a.n_tets - first);
-            const uint32_t bytes = (uint32_t)cnt * RS * sizeof(T);
-            mbar_expect_tx(&bars[buf], bytes);
-            bulk_g2s(tiles + buf * TILE * RS, far + first * RS, bytes, &bars[buf]);
-        };
-        if (tid == 0 && t0 < t1) issue(t0, 0);
+        // prologue: fill every stage while the points are loaded
+        if (tid == 0)
+            for (int i = 0; i < S && i < n_local; ++i) issue(t0 + i, i);
 
         for (int i = tid; i < BP; i += NT) {
             int64_t gi = pb * BP + i;
             if (gi >= k) gi = k - 1;  // pad with a real point; its result is not written
-            spts[3 * i + 0] = a.pts[3 * gi + 0];
-            spts[3 * i + 1] = a.pts[3 * gi + 1];
-            spts[3 * i + 2] = a.pts[3 * gi + 2];
+            const int64_t src = a.perm[gi];
+            spts[3 * i + 0] = a.pts[3 * src + 0];
+            spts[3 * i + 1] = a.pts[3 * src + 1];
+            spts[3 * i + 2] = a.pts[3 * src + 2];
         }
         __syncthreads();
 
@@ -372,166 +529,310 @@ __global__ void __launch_bounds__(NT) velocity_kernel(const VelocityArgs a)
         int nnear[P], nhit[P];
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const int slot = p * NT + tid;
+            const int slot = warp * 32 * P + p * 32 + lane;
             xp[p] = mk((T)spts[3 * slot], (T)spts[3 * slot + 1], (T)spts[3 * slot + 2]);
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 acc[p].s[j] = 0;
-                if constexpr (sizeof(T) == 4) acc[p].c[j] = 0;
+                if constexpr (F32) acc[p].c[j] = 0;
             }
             nnear[p] = 0;
             nhit[p] = 0;
         }
+        // bounding sphere of the warp's points (float, padded)
+        float cwx, cwy, cwz, rw;
+        {
+            float mnx = (float)xp[0].x, mxx = mnx, mny = (float)xp[0].y, mxy = mny, mnz = (float)xp[0].z, mxz = mnz;
+#pragma unroll
+            for (int p = 1; p < P; ++p) {
+                mnx = fminf(mnx, (float)xp[p].x); mxx = fmaxf(mxx, (float)xp[p].x);
+                mny = fminf(mny, (float)xp[p].y); mxy = fmaxf(mxy, (float)xp[p].y);
+                mnz = fminf(mnz, (float)xp[p].z); mxz = fmaxf(mxz, (float)xp[p].z);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+                mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+                mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+                mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+                mnz = fminf(mnz, __shfl_xor_sync(0xffffffffu, mnz, o));
+                mxz = fmaxf(mxz, __shfl_xor_sync(0xffffffffu, mxz, o));
+            }
+            cwx = 0.5f * (mnx + mxx);
+            cwy = 0.5f * (mny + mxy);
+            cwz = 0.5f * (mnz + mxz);
+            const float ex = mxx - mnx, ey = mxy - mny, ez = mxz - mnz;
+            rw = 0.5f * sqrtf(ex * ex + ey * ey + ez * ez) * 1.001f + 1e-6f;
+        }
         uint16_t *wq = queue + warp * QCAP;
 
         bool aborted = false;
-        for (int64_t t = t0; t < t1; ++t) {
-            const int buf = (int)((t - t0) & 1);
-            if (tid == 0 && t + 1 < t1) issue(t + 1, buf ^ 1);
-            if (!mbar_wait(&bars[buf], phase[buf])) {
+#pragma unroll 1
+        for (int i = 0; i < n_local; ++i) {
+            const int st = i % S;
+            const int64_t t = t0 + i;
+            // can any point of this warp be near a tet of this tile?
+            bool culled = false;
+            if (!a.all_ray) {
+                const float4 hd = a.tile_hdr[t];
+                const float dx = cwx - hd.x, dy = cwy - hd.y, dz = cwz - hd.z;
+                const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+                const float scale = fabsf(hd.x) + fabsf(hd.y) + fabsf(hd.z) + dist;
+                culled = dist - rw - hd.w > fr * a.tile_rho[t] * 1.001f + 1e-5f * scale;
+            }
+            if (!mbar_wait(&pipe->full[st], (phase >> st) & 1u)) {
                 aborted = true;
                 break;
             }
-            phase[buf] ^= 1u;
-            const T *tb = tiles + buf * TILE * RS;
+            phase ^= 1u << st;
+            const T *tb = tiles + st * TILE * RS;
             const int cnt = (int)min((int64_t)TILE, a.n_tets - t * TILE);
-
-            T tacc[P][3];
-#pragma unroll
-            for (int p = 0; p < P; ++p) tacc[p][0] = tacc[p][1] = tacc[p][2] = 0;
             int qn = 0;  // warp-uniform
-
-            auto drain = [&]() {
-                for (int e = 0; e < qn; ++e) {
-                    const int code = wq[e];
-                    const int slot = code >> 8, j = code & 255;
-                    const int pp = slot >> 5, owner = slot & 31;
-                    const int bi = pp * NT + warp * 32 + owner;
-                    const int64_t tet = t * TILE + j;
-                    const V3<double> xd = mk(spts[3 * bi], spts[3 * bi + 1], spts[3 * bi + 2]);
-                    NearOut o;
-                    if constexpr (sizeof(T) == 4)
-                        o = near_pair_f32(xd, a.near32 + tet * kNearF32Vec4, a.near64 + tet * kNearF64,
-                                          a.lines.f32, a.lines.f64, a.L, lane);
-                    else
-                        o = near_pair_f64(xd, a.near64 + tet * kNearF64, a.lines.f64, a.L, lane);
-                    if (lane == owner) {
-#pragma unroll
-                        for (int p = 0; p < P; ++p)
-                            if (p == pp) {
-                                tacc[p][0] += (T)o.vx;
-                                tacc[p][1] += (T)o.vy;
-                                tacc[p][2] += (T)o.vz;
-                                nhit[p] += o.hits;
-                            }
+            // this warp is done with stage st (the near pairs read global memory only);
+            // the last warp to finish refills it
+            auto release = [&]() {
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence_block();
+                    const int prev = atomicAdd(&pipe->done[st], 1);
+                    if (prev == NW - 1) {
+                        pipe->done[st] = 0;
+                        __threadfence_block();
+                        if (i + S < n_local) issue(t + S, st);
                     }
                 }
-                qn = 0;
-                __syncwarp();
             };
 
-            for (int j = 0; j < cnt; ++j) {
-                const T *rec = tb + j * RS;
-                const V3<T> c = mk(rec[0], rec[1], rec[2]);
-                const T thr2 = fr2 * rec[3];
-                bool nearp[P];
+            if constexpr (F32) {
+                // tile frame: x' = x - o
+                const float4 hd = a.tile_hdr[t];
+                float xl[P][3], xx[P], A[P][3], B[P][3];
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    const V3<T> d = mk(xp[p].x - c.x, xp[p].y - c.y, xp[p].z - c.z);
-                    nearp[p] = !(dot3(d, d) > thr2);
+                    xl[p][0] = xp[p].x - hd.x;
+                    xl[p][1] = xp[p].y - hd.y;
+                    xl[p][2] = xp[p].z - hd.z;
+                    xx[p] = xl[p][0] * xl[p][0] + xl[p][1] * xl[p][1] + xl[p][2] * xl[p][2];
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) A[p][jj] = B[p][jj] = 0.f;
                 }
+                const float4 *tb4 = reinterpret_cast<const float4 *>(tb);
+#pragma unroll 1
+                for (int j = 0; j < cnt; ++j) {
+                    const float4 *rec = tb4 + j * (RS / 4);
+                    bool nearp[P];
+                    if (culled) {
 #pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    const T *qq = rec + 4 + 6 * q;
-                    const V3<T> xq = mk(qq[0], qq[1], qq[2]);
-                    const V3<T> wv = mk(qq[3], qq[4], qq[5]);
+                        for (int p = 0; p < P; ++p) nearp[p] = false;
+                    } else {
+                        const float4 h0 = rec[0];
+                        const float thr2 = fr2 * h0.w;
 #pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        if (nearp[p]) continue;
-                        const T dx = xp[p].x - xq.x, dy = xp[p].y - xq.y, dz = xp[p].z - xq.z;
-                        const T r2 = dx * dx + dy * dy + dz * dz;
-                        const T ir = inv_sqrt<T>(r2);
-                        const T ir3 = ir * ir * ir;
-                        tacc[p][0] += ir3 * (dy * wv.z - dz * wv.y);
-                        tacc[p][1] += ir3 * (dz * wv.x - dx * wv.z);
-                        tacc[p][2] += ir3 * (dx * wv.y - dy * wv.x);
-                    }
-                }
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    const unsigned m = __ballot_sync(0xffffffffu, nearp[p]);
-                    if (m) {
-                        if (nearp[p]) {
-                            const int pos = qn + __popc(m & ((1u << lane) - 1u));
-                            wq[pos] = (uint16_t)(((p * 32 + lane) << 8) | j);
-                            ++nnear[p];
+                        for (int p = 0; p < P; ++p) {
+                            const float dx = xl[p][0] - h0.x, dy = xl[p][1] - h0.y, dz = xl[p][2] - h0.z;
+                            nearp[p] = !(dx * dx + dy * dy + dz * dz > thr2);
                         }
-                        qn += __popc(m);
+                    }
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const float4 u0 = rec[1 + 3 * q], u1 = rec[2 + 3 * q], u2 = rec[3 + 3 * q];
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            const float r2 = fmaf(xl[p][0], u0.x, fmaf(xl[p][1], u0.y, fmaf(xl[p][2], u0.z, xx[p] + u0.w)));
+                            const float ir = rsqrtf(r2);
+                            float ir3 = ir * ir * ir;
+                            if (!culled) ir3 = nearp[p] ? 0.f : ir3;
+                            A[p][0] = fmaf(ir3, u1.x, A[p][0]);
+                            A[p][1] = fmaf(ir3, u1.y, A[p][1]);
+                            A[p][2] = fmaf(ir3, u1.z, A[p][2]);
+                            B[p][0] = fmaf(ir3, u1.w, B[p][0]);
+                            B[p][1] = fmaf(ir3, u2.x, B[p][1]);
+                            B[p][2] = fmaf(ir3, u2.y, B[p][2]);
+                        }
+                    }
+                    if (!culled) {
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            const unsigned m = __ballot_sync(0xffffffffu, nearp[p]);
+                            if (m) {
+                                if (nearp[p]) {
+                                    const int pos = qn + __popc(m & ((1u << lane) - 1u));
+                                    wq[pos] = (uint16_t)(((p * 32 + lane) << 8) | j);
+                                    ++nnear[p];
+                                }
+                                qn += __popc(m);
+                            }
+                        }
                     }
                 }
-                if (qn > QCAP - 32 * P) {
-                    __syncwarp();
-                    drain();
+                release();
+                // tile partial: x' x A - B, folded into the compensated sum below
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const float v0 = xl[p][1] * A[p][2] - xl[p][2] * A[p][1] - B[p][0];
+                    const float v1 = xl[p][2] * A[p][0] - xl[p][0] * A[p][2] - B[p][1];
+                    const float v2 = xl[p][0] * A[p][1] - xl[p][1] * A[p][0] - B[p][2];
+                    A[p][0] = v0;
+                    A[p][1] = v1;
+                    A[p][2] = v2;
                 }
-            }
-            if (qn > 0) {
-                __syncwarp();
-                drain();
-            }
-            // fold the tile partial into the per-point sum
+                // A now holds the tile partial; add the near pairs of the tile to it
+                if (qn > 0) {
+                    __syncwarp();
+#pragma unroll 1
+                    for (int e = 0; e < qn; ++e) {
+                        const int code = wq[e];
+                        const int slot = code >> 8, j = code & 255;
+                        const int pp = slot >> 5, owner = slot & 31;
+                        const int bi = warp * 32 * P + slot;
+                        const int64_t tet = t * TILE + j;
+                        const V3<double> xd = mk(spts[3 * bi], spts[3 * bi + 1], spts[3 * bi + 2]);
+                        const NearOut o = near_pair_f32(xd, a.near32 + tet * kNearF32Vec4, a.near64 + tet * kNearF64,
+                                                        a.lines.f32, a.lines.f64, a.L, lane);
+                        if (lane == owner) {
 #pragma unroll
-            for (int p = 0; p < P; ++p)
+                            for (int p = 0; p < P; ++p)
+                                if (p == pp) {
+                                    A[p][0] += (float)o.vx;
+                                    A[p][1] += (float)o.vy;
+                                    A[p][2] += (float)o.vz;
+                                    nhit[p] += o.hits;
+                                }
+                        }
+                    }
+                    __syncwarp();
+                }
 #pragma unroll
-                for (int jj = 0; jj < 3; ++jj) {
-                    if constexpr (sizeof(T) == 4) {
-                        const float y = tacc[p][jj] - acc[p].c[jj];
+                for (int p = 0; p < P; ++p)
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) {
+                        const float y = A[p][jj] - acc[p].c[jj];
                         const float s2 = acc[p].s[jj] + y;
                         acc[p].c[jj] = (s2 - acc[p].s[jj]) - y;
                         acc[p].s[jj] = s2;
-                    } else {
-                        acc[p].s[jj] += tacc[p][jj];
+                    }
+            } else {
+                // float64: direct form in global coordinates
+                double tacc[P][3];
+#pragma unroll
+                for (int p = 0; p < P; ++p) tacc[p][0] = tacc[p][1] = tacc[p][2] = 0.0;
+#pragma unroll 1
+                for (int j = 0; j < cnt; ++j) {
+                    const double *rec = tb + j * RS;
+                    bool nearp[P];
+                    const double thr2 = fr2 * rec[3];
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        const double dx = xp[p].x - rec[0], dy = xp[p].y - rec[1], dz = xp[p].z - rec[2];
+                        nearp[p] = !culled && !(dx * dx + dy * dy + dz * dz > thr2);
+                    }
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const double *qq = rec + 4 + 6 * q;
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            if (nearp[p]) continue;
+                            const double dx = xp[p].x - qq[0], dy = xp[p].y - qq[1], dz = xp[p].z - qq[2];
+                            const double r2 = dx * dx + dy * dy + dz * dz;
+                            const double ir = 1.0 / sqrt(r2);
+                            const double ir3 = ir * ir * ir;
+                            tacc[p][0] += ir3 * (dy * qq[5] - dz * qq[4]);
+                            tacc[p][1] += ir3 * (dz * qq[3] - dx * qq[5]);
+                            tacc[p][2] += ir3 * (dx * qq[4] - dy * qq[3]);
+                        }
+                    }
+                    if (!culled) {
+#pragma unroll
+                        for (int p = 0; p < P; ++p) {
+                            const unsigned m = __ballot_sync(0xffffffffu, nearp[p]);
+                            if (m) {
+                                if (nearp[p]) {
+                                    const int pos = qn + __popc(m & ((1u << lane) - 1u));
+                                    wq[pos] = (uint16_t)(((p * 32 + lane) << 8) | j);
+                                    ++nnear[p];
+                                }
+                                qn += __popc(m);
+                            }
+                        }
                     }
                 }
-            __syncthreads();  // every warp is done with this buffer before it is refilled
+                release();
+                if (qn > 0) {
+                    __syncwarp();
+#pragma unroll 1
+                    for (int e = 0; e < qn; ++e) {
+                        const int code = wq[e];
+                        const int slot = code >> 8, j = code & 255;
+                        const int pp = slot >> 5, owner = slot & 31;
+                        const int bi = warp * 32 * P + slot;
+                        const int64_t tet = t * TILE + j;
+                        const V3<double> xd = mk(spts[3 * bi], spts[3 * bi + 1], spts[3 * bi + 2]);
+                        const NearOut o = near_pair_f64(xd, a.near64 + tet * kNearF64, a.lines.f64, a.L, lane);
+                        if (lane == owner) {
+#pragma unroll
+                            for (int p = 0; p < P; ++p)
+                                if (p == pp) {
+                                    tacc[p][0] += o.vx;
+                                    tacc[p][1] += o.vy;
+                                    tacc[p][2] += o.vz;
+                                    nhit[p] += o.hits;
+                                }
+                        }
+                    }
+                    __syncwarp();
+                }
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) acc[p].s[jj] += tacc[p][jj];
+            }
         }
         if (aborted) {
             if (tid == 0) atomicOr(a.flag, kFlagTimeout);
-            // let the copies still in flight land before the CTA leaves
-            mbar_wait(&bars[0], phase[0]);
-            mbar_wait(&bars[1], phase[1]);
             return;
         }
 
         const int64_t ntets_chunk = min(a.n_tets, t1 * TILE) - t0 * TILE;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const int64_t gi = pb * BP + p * NT + tid;
+            const int64_t gi = pb * BP + warp * 32 * P + p * 32 + lane;  // position in the spatial order
             if (gi >= k) continue;
             double *dst = a.partial + (ck * k + gi) * 3;
 #pragma unroll
             for (int jj = 0; jj < 3; ++jj) {
-                if constexpr (sizeof(T) == 4)
+                if constexpr (F32)
                     dst[jj] = (double)acc[p].s[jj] - (double)acc[p].c[jj];
                 else
                     dst[jj] = acc[p].s[jj];
             }
             if (a.counts) {
-                atomicAdd(&a.counts[3 * gi + 0], nnear[p]);
-                atomicAdd(&a.counts[3 * gi + 1], (int)(ntets_chunk - nnear[p]));
-                atomicAdd(&a.counts[3 * gi + 2], nhit[p]);
+                const int64_t src = a.perm[gi];
+                atomicAdd(&a.counts[3 * src + 0], nnear[p]);
+                atomicAdd(&a.counts[3 * src + 1], (int)(ntets_chunk - nnear[p]));
+                atomicAdd(&a.counts[3 * src + 2], nhit[p]);
             }
         }
-        __syncthreads();  // spts reused by the next item
+        __syncthreads();  // stages and points are reused by the next item
     }
 }
 
-__global__ void reduce_kernel(const double *__restrict__ partial, int n_chunks, int64_t k, double *__restrict__ out)
+// out[perm[i]] = sum over chunks of partial[chunk][i] (fixed chunk order)
+__global__ void reduce_kernel(const double *__restrict__ partial, int n_chunks, int64_t k, const int *__restrict__ perm,
+                              double *__restrict__ out)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= 3 * k) return;
-    double s = 0.0;
-    for (int c = 0; c < n_chunks; ++c) s += partial[c * 3 * k + i];
-    out[i] = s;
+    if (i >= k) return;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int c = 0; c < n_chunks; ++c) {
+        const double *q = partial + (c * k + i) * 3;
+        s0 += q[0];
+        s1 += q[1];
+        s2 += q[2];
+    }
+    const int64_t o = perm[i];
+    out[3 * o + 0] = s0;
+    out[3 * o + 1] = s1;
+    out[3 * o + 2] = s2;
 }
 
 __global__ void zero_kernel(int32_t *counts, int64_t n, int *work_counter)
@@ -541,19 +842,19 @@ __global__ void zero_kernel(int32_t *counts, int64_t n, int *work_counter)
     if (counts && i < n) counts[i] = 0;
 }
 
-template <typename T, int Q, int P, int NT, int TILE>
+template <typename T, int Q, int P, int NT, int TILE, int S>
 size_t smem_bytes()
 {
     constexpr int RS = far_stride<T>(Q);
-    return 2 * (size_t)TILE * RS * sizeof(T) + 3 * sizeof(double) * NT * P + (NT / 32) * 256 * sizeof(uint16_t) +
-           2 * sizeof(uint64_t) + 16;
+    return (size_t)S * TILE * RS * sizeof(T) + 3 * sizeof(double) * NT * P +
+           (NT / 32) * (32 * P * TILE) * sizeof(uint16_t) + sizeof(Pipe<S>) + 16;
 }
 
-template <typename T, int Q, int P, int NT, int TILE>
+template <typename T, int Q, int P, int NT, int TILE, int S, int MINB>
 cudaError_t launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out, bool query_only, int *occ_out)
 {
-    auto kern = velocity_kernel<T, Q, P, NT, TILE>;
-    const size_t sm = smem_bytes<T, Q, P, NT, TILE>();
+    auto kern = velocity_kernel<T, Q, P, NT, TILE, S, MINB>;
+    const size_t sm = smem_bytes<T, Q, P, NT, TILE, S>();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -570,15 +871,22 @@ cudaError_t launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
     return cudaGetLastError();
 }
 
+// Kernel variants: points per thread, tile (tets per pipeline stage), stages, min CTAs per SM.
+#define BS_VARIANTS(X)          \
+    X(1, 2, 32, 4, 4)           \
+    X(4, 2, 32, 4, 4)           \
+    X(8, 2, 16, 4, 4)           \
+    X(27, 1, 16, 4, 4)          \
+    X(64, 1, 8, 4, 4)
+
 template <typename T>
 cudaError_t dispatch(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out, bool qo, int *occ)
 {
     switch (a.Q) {
-    case 1: return launch_t<T, 1, 2, 128, 64>(a, n_sm, st, grid_out, qo, occ);
-    case 4: return launch_t<T, 4, 2, 128, 64>(a, n_sm, st, grid_out, qo, occ);
-    case 8: return launch_t<T, 8, 2, 128, 32>(a, n_sm, st, grid_out, qo, occ);
-    case 27: return launch_t<T, 27, 1, 128, 16>(a, n_sm, st, grid_out, qo, occ);
-    case 64: return launch_t<T, 64, 1, 128, 8>(a, n_sm, st, grid_out, qo, occ);
+#define BS_CASE(Q_, P_, TILE_, S_, MB_) \
+    case Q_: return launch_t<T, Q_, P_, 128, TILE_, S_, MB_>(a, n_sm, st, grid_out, qo, occ);
+        BS_VARIANTS(BS_CASE)
+#undef BS_CASE
     default: return cudaErrorInvalidValue;
     }
 }
@@ -590,8 +898,16 @@ LaunchShape shape_for(int precision, int Q)
     (void)precision;
     LaunchShape s;
     s.threads = 128;
-    s.points_per_thread = Q <= 8 ? 2 : 1;
-    s.tile = Q <= 4 ? 64 : Q == 8 ? 32 : Q == 27 ? 16 : 8;
+    switch (Q) {
+#define BS_SHAPE(Q_, P_, TILE_, S_, MB_) \
+    case Q_:                             \
+        s.points_per_thread = P_;        \
+        s.tile = TILE_;                  \
+        break;
+        BS_VARIANTS(BS_SHAPE)
+#undef BS_SHAPE
+    default: break;
+    }
     return s;
 }
 
@@ -623,8 +939,7 @@ cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cuda
 
 cudaError_t launch_reduce(const VelocityArgs &a, cudaStream_t st)
 {
-    const int64_t n = 3 * a.k;
-    reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.partial, a.n_chunks, a.k, a.out);
+    reduce_kernel<<<(unsigned)((a.k + 255) / 256), 256, 0, st>>>(a.partial, a.n_chunks, a.k, a.perm, a.out);
     return cudaGetLastError();
 }
 

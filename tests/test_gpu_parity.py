@@ -229,3 +229,15 @@ def test_fourier_64_full_size_sampled(orc):
     # float64 path on the same sampled nodes
     v64 = h.bs_velocity(torch.from_numpy(m.nodes[idx].copy()).cuda(), precision=bs.BS_FP64, **DEFAULT).cpu().numpy()
     assert rel_l2(v64, vo) <= TOL_FP64_REL_L2
+
+
+def test_point_order_does_not_change_results(c1):
+    """Points are visited in a spatial order; each point's result must not depend on it (bitwise)."""
+    m, h = c1
+    rng = np.random.default_rng(99)
+    pts = np.concatenate([m.nodes, rng.uniform(0, 1, size=(300, 3))])
+    perm = rng.permutation(len(pts))
+    for prec in (bs.BS_FP32, bs.BS_FP64):
+        a, _ = gpu_velocity(h, pts, prec, **DEFAULT)
+        b, _ = gpu_velocity(h, pts[perm], prec, **DEFAULT)
+        assert np.array_equal(a[perm], b)
