@@ -201,7 +201,8 @@ def main():
     h = bs.Mesh(mesh.nodes, mesh.tets, mesh.omega)
     eval_nodes = mesh.nodes
     if args.points:
-        sel = np.sort(np.random.default_rng(4242).choice(mesh.n_nodes, size=args.points, replace=False))
+        # a compact patch (the nodes nearest the centre): warps see the same culling as on the full grid
+        sel = np.sort(np.argsort(np.linalg.norm(mesh.nodes, axis=1), kind="stable")[:args.points])
         eval_nodes = np.ascontiguousarray(mesh.nodes[sel])
     k = len(eval_nodes)
     pairs = k * mesh.n_tets
@@ -293,7 +294,7 @@ def main():
         if tr.get("kernel_source_hash") == kernel_source_hash():
             traffic = tr.get("dram_bytes_per_launch")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "velocity_kernel<float,4,2,128,64>",
+                "traffic": traffic, "kernel": "velocity_kernel (float, 4-point far rule)",
                 "kernel_ms": kernel_avg_ms,
                 "peak_basis": f"{n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {MAX_SM_MHZ:.0f} MHz",
                 "flops_per_launch": flops}
@@ -312,7 +313,7 @@ def main():
 
     config = workload_config()
     if args.points:
-        config["workload"] = f"fourier-64^3 mesh (1500282 tets), velocity at {k} seeded nodes (profiling case)"
+        config["workload"] = f"fourier-64^3 mesh (1500282 tets), velocity at the {k} nodes nearest the centre (profiling case)"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,

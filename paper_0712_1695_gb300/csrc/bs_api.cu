@@ -2,6 +2,7 @@
 // checks, device buffer ownership, table caching and kernel sequencing.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -71,7 +72,6 @@ struct bs_ctx {
     float *far32 = nullptr;
     double *far64 = nullptr;
     float4 *tile_hdr = nullptr;
-    float *tile_rho = nullptr;
     int far_tile = 0;
     // spatial order of the evaluation points
     int *perm = nullptr;
@@ -88,7 +88,8 @@ struct bs_ctx {
     // staging for bs_velocity_host
     double *stage = nullptr;
     size_t stage_cap = 0;
-    int occ[2][65] = {};  // cached CTAs per SM by [precision][Q]
+    int occ[2][65][8] = {};  // cached CTAs per SM by [precision][Q][variant]
+    int variant[2][65] = {};  // chosen kernel variant by [precision][Q] (bs_autotune, or BS_VARIANT)
     // kernel timing (bs_profile)
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
@@ -112,7 +113,7 @@ void free_ctx(bs_ctx *h)
     }
     void *bufs[] = {h->nodes, h->tets,  h->omega,     h->near32,   h->near64,  h->rho2,         h->flag,
                     h->first_bad, h->work_counter, h->rule.bary, h->rule.w, h->far32, h->far64, h->lines.f32,
-                    h->lines.f64, h->partial, h->stage, h->tile_hdr, h->tile_rho, h->perm, h->keys,
+                    h->lines.f64, h->partial, h->stage, h->tile_hdr, h->perm, h->keys,
                     h->cell_count, h->box};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -144,14 +145,13 @@ cudaError_t ensure_far(bs_ctx *h, int Q, cudaStream_t st)
     cudaError_t e;
     const int tile = shape_for(BS_FP32, Q).tile;
     if (h->rule.order != Q) {
-        void *old[] = {h->rule.bary, h->rule.w, h->far32, h->far64, h->tile_hdr, h->tile_rho};
+        void *old[] = {h->rule.bary, h->rule.w, h->far32, h->far64, h->tile_hdr};
         for (void *b : old)
             if (b) cudaFreeAsync(b, st);
         h->rule = TetRule();
         h->far32 = nullptr;
         h->far64 = nullptr;
         h->tile_hdr = nullptr;
-        h->tile_rho = nullptr;
         if ((e = cudaMallocAsync((void **)&h->rule.bary, sizeof(double) * 4 * Q, st)) != cudaSuccess) return e;
         if ((e = cudaMallocAsync((void **)&h->rule.w, sizeof(double) * Q, st)) != cudaSuccess) return e;
         if ((e = build_tet_rule(Q, h->rule.bary, h->rule.w, st)) != cudaSuccess) return e;
@@ -162,13 +162,12 @@ cudaError_t ensure_far(bs_ctx *h, int Q, cudaStream_t st)
             return e;
         if ((e = cudaMallocAsync((void **)&h->far64, n * far_stride<double>(Q) * sizeof(double), st)) != cudaSuccess)
             return e;
-        if ((e = cudaMallocAsync((void **)&h->tile_hdr, nt * sizeof(float4), st)) != cudaSuccess) return e;
-        if ((e = cudaMallocAsync((void **)&h->tile_rho, nt * sizeof(float), st)) != cudaSuccess) return e;
+        if ((e = cudaMallocAsync((void **)&h->tile_hdr, 2 * nt * sizeof(float4), st)) != cudaSuccess) return e;
         h->rule.order = Q;
         h->far_tile = tile;
     }
-    if ((e = build_far_records(h->near64, h->rho2, h->n_tets, h->rule, tile, h->tile_hdr, h->tile_rho, h->far32,
-                               h->far64, st)) != cudaSuccess)
+    if ((e = build_far_records(h->near64, h->rho2, h->n_tets, h->rule, tile, h->tile_hdr, h->far32, h->far64,
+                               st)) != cudaSuccess)
         return e;
     if (h->prof) h->prof_all += 2;
     h->far_version = h->version;
@@ -324,9 +323,12 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
     BS_CUDA(ensure_lines(h, p->n_phi, p->n_theta, st));
     BS_CUDA(ensure_far(h, Q, st));
 
-    const LaunchShape shape = shape_for(p->precision, Q);
-    int &occ = h->occ[p->precision][Q];
-    if (occ == 0) occ = std::max(1, velocity_ctas_per_sm(p->precision, Q));
+    int variant = h->variant[p->precision][Q];
+    if (const char *env = getenv("BS_VARIANT")) variant = atoi(env);
+    if (variant < 0 || variant >= num_variants(p->precision, Q)) variant = 0;
+    const LaunchShape shape = shape_for(p->precision, Q, variant);
+    int &occ = h->occ[p->precision][Q][variant];
+    if (occ == 0) occ = std::max(1, velocity_ctas_per_sm(p->precision, Q, variant));
     const int64_t BP = (int64_t)shape.threads * shape.points_per_thread;
     const int64_t n_blocks = (k + BP - 1) / BP;
     const int64_t n_tiles = (h->n_tets + shape.tile - 1) / shape.tile;
@@ -346,7 +348,6 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
     a.near32 = h->near32;
     a.near64 = h->near64;
     a.tile_hdr = h->tile_hdr;
-    a.tile_rho = h->tile_rho;
     a.pts = eval_pts_dev;
     a.perm = h->perm;
     a.k = k;
@@ -362,6 +363,7 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
     a.n_chunks = (int)n_chunks;
     a.tiles_per_chunk = (int)per;
     a.partial = h->partial;
+    a.variant = variant;
     int grid = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->prof) {

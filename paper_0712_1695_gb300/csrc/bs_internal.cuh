@@ -23,7 +23,7 @@ constexpr double kPi = 3.14159265358979323846;
 //   float : tile frame (coordinates relative to the tile origin o):
 //           [c - o (3), rho^2] then per q three float4
 //           [-2 x_q' (3), |x_q'|^2] [w'_q (3), B.x] [B.y, B.z, 0, 0], B = x_q' x w'_q  (4 + 12Q)
-// Tile header (per TILE consecutive tets): float4 [o (3), rc], float rho_max.
+// Tile header (per TILE consecutive tets): float4 [o (3), rc], float4 [rho_max, 0, 0, 0].
 //
 // Near record (one per tet, independent of the parameters): what the ray rule
 // needs.  Barycentric coordinates lambda_i(y) = g_i . (y - v0) + delta_i0
@@ -78,7 +78,7 @@ cudaError_t build_near_records(const double *nodes, int64_t n_nodes, const int32
                                int *flag, unsigned long long *first_bad, cudaStream_t st);
 // tile headers and far records for a tet rule and tile size (needs near64 and rho2)
 cudaError_t build_far_records(const double *near64, const double *rho2, int64_t n_tets, const TetRule &rule,
-                              int tile, float4 *hdr, float *hrho, float *far32, double *far64, cudaStream_t st);
+                              int tile, float4 *hdr, float *far32, double *far64, cudaStream_t st);
 // spatial order of the evaluation points (Morton counting sort on a 2^bits grid)
 int order_grid_bits(int64_t k);
 cudaError_t spatial_order(const double *pts, int64_t k, int bits, int *box, unsigned *keys, int *count, int *perm,
@@ -90,8 +90,7 @@ struct VelocityArgs {
     const void *far = nullptr;      // far records (float or double)
     const float4 *near32 = nullptr;
     const double *near64 = nullptr;
-    const float4 *tile_hdr = nullptr;  // [n_tiles] origin + centroid radius
-    const float *tile_rho = nullptr;   // [n_tiles] largest circumradius
+    const float4 *tile_hdr = nullptr;  // [n_tiles][2] origin + centroid radius, largest circumradius
     // points
     const double *pts = nullptr;  // [k][3]
     const int *perm = nullptr;    // [k] visiting order (spatially sorted)
@@ -111,6 +110,7 @@ struct VelocityArgs {
     // decomposition
     int n_chunks = 1;
     int tiles_per_chunk = 1;
+    int variant = 0;  // kernel variant (points per thread / registers) for this precision and rule
 };
 
 struct LaunchShape {
@@ -119,9 +119,11 @@ struct LaunchShape {
     int tile = 64;  // tets per shared-memory tile
 };
 
-// kernel variant (points per thread, tile) used for a precision and tet rule
-LaunchShape shape_for(int precision, int Q);
-int velocity_ctas_per_sm(int precision, int Q);
+// kernel variants (points per thread, register budget) for a precision and tet rule;
+// all variants of a rule share the tile size (the far records depend on it)
+int num_variants(int precision, int Q);
+LaunchShape shape_for(int precision, int Q, int variant = 0);
+int velocity_ctas_per_sm(int precision, int Q, int variant = 0);
 // ev_start/ev_stop (optional) are recorded around the velocity kernel alone
 cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
                             cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);

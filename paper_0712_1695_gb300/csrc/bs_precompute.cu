@@ -116,12 +116,12 @@ __global__ void near_records_kernel(const double *__restrict__ nodes, int64_t n_
     f[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Tile headers, one thread per tile of `tile` consecutive tets: origin o (mean
-// of the centroids, rounded to float), radius rc of the centroids about o
-// (rounded up), and the largest circumradius.  A point x is far from every
+// Tile headers, one thread per tile of `tile` consecutive tets, two float4:
+// [origin o (mean of the centroids, rounded to float), radius rc of the
+// centroids about o (rounded up)] [largest circumradius, 0, 0, 0].  A point x is far from every
 // tet of the tile when |x - o| - rc > far_ratio * rho_max.
 __global__ void tile_headers_kernel(const double *__restrict__ near64, const double *__restrict__ rho2,
-                                    int64_t n_tets, int tile, float4 *__restrict__ hdr, float *__restrict__ hrho)
+                                    int64_t n_tets, int tile, float4 *__restrict__ hdr)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t first = t * tile;
@@ -142,8 +142,8 @@ __global__ void tile_headers_kernel(const double *__restrict__ near64, const dou
         const D3 d = sub(load3(near64 + (first + j) * kNearF64 + nf64::C), of);
         rc = fmax(rc, sqrt(dot(d, d)));
     }
-    hdr[t] = make_float4(ox, oy, oz, (float)(rc * (1.0 + 1e-6) + 1e-30));
-    hrho[t] = (float)(sqrt(rmax) * (1.0 + 1e-6));
+    hdr[2 * t] = make_float4(ox, oy, oz, (float)(rc * (1.0 + 1e-6) + 1e-30));
+    hdr[2 * t + 1] = make_float4((float)(sqrt(rmax) * (1.0 + 1e-6)), 0.f, 0.f, 0.f);
 }
 
 // float32 far record (tile frame, x' = x - o of the tet's tile):
@@ -170,7 +170,7 @@ __global__ void far_records_kernel(const double *__restrict__ near64, const doub
     const int s32 = far_stride<float>(Q), s64 = far_stride<double>(Q);
     float *f = far32 + e * s32;
     double *d = far64 + e * s64;
-    const float4 h = hdr[e / tile];
+    const float4 h = hdr[2 * (e / tile)];
     const D3 o = {(double)h.x, (double)h.y, (double)h.z};
     const D3 c = load3(r + nf64::C);
     d[0] = c.x;
@@ -225,12 +225,12 @@ cudaError_t build_near_records(const double *nodes, int64_t n_nodes, const int32
 }
 
 cudaError_t build_far_records(const double *near64, const double *rho2, int64_t n_tets, const TetRule &rule,
-                              int tile, float4 *hdr, float *hrho, float *far32, double *far64, cudaStream_t st)
+                              int tile, float4 *hdr, float *far32, double *far64, cudaStream_t st)
 {
     if (n_tets == 0) return cudaSuccess;
     const int tb = 128;
     const int64_t n_tiles = (n_tets + tile - 1) / tile;
-    tile_headers_kernel<<<(unsigned)((n_tiles + tb - 1) / tb), tb, 0, st>>>(near64, rho2, n_tets, tile, hdr, hrho);
+    tile_headers_kernel<<<(unsigned)((n_tiles + tb - 1) / tb), tb, 0, st>>>(near64, rho2, n_tets, tile, hdr);
     far_records_kernel<<<(unsigned)((n_tets + tb - 1) / tb), tb, 0, st>>>(near64, rho2, n_tets, rule.order, tile,
                                                                          rule.bary, rule.w, hdr, far32, far64);
     return cudaGetLastError();

@@ -29,6 +29,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "bs_internal.cuh"
 
@@ -461,13 +462,15 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
     constexpr int NW = NT / 32;
     constexpr int QCAP = 32 * P * TILE;  // a whole tile's pairs fit: the queue is drained between tiles only
     constexpr int TILE_BYTES = TILE * RS * (int)sizeof(T);
+    constexpr int HDR_BYTES = 32;  // tile header (two float4) in front of each stage's records
+    constexpr int STAGE_BYTES = HDR_BYTES + TILE_BYTES;
     constexpr bool F32 = sizeof(T) == 4;
     static_assert(TILE <= 256, "tet index in the near queue is 8 bits");
     static_assert(P * 32 <= 256, "point slot in the near queue is 8 bits");
 
     extern __shared__ __align__(128) unsigned char smem[];
-    T *tiles = reinterpret_cast<T *>(smem);                            // [S][TILE*RS]
-    double *spts = reinterpret_cast<double *>(smem + S * TILE_BYTES);  // [BP][3]
+    unsigned char *stages = smem;                                       // [S][header + TILE*RS]
+    double *spts = reinterpret_cast<double *>(smem + S * STAGE_BYTES);  // [BP][3]
     uint16_t *queue = reinterpret_cast<uint16_t *>(spts + 3 * BP);     // [NW][QCAP]
     Pipe<S> *pipe = reinterpret_cast<Pipe<S> *>(queue + NW * QCAP);
     int *s_item = reinterpret_cast<int *>(pipe + 1);
@@ -495,9 +498,11 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
         const int64_t first = t * TILE;
         const int cnt = (int)min((int64_t)TILE, a.n_tets - first);
         const uint32_t bytes = (uint32_t)cnt * RS * sizeof(T);
+        unsigned char *dst = stages + st * STAGE_BYTES;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&pipe->full[st], bytes);
-        bulk_g2s(tiles + st * TILE * RS, far + first * RS, bytes, &pipe->full[st]);
+        mbar_expect_tx(&pipe->full[st], bytes + HDR_BYTES);
+        bulk_g2s(dst, a.tile_hdr + 2 * t, HDR_BYTES, &pipe->full[st]);
+        bulk_g2s(dst + HDR_BYTES, far + first * RS, bytes, &pipe->full[st]);
     };
 
     for (;;) {
@@ -571,21 +576,22 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
         for (int i = 0; i < n_local; ++i) {
             const int st = i % S;
             const int64_t t = t0 + i;
-            // can any point of this warp be near a tet of this tile?
-            bool culled = false;
-            if (!a.all_ray) {
-                const float4 hd = a.tile_hdr[t];
-                const float dx = cwx - hd.x, dy = cwy - hd.y, dz = cwz - hd.z;
-                const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-                const float scale = fabsf(hd.x) + fabsf(hd.y) + fabsf(hd.z) + dist;
-                culled = dist - rw - hd.w > fr * a.tile_rho[t] * 1.001f + 1e-5f * scale;
-            }
             if (!mbar_wait(&pipe->full[st], (phase >> st) & 1u)) {
                 aborted = true;
                 break;
             }
             phase ^= 1u << st;
-            const T *tb = tiles + st * TILE * RS;
+            const float4 *sh = reinterpret_cast<const float4 *>(stages + st * STAGE_BYTES);
+            const float4 hd = sh[0];
+            const T *tb = reinterpret_cast<const T *>(stages + st * STAGE_BYTES + HDR_BYTES);
+            // can any point of this warp be near a tet of this tile?
+            bool culled = false;
+            if (!a.all_ray) {
+                const float dx = cwx - hd.x, dy = cwy - hd.y, dz = cwz - hd.z;
+                const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+                const float scale = fabsf(hd.x) + fabsf(hd.y) + fabsf(hd.z) + dist;
+                culled = dist - rw - hd.w > fr * sh[1].x * 1.001f + 1e-5f * scale;
+            }
             const int cnt = (int)min((int64_t)TILE, a.n_tets - t * TILE);
             int qn = 0;  // warp-uniform
             // this warp is done with stage st (the near pairs read global memory only);
@@ -605,7 +611,6 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
 
             if constexpr (F32) {
                 // tile frame: x' = x - o
-                const float4 hd = a.tile_hdr[t];
                 float xl[P][3], xx[P], A[P][3], B[P][3];
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
@@ -617,54 +622,60 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                     for (int jj = 0; jj < 3; ++jj) A[p][jj] = B[p][jj] = 0.f;
                 }
                 const float4 *tb4 = reinterpret_cast<const float4 *>(tb);
+                // far sweep over the tile; MIXED: per-pair near/far test, near pairs masked and queued
+                auto sweep = [&](auto mixed_tag) {
+                    constexpr bool MIXED = decltype(mixed_tag)::value;
 #pragma unroll 1
-                for (int j = 0; j < cnt; ++j) {
-                    const float4 *rec = tb4 + j * (RS / 4);
-                    bool nearp[P];
-                    if (culled) {
+                    for (int j = 0; j < cnt; ++j) {
+                        const float4 *rec = tb4 + j * (RS / 4);
+                        bool nearp[P];
+                        if constexpr (MIXED) {
+                            const float4 h0 = rec[0];
+                            const float thr2 = fr2 * h0.w;
 #pragma unroll
-                        for (int p = 0; p < P; ++p) nearp[p] = false;
-                    } else {
-                        const float4 h0 = rec[0];
-                        const float thr2 = fr2 * h0.w;
-#pragma unroll
-                        for (int p = 0; p < P; ++p) {
-                            const float dx = xl[p][0] - h0.x, dy = xl[p][1] - h0.y, dz = xl[p][2] - h0.z;
-                            nearp[p] = !(dx * dx + dy * dy + dz * dz > thr2);
+                            for (int p = 0; p < P; ++p) {
+                                const float dx = xl[p][0] - h0.x, dy = xl[p][1] - h0.y, dz = xl[p][2] - h0.z;
+                                nearp[p] = !(dx * dx + dy * dy + dz * dz > thr2);
+                            }
                         }
-                    }
 #pragma unroll
-                    for (int q = 0; q < Q; ++q) {
-                        const float4 u0 = rec[1 + 3 * q], u1 = rec[2 + 3 * q], u2 = rec[3 + 3 * q];
+                        for (int q = 0; q < Q; ++q) {
+                            const float4 u0 = rec[1 + 3 * q], u1 = rec[2 + 3 * q], u2 = rec[3 + 3 * q];
 #pragma unroll
-                        for (int p = 0; p < P; ++p) {
-                            const float r2 = fmaf(xl[p][0], u0.x, fmaf(xl[p][1], u0.y, fmaf(xl[p][2], u0.z, xx[p] + u0.w)));
-                            const float ir = rsqrtf(r2);
-                            float ir3 = ir * ir * ir;
-                            if (!culled) ir3 = nearp[p] ? 0.f : ir3;
-                            A[p][0] = fmaf(ir3, u1.x, A[p][0]);
-                            A[p][1] = fmaf(ir3, u1.y, A[p][1]);
-                            A[p][2] = fmaf(ir3, u1.z, A[p][2]);
-                            B[p][0] = fmaf(ir3, u1.w, B[p][0]);
-                            B[p][1] = fmaf(ir3, u2.x, B[p][1]);
-                            B[p][2] = fmaf(ir3, u2.y, B[p][2]);
+                            for (int p = 0; p < P; ++p) {
+                                const float r2 =
+                                    fmaf(xl[p][0], u0.x, fmaf(xl[p][1], u0.y, fmaf(xl[p][2], u0.z, xx[p] + u0.w)));
+                                const float ir = rsqrtf(r2);
+                                float ir3 = ir * ir * ir;
+                                if constexpr (MIXED) ir3 = nearp[p] ? 0.f : ir3;
+                                A[p][0] = fmaf(ir3, u1.x, A[p][0]);
+                                A[p][1] = fmaf(ir3, u1.y, A[p][1]);
+                                A[p][2] = fmaf(ir3, u1.z, A[p][2]);
+                                B[p][0] = fmaf(ir3, u1.w, B[p][0]);
+                                B[p][1] = fmaf(ir3, u2.x, B[p][1]);
+                                B[p][2] = fmaf(ir3, u2.y, B[p][2]);
+                            }
                         }
-                    }
-                    if (!culled) {
+                        if constexpr (MIXED) {
 #pragma unroll
-                        for (int p = 0; p < P; ++p) {
-                            const unsigned m = __ballot_sync(0xffffffffu, nearp[p]);
-                            if (m) {
-                                if (nearp[p]) {
-                                    const int pos = qn + __popc(m & ((1u << lane) - 1u));
-                                    wq[pos] = (uint16_t)(((p * 32 + lane) << 8) | j);
-                                    ++nnear[p];
+                            for (int p = 0; p < P; ++p) {
+                                const unsigned m = __ballot_sync(0xffffffffu, nearp[p]);
+                                if (m) {
+                                    if (nearp[p]) {
+                                        const int pos = qn + __popc(m & ((1u << lane) - 1u));
+                                        wq[pos] = (uint16_t)(((p * 32 + lane) << 8) | j);
+                                        ++nnear[p];
+                                    }
+                                    qn += __popc(m);
                                 }
-                                qn += __popc(m);
                             }
                         }
                     }
-                }
+                };
+                if (culled)
+                    sweep(std::false_type{});
+                else
+                    sweep(std::true_type{});
                 release();
                 // tile partial: x' x A - B, folded into the compensated sum below
 #pragma unroll
@@ -846,7 +857,7 @@ template <typename T, int Q, int P, int NT, int TILE, int S>
 size_t smem_bytes()
 {
     constexpr int RS = far_stride<T>(Q);
-    return (size_t)S * TILE * RS * sizeof(T) + 3 * sizeof(double) * NT * P +
+    return (size_t)S * (32 + TILE * RS * sizeof(T)) + 3 * sizeof(double) * NT * P +
            (NT / 32) * (32 * P * TILE) * sizeof(uint16_t) + sizeof(Pipe<S>) + 16;
 }
 
@@ -871,50 +882,73 @@ cudaError_t launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
     return cudaGetLastError();
 }
 
-// Kernel variants: points per thread, tile (tets per pipeline stage), stages, min CTAs per SM.
-#define BS_VARIANTS(X)          \
-    X(1, 2, 32, 4, 4)           \
-    X(4, 2, 32, 4, 4)           \
-    X(8, 2, 16, 4, 4)           \
-    X(27, 1, 16, 4, 4)          \
-    X(64, 1, 8, 4, 4)
+// Kernel variants: points per thread P, tile (tets per pipeline stage), stages S, min CTAs
+// per SM (register budget).  Variant 0 of each rule is the default; the four-point rule in
+// float32 (the workhorse) has alternatives for the autotuner.  All variants of a rule share
+// the tile size, so they share the far records.
+struct VariantShape {
+    int P, TILE, S, MINB;
+};
+constexpr VariantShape kQ1[] = {{2, 32, 4, 4}};
+constexpr VariantShape kQ4[] = {{2, 32, 4, 4}, {2, 32, 4, 3}, {4, 32, 4, 2}, {4, 32, 4, 3}, {1, 32, 4, 5}};
+constexpr VariantShape kQ8[] = {{2, 16, 4, 4}};
+constexpr VariantShape kQ27[] = {{1, 16, 4, 4}};
+constexpr VariantShape kQ64[] = {{1, 8, 4, 4}};
 
 template <typename T>
 cudaError_t dispatch(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out, bool qo, int *occ)
 {
+#define BS_L(Q_, V_)                                                                                            \
+    launch_t<T, Q_, V_.P, 128, V_.TILE, V_.S, V_.MINB>(a, n_sm, st, grid_out, qo, occ)
     switch (a.Q) {
-#define BS_CASE(Q_, P_, TILE_, S_, MB_) \
-    case Q_: return launch_t<T, Q_, P_, 128, TILE_, S_, MB_>(a, n_sm, st, grid_out, qo, occ);
-        BS_VARIANTS(BS_CASE)
-#undef BS_CASE
+    case 1: return BS_L(1, kQ1[0]);
+    case 4:
+        if constexpr (sizeof(T) == 4) {
+            switch (a.variant) {
+            case 1: return BS_L(4, kQ4[1]);
+            case 2: return BS_L(4, kQ4[2]);
+            case 3: return BS_L(4, kQ4[3]);
+            case 4: return BS_L(4, kQ4[4]);
+            default: return BS_L(4, kQ4[0]);
+            }
+        } else {
+            return BS_L(4, kQ4[0]);
+        }
+    case 8: return BS_L(8, kQ8[0]);
+    case 27: return BS_L(27, kQ27[0]);
+    case 64: return BS_L(64, kQ64[0]);
     default: return cudaErrorInvalidValue;
     }
+#undef BS_L
 }
 
 }  // namespace
 
-LaunchShape shape_for(int precision, int Q)
+int num_variants(int precision, int Q) { return (precision == BS_FP32 && Q == 4) ? 5 : 1; }
+
+LaunchShape shape_for(int precision, int Q, int variant)
 {
-    (void)precision;
-    LaunchShape s;
-    s.threads = 128;
+    VariantShape v = kQ4[0];
     switch (Q) {
-#define BS_SHAPE(Q_, P_, TILE_, S_, MB_) \
-    case Q_:                             \
-        s.points_per_thread = P_;        \
-        s.tile = TILE_;                  \
-        break;
-        BS_VARIANTS(BS_SHAPE)
-#undef BS_SHAPE
+    case 1: v = kQ1[0]; break;
+    case 4: v = (precision == BS_FP32 && variant >= 0 && variant < 5) ? kQ4[variant] : kQ4[0]; break;
+    case 8: v = kQ8[0]; break;
+    case 27: v = kQ27[0]; break;
+    case 64: v = kQ64[0]; break;
     default: break;
     }
+    LaunchShape s;
+    s.threads = 128;
+    s.points_per_thread = v.P;
+    s.tile = v.TILE;
     return s;
 }
 
-int velocity_ctas_per_sm(int precision, int Q)
+int velocity_ctas_per_sm(int precision, int Q, int variant)
 {
     VelocityArgs q;
     q.Q = Q;
+    q.variant = variant;
     int occ = 0;
     if (precision == BS_FP32)
         dispatch<float>(q, 1, 0, nullptr, true, &occ);
