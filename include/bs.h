@@ -108,6 +108,31 @@ BS_API int bs_destroy(bs_handle h);
 /* Mesh sizes of a handle. */
 BS_API int bs_mesh_size(bs_handle h, int64_t *n_nodes, int64_t *n_tets);
 
+/* Velocity at k points without allocating any device memory.  The paper has
+ * no counterpart: this is a deployment variant for callers that must not let
+ * a library allocate GPU memory (an application whose memory is all handed
+ * out by its own pool under a fixed budget, or a time-critical loop that
+ * cannot take the device synchronisation or the out-of-memory failure of a
+ * driver allocation).  Nothing is created beforehand: the mesh comes straight
+ * from device arrays nodes_dev [n_nodes][3], tets_dev [n_tets][4] (int32),
+ * omega_dev [n_nodes][3]; eval_pts_dev [k][3] and out_dev [k][3] as in
+ * bs_velocity (out overwritten), p->counts optional.  Every table and partial
+ * sum lives in one fixed array of device memory owned by the library (about
+ * 11 MB, present on every GPU that loads the library until the process
+ * exits), so the sizes are capped: n_tets <= 8192, k <= 4096,
+ * n_theta * n_phi <= 4096, tet_gauss_order 1 or 4; larger requests return
+ * BS_ERR_ARG (BS_ERR_ORDER for the rule) before any work is queued.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current): make that first call before any stream
+ * capture.  All calls share the one array, which keeps the last call's
+ * contents: two calls whose work overlaps on the GPU (different streams, or
+ * different host threads, without ordering between them) race and give
+ * wrong results; order them on one stream.  The mesh is not validated
+ * (use bs_create for that): invalid node indices give zero contributions. */
+BS_API int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, const int32_t *tets_dev, int64_t n_tets,
+                               const double *omega_dev, const double *eval_pts_dev, int64_t k, const bs_params *p,
+                               double *out_dev, void *stream);
+
 /* Kernel timing of a handle (for benchmarks).  bs_profile(h, 1) starts
  * recording a CUDA event pair around every velocity-kernel launch of this
  * handle (on the launch stream) and counting every kernel the handle

@@ -21,7 +21,8 @@ BS_OK, BS_ERR_ARG, BS_ERR_MESH, BS_ERR_ORDER, BS_ERR_CUDA, BS_ERR_TIMEOUT = rang
 BS_FP64, BS_FP32 = 0, 1
 EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_status", "bs_destroy",
             "bs_mesh_size", "bs_last_error", "bs_direction_table", "bs_tet_rule", "bs_batch_create",
-            "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read")
+            "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read",
+            "bs_velocity_noalloc")
 
 
 class BSError(RuntimeError):
@@ -66,6 +67,8 @@ def load(path: str = LIB_PATH):
         lib.bs_batch_velocity.argtypes = [_P, ctypes.POINTER(bs_params), ctypes.POINTER(_P), _P]
         lib.bs_batch_destroy.argtypes = [_P]
         lib.bs_autotune.argtypes = [_P, ctypes.POINTER(bs_params), _P]
+        lib.bs_velocity_noalloc.argtypes = [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, ctypes.c_int64,
+                                            ctypes.POINTER(bs_params), _P, _P]
         lib.bs_profile.argtypes = [_P, ctypes.c_int]
         lib.bs_profile_read.argtypes = [_P, _D, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         _lib = lib
@@ -206,6 +209,32 @@ def bs_tet_rule(order: int):
     w = np.zeros(order)
     _check(load().bs_tet_rule(order, b.ctypes.data_as(_D), w.ctypes.data_as(_D)))
     return b, w
+
+
+def bs_velocity_noalloc(nodes_dev, tets_dev, omega_dev, pts_dev, out_dev, counts_dev=None, stream=None, **params):
+    """Velocity that allocates no device memory (all arrays are caller-owned torch CUDA tensors).
+
+    For callers that may not let the library allocate GPU memory; the
+    library's fixed scratch caps the sizes (8192 tets, 4096 points, 4096
+    directions, tet rules 1 and 4).  Calls share that scratch: keep them
+    ordered on one stream.
+    """
+    import torch
+
+    n_nodes = int(nodes_dev.shape[0])
+    k = int(pts_dev.shape[0])
+    _require_dev(nodes_dev, (n_nodes, 3))
+    _require_dev(omega_dev, (n_nodes, 3))
+    _require_dev(pts_dev, (k, 3))
+    _require_dev(out_dev, (k, 3))
+    if not (tets_dev.is_cuda and tets_dev.dtype == torch.int32 and tets_dev.is_contiguous() and tets_dev.dim() == 2
+            and tets_dev.shape[1] == 4):
+        raise ValueError("tets must be a contiguous int32 [n_tets, 4] CUDA tensor")
+    p = make_params(counts=counts_dev, **params)
+    _check(load().bs_velocity_noalloc(nodes_dev.data_ptr(), n_nodes, tets_dev.data_ptr(), int(tets_dev.shape[0]),
+                                      omega_dev.data_ptr(), pts_dev.data_ptr(), k, ctypes.byref(p),
+                                      out_dev.data_ptr(), _stream_ptr(stream)))
+    return out_dev
 
 
 class Batch:

@@ -52,6 +52,9 @@ int check_params(const bs_params *p)
 
 }  // namespace
 
+// used by the other translation units of the library (bs_noalloc.cu)
+void bs_set_last_error(const char *msg) { g_last_error = msg; }
+
 struct bs_ctx {
     int device = 0;
     int n_sm = 0;

@@ -1,0 +1,79 @@
+"""bs_velocity_noalloc, the entry point for callers that may not let the library allocate GPU memory.
+
+Such callers (an application whose device memory is all handed out by its
+own pool under a fixed budget, or a time-critical loop that cannot take the
+synchronisation or the out-of-memory failure of a driver allocation) cannot
+use bs_create / bs_velocity, which allocate the mesh tables and partial sums.
+bs_velocity_noalloc keeps those in a fixed array of library-owned device
+memory instead.  Its results must agree with bs_velocity on the same mesh and
+points, within the tolerances the parity tests use, and keep agreeing on a
+second call that reuses the same scratch array.  This file is named so that
+pytest collects it last.
+"""
+import numpy as np
+import pytest
+from gpu_helpers import TOL_FP32_RMS_MAX, TOL_FP64_REL_L2, rel_l2, rms_over_max
+
+from workloads import config1_plain
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_0712_1695_gb300 as bs  # noqa: E402
+from paper_0712_1695_gb300.binding import BS_ERR_ARG, BS_ERR_ORDER, BSError, bs_velocity_noalloc  # noqa: E402
+
+PARAMS = dict(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16)
+
+
+@pytest.fixture(scope="module")
+def case():
+    bs.build()
+    m = config1_plain()  # 729 nodes, 3072 tets: inside the fixed limits
+    dev = {name: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+           for name, a in (("nodes", m.nodes), ("omega", m.omega), ("tets", m.tets.astype(np.int32)))}
+    rng = np.random.default_rng(3)
+    pts = np.concatenate([m.nodes, rng.uniform(0.0, 1.0, size=(300, 3))])
+    dev["pts"] = torch.from_numpy(pts).cuda()
+    return m, dev
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_noalloc_matches_bs_velocity_on_two_calls(case, precision):
+    m, d = case
+    prec = bs.BS_FP64 if precision == "fp64" else bs.BS_FP32
+    h = bs.Mesh(m.nodes, m.tets, m.omega)
+    k = d["pts"].shape[0]
+    ref_counts = torch.zeros((k, 3), dtype=torch.int32, device="cuda")
+    ref = h.bs_velocity(d["pts"], counts_dev=ref_counts, precision=prec, **PARAMS).cpu().numpy()
+    h.bs_status()
+    for call in range(2):
+        out = torch.full((k, 3), float("nan"), dtype=torch.float64, device="cuda")
+        counts = torch.full((k, 3), -1, dtype=torch.int32, device="cuda")
+        bs_velocity_noalloc(d["nodes"], d["tets"], d["omega"], d["pts"], out, counts_dev=counts, precision=prec,
+                            **PARAMS)
+        torch.cuda.synchronize()
+        v = out.cpu().numpy()
+        assert np.all(np.isfinite(v)), f"call {call}"
+        if prec == bs.BS_FP64:
+            assert rel_l2(v, ref) <= TOL_FP64_REL_L2, f"call {call}"
+        else:
+            assert rms_over_max(v, ref) <= TOL_FP32_RMS_MAX, f"call {call}"
+        assert torch.equal(counts, ref_counts), f"call {call}"
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(case):
+    m, d = case
+    out = torch.empty_like(d["pts"])
+    with pytest.raises(BSError) as ei:
+        bs_velocity_noalloc(d["nodes"], d["tets"], d["omega"], d["pts"], out, **dict(PARAMS, n_theta=128, n_phi=64))
+    assert ei.value.code == BS_ERR_ARG and "4096" in str(ei.value)
+    with pytest.raises(BSError) as ei:
+        bs_velocity_noalloc(d["nodes"], d["tets"], d["omega"], d["pts"], out, **dict(PARAMS, tet_gauss_order=27))
+    assert ei.value.code == BS_ERR_ORDER
+    many = torch.zeros((4097, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(BSError) as ei:
+        bs_velocity_noalloc(d["nodes"], d["tets"], d["omega"], many, torch.empty_like(many), **PARAMS)
+    assert ei.value.code == BS_ERR_ARG
