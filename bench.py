@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import config3_fourier, config3_samples  # noqa: E402
+from workloads import config3_fourier, config3_samples, config4_batch  # noqa: E402
 
 PARAMS = dict(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16)
 METRIC = "node-tet interactions/s (velocity at all nodes, FP32 path)"
@@ -158,12 +158,78 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def batch_workload(args):
+    """256 independent Kuhn meshes (n ~ U{8..24}) with Gaussian blobs: one batched launch (CUDA graph)
+    against 256 separate bs_velocity calls, FP32, evaluation points = each mesh's nodes."""
+    import torch
+
+    import paper_0712_1695_gb300 as bs
+
+    bs.load()
+    meshes = config4_batch()
+    hs = [bs.Mesh(m.nodes, m.tets, m.omega) for m in meshes]
+    pairs = sum(m.n_nodes * m.n_tets for m in meshes)
+    stream = torch.cuda.Stream()
+    P = dict(PARAMS, precision=bs.BS_FP32)
+    pts = [torch.from_numpy(m.nodes).cuda() for m in meshes]
+    outs_sep = [torch.empty_like(t) for t in pts]
+    outs_bat = [torch.empty_like(t) for t in pts]
+    batch = bs.Batch(hs)
+
+    def separate():
+        for h, t, o in zip(hs, pts, outs_sep):
+            h.bs_velocity(t, out_dev=o, stream=stream, **P)
+
+    def batched():
+        batch.bs_batch_velocity(outs_bat, stream=stream, **P)
+
+    def timeit(fn, steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(steps):
+                fn()
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / steps
+
+    ms_sep = timeit(separate, args.steps)
+    with ClockSampler(0) as clk:
+        ms_bat = timeit(batched, args.steps)
+    # accuracy of the FP32 batch against the FP64 path (which is checked against the oracle in the tests)
+    outs64 = [torch.empty_like(t) for t in pts]
+    with torch.cuda.stream(stream):
+        batch.bs_batch_velocity(outs64, stream=stream, **dict(PARAMS, precision=bs.BS_FP64))
+        batched()
+    torch.cuda.synchronize()
+    errs = []
+    for a, b in zip(outs_bat, outs64):
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        errs.append(np.linalg.norm(a - b) / (np.sqrt(len(b)) * np.linalg.norm(b, axis=1).max()))
+    line = {"metric": "node-tet interactions/s (256-mesh batch, FP32 path)", "value": pairs / (ms_bat * 1e-3),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_bat,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"256 Kuhn meshes n~U{{8..24}}, Gaussian blobs, {pairs} node-tet pairs",
+                       **{k: v for k, v in PARAMS.items()}, "precision": "fp32"},
+            "separate_launches": {"ms_per_step": ms_sep, "value": pairs / (ms_sep * 1e-3)},
+            "batched_over_separate": ms_sep / ms_bat,
+            "fp32_vs_fp64_rms_over_max": {"max": float(max(errs)), "median": float(np.median(errs))},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fourier64", choices=["fourier64", "batch"],
+                    help="fourier64: the headline workload; batch: 256 uneven meshes, batched vs separate launches")
     ap.add_argument("--cpu-sample", type=int, default=640, help="oracle sample nodes for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=96, help="oracle sample nodes per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -179,6 +245,8 @@ def main():
 
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.workload == "batch":
+        return batch_workload(args)
 
     import torch
 

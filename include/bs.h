@@ -167,6 +167,8 @@ BS_API int bs_batch_destroy(bs_batch b);
  * parameters on `stream` and keep the fastest for later calls with the same
  * precision/order/direction count.  Synchronises the stream. */
 BS_API int bs_autotune(bs_handle h, const bs_params *p, void *stream);
+/* The kernel variant bs_autotune chose for this precision and rule (0 = default). */
+BS_API int bs_tuned_variant(bs_handle h, int precision, int tet_gauss_order, int *variant);
 
 #ifdef __cplusplus
 }

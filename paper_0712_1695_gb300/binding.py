@@ -22,7 +22,7 @@ BS_FP64, BS_FP32 = 0, 1
 EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_status", "bs_destroy",
             "bs_mesh_size", "bs_last_error", "bs_direction_table", "bs_tet_rule", "bs_batch_create",
             "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read",
-            "bs_velocity_noalloc")
+            "bs_velocity_noalloc", "bs_tuned_variant")
 
 
 class BSError(RuntimeError):
@@ -69,6 +69,7 @@ def load(path: str = LIB_PATH):
         lib.bs_autotune.argtypes = [_P, ctypes.POINTER(bs_params), _P]
         lib.bs_velocity_noalloc.argtypes = [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, ctypes.c_int64,
                                             ctypes.POINTER(bs_params), _P, _P]
+        lib.bs_tuned_variant.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         lib.bs_profile.argtypes = [_P, ctypes.c_int]
         lib.bs_profile_read.argtypes = [_P, _D, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         _lib = lib
@@ -183,6 +184,12 @@ class Mesh:
     def bs_autotune(self, stream=None, **params):
         p = make_params(**params)
         _check(load().bs_autotune(self.handle, ctypes.byref(p), _stream_ptr(stream)))
+        return self.bs_tuned_variant(params.get("precision", BS_FP64), params.get("tet_gauss_order", 4))
+
+    def bs_tuned_variant(self, precision, tet_gauss_order):
+        v = ctypes.c_int()
+        _check(load().bs_tuned_variant(self.handle, int(precision), int(tet_gauss_order), ctypes.byref(v)))
+        return v.value
 
 
 def _require_dev(t, shape):

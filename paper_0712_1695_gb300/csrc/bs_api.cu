@@ -1,9 +1,13 @@
 // bs_api.cu -- the C ABI of libbs (declared in include/bs.h): argument
 // checks, device buffer ownership, table caching and kernel sequencing.
 #include <math.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+
+#include <cmath>
+#include <cstring>
 
 #include <algorithm>
 #include <string>
@@ -123,6 +127,44 @@ void free_ctx(bs_ctx *h)
     delete h;
 }
 
+}  // namespace
+
+struct bs_batch_ctx {
+    std::vector<bs_ctx *> meshes;
+    int device = 0, n_sm = 0;
+    std::vector<int64_t> point_begin;
+    int64_t n_points = 0;
+    std::vector<uint64_t> order_version;  // mesh version when its point order was computed
+    int *perm = nullptr;                  // [n_points] per-mesh visiting orders, concatenated
+    unsigned *keys = nullptr;
+    int *cell_count = nullptr;
+    int cell_bits = 0;
+    int *box = nullptr;
+    MeshDesc *d_meshes = nullptr;
+    std::vector<MeshDesc> h_meshes;  // last descriptor table copied to the device
+    double *partial = nullptr;
+    size_t partial_cap = 0;
+    int *work_counter = nullptr;
+    int *flag = nullptr;
+    LineTables lines;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    int graph_prec = -1;
+    VelocityArgs graph_args;
+};
+
+namespace {
+
+void free_batch(bs_batch_ctx *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    void *bufs[] = {b->perm, b->keys, b->cell_count, b->box, b->d_meshes, b->partial, b->work_counter, b->flag,
+                    b->lines.f32, b->lines.f64};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    delete b;
+}
+
 cudaError_t ensure_lines(bs_ctx *h, int n_phi, int n_theta, cudaStream_t st)
 {
     if (h->lines.f32 && h->lines.n_phi == n_phi && h->lines.n_theta == n_theta) return cudaSuccess;
@@ -240,7 +282,7 @@ int bs_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t
     if (e == cudaSuccess) e = cudaMalloc(&h->rho2, sizeof(double) * nt);
     if (e == cudaSuccess) e = cudaMalloc(&h->flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&h->first_bad, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMalloc(&h->work_counter, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&h->work_counter, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(h->nodes, nodes, sizeof(double) * 3 * n_nodes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->omega, omega, sizeof(double) * 3 * n_nodes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && n_tets > 0)
@@ -346,27 +388,28 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
     BS_CUDA(spatial_order(eval_pts_dev, k, bits, h->box, h->keys, h->cell_count, h->perm, st));
 
     VelocityArgs a;
-    a.n_tets = h->n_tets;
-    a.far = p->precision == BS_FP32 ? (const void *)h->far32 : (const void *)h->far64;
-    a.near32 = h->near32;
-    a.near64 = h->near64;
-    a.tile_hdr = h->tile_hdr;
-    a.pts = eval_pts_dev;
-    a.perm = h->perm;
-    a.k = k;
+    a.m.n_tets = h->n_tets;
+    a.m.far = p->precision == BS_FP32 ? (const void *)h->far32 : (const void *)h->far64;
+    a.m.near32 = h->near32;
+    a.m.near64 = h->near64;
+    a.m.tile_hdr = h->tile_hdr;
+    a.m.pts = eval_pts_dev;
+    a.m.perm = h->perm;
+    a.m.k = k;
     a.Q = Q;
     a.far_ratio2 = isinf(p->far_ratio) ? INFINITY : p->far_ratio * p->far_ratio;
     a.all_ray = isinf(p->far_ratio) ? 1 : 0;
     a.lines = h->lines;
     a.L = p->n_phi * p->n_theta;
     a.counts = p->counts;
-    a.out = out_dev;
+    a.m.out = out_dev;
     a.flag = h->flag;
     a.work_counter = h->work_counter;
-    a.n_chunks = (int)n_chunks;
-    a.tiles_per_chunk = (int)per;
-    a.partial = h->partial;
+    a.m.n_chunks = (int)n_chunks;
+    a.m.tiles_per_chunk = (int)per;
+    a.m.partial = h->partial;
     a.variant = variant;
+    a.n_items = n_blocks * n_chunks;
     int grid = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->prof) {
@@ -491,16 +534,262 @@ int bs_profile_read(bs_handle h, double *kernel_ms, int64_t *kernel_launches, in
     return BS_OK;
 }
 
-int bs_batch_create(const bs_handle *, int, bs_batch *out)
+int bs_batch_create(const bs_handle *meshes, int n, bs_batch *out)
 {
-    if (out) *out = nullptr;
-    return fail(BS_ERR_ARG, "bs_batch_create: not available in this build");
+    if (!out) return fail(BS_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!meshes || n < 1) return fail(BS_ERR_ARG, "need at least one mesh");
+    for (int i = 0; i < n; ++i)
+        if (!meshes[i]) return fail(BS_ERR_ARG, "NULL mesh handle in the batch");
+    bs_batch_ctx *b = new bs_batch_ctx();
+    b->meshes.assign(meshes, meshes + n);
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        b->point_begin.push_back(total);
+        total += meshes[i]->n_nodes;
+    }
+    b->n_points = total;
+    b->order_version.assign(n, 0);
+    if (e == cudaSuccess) e = cudaMalloc(&b->perm, sizeof(int) * total);
+    if (e == cudaSuccess) e = cudaMalloc(&b->keys, sizeof(unsigned) * total);
+    if (e == cudaSuccess) e = cudaMalloc(&b->box, sizeof(int) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_meshes, sizeof(MeshDesc) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->work_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->flag, 0, sizeof(int));
+    int64_t kmax = 1;
+    for (int i = 0; i < n; ++i) kmax = std::max(kmax, meshes[i]->n_nodes);
+    b->cell_bits = order_grid_bits(kmax);
+    if (e == cudaSuccess) e = cudaMalloc(&b->cell_count, sizeof(int) << (3 * b->cell_bits));
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail(e, "bs_batch_create");
+    }
+    *out = b;
+    return BS_OK;
 }
-int bs_batch_velocity(bs_batch, const bs_params *, double *const *, void *)
+
+int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void *stream)
 {
-    return fail(BS_ERR_ARG, "bs_batch_velocity: not available in this build");
+    if (!b) return fail(BS_ERR_ARG, "batch is NULL");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->counts) return fail(BS_ERR_ARG, "bs_batch_velocity: counts are not supported (set p->counts = NULL)");
+    if (!outs) return fail(BS_ERR_ARG, "outs is NULL");
+    const int n = (int)b->meshes.size();
+    for (int i = 0; i < n; ++i)
+        if (!outs[i]) return fail(BS_ERR_ARG, "NULL output in outs");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int Q = p->tet_gauss_order;
+    const int prec = p->precision;
+    bool changed = false;
+
+    // per-mesh tables (rebuilt only when stale) and per-mesh point orders (nodes = evaluation points)
+    for (int i = 0; i < n; ++i) {
+        bs_ctx *h = b->meshes[i];
+        const uint64_t before = h->far_version;
+        const int before_q = h->rule.order;
+        BS_CUDA(ensure_far(h, Q, st));
+        changed = changed || before != h->far_version || before_q != h->rule.order;
+        if (b->order_version[i] != h->version) {
+            const int bits = order_grid_bits(h->n_nodes);
+            BS_CUDA(spatial_order(h->nodes, h->n_nodes, bits, b->box, b->keys, b->cell_count,
+                                  b->perm + b->point_begin[i], st));
+            b->order_version[i] = h->version;
+        }
+    }
+    if (!b->lines.f32 || b->lines.n_phi != p->n_phi || b->lines.n_theta != p->n_theta) {
+        if (b->lines.f32) cudaFreeAsync(b->lines.f32, st);
+        if (b->lines.f64) cudaFreeAsync(b->lines.f64, st);
+        b->lines = LineTables();
+        const size_t L = (size_t)p->n_phi * p->n_theta;
+        BS_CUDA(cudaMallocAsync((void **)&b->lines.f32, L * sizeof(float4), st));
+        BS_CUDA(cudaMallocAsync((void **)&b->lines.f64, L * sizeof(dbl4), st));
+        BS_CUDA(build_lines(p->n_phi, p->n_theta, b->lines.f32, b->lines.f64, st));
+        b->lines.n_phi = p->n_phi;
+        b->lines.n_theta = p->n_theta;
+        changed = true;
+    }
+
+    // decomposition: items of roughly equal work over all meshes
+    int variant = b->meshes[0]->variant[prec][Q];
+    if (const char *env = getenv("BS_VARIANT")) variant = atoi(env);
+    if (variant < 0 || variant >= num_variants(prec, Q)) variant = 0;
+    const LaunchShape shape = shape_for(prec, Q, variant);
+    int &occ = b->meshes[0]->occ[prec][Q][variant];
+    if (occ == 0) occ = std::max(1, velocity_ctas_per_sm(prec, Q, variant));
+    const int64_t BP = (int64_t)shape.threads * shape.points_per_thread;
+    double total_pairs = 0.0;
+    for (int i = 0; i < n; ++i) total_pairs += (double)b->meshes[i]->n_nodes * b->meshes[i]->n_tets;
+    const double per_item = std::max(1.0, total_pairs / (16.0 * b->n_sm * occ));
+    std::vector<MeshDesc> md(n);
+    int64_t items = 0, partial_elems = 0;
+    for (int i = 0; i < n; ++i) {
+        bs_ctx *h = b->meshes[i];
+        MeshDesc &m = md[i];
+        const int64_t k = h->n_nodes;
+        const int64_t n_tiles = std::max<int64_t>(1, (h->n_tets + shape.tile - 1) / shape.tile);
+        const double block_pairs = (double)std::min<int64_t>(BP, k) * shape.tile;
+        int64_t per = (int64_t)std::ceil(per_item / block_pairs);
+        per = std::min<int64_t>(std::max<int64_t>(per, 1), n_tiles);
+        // a mesh without tets owns no items and no partial sums: the reduction writes zeros
+        const int64_t n_chunks = h->n_tets > 0 ? (n_tiles + per - 1) / per : 0;
+        m.far = prec == BS_FP32 ? (const void *)h->far32 : (const void *)h->far64;
+        m.near32 = h->near32;
+        m.near64 = h->near64;
+        m.tile_hdr = h->tile_hdr;
+        m.pts = h->nodes;
+        m.perm = b->perm + b->point_begin[i];
+        m.out = outs[i];
+        m.k = k;
+        m.n_tets = h->n_tets;
+        m.n_chunks = (int)n_chunks;
+        m.tiles_per_chunk = (int)per;
+        m.item_begin = items;
+        m.point_begin = b->point_begin[i];
+        items += h->n_tets > 0 ? ((k + BP - 1) / BP) * n_chunks : 0;
+        m.partial = reinterpret_cast<double *>(partial_elems);  // offset, fixed below
+        partial_elems += 3 * k * n_chunks;
+    }
+    if ((size_t)partial_elems * sizeof(double) > b->partial_cap) {
+        if (b->partial) cudaFreeAsync(b->partial, st);
+        b->partial = nullptr;
+        b->partial_cap = 0;
+        BS_CUDA(cudaMallocAsync((void **)&b->partial, sizeof(double) * partial_elems, st));
+        b->partial_cap = sizeof(double) * partial_elems;
+        changed = true;
+    }
+    for (int i = 0; i < n; ++i) md[i].partial = b->partial + reinterpret_cast<intptr_t>(md[i].partial);
+
+    const bool same_desc = b->h_meshes.size() == md.size() &&
+                           memcmp(b->h_meshes.data(), md.data(), sizeof(MeshDesc) * md.size()) == 0;
+    if (!same_desc) {
+        BS_CUDA(cudaMemcpyAsync(b->d_meshes, md.data(), sizeof(MeshDesc) * n, cudaMemcpyHostToDevice, st));
+        BS_CUDA(cudaStreamSynchronize(st));  // md is a host temporary
+        b->h_meshes = md;
+        changed = true;
+    }
+
+    VelocityArgs a;
+    std::memset(static_cast<void *>(&a), 0, sizeof(a));  // padding too: the graph cache compares bytes
+    a.meshes = b->d_meshes;
+    a.n_meshes = n;
+    a.n_items = items;
+    a.n_points = b->n_points;
+    a.Q = Q;
+    a.far_ratio2 = isinf(p->far_ratio) ? INFINITY : p->far_ratio * p->far_ratio;
+    a.all_ray = isinf(p->far_ratio) ? 1 : 0;
+    a.lines = b->lines;
+    a.L = p->n_phi * p->n_theta;
+    a.flag = b->flag;
+    a.work_counter = b->work_counter;
+    a.variant = variant;
+    if (items == 0) {  // every mesh is empty: the reduction alone writes the zeros
+        BS_CUDA(launch_reduce(a, st));
+        return BS_OK;
+    }
+
+    // the launch sequence {zero counter, persistent velocity kernel, batched reduction} is captured
+    // once per (launch arguments, stream) into a CUDA graph and replayed
+    const bool graphable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+    const bool same_graph = b->graph && !changed && b->graph_stream == st && b->graph_prec == prec &&
+                            memcmp(&b->graph_args, &a, sizeof(a)) == 0;
+    if (graphable && !same_graph) {
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        // attributes and occupancy are set outside the capture
+        BS_CUDA(velocity_ctas_per_sm(prec, Q, variant) > 0 ? cudaSuccess : cudaErrorUnknown);
+        cudaGraph_t g = nullptr;
+        BS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int grid = 0;
+        cudaError_t e1 = launch_velocity(prec, a, b->n_sm, st, &grid);
+        cudaError_t e2 = e1 == cudaSuccess ? launch_reduce(a, st) : e1;
+        cudaError_t e3 = cudaStreamEndCapture(st, &g);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "bs_batch_velocity (capture)");
+        if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamEndCapture");
+        cudaError_t e4 = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e4 != cudaSuccess) return cuda_fail(e4, "cudaGraphInstantiate");
+        b->graph_stream = st;
+        b->graph_prec = prec;
+        b->graph_args = a;
+    }
+    if (graphable) {
+        BS_CUDA(cudaGraphLaunch(b->graph, st));
+    } else {
+        int grid = 0;
+        BS_CUDA(launch_velocity(prec, a, b->n_sm, st, &grid));
+        BS_CUDA(launch_reduce(a, st));
+    }
+    return BS_OK;
 }
-int bs_batch_destroy(bs_batch) { return BS_OK; }
-int bs_autotune(bs_handle, const bs_params *, void *) { return fail(BS_ERR_ARG, "bs_autotune: not available in this build"); }
+
+int bs_batch_destroy(bs_batch b)
+{
+    if (!b) return fail(BS_ERR_ARG, "batch is NULL");
+    cudaDeviceSynchronize();
+    free_batch(b);
+    return BS_OK;
+}
+
+int bs_autotune(bs_handle h, const bs_params *p, void *stream)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    int rc = check_params(p);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int prec = p->precision, Q = p->tet_gauss_order;
+    const int nv = num_variants(prec, Q);
+    if (nv <= 1 || h->n_tets == 0) {
+        h->variant[prec][Q] = 0;
+        return BS_OK;
+    }
+    // time every variant on the mesh's own nodes (the common use), keep the fastest
+    double *out = nullptr;
+    BS_CUDA(cudaMallocAsync((void **)&out, sizeof(double) * 3 * h->n_nodes, st));
+    bs_params q = *p;
+    q.counts = nullptr;
+    cudaEvent_t e0, e1;
+    BS_CUDA(cudaEventCreate(&e0));
+    BS_CUDA(cudaEventCreate(&e1));
+    float best = INFINITY;
+    int best_v = 0;
+    const int saved = h->variant[prec][Q];
+    for (int v = 0; v < nv; ++v) {
+        h->variant[prec][Q] = v;
+        rc = bs_velocity(h, h->nodes, h->n_nodes, &q, out, stream);  // warm-up (also builds tables)
+        if (rc) break;
+        BS_CUDA(cudaEventRecord(e0, st));
+        for (int r = 0; r < 3 && rc == 0; ++r) rc = bs_velocity(h, h->nodes, h->n_nodes, &q, out, stream);
+        BS_CUDA(cudaEventRecord(e1, st));
+        BS_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_v = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFreeAsync(out, st);
+    if (rc) {
+        h->variant[prec][Q] = saved;
+        return rc;
+    }
+    h->variant[prec][Q] = best_v;
+    BS_CUDA(cudaStreamSynchronize(st));
+    return BS_OK;
+}
+
+int bs_tuned_variant(bs_handle h, int precision, int tet_gauss_order, int *variant)
+{
+    if (!h || !variant || (precision != BS_FP32 && precision != BS_FP64) || !valid_order(tet_gauss_order))
+        return fail(BS_ERR_ARG, "bad argument");
+    *variant = h->variant[precision][tet_gauss_order];
+    return BS_OK;
+}
 
 }  // extern "C"

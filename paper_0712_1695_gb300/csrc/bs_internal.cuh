@@ -84,17 +84,29 @@ int order_grid_bits(int64_t k);
 cudaError_t spatial_order(const double *pts, int64_t k, int bits, int *box, unsigned *keys, int *count, int *perm,
                           cudaStream_t st);
 
-struct VelocityArgs {
-    // mesh
-    int64_t n_tets = 0;
-    const void *far = nullptr;      // far records (float or double)
+// One mesh of a launch: its tables, its evaluation points and where the
+// per-chunk partial sums go.  A batch launch reads an array of these.
+struct MeshDesc {
+    const void *far = nullptr;  // far records (float or double)
     const float4 *near32 = nullptr;
     const double *near64 = nullptr;
     const float4 *tile_hdr = nullptr;  // [n_tiles][2] origin + centroid radius, largest circumradius
-    // points
-    const double *pts = nullptr;  // [k][3]
-    const int *perm = nullptr;    // [k] visiting order (spatially sorted)
-    int64_t k = 0;
+    const double *pts = nullptr;       // [k][3]
+    const int *perm = nullptr;         // [k] visiting order (spatially sorted)
+    double *partial = nullptr;         // [n_chunks][k][3]
+    double *out = nullptr;             // [k][3]
+    int64_t k = 0, n_tets = 0;
+    int n_chunks = 1, tiles_per_chunk = 1;
+    int64_t item_begin = 0;   // batch: first work item of this mesh
+    int64_t point_begin = 0;  // batch: first point of this mesh in the batched reduction
+};
+
+struct VelocityArgs {
+    MeshDesc m;                        // single-mesh launch
+    const MeshDesc *meshes = nullptr;  // batch launch: device array [n_meshes] (m unused)
+    int n_meshes = 0;
+    int64_t n_items = 0;   // work items (point block x tet chunk) over all meshes
+    int64_t n_points = 0;  // batch: points over all meshes
     // rule
     int Q = 4;
     double far_ratio2 = 4.0;  // +inf for all-ray
@@ -102,14 +114,9 @@ struct VelocityArgs {
     LineTables lines;
     int L = 0;
     // outputs
-    double *partial = nullptr;  // [n_chunks][k][3]
-    int32_t *counts = nullptr;  // [k][3] or null (zeroed before)
-    double *out = nullptr;      // [k][3]
+    int32_t *counts = nullptr;  // [k][3] or null (single mesh only; zeroed before)
     int *flag = nullptr;
     int *work_counter = nullptr;  // device int, zeroed by launch_velocity
-    // decomposition
-    int n_chunks = 1;
-    int tiles_per_chunk = 1;
     int variant = 0;  // kernel variant (points per thread / registers) for this precision and rule
 };
 

@@ -192,27 +192,28 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
         return cuda_fail(e, "spatial order");
 
     VelocityArgs a;
-    a.n_tets = n_tets;
-    a.far = p->precision == BS_FP32 ? (const void *)far32 : (const void *)far64;
-    a.near32 = near32;
-    a.near64 = near64;
-    a.tile_hdr = hdr;
-    a.pts = eval_pts_dev;
-    a.perm = perm;
-    a.k = k;
+    a.m.n_tets = n_tets;
+    a.m.far = p->precision == BS_FP32 ? (const void *)far32 : (const void *)far64;
+    a.m.near32 = near32;
+    a.m.near64 = near64;
+    a.m.tile_hdr = hdr;
+    a.m.pts = eval_pts_dev;
+    a.m.perm = perm;
+    a.m.k = k;
     a.Q = Q;
     a.far_ratio2 = isinf(fr) ? INFINITY : fr * fr;
     a.all_ray = isinf(fr) ? 1 : 0;
     a.lines = lines;
     a.L = p->n_phi * p->n_theta;
     a.counts = p->counts;
-    a.out = out_dev;
+    a.m.out = out_dev;
     a.flag = flag;
     a.work_counter = reinterpret_cast<int *>(base + kCounter);
-    a.n_chunks = (int)n_chunks;
-    a.tiles_per_chunk = (int)per;
-    a.partial = reinterpret_cast<double *>(base + kPartial);
+    a.m.n_chunks = (int)n_chunks;
+    a.m.tiles_per_chunk = (int)per;
+    a.m.partial = reinterpret_cast<double *>(base + kPartial);
     a.variant = 0;
+    a.n_items = n_blocks * n_chunks;
     int grid = 0;
     if ((e = launch_velocity(p->precision, a, n_sm, st, &grid)) != cudaSuccess) return cuda_fail(e, "velocity");
     if ((e = launch_reduce(a, st)) != cudaSuccess) return cuda_fail(e, "reduce");

@@ -473,16 +473,13 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
     double *spts = reinterpret_cast<double *>(smem + S * STAGE_BYTES);  // [BP][3]
     uint16_t *queue = reinterpret_cast<uint16_t *>(spts + 3 * BP);     // [NW][QCAP]
     Pipe<S> *pipe = reinterpret_cast<Pipe<S> *>(queue + NW * QCAP);
-    int *s_item = reinterpret_cast<int *>(pipe + 1);
+    MeshDesc *s_md = reinterpret_cast<MeshDesc *>(pipe + 1);
+    int64_t *s_item = reinterpret_cast<int64_t *>(s_md + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t k = a.k;
-    const int64_t n_blocks = (k + BP - 1) / BP;
-    const int64_t n_items = n_blocks * a.n_chunks;
-    const int64_t n_tiles = (a.n_tets + TILE - 1) / TILE;
     const T fr2 = (T)a.far_ratio2;
     const float fr = a.all_ray ? INFINITY : (float)sqrt(a.far_ratio2);
-    const T *far = reinterpret_cast<const T *>(a.far);
+    const MeshDesc &md = *s_md;  // mesh of the current item (shared memory)
 
     if (tid == 0) {
         for (int st = 0; st < S; ++st) {
@@ -496,23 +493,46 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
 
     auto issue = [&](int64_t t, int st) {
         const int64_t first = t * TILE;
-        const int cnt = (int)min((int64_t)TILE, a.n_tets - first);
+        const int cnt = (int)min((int64_t)TILE, md.n_tets - first);
         const uint32_t bytes = (uint32_t)cnt * RS * sizeof(T);
         unsigned char *dst = stages + st * STAGE_BYTES;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&pipe->full[st], bytes + HDR_BYTES);
-        bulk_g2s(dst, a.tile_hdr + 2 * t, HDR_BYTES, &pipe->full[st]);
-        bulk_g2s(dst + HDR_BYTES, far + first * RS, bytes, &pipe->full[st]);
+        bulk_g2s(dst, md.tile_hdr + 2 * t, HDR_BYTES, &pipe->full[st]);
+        bulk_g2s(dst + HDR_BYTES, reinterpret_cast<const T *>(md.far) + first * RS, bytes, &pipe->full[st]);
     };
 
     for (;;) {
-        if (tid == 0) *s_item = atomicAdd(a.work_counter, 1);
+        if (tid == 0) {
+            int64_t item = atomicAdd(reinterpret_cast<unsigned long long *>(a.work_counter), 1ull);
+            if (item < a.n_items) {
+                if (a.meshes) {
+                    // the mesh whose item range holds this item (binary search on item_begin)
+                    int lo = 0, hi = a.n_meshes - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (a.meshes[mid].item_begin <= item) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    *s_md = a.meshes[lo];
+                    item -= s_md->item_begin;
+                } else {
+                    *s_md = a.m;
+                }
+            } else {
+                item = -1;
+            }
+            *s_item = item;
+        }
         __syncthreads();
         const int64_t item = *s_item;
-        if (item >= n_items) break;
+        if (item < 0) break;
+        const int64_t k = md.k;
+        const int64_t n_blocks = (k + BP - 1) / BP;
+        const int64_t n_tiles = (md.n_tets + TILE - 1) / TILE;
         const int64_t pb = item % n_blocks, ck = item / n_blocks;
-        const int64_t t0 = ck * a.tiles_per_chunk;
-        const int64_t t1 = min(t0 + (int64_t)a.tiles_per_chunk, n_tiles);
+        const int64_t t0 = ck * md.tiles_per_chunk;
+        const int64_t t1 = min(t0 + (int64_t)md.tiles_per_chunk, n_tiles);
         const int n_local = (int)(t1 - t0);
 
         // prologue: fill every stage while the points are loaded
@@ -522,10 +542,10 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
         for (int i = tid; i < BP; i += NT) {
             int64_t gi = pb * BP + i;
             if (gi >= k) gi = k - 1;  // pad with a real point; its result is not written
-            const int64_t src = a.perm[gi];
-            spts[3 * i + 0] = a.pts[3 * src + 0];
-            spts[3 * i + 1] = a.pts[3 * src + 1];
-            spts[3 * i + 2] = a.pts[3 * src + 2];
+            const int64_t src = md.perm[gi];
+            spts[3 * i + 0] = md.pts[3 * src + 0];
+            spts[3 * i + 1] = md.pts[3 * src + 1];
+            spts[3 * i + 2] = md.pts[3 * src + 2];
         }
         __syncthreads();
 
@@ -592,7 +612,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                 const float scale = fabsf(hd.x) + fabsf(hd.y) + fabsf(hd.z) + dist;
                 culled = dist - rw - hd.w > fr * sh[1].x * 1.001f + 1e-5f * scale;
             }
-            const int cnt = (int)min((int64_t)TILE, a.n_tets - t * TILE);
+            const int cnt = (int)min((int64_t)TILE, md.n_tets - t * TILE);
             int qn = 0;  // warp-uniform
             // this warp is done with stage st (the near pairs read global memory only);
             // the last warp to finish refills it
@@ -698,7 +718,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         const int bi = warp * 32 * P + slot;
                         const int64_t tet = t * TILE + j;
                         const V3<double> xd = mk(spts[3 * bi], spts[3 * bi + 1], spts[3 * bi + 2]);
-                        const NearOut o = near_pair_f32(xd, a.near32 + tet * kNearF32Vec4, a.near64 + tet * kNearF64,
+                        const NearOut o = near_pair_f32(xd, md.near32 + tet * kNearF32Vec4, md.near64 + tet * kNearF64,
                                                         a.lines.f32, a.lines.f64, a.L, lane);
                         if (lane == owner) {
 #pragma unroll
@@ -778,7 +798,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         const int bi = warp * 32 * P + slot;
                         const int64_t tet = t * TILE + j;
                         const V3<double> xd = mk(spts[3 * bi], spts[3 * bi + 1], spts[3 * bi + 2]);
-                        const NearOut o = near_pair_f64(xd, a.near64 + tet * kNearF64, a.lines.f64, a.L, lane);
+                        const NearOut o = near_pair_f64(xd, md.near64 + tet * kNearF64, a.lines.f64, a.L, lane);
                         if (lane == owner) {
 #pragma unroll
                             for (int p = 0; p < P; ++p)
@@ -803,12 +823,12 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
             return;
         }
 
-        const int64_t ntets_chunk = min(a.n_tets, t1 * TILE) - t0 * TILE;
+        const int64_t ntets_chunk = min(md.n_tets, t1 * TILE) - t0 * TILE;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const int64_t gi = pb * BP + warp * 32 * P + p * 32 + lane;  // position in the spatial order
             if (gi >= k) continue;
-            double *dst = a.partial + (ck * k + gi) * 3;
+            double *dst = md.partial + (ck * k + gi) * 3;
 #pragma unroll
             for (int jj = 0; jj < 3; ++jj) {
                 if constexpr (F32)
@@ -817,7 +837,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                     dst[jj] = acc[p].s[jj];
             }
             if (a.counts) {
-                const int64_t src = a.perm[gi];
+                const int64_t src = md.perm[gi];
                 atomicAdd(&a.counts[3 * src + 0], nnear[p]);
                 atomicAdd(&a.counts[3 * src + 1], (int)(ntets_chunk - nnear[p]));
                 atomicAdd(&a.counts[3 * src + 2], nhit[p]);
@@ -827,29 +847,43 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
     }
 }
 
-// out[perm[i]] = sum over chunks of partial[chunk][i] (fixed chunk order)
-__global__ void reduce_kernel(const double *__restrict__ partial, int n_chunks, int64_t k, const int *__restrict__ perm,
-                              double *__restrict__ out)
+// out[perm[i]] = sum over chunks of partial[chunk][i] (fixed chunk order);
+// batch: one thread per point of all meshes, the mesh found from point_begin.
+__global__ void reduce_kernel(const VelocityArgs a)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const MeshDesc *m = &a.m;
+    int64_t i = g;
+    if (a.meshes) {
+        if (g >= a.n_points) return;
+        int lo = 0, hi = a.n_meshes - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.meshes[mid].point_begin <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        m = &a.meshes[lo];
+        i = g - m->point_begin;
+    }
+    const int64_t k = m->k;
     if (i >= k) return;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int c = 0; c < n_chunks; ++c) {
-        const double *q = partial + (c * k + i) * 3;
+    for (int c = 0; c < m->n_chunks; ++c) {
+        const double *q = m->partial + (c * k + i) * 3;
         s0 += q[0];
         s1 += q[1];
         s2 += q[2];
     }
-    const int64_t o = perm[i];
-    out[3 * o + 0] = s0;
-    out[3 * o + 1] = s1;
-    out[3 * o + 2] = s2;
+    const int64_t o = m->perm[i];
+    m->out[3 * o + 0] = s0;
+    m->out[3 * o + 1] = s1;
+    m->out[3 * o + 2] = s2;
 }
 
 __global__ void zero_kernel(int32_t *counts, int64_t n, int *work_counter)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i == 0) *work_counter = 0;
+    if (i == 0) *reinterpret_cast<unsigned long long *>(work_counter) = 0ull;
     if (counts && i < n) counts[i] = 0;
 }
 
@@ -858,7 +892,7 @@ size_t smem_bytes()
 {
     constexpr int RS = far_stride<T>(Q);
     return (size_t)S * (32 + TILE * RS * sizeof(T)) + 3 * sizeof(double) * NT * P +
-           (NT / 32) * (32 * P * TILE) * sizeof(uint16_t) + sizeof(Pipe<S>) + 16;
+           (NT / 32) * (32 * P * TILE) * sizeof(uint16_t) + sizeof(Pipe<S>) + sizeof(MeshDesc) + 16;
 }
 
 template <typename T, int Q, int P, int NT, int TILE, int S, int MINB>
@@ -874,9 +908,7 @@ cudaError_t launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
     if (occ < 1) occ = 1;
     if (occ_out) *occ_out = occ;
     if (query_only) return cudaSuccess;
-    const int64_t BP = (int64_t)NT * P;
-    const int64_t n_items = ((a.k + BP - 1) / BP) * a.n_chunks;
-    const int64_t grid = std::min<int64_t>(n_items, (int64_t)n_sm * occ);
+    const int64_t grid = std::min<int64_t>(a.n_items, (int64_t)n_sm * occ);
     if (grid_out) *grid_out = (int)grid;
     kern<<<(unsigned)grid, NT, sm, st>>>(a);
     return cudaGetLastError();
@@ -960,7 +992,8 @@ int velocity_ctas_per_sm(int precision, int Q, int variant)
 cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
                             cudaEvent_t ev_start, cudaEvent_t ev_stop)
 {
-    zero_kernel<<<(unsigned)((3 * a.k + 255) / 256 + 1), 256, 0, st>>>(a.counts, 3 * a.k, a.work_counter);
+    const int64_t nc = a.counts ? 3 * a.m.k : 0;
+    zero_kernel<<<(unsigned)((nc + 255) / 256 + 1), 256, 0, st>>>(a.counts, nc, a.work_counter);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev_start && (e = cudaEventRecord(ev_start, st)) != cudaSuccess) return e;
@@ -973,7 +1006,8 @@ cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cuda
 
 cudaError_t launch_reduce(const VelocityArgs &a, cudaStream_t st)
 {
-    reduce_kernel<<<(unsigned)((a.k + 255) / 256), 256, 0, st>>>(a.partial, a.n_chunks, a.k, a.perm, a.out);
+    const int64_t n = a.meshes ? a.n_points : a.m.k;
+    reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
