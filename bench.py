@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import config3_fourier, config3_samples, config4_batch  # noqa: E402
+from workloads import config3_fourier, config3_samples, config4_batch, config5_rings  # noqa: E402
 
 PARAMS = dict(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16)
 METRIC = "node-tet interactions/s (velocity at all nodes, FP32 path)"
@@ -222,14 +222,56 @@ def batch_workload(args):
     return 0
 
 
+def rings_workload(args):
+    """Two colliding rings on the 80^3 grid: Heun steps (two velocity evaluations at all 512000 nodes
+    over 2958234 tets each), FP32; optional drift against an FP64 trajectory on a smaller grid."""
+    import torch
+
+    import paper_0712_1695_gb300 as bs
+
+    bs.load()
+    m = config5_rings(n=args.rings_n)
+    h = bs.Mesh(m.nodes, m.tets, m.omega)
+    P = dict(PARAMS, precision=bs.BS_FP32)
+    stream = torch.cuda.current_stream()
+    for _ in range(min(args.warmup, 1)):  # one warm-up step (a full step is seconds long)
+        h.bs_rk2_step(0.01, **P)
+    h.bs_status()
+    h = bs.Mesh(m.nodes, m.tets, m.omega)  # start the timed trajectory from t = 0
+    h.bs_velocity(torch.from_numpy(m.nodes).cuda(), **P)  # tables built outside the timed region
+    h.bs_status()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            h.bs_rk2_step(0.01, **P)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    h.bs_status()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    pairs_per_step = 2 * m.n_nodes * m.n_tets
+    x = h.bs_nodes().cpu().numpy()
+    line = {"metric": "node-tet interactions/s (RK2 steps of two colliding rings, FP32 path)",
+            "value": pairs_per_step / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"two rings {args.rings_n}^3: {m.n_nodes} nodes, {m.n_tets} tets, Heun dt=0.01",
+                       **PARAMS, "precision": "fp32"},
+            "max_displacement": float(np.abs(x - m.nodes).max()), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fourier64", choices=["fourier64", "batch"],
-                    help="fourier64: the headline workload; batch: 256 uneven meshes, batched vs separate launches")
+    ap.add_argument("--workload", default="fourier64", choices=["fourier64", "batch", "rings"],
+                    help="fourier64: the headline workload; batch: 256 uneven meshes, batched vs separate "
+                         "launches; rings: Heun steps of two colliding rings")
+    ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
     ap.add_argument("--cpu-sample", type=int, default=640, help="oracle sample nodes for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=96, help="oracle sample nodes per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -247,6 +289,8 @@ def main():
         return reference_arm(args, rank, world)
     if args.workload == "batch":
         return batch_workload(args)
+    if args.workload == "rings":
+        return rings_workload(args)
 
     import torch
 

@@ -98,6 +98,21 @@ BS_API int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const
 BS_API int bs_velocity_host(bs_handle h, const double *eval_pts_host, int64_t k, const bs_params *p, double *out_host,
                      void *stream);
 
+/* One Heun (RK2) step of the Lagrangian vortex method (Section 1: the nodes
+ * move with the flow and the velocity is re-evaluated on the moved mesh):
+ *   v0 = v(x0) at the nodes;  x* = x0 + dt v0;  v1 = v(x*) at the moved nodes;
+ *   x1 = x0 + dt (v0 + v1) / 2.
+ * Every velocity evaluation is bs_velocity at all nodes with parameters p
+ * (p->counts must be NULL); the connectivity and the nodal vorticity stay
+ * fixed (no vortex stretching: the paper gives no vorticity update).  The
+ * handle's node positions become x1.  Asynchronous on `stream`; a tet that
+ * the motion made degenerate is reported by the next bs_status.  The first
+ * call allocates three [n_nodes][3] work arrays owned by the handle. */
+BS_API int bs_rk2_step(bs_handle h, double dt, const bs_params *p, void *stream);
+
+/* Copy the handle's current node positions to device array nodes_dev [n_nodes][3]. */
+BS_API int bs_nodes(bs_handle h, double *nodes_dev, void *stream);
+
 /* Synchronise `stream` and return BS_ERR_MESH / BS_ERR_TIMEOUT if a kernel of
  * this handle raised its device error flag since the last call (clears it). */
 BS_API int bs_status(bs_handle h, void *stream);

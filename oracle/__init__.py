@@ -146,6 +146,20 @@ class OracleLib:
         return (vel, cnt) if counts else vel
 
 
+def heun_step(orc, nodes, tets, omega, dt, **params):
+    """One Heun (RK2) step of the node positions with the oracle's velocity (plain numpy arithmetic).
+
+    v0 = v(x0) at the nodes of the mesh as it is; x* = x0 + dt v0; v1 = v(x*)
+    at the nodes of the moved mesh (same tets, same nodal vorticity);
+    x1 = x0 + dt (v0 + v1) / 2.
+    """
+    x0 = np.ascontiguousarray(nodes, dtype=np.float64)
+    v0 = orc.velocity(x0, tets, omega, x0, **params)
+    xs = x0 + dt * v0
+    v1 = orc.velocity(xs, tets, omega, xs, **params)
+    return x0 + 0.5 * dt * (v0 + v1)
+
+
 def _load() -> OracleLib:
     global _lib
     with _lock:

@@ -22,7 +22,7 @@ BS_FP64, BS_FP32 = 0, 1
 EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_status", "bs_destroy",
             "bs_mesh_size", "bs_last_error", "bs_direction_table", "bs_tet_rule", "bs_batch_create",
             "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read",
-            "bs_velocity_noalloc", "bs_tuned_variant")
+            "bs_velocity_noalloc", "bs_tuned_variant", "bs_rk2_step", "bs_nodes")
 
 
 class BSError(RuntimeError):
@@ -69,6 +69,8 @@ def load(path: str = LIB_PATH):
         lib.bs_autotune.argtypes = [_P, ctypes.POINTER(bs_params), _P]
         lib.bs_velocity_noalloc.argtypes = [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, ctypes.c_int64,
                                             ctypes.POINTER(bs_params), _P, _P]
+        lib.bs_rk2_step.argtypes = [_P, ctypes.c_double, ctypes.POINTER(bs_params), _P]
+        lib.bs_nodes.argtypes = [_P, _P, _P]
         lib.bs_tuned_variant.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         lib.bs_profile.argtypes = [_P, ctypes.c_int]
         lib.bs_profile_read.argtypes = [_P, _D, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -169,6 +171,21 @@ class Mesh:
         _check(load().bs_velocity_host(self.handle, pts.ctypes.data_as(_D), len(pts), ctypes.byref(p),
                                        out.ctypes.data_as(_D), _stream_ptr(stream)))
         return out
+
+    def bs_rk2_step(self, dt: float, stream=None, **params):
+        """One Heun step: the mesh nodes move with the velocity (vorticity carried unchanged)."""
+        p = make_params(**params)
+        _check(load().bs_rk2_step(self.handle, float(dt), ctypes.byref(p), _stream_ptr(stream)))
+
+    def bs_nodes(self, out_dev=None, stream=None):
+        """Current node positions as a float64 [n_nodes, 3] CUDA tensor."""
+        import torch
+
+        if out_dev is None:
+            out_dev = torch.empty((self.n_nodes, 3), dtype=torch.float64, device="cuda")
+        _require_dev(out_dev, (self.n_nodes, 3))
+        _check(load().bs_nodes(self.handle, out_dev.data_ptr(), _stream_ptr(stream)))
+        return out_dev
 
     def bs_profile(self, enable: bool):
         _check(load().bs_profile(self.handle, int(bool(enable))))

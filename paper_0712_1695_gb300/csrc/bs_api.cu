@@ -95,6 +95,8 @@ struct bs_ctx {
     // staging for bs_velocity_host
     double *stage = nullptr;
     size_t stage_cap = 0;
+    // work arrays of bs_rk2_step: x0, v0, v1 (each [n_nodes][3])
+    double *rk = nullptr;
     int occ[2][65][8] = {};  // cached CTAs per SM by [precision][Q][variant]
     int variant[2][65] = {};  // chosen kernel variant by [precision][Q] (bs_autotune, or BS_VARIANT)
     // kernel timing (bs_profile)
@@ -120,7 +122,7 @@ void free_ctx(bs_ctx *h)
     }
     void *bufs[] = {h->nodes, h->tets,  h->omega,     h->near32,   h->near64,  h->rho2,         h->flag,
                     h->first_bad, h->work_counter, h->rule.bary, h->rule.w, h->far32, h->far64, h->lines.f32,
-                    h->lines.f64, h->partial, h->stage, h->tile_hdr, h->perm, h->keys,
+                    h->lines.f64, h->partial, h->stage, h->rk, h->tile_hdr, h->perm, h->keys,
                     h->cell_count, h->box};
     for (void *b : bufs)
         if (b) cudaFree(b);
@@ -326,6 +328,36 @@ int bs_update(bs_handle h, const double *nodes_dev, const double *omega_dev, voi
                                h->flag, h->first_bad, st));
     if (h->prof && h->n_tets > 0) h->prof_all += 1;
     ++h->version;
+    return BS_OK;
+}
+
+int bs_rk2_step(bs_handle h, double dt, const bs_params *p, void *stream)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->counts) return fail(BS_ERR_ARG, "bs_rk2_step: counts are not supported (set p->counts = NULL)");
+    if (!std::isfinite(dt)) return fail(BS_ERR_ARG, "bs_rk2_step: dt must be finite");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = h->n_nodes, nv = 3 * n;
+    if (!h->rk) BS_CUDA(cudaMallocAsync((void **)&h->rk, sizeof(double) * 3 * nv, st));
+    double *x0 = h->rk, *v0 = h->rk + nv, *v1 = h->rk + 2 * nv;
+    BS_CUDA(cudaMemcpyAsync(x0, h->nodes, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+    if ((rc = bs_velocity(h, x0, n, p, v0, stream))) return rc;
+    BS_CUDA(launch_euler(x0, v0, dt, nv, h->nodes, st));  // the mesh moves to x*
+    if ((rc = bs_update(h, nullptr, nullptr, stream))) return rc;
+    if ((rc = bs_velocity(h, h->nodes, n, p, v1, stream))) return rc;
+    BS_CUDA(launch_heun(x0, v0, v1, dt, nv, h->nodes, st));  // and on to x1
+    if ((rc = bs_update(h, nullptr, nullptr, stream))) return rc;
+    if (h->prof) h->prof_all += 2;
+    return BS_OK;
+}
+
+int bs_nodes(bs_handle h, double *nodes_dev, void *stream)
+{
+    if (!h || !nodes_dev) return fail(BS_ERR_ARG, "NULL argument");
+    BS_CUDA(cudaMemcpyAsync(nodes_dev, h->nodes, sizeof(double) * 3 * h->n_nodes, cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
     return BS_OK;
 }
 

@@ -135,5 +135,9 @@ int velocity_ctas_per_sm(int precision, int Q, int variant = 0);
 cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
                             cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);
 cudaError_t launch_reduce(const VelocityArgs &a, cudaStream_t st);
+// Heun step position updates (n_values = 3 * nodes)
+cudaError_t launch_euler(const double *x0, const double *v0, double dt, int64_t n_values, double *x, cudaStream_t st);
+cudaError_t launch_heun(const double *x0, const double *v0, const double *v1, double dt, int64_t n_values, double *x,
+                        cudaStream_t st);
 
 }  // namespace bs
