@@ -166,7 +166,7 @@ def batch_workload(args):
     import paper_0712_1695_gb300 as bs
 
     bs.load()
-    meshes = config4_batch()
+    meshes = config4_batch(count=args.batch_count)
     hs = [bs.Mesh(m.nodes, m.tets, m.omega) for m in meshes]
     pairs = sum(m.n_nodes * m.n_tets for m in meshes)
     stream = torch.cuda.Stream()
@@ -196,7 +196,7 @@ def batch_workload(args):
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1) / steps
 
-    ms_sep = timeit(separate, args.steps)
+    ms_sep = timeit(separate, args.steps) if not args.batch_only else float("nan")
     with ClockSampler(0) as clk:
         ms_bat = timeit(batched, args.steps)
     # accuracy of the FP32 batch against the FP64 path (which is checked against the oracle in the tests)
@@ -209,10 +209,10 @@ def batch_workload(args):
     for a, b in zip(outs_bat, outs64):
         a, b = a.cpu().numpy(), b.cpu().numpy()
         errs.append(np.linalg.norm(a - b) / (np.sqrt(len(b)) * np.linalg.norm(b, axis=1).max()))
-    line = {"metric": "node-tet interactions/s (256-mesh batch, FP32 path)", "value": pairs / (ms_bat * 1e-3),
+    line = {"metric": f"node-tet interactions/s ({len(meshes)}-mesh batch, FP32 path)", "value": pairs / (ms_bat * 1e-3),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_bat,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"256 Kuhn meshes n~U{{8..24}}, Gaussian blobs, {pairs} node-tet pairs",
+            "config": {"workload": f"{len(meshes)} Kuhn meshes n~U{{8..24}}, Gaussian blobs, {pairs} node-tet pairs",
                        **{k: v for k, v in PARAMS.items()}, "precision": "fp32"},
             "separate_launches": {"ms_per_step": ms_sep, "value": pairs / (ms_sep * 1e-3)},
             "batched_over_separate": ms_sep / ms_bat,
@@ -272,6 +272,8 @@ def main():
                     help="fourier64: the headline workload; batch: 256 uneven meshes, batched vs separate "
                          "launches; rings: Heun steps of two colliding rings")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
+    ap.add_argument("--batch-count", type=int, default=256, help="meshes in the batch workload")
+    ap.add_argument("--batch-only", action="store_true", help="batch workload: skip the separate-launch timing")
     ap.add_argument("--cpu-sample", type=int, default=640, help="oracle sample nodes for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=96, help="oracle sample nodes per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -411,7 +411,9 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
     const int64_t n_tiles = (h->n_tets + shape.tile - 1) / shape.tile;
     const int64_t target = 16LL * h->n_sm * occ;
     int64_t n_chunks = std::min<int64_t>(std::max<int64_t>((target + n_blocks - 1) / n_blocks, 1), n_tiles);
-    const int64_t per = (n_tiles + n_chunks - 1) / n_chunks;
+    // at least kMinTilesPerItem tiles per item: shorter items are dominated by their set-up
+    const int64_t per = std::min<int64_t>(std::max<int64_t>((n_tiles + n_chunks - 1) / n_chunks, kMinTilesPerItem),
+                                          n_tiles);
     n_chunks = (n_tiles + per - 1) / per;
 
     const int bits = order_grid_bits(k);
@@ -433,6 +435,7 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
     a.all_ray = isinf(p->far_ratio) ? 1 : 0;
     a.lines = h->lines;
     a.L = p->n_phi * p->n_theta;
+    a.smem_lines = a.L <= kSmemLinesMax ? 1 : 0;
     a.counts = p->counts;
     a.m.out = out_dev;
     a.flag = h->flag;
@@ -665,7 +668,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         const int64_t n_tiles = std::max<int64_t>(1, (h->n_tets + shape.tile - 1) / shape.tile);
         const double block_pairs = (double)std::min<int64_t>(BP, k) * shape.tile;
         int64_t per = (int64_t)std::ceil(per_item / block_pairs);
-        per = std::min<int64_t>(std::max<int64_t>(per, 1), n_tiles);
+        per = std::min<int64_t>(std::max<int64_t>(per, kMinTilesPerItem), n_tiles);
         // a mesh without tets owns no items and no partial sums: the reduction writes zeros
         const int64_t n_chunks = h->n_tets > 0 ? (n_tiles + per - 1) / per : 0;
         m.far = prec == BS_FP32 ? (const void *)h->far32 : (const void *)h->far64;
@@ -715,6 +718,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     a.all_ray = isinf(p->far_ratio) ? 1 : 0;
     a.lines = b->lines;
     a.L = p->n_phi * p->n_theta;
+    a.smem_lines = a.L <= kSmemLinesMax ? 1 : 0;
     a.flag = b->flag;
     a.work_counter = b->work_counter;
     a.variant = variant;

@@ -28,7 +28,10 @@ constexpr double kPi = 3.14159265358979323846;
 // Near record (one per tet, independent of the parameters): what the ray rule
 // needs.  Barycentric coordinates lambda_i(y) = g_i . (y - v0) + delta_i0
 // with g_0 = -(g_1 + g_2 + g_3) (the face planes of the tet).
-//   float  : 8 x float4  [v0 h] [g1 Rb^2] [g2 c.x] [g3 c.y] [w0 c.z] [w1 -] [w2 -] [w3 -]
+//   float  : 15 x float4  [g1 h] [g2 Rb^2] [g3 -] [w0 -] [w1 -] [w2 -] [w3 -]
+//            [c hi (3) -] [c mid (3) -] [vertex hi: 12 floats] [vertex mid: 12 floats]
+//            (coordinates as float splits x = hi + mid + lo, see split3: the float path
+//            takes differences and vertex tests without float64 arithmetic)
 //   double : 40 doubles  v0..v3 (12) g1 g2 g3 (9) w0..w3 (12) c (3) h Rb^2 (2) pad (2)
 //   h = longest edge, c = centroid, Rb = largest vertex distance from c.
 // ---------------------------------------------------------------------------
@@ -37,7 +40,24 @@ __host__ __device__ constexpr int far_stride(int Q)
 {
     return sizeof(T) == 4 ? (4 + 12 * Q) : (4 + 6 * Q);
 }
-constexpr int kNearF32Vec4 = 8;  // float4 per near record
+constexpr int kNearF32Vec4 = 15;  // float4 per near record
+namespace nf32 {
+constexpr int G1 = 0, G2 = 1, G3 = 2, W = 3, CH = 7, CM = 8, VH = 9, VM = 12;  // float4 index
+}
+
+// x = hi + mid + lo exactly (three floats hold the 53 bits of a normal double):
+// hi = fl(x), mid = fl(x - hi), lo = fl(x - hi - mid); each difference is exact.
+__host__ __device__ inline void split3(double x, float &hi, float &mid, float &lo)
+{
+    hi = (float)x;
+    const double r = x - (double)hi;
+    mid = (float)r;
+    lo = (float)(r - (double)mid);
+}
+__host__ __device__ inline double join3(float hi, float mid, float lo)
+{
+    return ((double)hi + (double)mid) + (double)lo;
+}
 constexpr int kNearF64 = 40;     // doubles per near record
 namespace nf64 {
 constexpr int V = 0, G = 12, W = 21, C = 33, H = 36, RB2 = 37;
@@ -113,12 +133,16 @@ struct VelocityArgs {
     int all_ray = 0;
     LineTables lines;
     int L = 0;
+    int smem_lines = 0;  // the float32 direction table is copied to shared memory (set for small L)
     // outputs
     int32_t *counts = nullptr;  // [k][3] or null (single mesh only; zeroed before)
     int *flag = nullptr;
     int *work_counter = nullptr;  // device int, zeroed by launch_velocity
     int variant = 0;  // kernel variant (points per thread / registers) for this precision and rule
 };
+
+constexpr int64_t kMinTilesPerItem = 2;  // work items shorter than this are dominated by their set-up
+constexpr int kSmemLinesMax = 256;       // direction tables up to this many lines live in shared memory
 
 struct LaunchShape {
     int points_per_thread = 2;  // P

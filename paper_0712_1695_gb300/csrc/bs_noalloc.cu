@@ -181,7 +181,9 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
     const int64_t target = 16LL * n_sm * occ;
     int64_t n_chunks = std::min<int64_t>(std::max<int64_t>((target + n_blocks - 1) / n_blocks, 1), n_tiles);
     n_chunks = std::min<int64_t>(n_chunks, kMaxChunks);
-    const int64_t per = (n_tiles + n_chunks - 1) / n_chunks;
+    // at least kMinTilesPerItem tiles per item: shorter items are dominated by their set-up
+    const int64_t per = std::min<int64_t>(std::max<int64_t>((n_tiles + n_chunks - 1) / n_chunks, kMinTilesPerItem),
+                                          n_tiles);
     n_chunks = (n_tiles + per - 1) / per;
 
     const int bits = std::min(order_grid_bits(k), kMaxCellBits);
@@ -205,6 +207,7 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
     a.all_ray = isinf(fr) ? 1 : 0;
     a.lines = lines;
     a.L = p->n_phi * p->n_theta;
+    a.smem_lines = a.L <= kSmemLinesMax ? 1 : 0;
     a.counts = p->counts;
     a.m.out = out_dev;
     a.flag = flag;

@@ -122,10 +122,11 @@ __global__ void init_box_kernel(int *box)
 
 }  // namespace
 
+// cells ~ k/8 (about eight points per cell: a warp's 32-64 points still span only a few cells)
 int order_grid_bits(int64_t k)
 {
     int bits = 1;
-    while (bits < 7 && (int64_t)1 << (3 * bits) < k) ++bits;
+    while (bits < 7 && ((int64_t)1 << (3 * bits)) < (k + 7) / 8) ++bits;
     return bits;
 }
 

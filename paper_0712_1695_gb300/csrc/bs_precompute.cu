@@ -107,13 +107,22 @@ __global__ void near_records_kernel(const double *__restrict__ nodes, int64_t n_
     r[nf64::RB2] = rb2;
     r[38] = 0.0;
     r[39] = 0.0;
-    // float32 record: [g1 h] [g2 Rb^2] [g3 0] [w0 0] [w1 0] [w2 0] [w3 0] [0]
+    // float32 record (layout in bs_internal.cuh)
     float4 *f = near32 + e * kNearF32Vec4;
-    f[0] = make_float4((float)g1.x, (float)g1.y, (float)g1.z, (float)h);
-    f[1] = make_float4((float)g2.x, (float)g2.y, (float)g2.z, (float)rb2);
-    f[2] = make_float4((float)g3.x, (float)g3.y, (float)g3.z, 0.f);
-    for (int i = 0; i < 4; ++i) f[3 + i] = make_float4((float)w[i].x, (float)w[i].y, (float)w[i].z, 0.f);
-    f[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+    f[nf32::G1] = make_float4((float)g1.x, (float)g1.y, (float)g1.z, (float)h);
+    f[nf32::G2] = make_float4((float)g2.x, (float)g2.y, (float)g2.z, (float)rb2);
+    f[nf32::G3] = make_float4((float)g3.x, (float)g3.y, (float)g3.z, 0.f);
+    for (int i = 0; i < 4; ++i) f[nf32::W + i] = make_float4((float)w[i].x, (float)w[i].y, (float)w[i].z, 0.f);
+    float hi[3], mid[3], lo;
+    const double cc[3] = {c.x, c.y, c.z};
+    for (int j = 0; j < 3; ++j) split3(cc[j], hi[j], mid[j], lo);
+    f[nf32::CH] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    f[nf32::CM] = make_float4(mid[0], mid[1], mid[2], 0.f);
+    float *vh = reinterpret_cast<float *>(f + nf32::VH), *vm = reinterpret_cast<float *>(f + nf32::VM);
+    for (int i = 0; i < 4; ++i) {
+        const double vv[3] = {v[i].x, v[i].y, v[i].z};
+        for (int j = 0; j < 3; ++j) split3(vv[j], vh[3 * i + j], vm[3 * i + j], lo);
+    }
 }
 
 // Tile headers, one thread per tile of `tile` consecutive tets, two float4:

@@ -127,6 +127,10 @@ struct NearOut {
     double vx, vy, vz;
     int hits;
 };
+struct NearOut32 {
+    float vx, vy, vz;
+    int hits;
+};
 
 // Everything about a pair that does not depend on the line, in float64.
 struct PairF64 {
@@ -292,8 +296,15 @@ __device__ __noinline__ bool line_f64_lean(V3<double> x, const double *__restric
     return true;
 }
 
-// float32 version.  The differences x - v0 and c - x are taken in float64
-// and rounded once, so a_i carries no error from the absolute coordinates.
+__device__ __noinline__ void line_fallback_f64(V3<double> x, const float *__restrict__ xs,
+                                               const float4 *__restrict__ r32, const double *__restrict__ r64,
+                                               const float4 *__restrict__ lines, const dbl4 *__restrict__ lines64,
+                                               int L, int lane, int vk, bool whole_f64, V3<double> &acc, int &hits);
+
+// float32 version.  The point, the centroid and the vertices are float
+// splits (hi + mid + lo), so the differences x - v0 and c - x and the vertex
+// test need no float64 arithmetic and a_i carries no error from the absolute
+// coordinates.
 // When x is vertex k of the tet, a = e_k exactly and the chord is decided by
 // the signs of b_i on the three faces through x; a line with
 // |b_i| <= 1e-5 |g_i| on one of them (nearly in that face plane, where the
@@ -301,17 +312,28 @@ __device__ __noinline__ bool line_f64_lean(V3<double> x, const double *__restric
 // the float32 state is dead (keeps the register footprint of the pass
 // small).  Pairs whose point is within 1e-5 (barycentric) of the tet's
 // boundary without being a vertex run wholly in float64.
-__device__ __noinline__ NearOut near_pair_f32(V3<double> x, const float4 *__restrict__ r32,
-                                              const double *__restrict__ r64, const float4 *__restrict__ lines,
-                                              const dbl4 *__restrict__ lines64, int L, int lane)
+__device__ __noinline__ NearOut32 near_pair_f32(const float *__restrict__ xs, const float4 *__restrict__ r32,
+                                                const double *__restrict__ r64, const float4 *__restrict__ lines,
+                                                const dbl4 *__restrict__ lines64, int L, int lane)
 {
-    const int vk = vertex_index(x, r64);
+    // xs: the point as float splits [component][hi, mid, lo]
+    const float xh0 = xs[0], xm0 = xs[1], xh1 = xs[3], xm1 = xs[4], xh2 = xs[6], xm2 = xs[7];
+    int vk = -1;
+    {
+        const float *vh = reinterpret_cast<const float *>(r32 + nf32::VH);
+        const float *vm = reinterpret_cast<const float *>(r32 + nf32::VM);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (vk < 0 && vh[3 * i] == xh0 && vm[3 * i] == xm0 && vh[3 * i + 1] == xh1 && vm[3 * i + 1] == xm1 &&
+                vh[3 * i + 2] == xh2 && vm[3 * i + 2] == xm2)
+                vk = i;
+    }
     float ax = 0.f, ay = 0.f, az = 0.f;
     int hits = 0;
     bool any_redo = false;
     bool whole_f64 = false;
     {
-        const float4 q0 = r32[0], q1 = r32[1], q2 = r32[2];
+        const float4 q0 = r32[nf32::G1], q1 = r32[nf32::G2], q2 = r32[nf32::G3];
         V3<float> g[4];
         g[1] = mk(q0.x, q0.y, q0.z);
         g[2] = mk(q1.x, q1.y, q1.z);
@@ -323,8 +345,11 @@ __device__ __noinline__ NearOut near_pair_f32(V3<double> x, const float4 *__rest
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = (i == vk) ? 1.0f : 0.0f;
         } else {
-            const V3<float> d0 = mk((float)(x.x - r64[nf64::V]), (float)(x.y - r64[nf64::V + 1]),
-                                    (float)(x.z - r64[nf64::V + 2]));
+            // x - v0 from the splits: the hi parts are within a few tet sizes of each other
+            const float *vh = reinterpret_cast<const float *>(r32 + nf32::VH);
+            const float *vm = reinterpret_cast<const float *>(r32 + nf32::VM);
+            const V3<float> d0 = mk((xh0 - vh[0]) + (xm0 - vm[0]), (xh1 - vh[1]) + (xm1 - vm[1]),
+                                    (xh2 - vh[2]) + (xm2 - vm[2]));
             a[1] = dot3(g[1], d0);
             a[2] = dot3(g[2], d0);
             a[3] = dot3(g[3], d0);
@@ -337,14 +362,14 @@ __device__ __noinline__ NearOut near_pair_f32(V3<double> x, const float4 *__rest
             V3<float> w[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const float4 t = r32[3 + i];
+                const float4 t = r32[nf32::W + i];
                 w[i] = mk(t.x, t.y, t.z);
             }
             const V3<float> Wa = mk(a[0] * w[0].x + a[1] * w[1].x + a[2] * w[2].x + a[3] * w[3].x,
                                     a[0] * w[0].y + a[1] * w[1].y + a[2] * w[2].y + a[3] * w[3].y,
                                     a[0] * w[0].z + a[1] * w[1].z + a[2] * w[2].z + a[3] * w[3].z);
-            const V3<float> rc = mk((float)(r64[nf64::C] - x.x), (float)(r64[nf64::C + 1] - x.y),
-                                    (float)(r64[nf64::C + 2] - x.z));
+            const float4 ch = r32[nf32::CH], cm = r32[nf32::CM];
+            const V3<float> rc = mk((ch.x - xh0) + (cm.x - xm0), (ch.y - xh1) + (cm.y - xm1), (ch.z - xh2) + (cm.z - xm2));
             const float rc2 = dot3(rc, rc);
             const float bound = rb2 * (1.0f + kBoundPadF);
             const float tau_h = (float)kTau * h;
@@ -396,17 +421,41 @@ __device__ __noinline__ NearOut near_pair_f32(V3<double> x, const float4 *__rest
             }
         }
     }
-    V3<double> acc = mk((double)ax, (double)ay, (double)az);
+    if (whole_f64 || any_redo) {
+        // rare: lines (or whole pairs) that need float64; the point's exact coordinates from its splits
+        V3<double> acc = mk(0.0, 0.0, 0.0);
+        const V3<double> x = mk(join3(xs[0], xs[1], xs[2]), join3(xs[3], xs[4], xs[5]), join3(xs[6], xs[7], xs[8]));
+        line_fallback_f64(x, xs, r32, r64, lines, lines64, L, lane, vk, whole_f64, acc, hits);
+        ax += (float)acc.x;
+        ay += (float)acc.y;
+        az += (float)acc.z;
+    }
+    NearOut32 o;
+    o.vx = warp_sum(ax);
+    o.vy = warp_sum(ay);
+    o.vz = warp_sum(az);
+    o.hits = warp_sum(hits);
+    return o;
+}
+
+// The float64 steps of near_pair_f32 (kept out of line: they are rare, and their registers would
+// otherwise count against the common path).
+__device__ __noinline__ void line_fallback_f64(V3<double> x, const float *__restrict__ xs,
+                                               const float4 *__restrict__ r32, const double *__restrict__ r64,
+                                               const float4 *__restrict__ lines, const dbl4 *__restrict__ lines64,
+                                               int L, int lane, int vk, bool whole_f64, V3<double> &acc, int &hits)
+{
+    const float xh0 = xs[0], xm0 = xs[1], xh1 = xs[3], xm1 = xs[4], xh2 = xs[6], xm2 = xs[7];
     if (whole_f64) {
 #pragma unroll 1
         for (int l = lane; l < L; l += 32) hits += line_f64_lean(x, r64, -1, lines64[l], acc) ? 1 : 0;
-    } else if (any_redo) {
+    } else {
         // second pass: find this lane's flagged lines again (same float32 test) and redo them in float64
-        const float4 q0 = r32[0], q1 = r32[1], q2 = r32[2];
+        const float4 q0 = r32[nf32::G1], q1 = r32[nf32::G2], q2 = r32[nf32::G3];
         const V3<float> g1 = mk(q0.x, q0.y, q0.z), g2 = mk(q1.x, q1.y, q1.z), g3 = mk(q2.x, q2.y, q2.z);
         const V3<float> g0 = mk(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
-        const V3<float> rc = mk((float)(r64[nf64::C] - x.x), (float)(r64[nf64::C + 1] - x.y),
-                                (float)(r64[nf64::C + 2] - x.z));
+        const float4 ch = r32[nf32::CH], cm = r32[nf32::CM];
+        const V3<float> rc = mk((ch.x - xh0) + (cm.x - xm0), (ch.y - xh1) + (cm.y - xm1), (ch.z - xh2) + (cm.z - xm2));
         const float rc2 = dot3(rc, rc), bound = q1.w * (1.0f + kBoundPadF);
         const float f = kVertexFallback * kVertexFallback;
 #pragma unroll 1
@@ -421,12 +470,6 @@ __device__ __noinline__ NearOut near_pair_f32(V3<double> x, const float4 *__rest
             if (redo && line_f64_lean(x, r64, vk, lines64[l], acc)) ++hits;
         }
     }
-    NearOut o;
-    o.vx = warp_sum(acc.x);
-    o.vy = warp_sum(acc.y);
-    o.vz = warp_sum(acc.z);
-    o.hits = warp_sum(hits);
-    return o;
 }
 
 // ---------------------------------------------------------------------------
@@ -442,6 +485,18 @@ template <>
 struct Acc<double> {
     double s[3];
 };
+
+// Bump allocator over the dynamic shared memory; every region starts on a 16-byte boundary.
+struct SmemCarve {
+    unsigned char *p;
+    __device__ unsigned char *take(size_t bytes)
+    {
+        unsigned char *r = p;
+        p += (bytes + 15) & ~(size_t)15;
+        return r;
+    }
+};
+__host__ __device__ constexpr size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 template <int S>
 struct Pipe {
@@ -469,12 +524,22 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
     static_assert(P * 32 <= 256, "point slot in the near queue is 8 bits");
 
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *stages = smem;                                       // [S][header + TILE*RS]
-    double *spts = reinterpret_cast<double *>(smem + S * STAGE_BYTES);  // [BP][3]
-    uint16_t *queue = reinterpret_cast<uint16_t *>(spts + 3 * BP);     // [NW][QCAP]
-    Pipe<S> *pipe = reinterpret_cast<Pipe<S> *>(queue + NW * QCAP);
-    MeshDesc *s_md = reinterpret_cast<MeshDesc *>(pipe + 1);
-    int64_t *s_item = reinterpret_cast<int64_t *>(s_md + 1);
+    // shared-memory regions, each rounded up to 16 bytes (the same rule as smem_bytes below)
+    SmemCarve carve{smem};
+    unsigned char *stages = carve.take(S * STAGE_BYTES);                              // [S][header + TILE*RS]
+    float *spts = reinterpret_cast<float *>(carve.take(9 * sizeof(float) * BP));      // [BP][3][hi, mid, lo]
+    uint16_t *queue = reinterpret_cast<uint16_t *>(carve.take(2 * NW * QCAP));        // [NW][QCAP]
+    float4 *srec = reinterpret_cast<float4 *>(carve.take(sizeof(float4) * NW * kNearF32Vec4));  // staged near records
+    Pipe<S> *pipe = reinterpret_cast<Pipe<S> *>(carve.take(sizeof(Pipe<S>)));
+    MeshDesc *s_md = reinterpret_cast<MeshDesc *>(carve.take(sizeof(MeshDesc)));
+    int64_t *s_item = reinterpret_cast<int64_t *>(carve.take(16));
+    float4 *sdir = reinterpret_cast<float4 *>(carve.take(a.smem_lines ? sizeof(float4) * a.L : 0));
+    // direction table: a shared copy when it fits in the launch's dynamic shared memory
+    const float4 *slines = a.lines.f32;
+    if (F32 && a.smem_lines) {
+        for (int l = threadIdx.x; l < a.L; l += NT) sdir[l] = a.lines.f32[l];
+        slines = sdir;
+    }
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const T fr2 = (T)a.far_ratio2;
@@ -543,9 +608,9 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
             int64_t gi = pb * BP + i;
             if (gi >= k) gi = k - 1;  // pad with a real point; its result is not written
             const int64_t src = md.perm[gi];
-            spts[3 * i + 0] = md.pts[3 * src + 0];
-            spts[3 * i + 1] = md.pts[3 * src + 1];
-            spts[3 * i + 2] = md.pts[3 * src + 2];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) split3(md.pts[3 * src + j], spts[9 * i + 3 * j], spts[9 * i + 3 * j + 1],
+                                               spts[9 * i + 3 * j + 2]);
         }
         __syncthreads();
 
@@ -555,7 +620,11 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const int slot = warp * 32 * P + p * 32 + lane;
-            xp[p] = mk((T)spts[3 * slot], (T)spts[3 * slot + 1], (T)spts[3 * slot + 2]);
+            const float *sp = spts + 9 * slot;
+            if constexpr (F32)
+                xp[p] = mk((T)sp[0], (T)sp[3], (T)sp[6]);
+            else
+                xp[p] = mk((T)join3(sp[0], sp[1], sp[2]), (T)join3(sp[3], sp[4], sp[5]), (T)join3(sp[6], sp[7], sp[8]));
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 acc[p].s[j] = 0;
@@ -717,16 +786,19 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         const int pp = slot >> 5, owner = slot & 31;
                         const int bi = warp * 32 * P + slot;
                         const int64_t tet = t * TILE + j;
-                        const V3<double> xd = mk(spts[3 * bi], spts[3 * bi + 1], spts[3 * bi + 2]);
-                        const NearOut o = near_pair_f32(xd, md.near32 + tet * kNearF32Vec4, md.near64 + tet * kNearF64,
-                                                        a.lines.f32, a.lines.f64, a.L, lane);
+                        // the near record, one coalesced load into this warp's shared slot, read by broadcast
+                        if (lane < kNearF32Vec4) srec[warp * kNearF32Vec4 + lane] = md.near32[tet * kNearF32Vec4 + lane];
+                        __syncwarp();
+                        const NearOut32 o = near_pair_f32(spts + 9 * bi, srec + warp * kNearF32Vec4,
+                                                          md.near64 + tet * kNearF64, slines, a.lines.f64, a.L, lane);
+                        __syncwarp();
                         if (lane == owner) {
 #pragma unroll
                             for (int p = 0; p < P; ++p)
                                 if (p == pp) {
-                                    A[p][0] += (float)o.vx;
-                                    A[p][1] += (float)o.vy;
-                                    A[p][2] += (float)o.vz;
+                                    A[p][0] += o.vx;
+                                    A[p][1] += o.vy;
+                                    A[p][2] += o.vz;
                                     nhit[p] += o.hits;
                                 }
                         }
@@ -797,7 +869,9 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         const int pp = slot >> 5, owner = slot & 31;
                         const int bi = warp * 32 * P + slot;
                         const int64_t tet = t * TILE + j;
-                        const V3<double> xd = mk(spts[3 * bi], spts[3 * bi + 1], spts[3 * bi + 2]);
+                        const float *sp = spts + 9 * bi;
+                        const V3<double> xd = mk(join3(sp[0], sp[1], sp[2]), join3(sp[3], sp[4], sp[5]),
+                                                 join3(sp[6], sp[7], sp[8]));
                         const NearOut o = near_pair_f64(xd, md.near64 + tet * kNearF64, a.lines.f64, a.L, lane);
                         if (lane == owner) {
 #pragma unroll
@@ -888,18 +962,20 @@ __global__ void zero_kernel(int32_t *counts, int64_t n, int *work_counter)
 }
 
 template <typename T, int Q, int P, int NT, int TILE, int S>
-size_t smem_bytes()
+size_t smem_bytes(int lines_in_smem)
 {
     constexpr int RS = far_stride<T>(Q);
-    return (size_t)S * (32 + TILE * RS * sizeof(T)) + 3 * sizeof(double) * NT * P +
-           (NT / 32) * (32 * P * TILE) * sizeof(uint16_t) + sizeof(Pipe<S>) + sizeof(MeshDesc) + 16;
+    constexpr size_t NW = NT / 32;
+    return round16((size_t)S * (32 + TILE * RS * sizeof(T))) + round16(9 * sizeof(float) * NT * P) +
+           round16(2 * NW * 32 * P * TILE) + round16(sizeof(float4) * NW * kNearF32Vec4) + round16(sizeof(Pipe<S>)) +
+           round16(sizeof(MeshDesc)) + 16 + round16(sizeof(float4) * lines_in_smem);
 }
 
 template <typename T, int Q, int P, int NT, int TILE, int S, int MINB>
 cudaError_t launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out, bool query_only, int *occ_out)
 {
     auto kern = velocity_kernel<T, Q, P, NT, TILE, S, MINB>;
-    const size_t sm = smem_bytes<T, Q, P, NT, TILE, S>();
+    const size_t sm = smem_bytes<T, Q, P, NT, TILE, S>(a.smem_lines ? a.L : 0);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int occ = 0;
