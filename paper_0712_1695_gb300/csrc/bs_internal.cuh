@@ -21,8 +21,11 @@ constexpr double kPi = 3.14159265358979323846;
 // w'_q = -(w_q |V| / 4pi) omega(x_q) (sign and 1/4pi of Eq. 1 folded in).
 //   double: [c (3), rho^2] then per quadrature point [x_q (3), w'_q (3)]  (4 + 6Q)
 //   float : tile frame (coordinates relative to the tile origin o):
-//           [c - o (3), rho^2] then per q three float4
-//           [-2 x_q' (3), |x_q'|^2] [w'_q (3), B.x] [B.y, B.z, 0, 0], B = x_q' x w'_q  (4 + 12Q)
+//           [c - o (3), rho^2] then the quadrature points in pairs (a, b), five float4 per pair,
+//           every value stored as the pair (value_a, value_b) so that one packed f32x2
+//           instruction serves both points:
+//           [-2x'.x, -2x'.y] [-2x'.z, |x'|^2] [w'.x, w'.y] [w'.z, B.x] [B.y, B.z]
+//           (B = x_q' x w'_q; an odd Q is padded with a point of zero weight)  (4 + 20 ceil(Q/2))
 // Tile header (per TILE consecutive tets): float4 [o (3), rc], float4 [rho_max, 0, 0, 0].
 //
 // Near record (one per tet, independent of the parameters): what the ray rule
@@ -38,7 +41,7 @@ constexpr double kPi = 3.14159265358979323846;
 template <typename T>
 __host__ __device__ constexpr int far_stride(int Q)
 {
-    return sizeof(T) == 4 ? (4 + 12 * Q) : (4 + 6 * Q);
+    return sizeof(T) == 4 ? (4 + 20 * ((Q + 1) / 2)) : (4 + 6 * Q);
 }
 constexpr int kNearF32Vec4 = 15;  // float4 per near record
 namespace nf32 {

@@ -204,19 +204,16 @@ __global__ void far_records_kernel(const double *__restrict__ near64, const doub
         for (int j = 0; j < 6; ++j) d[4 + 6 * q + j] = vals[j];
         const D3 xl = sub(xq, o);
         const D3 B = cross(xl, wv);
-        float *g = f + 4 + 12 * q;
-        g[0] = (float)(-2.0 * xl.x);
-        g[1] = (float)(-2.0 * xl.y);
-        g[2] = (float)(-2.0 * xl.z);
-        g[3] = (float)dot(xl, xl);
-        g[4] = (float)wv.x;
-        g[5] = (float)wv.y;
-        g[6] = (float)wv.z;
-        g[7] = (float)B.x;
-        g[8] = (float)B.y;
-        g[9] = (float)B.z;
-        g[10] = 0.f;
-        g[11] = 0.f;
+        // pair q/2, slot q%2: value k of the point goes to float 2k + slot of the pair's 20
+        float *g = f + 4 + 20 * (q / 2) + (q % 2);
+        const double vals32[10] = {-2.0 * xl.x, -2.0 * xl.y, -2.0 * xl.z, dot(xl, xl), wv.x, wv.y, wv.z,
+                                   B.x, B.y, B.z};
+        for (int k = 0; k < 10; ++k) g[2 * k] = (float)vals32[k];
+    }
+    if (Q % 2) {
+        // pad the last pair with a point of zero weight (|x - x_q| = sqrt(|x'|^2 + 1) > 0)
+        float *g = f + 4 + 20 * (Q / 2) + 1;
+        for (int k = 0; k < 10; ++k) g[2 * k] = (k == 3) ? 1.0f : 0.0f;
     }
 }
 

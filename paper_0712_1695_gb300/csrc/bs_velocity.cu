@@ -119,6 +119,42 @@ __device__ inline T warp_sum(T v)
     return v;
 }
 
+// packed float pairs (lo = first value, hi = second) and the f32x2 arithmetic of sm_100+
+__device__ __forceinline__ unsigned long long pack2(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float sum2(unsigned long long v)
+{
+    float a, b;
+    unpack2(v, a, b);
+    return a + b;
+}
+
 // ---------------------------------------------------------------------------
 // Ray rule for one (point, tet) pair, lines split across the 32 lanes.
 // Returns the warp-reduced contribution (all lanes) and the hit count.
@@ -699,16 +735,22 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
             };
 
             if constexpr (F32) {
-                // tile frame: x' = x - o
-                float xl[P][3], xx[P], A[P][3], B[P][3];
+                // tile frame: x' = x - o; quadrature points two at a time in packed f32x2 registers
+                constexpr int QP = (Q + 1) / 2;
+                float xl[P][3];
+                unsigned long long x2[P][3], xx2[P], A2[P][3], B2[P][3];
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     xl[p][0] = xp[p].x - hd.x;
                     xl[p][1] = xp[p].y - hd.y;
                     xl[p][2] = xp[p].z - hd.z;
-                    xx[p] = xl[p][0] * xl[p][0] + xl[p][1] * xl[p][1] + xl[p][2] * xl[p][2];
+                    const float xx = xl[p][0] * xl[p][0] + xl[p][1] * xl[p][1] + xl[p][2] * xl[p][2];
 #pragma unroll
-                    for (int jj = 0; jj < 3; ++jj) A[p][jj] = B[p][jj] = 0.f;
+                    for (int jj = 0; jj < 3; ++jj) {
+                        x2[p][jj] = pack2(xl[p][jj], xl[p][jj]);
+                        A2[p][jj] = B2[p][jj] = 0ull;
+                    }
+                    xx2[p] = pack2(xx, xx);
                 }
                 const float4 *tb4 = reinterpret_cast<const float4 *>(tb);
                 // far sweep over the tile; MIXED: per-pair near/far test, near pairs masked and queued
@@ -717,6 +759,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
 #pragma unroll 1
                     for (int j = 0; j < cnt; ++j) {
                         const float4 *rec = tb4 + j * (RS / 4);
+                        const ulonglong2 *rec2 = reinterpret_cast<const ulonglong2 *>(rec);
                         bool nearp[P];
                         if constexpr (MIXED) {
                             const float4 h0 = rec[0];
@@ -728,21 +771,25 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             }
                         }
 #pragma unroll
-                        for (int q = 0; q < Q; ++q) {
-                            const float4 u0 = rec[1 + 3 * q], u1 = rec[2 + 3 * q], u2 = rec[3 + 3 * q];
+                        for (int pp = 0; pp < QP; ++pp) {
+                            // (mx, my) (mz, qq) (wx, wy) (wz, bx) (by, bz), each a packed pair of points
+                            const ulonglong2 v0 = rec2[1 + 5 * pp], v1 = rec2[2 + 5 * pp], v2 = rec2[3 + 5 * pp],
+                                             v3 = rec2[4 + 5 * pp], v4 = rec2[5 + 5 * pp];
 #pragma unroll
                             for (int p = 0; p < P; ++p) {
-                                const float r2 =
-                                    fmaf(xl[p][0], u0.x, fmaf(xl[p][1], u0.y, fmaf(xl[p][2], u0.z, xx[p] + u0.w)));
-                                const float ir = rsqrtf(r2);
-                                float ir3 = ir * ir * ir;
-                                if constexpr (MIXED) ir3 = nearp[p] ? 0.f : ir3;
-                                A[p][0] = fmaf(ir3, u1.x, A[p][0]);
-                                A[p][1] = fmaf(ir3, u1.y, A[p][1]);
-                                A[p][2] = fmaf(ir3, u1.z, A[p][2]);
-                                B[p][0] = fmaf(ir3, u1.w, B[p][0]);
-                                B[p][1] = fmaf(ir3, u2.x, B[p][1]);
-                                B[p][2] = fmaf(ir3, u2.y, B[p][2]);
+                                const unsigned long long r2 =
+                                    fma2(x2[p][0], v0.x, fma2(x2[p][1], v0.y, fma2(x2[p][2], v1.x, add2(xx2[p], v1.y))));
+                                float ra, rb;
+                                unpack2(r2, ra, rb);
+                                const unsigned long long ir = pack2(rsqrtf(ra), rsqrtf(rb));
+                                unsigned long long ir3 = mul2(mul2(ir, ir), ir);
+                                if constexpr (MIXED) ir3 = nearp[p] ? 0ull : ir3;
+                                A2[p][0] = fma2(ir3, v2.x, A2[p][0]);
+                                A2[p][1] = fma2(ir3, v2.y, A2[p][1]);
+                                A2[p][2] = fma2(ir3, v3.x, A2[p][2]);
+                                B2[p][0] = fma2(ir3, v3.y, B2[p][0]);
+                                B2[p][1] = fma2(ir3, v4.x, B2[p][1]);
+                                B2[p][2] = fma2(ir3, v4.y, B2[p][2]);
                             }
                         }
                         if constexpr (MIXED) {
@@ -765,6 +812,14 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                     sweep(std::false_type{});
                 else
                     sweep(std::true_type{});
+                float A[P][3], B[P][3];
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) {
+                        A[p][jj] = sum2(A2[p][jj]);
+                        B[p][jj] = sum2(B2[p][jj]);
+                    }
                 release();
                 // tile partial: x' x A - B, folded into the compensated sum below
 #pragma unroll
