@@ -348,9 +348,9 @@ __device__ __noinline__ void line_fallback_f64(V3<double> x, const float *__rest
 // the float32 state is dead (keeps the register footprint of the pass
 // small).  Pairs whose point is within 1e-5 (barycentric) of the tet's
 // boundary without being a vertex run wholly in float64.
-__device__ __noinline__ NearOut32 near_pair_f32(const float *__restrict__ xs, const float4 *__restrict__ r32,
-                                                const double *__restrict__ r64, const float4 *__restrict__ lines,
-                                                const dbl4 *__restrict__ lines64, int L, int lane)
+__device__ __forceinline__ NearOut32 near_pair_f32_body(const float *__restrict__ xs, const float4 *__restrict__ r32,
+                                                        const double *__restrict__ r64, const float4 *__restrict__ lines,
+                                                        const dbl4 *__restrict__ lines64, int L, int lane)
 {
     // xs: the point as float splits [component][hi, mid, lo]
     const float xh0 = xs[0], xm0 = xs[1], xh1 = xs[3], xm1 = xs[4], xh2 = xs[6], xm2 = xs[7];
@@ -474,6 +474,13 @@ __device__ __noinline__ NearOut32 near_pair_f32(const float *__restrict__ xs, co
     return o;
 }
 
+__device__ __noinline__ NearOut32 near_pair_f32(const float *__restrict__ xs, const float4 *__restrict__ r32,
+                                                const double *__restrict__ r64, const float4 *__restrict__ lines,
+                                                const dbl4 *__restrict__ lines64, int L, int lane)
+{
+    return near_pair_f32_body(xs, r32, r64, lines, lines64, L, lane);
+}
+
 // The float64 steps of near_pair_f32 (kept out of line: they are rare, and their registers would
 // otherwise count against the common path).
 __device__ __noinline__ void line_fallback_f64(V3<double> x, const float *__restrict__ xs,
@@ -545,7 +552,7 @@ struct Pipe {
 // slots w*32*P + p*32 + l.  A warp therefore covers a compact patch of
 // points, and a tile whose tets are all far from that patch skips the
 // per-pair near/far test (culled=true below).
-template <typename T, int Q, int P, int NT, int TILE, int S, int MINB>
+template <typename T, int Q, int P, int NT, int TILE, int S, int MINB, bool INL>
 __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a)
 {
     constexpr int RS = far_stride<T>(Q);
@@ -844,8 +851,13 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         // the near record, one coalesced load into this warp's shared slot, read by broadcast
                         if (lane < kNearF32Vec4) srec[warp * kNearF32Vec4 + lane] = md.near32[tet * kNearF32Vec4 + lane];
                         __syncwarp();
-                        const NearOut32 o = near_pair_f32(spts + 9 * bi, srec + warp * kNearF32Vec4,
-                                                          md.near64 + tet * kNearF64, slines, a.lines.f64, a.L, lane);
+                        NearOut32 o;
+                        if constexpr (INL)
+                            o = near_pair_f32_body(spts + 9 * bi, srec + warp * kNearF32Vec4, md.near64 + tet * kNearF64,
+                                                   slines, a.lines.f64, a.L, lane);
+                        else
+                            o = near_pair_f32(spts + 9 * bi, srec + warp * kNearF32Vec4, md.near64 + tet * kNearF64,
+                                              slines, a.lines.f64, a.L, lane);
                         __syncwarp();
                         if (lane == owner) {
 #pragma unroll
@@ -1026,10 +1038,10 @@ size_t smem_bytes(int lines_in_smem)
            round16(sizeof(MeshDesc)) + 16 + round16(sizeof(float4) * lines_in_smem);
 }
 
-template <typename T, int Q, int P, int NT, int TILE, int S, int MINB>
+template <typename T, int Q, int P, int NT, int TILE, int S, int MINB, bool INL>
 cudaError_t launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out, bool query_only, int *occ_out)
 {
-    auto kern = velocity_kernel<T, Q, P, NT, TILE, S, MINB>;
+    auto kern = velocity_kernel<T, Q, P, NT, TILE, S, MINB, INL>;
     const size_t sm = smem_bytes<T, Q, P, NT, TILE, S>(a.smem_lines ? a.L : 0);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -1051,18 +1063,21 @@ cudaError_t launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
 // the tile size, so they share the far records.
 struct VariantShape {
     int P, TILE, S, MINB;
+    bool INL;  // near-pair routine inlined (no call inside the tile loop)
 };
-constexpr VariantShape kQ1[] = {{2, 32, 4, 4}};
-constexpr VariantShape kQ4[] = {{2, 32, 4, 4}, {2, 32, 4, 3}, {4, 32, 4, 2}, {4, 32, 4, 3}, {1, 32, 4, 5}};
-constexpr VariantShape kQ8[] = {{2, 16, 4, 4}};
-constexpr VariantShape kQ27[] = {{1, 16, 4, 4}};
-constexpr VariantShape kQ64[] = {{1, 8, 4, 4}};
+constexpr VariantShape kQ1[] = {{2, 32, 4, 4, false}};
+constexpr VariantShape kQ4[] = {{2, 32, 4, 4, false}, {2, 32, 4, 3, false}, {4, 32, 4, 2, false},
+                                {4, 32, 4, 3, false}, {1, 32, 4, 5, false}, {2, 32, 4, 4, true},
+                                {2, 32, 4, 3, true}};
+constexpr int kNumQ4 = sizeof(kQ4) / sizeof(kQ4[0]);
+constexpr VariantShape kQ8[] = {{2, 16, 4, 4, false}};
+constexpr VariantShape kQ27[] = {{1, 16, 4, 4, false}};
+constexpr VariantShape kQ64[] = {{1, 8, 4, 4, false}};
 
 template <typename T>
 cudaError_t dispatch(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out, bool qo, int *occ)
 {
-#define BS_L(Q_, V_)                                                                                            \
-    launch_t<T, Q_, V_.P, 128, V_.TILE, V_.S, V_.MINB>(a, n_sm, st, grid_out, qo, occ)
+#define BS_L(Q_, V_) launch_t<T, Q_, V_.P, 128, V_.TILE, V_.S, V_.MINB, V_.INL>(a, n_sm, st, grid_out, qo, occ)
     switch (a.Q) {
     case 1: return BS_L(1, kQ1[0]);
     case 4:
@@ -1072,6 +1087,8 @@ cudaError_t dispatch(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
             case 2: return BS_L(4, kQ4[2]);
             case 3: return BS_L(4, kQ4[3]);
             case 4: return BS_L(4, kQ4[4]);
+            case 5: return BS_L(4, kQ4[5]);
+            case 6: return BS_L(4, kQ4[6]);
             default: return BS_L(4, kQ4[0]);
             }
         } else {
@@ -1087,14 +1104,14 @@ cudaError_t dispatch(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
 
 }  // namespace
 
-int num_variants(int precision, int Q) { return (precision == BS_FP32 && Q == 4) ? 5 : 1; }
+int num_variants(int precision, int Q) { return (precision == BS_FP32 && Q == 4) ? kNumQ4 : 1; }
 
 LaunchShape shape_for(int precision, int Q, int variant)
 {
     VariantShape v = kQ4[0];
     switch (Q) {
     case 1: v = kQ1[0]; break;
-    case 4: v = (precision == BS_FP32 && variant >= 0 && variant < 5) ? kQ4[variant] : kQ4[0]; break;
+    case 4: v = (precision == BS_FP32 && variant >= 0 && variant < kNumQ4) ? kQ4[variant] : kQ4[0]; break;
     case 8: v = kQ8[0]; break;
     case 27: v = kQ27[0]; break;
     case 64: v = kQ64[0]; break;
