@@ -9,8 +9,8 @@
 //   ring with one bulk asynchronous copy (cp.async.bulk + mbarrier) per tile.
 //   Every thread classifies its points against each tet of the tile (one
 //   warp-uniform broadcast read of the record per tet); far pairs go through
-//   the tet Gauss rule, near pairs are appended to a per-warp queue with a
-//   warp ballot.  The queue is drained by the whole warp: the 32 lanes split
+//   the tet Gauss rule, near pairs are recorded in a per-warp queue as warp
+//   ballot masks.  The queue is drained by the whole warp: the 32 lanes split
 //   the n_theta*n_phi lines of one pair, and the three velocity components
 //   are reduced with shuffles and handed to the lane that owns the point.
 //   float32: per-tile partial sums in float32, Kahan-compensated across
@@ -129,6 +129,15 @@ __device__ __forceinline__ unsigned long long pack2(float a, float b)
 __device__ __forceinline__ void unpack2(unsigned long long v, float &a, float &b)
 {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+// 1/sqrt(x) with subnormal inputs flushed: the far sweep's r^2 is never subnormal (a far pair
+// is at least the far ratio times the tet radius apart) and a masked near pair may give inf,
+// which the mask discards; the flush drops the subnormal rescaling around every evaluation.
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c)
 {
@@ -518,16 +527,6 @@ __device__ __noinline__ void line_fallback_f64(V3<double> x, const float *__rest
 // ---------------------------------------------------------------------------
 // The velocity kernel.
 // ---------------------------------------------------------------------------
-template <typename T>
-struct Acc;  // per-point accumulator
-template <>
-struct Acc<float> {
-    float s[3], c[3];  // Kahan sum across tiles
-};
-template <>
-struct Acc<double> {
-    double s[3];
-};
 
 // Bump allocator over the dynamic shared memory; every region starts on a 16-byte boundary.
 struct SmemCarve {
@@ -558,25 +557,32 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
     constexpr int RS = far_stride<T>(Q);
     constexpr int BP = NT * P;
     constexpr int NW = NT / 32;
-    constexpr int QCAP = 32 * P * TILE;  // a whole tile's pairs fit: the queue is drained between tiles only
+    constexpr int QCAP = P * TILE;  // one entry per (tet, point row) of the tile: drained between tiles only
     constexpr int TILE_BYTES = TILE * RS * (int)sizeof(T);
     constexpr int HDR_BYTES = 32;  // tile header (two float4) in front of each stage's records
     constexpr int STAGE_BYTES = HDR_BYTES + TILE_BYTES;
     constexpr bool F32 = sizeof(T) == 4;
+    constexpr int NACC = F32 ? 6 : 3;  // float: (sum, compensation) per component; double: sum
     static_assert(TILE <= 256, "tet index in the near queue is 8 bits");
-    static_assert(P * 32 <= 256, "point slot in the near queue is 8 bits");
 
     extern __shared__ __align__(128) unsigned char smem[];
     // shared-memory regions, each rounded up to 16 bytes (the same rule as smem_bytes below)
     SmemCarve carve{smem};
     unsigned char *stages = carve.take(S * STAGE_BYTES);                              // [S][header + TILE*RS]
     float *spts = reinterpret_cast<float *>(carve.take(9 * sizeof(float) * BP));      // [BP][3][hi, mid, lo]
-    uint16_t *queue = reinterpret_cast<uint16_t *>(carve.take(2 * NW * QCAP));        // [NW][QCAP]
+    // near queue per warp: (lane mask, point row p << 8 | tet j) for each (j, p) with a near pair
+    uint32_t *qmask = reinterpret_cast<uint32_t *>(carve.take(sizeof(uint32_t) * NW * QCAP));  // [NW][QCAP]
+    uint16_t *qcode = reinterpret_cast<uint16_t *>(carve.take(sizeof(uint16_t) * NW * QCAP));  // [NW][QCAP]
     float4 *srec = reinterpret_cast<float4 *>(carve.take(sizeof(float4) * NW * kNearF32Vec4));  // staged near records
     Pipe<S> *pipe = reinterpret_cast<Pipe<S> *>(carve.take(sizeof(Pipe<S>)));
     MeshDesc *s_md = reinterpret_cast<MeshDesc *>(carve.take(sizeof(MeshDesc)));
     int64_t *s_item = reinterpret_cast<int64_t *>(carve.take(16));
     float4 *sdir = reinterpret_cast<float4 *>(carve.take(a.smem_lines ? sizeof(float4) * a.L : 0));
+    // per-point state, touched once per tile: compensated sums [NACC][BP] and counts [2][BP]
+    // (near pairs, chord hits); the warp's bounding sphere [NW]
+    T *sacc = reinterpret_cast<T *>(carve.take(sizeof(T) * NACC * BP));
+    int *scnt = reinterpret_cast<int *>(carve.take(sizeof(int) * 2 * BP));
+    float4 *swarp = reinterpret_cast<float4 *>(carve.take(sizeof(float4) * NW));
     // direction table: a shared copy when it fits in the launch's dynamic shared memory
     const float4 *slines = a.lines.f32;
     if (F32 && a.smem_lines) {
@@ -657,34 +663,23 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
         }
         __syncthreads();
 
-        V3<T> xp[P];
-        Acc<T> acc[P];
-        int nnear[P], nhit[P];
+        const int slot0 = warp * 32 * P + lane;  // block slot of this thread's point p: slot0 + 32 p
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const int slot = warp * 32 * P + p * 32 + lane;
-            const float *sp = spts + 9 * slot;
-            if constexpr (F32)
-                xp[p] = mk((T)sp[0], (T)sp[3], (T)sp[6]);
-            else
-                xp[p] = mk((T)join3(sp[0], sp[1], sp[2]), (T)join3(sp[3], sp[4], sp[5]), (T)join3(sp[6], sp[7], sp[8]));
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                acc[p].s[j] = 0;
-                if constexpr (F32) acc[p].c[j] = 0;
-            }
-            nnear[p] = 0;
-            nhit[p] = 0;
+            for (int j = 0; j < NACC; ++j) sacc[j * BP + slot0 + 32 * p] = 0;
+            scnt[slot0 + 32 * p] = 0;
+            scnt[BP + slot0 + 32 * p] = 0;
         }
         // bounding sphere of the warp's points (float, padded)
-        float cwx, cwy, cwz, rw;
         {
-            float mnx = (float)xp[0].x, mxx = mnx, mny = (float)xp[0].y, mxy = mny, mnz = (float)xp[0].z, mxz = mnz;
+            float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY, mnz = INFINITY, mxz = -INFINITY;
 #pragma unroll
-            for (int p = 1; p < P; ++p) {
-                mnx = fminf(mnx, (float)xp[p].x); mxx = fmaxf(mxx, (float)xp[p].x);
-                mny = fminf(mny, (float)xp[p].y); mxy = fmaxf(mxy, (float)xp[p].y);
-                mnz = fminf(mnz, (float)xp[p].z); mxz = fmaxf(mxz, (float)xp[p].z);
+            for (int p = 0; p < P; ++p) {
+                const float *sp = spts + 9 * (slot0 + 32 * p);
+                mnx = fminf(mnx, sp[0]); mxx = fmaxf(mxx, sp[0]);
+                mny = fminf(mny, sp[3]); mxy = fmaxf(mxy, sp[3]);
+                mnz = fminf(mnz, sp[6]); mxz = fmaxf(mxz, sp[6]);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -695,13 +690,14 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                 mnz = fminf(mnz, __shfl_xor_sync(0xffffffffu, mnz, o));
                 mxz = fmaxf(mxz, __shfl_xor_sync(0xffffffffu, mxz, o));
             }
-            cwx = 0.5f * (mnx + mxx);
-            cwy = 0.5f * (mny + mxy);
-            cwz = 0.5f * (mnz + mxz);
             const float ex = mxx - mnx, ey = mxy - mny, ez = mxz - mnz;
-            rw = 0.5f * sqrtf(ex * ex + ey * ey + ez * ez) * 1.001f + 1e-6f;
+            if (lane == 0)
+                swarp[warp] = make_float4(0.5f * (mnx + mxx), 0.5f * (mny + mxy), 0.5f * (mnz + mxz),
+                                          0.5f * sqrtf(ex * ex + ey * ey + ez * ez) * 1.001f + 1e-6f);
+            __syncwarp();
         }
-        uint16_t *wq = queue + warp * QCAP;
+        uint32_t *wm = qmask + warp * QCAP;
+        uint16_t *wc = qcode + warp * QCAP;
 
         bool aborted = false;
 #pragma unroll 1
@@ -719,10 +715,11 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
             // can any point of this warp be near a tet of this tile?
             bool culled = false;
             if (!a.all_ray) {
-                const float dx = cwx - hd.x, dy = cwy - hd.y, dz = cwz - hd.z;
+                const float4 cw = swarp[warp];
+                const float dx = cw.x - hd.x, dy = cw.y - hd.y, dz = cw.z - hd.z;
                 const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
                 const float scale = fabsf(hd.x) + fabsf(hd.y) + fabsf(hd.z) + dist;
-                culled = dist - rw - hd.w > fr * sh[1].x * 1.001f + 1e-5f * scale;
+                culled = dist - cw.w - hd.w > fr * sh[1].x * 1.001f + 1e-5f * scale;
             }
             const int cnt = (int)min((int64_t)TILE, md.n_tets - t * TILE);
             int qn = 0;  // warp-uniform
@@ -744,19 +741,23 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
             if constexpr (F32) {
                 // tile frame: x' = x - o; quadrature points two at a time in packed f32x2 registers
                 constexpr int QP = (Q + 1) / 2;
-                float xl[P][3];
+                // x' of point p is the low half of x2[p] (both halves hold it)
                 unsigned long long x2[P][3], xx2[P], A2[P][3], B2[P][3];
+                auto xl = [&](int p, int jj) {
+                    float lo, hi;
+                    unpack2(x2[p][jj], lo, hi);
+                    return lo;
+                };
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    xl[p][0] = xp[p].x - hd.x;
-                    xl[p][1] = xp[p].y - hd.y;
-                    xl[p][2] = xp[p].z - hd.z;
-                    const float xx = xl[p][0] * xl[p][0] + xl[p][1] * xl[p][1] + xl[p][2] * xl[p][2];
+                    const float *sp = spts + 9 * (slot0 + 32 * p);
+                    const float x = sp[0] - hd.x, y = sp[3] - hd.y, z = sp[6] - hd.z;
+                    const float xx = x * x + y * y + z * z;
+                    x2[p][0] = pack2(x, x);
+                    x2[p][1] = pack2(y, y);
+                    x2[p][2] = pack2(z, z);
 #pragma unroll
-                    for (int jj = 0; jj < 3; ++jj) {
-                        x2[p][jj] = pack2(xl[p][jj], xl[p][jj]);
-                        A2[p][jj] = B2[p][jj] = 0ull;
-                    }
+                    for (int jj = 0; jj < 3; ++jj) A2[p][jj] = B2[p][jj] = 0ull;
                     xx2[p] = pack2(xx, xx);
                 }
                 const float4 *tb4 = reinterpret_cast<const float4 *>(tb);
@@ -773,7 +774,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             const float thr2 = fr2 * h0.w;
 #pragma unroll
                             for (int p = 0; p < P; ++p) {
-                                const float dx = xl[p][0] - h0.x, dy = xl[p][1] - h0.y, dz = xl[p][2] - h0.z;
+                                const float dx = xl(p, 0) - h0.x, dy = xl(p, 1) - h0.y, dz = xl(p, 2) - h0.z;
                                 nearp[p] = !(dx * dx + dy * dy + dz * dz > thr2);
                             }
                         }
@@ -788,7 +789,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                                     fma2(x2[p][0], v0.x, fma2(x2[p][1], v0.y, fma2(x2[p][2], v1.x, add2(xx2[p], v1.y))));
                                 float ra, rb;
                                 unpack2(r2, ra, rb);
-                                const unsigned long long ir = pack2(rsqrtf(ra), rsqrtf(rb));
+                                const unsigned long long ir = pack2(rsqrt_ftz(ra), rsqrt_ftz(rb));
                                 unsigned long long ir3 = mul2(mul2(ir, ir), ir);
                                 if constexpr (MIXED) ir3 = nearp[p] ? 0ull : ir3;
                                 A2[p][0] = fma2(ir3, v2.x, A2[p][0]);
@@ -804,12 +805,12 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             for (int p = 0; p < P; ++p) {
                                 const unsigned m = __ballot_sync(0xffffffffu, nearp[p]);
                                 if (m) {
-                                    if (nearp[p]) {
-                                        const int pos = qn + __popc(m & ((1u << lane) - 1u));
-                                        wq[pos] = (uint16_t)(((p * 32 + lane) << 8) | j);
-                                        ++nnear[p];
+                                    if (lane == 0) {
+                                        wm[qn] = m;
+                                        wc[qn] = (uint16_t)((p << 8) | j);
                                     }
-                                    qn += __popc(m);
+                                    if (nearp[p]) ++scnt[slot0 + 32 * p];
+                                    ++qn;
                                 }
                             }
                         }
@@ -828,64 +829,74 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         B[p][jj] = sum2(B2[p][jj]);
                     }
                 release();
-                // tile partial: x' x A - B, folded into the compensated sum below
+                // compensated add of v into the sums of block slot sl
+                auto kahan = [&](int sl, float v0, float v1, float v2) {
+                    const float v[3] = {v0, v1, v2};
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) {
+                        float &sum = sacc[(2 * jj) * BP + sl];
+                        float &cmp = sacc[(2 * jj + 1) * BP + sl];
+                        const float y = v[jj] - cmp;
+                        const float s2 = sum + y;
+                        cmp = (s2 - sum) - y;
+                        sum = s2;
+                    }
+                };
+                // far part of the tile: x' x A - B
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    const float v0 = xl[p][1] * A[p][2] - xl[p][2] * A[p][1] - B[p][0];
-                    const float v1 = xl[p][2] * A[p][0] - xl[p][0] * A[p][2] - B[p][1];
-                    const float v2 = xl[p][0] * A[p][1] - xl[p][1] * A[p][0] - B[p][2];
-                    A[p][0] = v0;
-                    A[p][1] = v1;
-                    A[p][2] = v2;
+                    const float x = xl(p, 0), y = xl(p, 1), z = xl(p, 2);
+                    kahan(slot0 + 32 * p, y * A[p][2] - z * A[p][1] - B[p][0], z * A[p][0] - x * A[p][2] - B[p][1],
+                          x * A[p][1] - y * A[p][0] - B[p][2]);
                 }
-                // A now holds the tile partial; add the near pairs of the tile to it
+                // near pairs of the tile: the warp takes them one at a time; each tet's near record is
+                // staged once (one coalesced load into this warp's shared slot, read by broadcast)
                 if (qn > 0) {
                     __syncwarp();
+                    int held = -1;
 #pragma unroll 1
                     for (int e = 0; e < qn; ++e) {
-                        const int code = wq[e];
-                        const int slot = code >> 8, j = code & 255;
-                        const int pp = slot >> 5, owner = slot & 31;
-                        const int bi = warp * 32 * P + slot;
+                        unsigned m = wm[e];
+                        const int code = wc[e];
+                        const int pp = code >> 8, j = code & 255;
                         const int64_t tet = t * TILE + j;
-                        // the near record, one coalesced load into this warp's shared slot, read by broadcast
-                        if (lane < kNearF32Vec4) srec[warp * kNearF32Vec4 + lane] = md.near32[tet * kNearF32Vec4 + lane];
-                        __syncwarp();
-                        NearOut32 o;
-                        if constexpr (INL)
-                            o = near_pair_f32_body(spts + 9 * bi, srec + warp * kNearF32Vec4, md.near64 + tet * kNearF64,
-                                                   slines, a.lines.f64, a.L, lane);
-                        else
-                            o = near_pair_f32(spts + 9 * bi, srec + warp * kNearF32Vec4, md.near64 + tet * kNearF64,
-                                              slines, a.lines.f64, a.L, lane);
-                        __syncwarp();
-                        if (lane == owner) {
-#pragma unroll
-                            for (int p = 0; p < P; ++p)
-                                if (p == pp) {
-                                    A[p][0] += o.vx;
-                                    A[p][1] += o.vy;
-                                    A[p][2] += o.vz;
-                                    nhit[p] += o.hits;
-                                }
+                        if (j != held) {
+                            __syncwarp();
+                            if (lane < kNearF32Vec4)
+                                srec[warp * kNearF32Vec4 + lane] = md.near32[tet * kNearF32Vec4 + lane];
+                            __syncwarp();
+                            held = j;
+                        }
+#pragma unroll 1
+                        while (m) {
+                            const int owner = __ffs(m) - 1;
+                            m &= m - 1u;
+                            const int bi = warp * 32 * P + pp * 32 + owner;
+                            NearOut32 o;
+                            if constexpr (INL)
+                                o = near_pair_f32_body(spts + 9 * bi, srec + warp * kNearF32Vec4,
+                                                       md.near64 + tet * kNearF64, slines, a.lines.f64, a.L, lane);
+                            else
+                                o = near_pair_f32(spts + 9 * bi, srec + warp * kNearF32Vec4, md.near64 + tet * kNearF64,
+                                                  slines, a.lines.f64, a.L, lane);
+                            if (lane == owner) {
+                                kahan(bi, o.vx, o.vy, o.vz);
+                                scnt[BP + bi] += o.hits;
+                            }
                         }
                     }
                     __syncwarp();
                 }
-#pragma unroll
-                for (int p = 0; p < P; ++p)
-#pragma unroll
-                    for (int jj = 0; jj < 3; ++jj) {
-                        const float y = A[p][jj] - acc[p].c[jj];
-                        const float s2 = acc[p].s[jj] + y;
-                        acc[p].c[jj] = (s2 - acc[p].s[jj]) - y;
-                        acc[p].s[jj] = s2;
-                    }
             } else {
                 // float64: direct form in global coordinates
                 double tacc[P][3];
+                V3<double> xp[P];
 #pragma unroll
-                for (int p = 0; p < P; ++p) tacc[p][0] = tacc[p][1] = tacc[p][2] = 0.0;
+                for (int p = 0; p < P; ++p) {
+                    tacc[p][0] = tacc[p][1] = tacc[p][2] = 0.0;
+                    const float *sp = spts + 9 * (slot0 + 32 * p);
+                    xp[p] = mk(join3(sp[0], sp[1], sp[2]), join3(sp[3], sp[4], sp[5]), join3(sp[6], sp[7], sp[8]));
+                }
 #pragma unroll 1
                 for (int j = 0; j < cnt; ++j) {
                     const double *rec = tb + j * RS;
@@ -916,12 +927,12 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         for (int p = 0; p < P; ++p) {
                             const unsigned m = __ballot_sync(0xffffffffu, nearp[p]);
                             if (m) {
-                                if (nearp[p]) {
-                                    const int pos = qn + __popc(m & ((1u << lane) - 1u));
-                                    wq[pos] = (uint16_t)(((p * 32 + lane) << 8) | j);
-                                    ++nnear[p];
+                                if (lane == 0) {
+                                    wm[qn] = m;
+                                    wc[qn] = (uint16_t)((p << 8) | j);
                                 }
-                                qn += __popc(m);
+                                if (nearp[p]) ++scnt[slot0 + 32 * p];
+                                ++qn;
                             }
                         }
                     }
@@ -931,24 +942,29 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                     __syncwarp();
 #pragma unroll 1
                     for (int e = 0; e < qn; ++e) {
-                        const int code = wq[e];
-                        const int slot = code >> 8, j = code & 255;
-                        const int pp = slot >> 5, owner = slot & 31;
-                        const int bi = warp * 32 * P + slot;
+                        unsigned m = wm[e];
+                        const int code = wc[e];
+                        const int pp = code >> 8, j = code & 255;
                         const int64_t tet = t * TILE + j;
-                        const float *sp = spts + 9 * bi;
-                        const V3<double> xd = mk(join3(sp[0], sp[1], sp[2]), join3(sp[3], sp[4], sp[5]),
-                                                 join3(sp[6], sp[7], sp[8]));
-                        const NearOut o = near_pair_f64(xd, md.near64 + tet * kNearF64, a.lines.f64, a.L, lane);
-                        if (lane == owner) {
+#pragma unroll 1
+                        while (m) {
+                            const int owner = __ffs(m) - 1;
+                            m &= m - 1u;
+                            const int bi = warp * 32 * P + pp * 32 + owner;
+                            const float *sp = spts + 9 * bi;
+                            const V3<double> xd = mk(join3(sp[0], sp[1], sp[2]), join3(sp[3], sp[4], sp[5]),
+                                                     join3(sp[6], sp[7], sp[8]));
+                            const NearOut o = near_pair_f64(xd, md.near64 + tet * kNearF64, a.lines.f64, a.L, lane);
+                            if (lane == owner) {
 #pragma unroll
-                            for (int p = 0; p < P; ++p)
-                                if (p == pp) {
-                                    tacc[p][0] += o.vx;
-                                    tacc[p][1] += o.vy;
-                                    tacc[p][2] += o.vz;
-                                    nhit[p] += o.hits;
-                                }
+                                for (int p = 0; p < P; ++p)
+                                    if (p == pp) {
+                                        tacc[p][0] += o.vx;
+                                        tacc[p][1] += o.vy;
+                                        tacc[p][2] += o.vz;
+                                    }
+                                scnt[BP + bi] += o.hits;
+                            }
                         }
                     }
                     __syncwarp();
@@ -956,7 +972,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
 #pragma unroll
                 for (int p = 0; p < P; ++p)
 #pragma unroll
-                    for (int jj = 0; jj < 3; ++jj) acc[p].s[jj] += tacc[p][jj];
+                    for (int jj = 0; jj < 3; ++jj) sacc[jj * BP + slot0 + 32 * p] += tacc[p][jj];
             }
         }
         if (aborted) {
@@ -970,18 +986,20 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
             const int64_t gi = pb * BP + warp * 32 * P + p * 32 + lane;  // position in the spatial order
             if (gi >= k) continue;
             double *dst = md.partial + (ck * k + gi) * 3;
+            const int sl = slot0 + 32 * p;
 #pragma unroll
             for (int jj = 0; jj < 3; ++jj) {
                 if constexpr (F32)
-                    dst[jj] = (double)acc[p].s[jj] - (double)acc[p].c[jj];
+                    dst[jj] = (double)sacc[(2 * jj) * BP + sl] - (double)sacc[(2 * jj + 1) * BP + sl];
                 else
-                    dst[jj] = acc[p].s[jj];
+                    dst[jj] = sacc[jj * BP + sl];
             }
             if (a.counts) {
                 const int64_t src = md.perm[gi];
-                atomicAdd(&a.counts[3 * src + 0], nnear[p]);
-                atomicAdd(&a.counts[3 * src + 1], (int)(ntets_chunk - nnear[p]));
-                atomicAdd(&a.counts[3 * src + 2], nhit[p]);
+                const int nnear = scnt[sl];
+                atomicAdd(&a.counts[3 * src + 0], nnear);
+                atomicAdd(&a.counts[3 * src + 1], (int)(ntets_chunk - nnear));
+                atomicAdd(&a.counts[3 * src + 2], scnt[BP + sl]);
             }
         }
         __syncthreads();  // stages and points are reused by the next item
@@ -1034,8 +1052,11 @@ size_t smem_bytes(int lines_in_smem)
     constexpr int RS = far_stride<T>(Q);
     constexpr size_t NW = NT / 32;
     return round16((size_t)S * (32 + TILE * RS * sizeof(T))) + round16(9 * sizeof(float) * NT * P) +
-           round16(2 * NW * 32 * P * TILE) + round16(sizeof(float4) * NW * kNearF32Vec4) + round16(sizeof(Pipe<S>)) +
-           round16(sizeof(MeshDesc)) + 16 + round16(sizeof(float4) * lines_in_smem);
+           round16(sizeof(uint32_t) * NW * P * TILE) + round16(sizeof(uint16_t) * NW * P * TILE) +
+           round16(sizeof(float4) * NW * kNearF32Vec4) + round16(sizeof(Pipe<S>)) +
+           round16(sizeof(MeshDesc)) + 16 + round16(sizeof(float4) * lines_in_smem) +
+           round16(sizeof(T) * (sizeof(T) == 4 ? 6 : 3) * NT * P) + round16(sizeof(int) * 2 * NT * P) +
+           round16(sizeof(float4) * NW);
 }
 
 template <typename T, int Q, int P, int NT, int TILE, int S, int MINB, bool INL>
@@ -1065,12 +1086,13 @@ struct VariantShape {
     int P, TILE, S, MINB;
     bool INL;  // near-pair routine inlined (no call inside the tile loop)
 };
-constexpr VariantShape kQ1[] = {{2, 32, 4, 4, false}};
-constexpr VariantShape kQ4[] = {{2, 32, 4, 4, false}, {2, 32, 4, 3, false}, {4, 32, 4, 2, false},
-                                {4, 32, 4, 3, false}, {1, 32, 4, 5, false}, {2, 32, 4, 4, true},
-                                {2, 32, 4, 3, true}};
+constexpr VariantShape kQ1[] = {{2, 32, 4, 4, true}};
+constexpr VariantShape kQ4[] = {{3, 32, 2, 4, true},  {2, 32, 4, 3, false}, {4, 32, 4, 2, false},
+                                {2, 32, 2, 4, false}, {1, 32, 4, 5, false}, {2, 32, 3, 4, false},
+                                {2, 32, 4, 3, true},  {3, 32, 3, 4, true},  {2, 32, 4, 5, true},
+                                {2, 32, 3, 4, true},  {4, 32, 3, 3, true},  {3, 32, 3, 4, false}};
 constexpr int kNumQ4 = sizeof(kQ4) / sizeof(kQ4[0]);
-constexpr VariantShape kQ8[] = {{2, 16, 4, 4, false}};
+constexpr VariantShape kQ8[] = {{2, 16, 4, 4, true}};
 constexpr VariantShape kQ27[] = {{1, 16, 4, 4, false}};
 constexpr VariantShape kQ64[] = {{1, 8, 4, 4, false}};
 
@@ -1089,6 +1111,11 @@ cudaError_t dispatch(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
             case 4: return BS_L(4, kQ4[4]);
             case 5: return BS_L(4, kQ4[5]);
             case 6: return BS_L(4, kQ4[6]);
+            case 7: return BS_L(4, kQ4[7]);
+            case 8: return BS_L(4, kQ4[8]);
+            case 9: return BS_L(4, kQ4[9]);
+            case 10: return BS_L(4, kQ4[10]);
+            case 11: return BS_L(4, kQ4[11]);
             default: return BS_L(4, kQ4[0]);
             }
         } else {
