@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import config3_fourier, config3_samples, config4_batch, config5_rings  # noqa: E402
+from workloads import config2_ring, config3_fourier, config3_samples, config4_batch, config5_rings  # noqa: E402
 
 PARAMS = dict(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16)
 METRIC = "node-tet interactions/s (velocity at all nodes, FP32 path)"
@@ -43,7 +43,7 @@ FLOPS_PER_HIT = 80
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ = 2070.0
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "velocity_fp32_fourier64_traffic.json")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_0712_1695_gb300", "csrc", f) for f in ("bs_velocity.cu", "bs_internal.cuh")]
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_0712_1695_gb300", "csrc", f) for f in ("bs_velocity.cu", "bs_near.cuh", "bs_internal.cuh")]
 
 
 def workload_config():
@@ -262,15 +262,87 @@ def rings_workload(args):
     return 0
 
 
+def allray_workload(args):
+    """All-ray evaluation (far_ratio = inf: the ray rule for every pair, the paper's own method) on the
+    32^3 Gaussian-ring mesh, velocity at all 32768 nodes, 8x16 directions, FP32: the all-ray kernel
+    (direction windows) against the velocity kernel's dense all-ray path."""
+    import torch
+
+    import paper_0712_1695_gb300 as bs
+
+    bs.load()
+    m = config2_ring()
+    h = bs.Mesh(m.nodes, m.tets, m.omega)
+    P = dict(PARAMS, far_ratio=float("inf"), precision=bs.BS_FP32)
+    L = P["n_theta"] * P["n_phi"]
+    nodes = m.nodes
+    if args.points:  # a seeded subset of the nodes (small case for profiler captures)
+        nodes = m.nodes[np.sort(np.random.default_rng(2002).permutation(m.n_nodes)[:args.points])]
+    pairs = len(nodes) * m.n_tets
+    stream = torch.cuda.current_stream()
+    pts = torch.from_numpy(nodes).cuda()
+    out = torch.empty_like(pts)
+
+    def timeit(steps, generic):
+        os.environ["BS_ALLRAY_GENERIC"] = "1" if generic else "0"
+        for _ in range(args.warmup if not generic else 1):
+            h.bs_velocity(pts, out_dev=out, **P)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            h.bs_velocity(pts, out_dev=out, **P)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        h.bs_status()
+        return ev0.elapsed_time(ev1) / steps
+
+    with ClockSampler(0) as clk:
+        ms = timeit(args.steps, False)
+    v32 = out.cpu().numpy()
+    ms_dense = timeit(1, True)
+    os.environ["BS_ALLRAY_GENERIC"] = "0"
+    # FP32 against the FP64 all-ray kernel on 512 seeded nodes
+    idx = np.random.default_rng(2002).choice(len(nodes), size=min(512, len(nodes)), replace=False)
+    v64 = h.bs_velocity(torch.from_numpy(nodes[idx]).cuda(), **dict(P, precision=bs.BS_FP64)).cpu().numpy()
+    h.bs_status()
+    err = float(np.linalg.norm(v32[idx] - v64) / (np.sqrt(len(idx)) * np.linalg.norm(v64, axis=1).max()))
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        sel = idx[:256]
+        t = time.perf_counter()
+        oracle.velocity(m.nodes, m.tets, m.omega, nodes[sel], far_ratio=float("inf"),
+                        tet_order=PARAMS["tet_gauss_order"], n_theta=PARAMS["n_theta"], n_phi=PARAMS["n_phi"])
+        dt = time.perf_counter() - t
+        cpu = {"value": len(sel) * m.n_tets / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"{len(sel)} seeded nodes x all {m.n_tets} tets, all-ray ({dt:.1f} s)"}
+    line = {"metric": "node-tet interactions/s (all-ray: ray rule for every pair, FP32 path)",
+            "value": pairs / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"gaussian ring 32^3: {len(nodes)} of {m.n_nodes} nodes x {m.n_tets} tets",
+                       **dict(PARAMS, far_ratio="inf"), "precision": "fp32"},
+            "line_tests_per_s_dense_equivalent": pairs * L / (ms * 1e-3),
+            "dense_loop": {"ms_per_step": ms_dense, "value": pairs / (ms_dense * 1e-3)},
+            "window_over_dense": ms_dense / ms,
+            "fp32_vs_fp64_rms_over_max": err, "cpu_baseline": cpu, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fourier64", choices=["fourier64", "batch", "rings"],
+    ap.add_argument("--workload", default="fourier64", choices=["fourier64", "batch", "rings", "allray"],
                     help="fourier64: the headline workload; batch: 256 uneven meshes, batched vs separate "
-                         "launches; rings: Heun steps of two colliding rings")
+                         "launches; rings: Heun steps of two colliding rings; allray: the ray rule for every "
+                         "pair on the 32^3 ring mesh")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
     ap.add_argument("--batch-count", type=int, default=256, help="meshes in the batch workload")
     ap.add_argument("--batch-only", action="store_true", help="batch workload: skip the separate-launch timing")
@@ -293,6 +365,8 @@ def main():
         return batch_workload(args)
     if args.workload == "rings":
         return rings_workload(args)
+    if args.workload == "allray":
+        return allray_workload(args)
 
     import torch
 

@@ -97,7 +97,9 @@ struct bs_ctx {
     size_t stage_cap = 0;
     // work arrays of bs_rk2_step: x0, v0, v1 (each [n_nodes][3])
     double *rk = nullptr;
-    int occ[2][65][8] = {};  // cached CTAs per SM by [precision][Q][variant]
+    int occ[2][65][kMaxVariants] = {};  // cached CTAs per SM by [precision][Q][variant]
+    int ray_occ[2] = {};                // cached CTAs per SM of the all-ray kernel by [precision]
+    int ray_occ_L[2] = {};              // ... for this many directions
     int variant[2][65] = {};  // chosen kernel variant by [precision][Q] (bs_autotune, or BS_VARIANT)
     // kernel timing (bs_profile)
     bool prof = false;
@@ -397,14 +399,27 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
         return BS_OK;
     }
     const int Q = p->tet_gauss_order;
+    const int L = p->n_phi * p->n_theta;
     BS_CUDA(ensure_lines(h, p->n_phi, p->n_theta, st));
-    BS_CUDA(ensure_far(h, Q, st));
+    // far_ratio = +inf: every pair takes the ray rule, in the all-ray kernel (one point per thread,
+    // direction windows); BS_ALLRAY_GENERIC=1 keeps such calls on the velocity kernel
+    const char *generic_env = getenv("BS_ALLRAY_GENERIC");
+    const bool ray = isinf(p->far_ratio) && !(generic_env && atoi(generic_env) != 0);
+    if (!ray) BS_CUDA(ensure_far(h, Q, st));
 
     int variant = h->variant[p->precision][Q];
     if (const char *env = getenv("BS_VARIANT")) variant = atoi(env);
     if (variant < 0 || variant >= num_variants(p->precision, Q)) variant = 0;
-    const LaunchShape shape = shape_for(p->precision, Q, variant);
-    int &occ = h->occ[p->precision][Q][variant];
+    const LaunchShape shape = ray ? ray_shape() : shape_for(p->precision, Q, variant);
+    int occ_ray = 0;
+    if (ray) {
+        if (h->ray_occ[p->precision] == 0 || h->ray_occ_L[p->precision] != L) {
+            h->ray_occ[p->precision] = std::max(1, ray_ctas_per_sm(p->precision, L));
+            h->ray_occ_L[p->precision] = L;
+        }
+        occ_ray = h->ray_occ[p->precision];
+    }
+    int &occ = ray ? occ_ray : h->occ[p->precision][Q][variant];
     if (occ == 0) occ = std::max(1, velocity_ctas_per_sm(p->precision, Q, variant));
     const int64_t BP = (int64_t)shape.threads * shape.points_per_thread;
     const int64_t n_blocks = (k + BP - 1) / BP;
@@ -434,8 +449,8 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
     a.far_ratio2 = isinf(p->far_ratio) ? INFINITY : p->far_ratio * p->far_ratio;
     a.all_ray = isinf(p->far_ratio) ? 1 : 0;
     a.lines = h->lines;
-    a.L = p->n_phi * p->n_theta;
-    a.smem_lines = a.L <= kSmemLinesMax ? 1 : 0;
+    a.L = L;
+    a.smem_lines = a.L <= (ray ? kRayLinesSmemMax : kSmemLinesMax) ? 1 : 0;
     a.counts = p->counts;
     a.m.out = out_dev;
     a.flag = h->flag;
@@ -458,7 +473,8 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
         }
         h->ev_used.push_back({e0, e1});
     }
-    BS_CUDA(launch_velocity(p->precision, a, h->n_sm, st, &grid, e0, e1));
+    if (ray) BS_CUDA(launch_ray(p->precision, a, h->n_sm, st, &grid, e0, e1));
+    else BS_CUDA(launch_velocity(p->precision, a, h->n_sm, st, &grid, e0, e1));
     BS_CUDA(launch_reduce(a, st));
     if (h->prof) {
         h->prof_kernel += 1;

@@ -155,6 +155,7 @@ struct LaunchShape {
 
 // kernel variants (points per thread, register budget) for a precision and tet rule;
 // all variants of a rule share the tile size (the far records depend on it)
+constexpr int kMaxVariants = 16;  // num_variants() never exceeds this
 int num_variants(int precision, int Q);
 LaunchShape shape_for(int precision, int Q, int variant = 0);
 int velocity_ctas_per_sm(int precision, int Q, int variant = 0);
@@ -162,6 +163,14 @@ int velocity_ctas_per_sm(int precision, int Q, int variant = 0);
 cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
                             cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);
 cudaError_t launch_reduce(const VelocityArgs &a, cudaStream_t st);
+// all-ray kernel (bs_ray.cu): one point per thread, near records streamed in tiles of ray_shape().tile;
+// single-mesh launches (a.meshes == nullptr); the partial sums and the reduction are those of the
+// velocity kernel.  Direction tables of up to kRayLinesSmemMax lines are staged in shared memory.
+constexpr int kRayLinesSmemMax = 4096;
+LaunchShape ray_shape();
+int ray_ctas_per_sm(int precision, int L);
+cudaError_t launch_ray(int precision, const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
+                       cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);
 // Heun step position updates (n_values = 3 * nodes)
 cudaError_t launch_euler(const double *x0, const double *v0, double dt, int64_t n_values, double *x, cudaStream_t st);
 cudaError_t launch_heun(const double *x0, const double *v0, const double *v1, double dt, int64_t n_values, double *x,

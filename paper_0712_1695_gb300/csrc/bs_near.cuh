@@ -1,0 +1,236 @@
+// bs_near.cuh -- device helpers shared by the velocity kernels (bs_velocity.cu) and the
+// all-ray kernel (bs_ray.cu): tolerances of the ray rule, mbarrier / bulk-copy wrappers,
+// small vectors, and the float64 form of the ray rule for one (point, tet) pair.
+#pragma once
+
+#include <math.h>
+
+#include "bs_internal.cuh"
+
+namespace bs {
+namespace {
+
+constexpr float kBoundPadF = 1e-4f;  // relative safety on the bounding-sphere line test
+constexpr double kBoundPadD = 1e-9;
+constexpr double kTau = 1e-9;        // chord length threshold, in units of the longest edge
+constexpr float kDegenA = 1e-5f;     // float32: |a_i| below this with x inside/on the tet -> float64 pair
+// A line with |b_i| <= eps |g_i| (|s . n_i| <= eps) is parallel to face i: that face bounds nothing
+// and the line is outside the tet when a_i < -eps (the oracle's Moller-Trumbore treats
+// |det| <= 1e-12 |e1||e2| as parallel and accepts area coordinates down to -1e-12).
+constexpr double kParD = 1e-12;
+constexpr float kParF = 1e-6f;
+constexpr float kVertexFallback = 1e-5f;
+constexpr long long kWaitCap = 1LL << 26;
+
+// ---------------------------------------------------------------------------
+// mbarrier / bulk-copy helpers (inline PTX, sm_90+ forms valid on sm_103a)
+// ---------------------------------------------------------------------------
+__device__ inline uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ inline void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ inline void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ inline void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false when the cap is reached
+__device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (long long i = 0; i < kWaitCap; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// small vector helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+struct V3 {
+    T x, y, z;
+};
+template <typename T>
+__device__ inline V3<T> mk(T x, T y, T z) { return {x, y, z}; }
+template <typename T>
+__device__ inline T dot3(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+template <typename T>
+__device__ inline T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Everything about a pair that does not depend on the line, in float64.
+struct PairF64 {
+    double a[4];           // lambda_i(x); exactly e_k when x is vertex k
+    V3<double> g[4];       // face-plane gradients, g0 = -(g1 + g2 + g3)
+    V3<double> w[4];       // nodal vorticity
+    V3<double> Wa;         // omega interpolated (linearly extended) at x
+    V3<double> rc;         // centroid - x
+    double rc2, bound, tau_h, par2[4];
+};
+
+__device__ inline int vertex_index(V3<double> x, const double *__restrict__ r)
+{
+    int vk = -1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        if (vk < 0 && r[nf64::V + 3 * i] == x.x && r[nf64::V + 3 * i + 1] == x.y && r[nf64::V + 3 * i + 2] == x.z)
+            vk = i;
+    return vk;
+}
+
+__device__ inline void pair_setup_f64(PairF64 &P, V3<double> x, const double *__restrict__ r, int vk)
+{
+    P.g[1] = mk(r[nf64::G + 0], r[nf64::G + 1], r[nf64::G + 2]);
+    P.g[2] = mk(r[nf64::G + 3], r[nf64::G + 4], r[nf64::G + 5]);
+    P.g[3] = mk(r[nf64::G + 6], r[nf64::G + 7], r[nf64::G + 8]);
+    P.g[0] = mk(-(P.g[1].x + P.g[2].x + P.g[3].x), -(P.g[1].y + P.g[2].y + P.g[3].y),
+                -(P.g[1].z + P.g[2].z + P.g[3].z));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) P.w[i] = mk(r[nf64::W + 3 * i], r[nf64::W + 3 * i + 1], r[nf64::W + 3 * i + 2]);
+    if (vk >= 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) P.a[i] = (i == vk) ? 1.0 : 0.0;
+    } else {
+        const V3<double> d0 = mk(x.x - r[nf64::V], x.y - r[nf64::V + 1], x.z - r[nf64::V + 2]);
+        P.a[1] = dot3(P.g[1], d0);
+        P.a[2] = dot3(P.g[2], d0);
+        P.a[3] = dot3(P.g[3], d0);
+        P.a[0] = 1.0 - P.a[1] - P.a[2] - P.a[3];
+    }
+    const double *a = P.a;
+    P.Wa = mk(a[0] * P.w[0].x + a[1] * P.w[1].x + a[2] * P.w[2].x + a[3] * P.w[3].x,
+              a[0] * P.w[0].y + a[1] * P.w[1].y + a[2] * P.w[2].y + a[3] * P.w[3].y,
+              a[0] * P.w[0].z + a[1] * P.w[1].z + a[2] * P.w[2].z + a[3] * P.w[3].z);
+    P.rc = mk(r[nf64::C] - x.x, r[nf64::C + 1] - x.y, r[nf64::C + 2] - x.z);
+    P.rc2 = dot3(P.rc, P.rc);
+    P.bound = r[nf64::RB2] * (1.0 + kBoundPadD);
+    P.tau_h = kTau * r[nf64::H];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) P.par2[i] = kParD * kParD * dot3(P.g[i], P.g[i]);
+}
+
+// One line in float64; adds k * s x J to acc and returns true on a hit.
+__device__ inline bool line_f64(const PairF64 &P, const dbl4 ln, V3<double> &acc)
+{
+    const V3<double> s = mk(ln.x, ln.y, ln.z);
+    const double rs = dot3(P.rc, s);
+    if (P.rc2 - rs * rs > P.bound) return false;  // line farther than Rb from the centroid
+    double b[4];
+    b[1] = dot3(P.g[1], s);
+    b[2] = dot3(P.g[2], s);
+    b[3] = dot3(P.g[3], s);
+    b[0] = -(b[1] + b[2] + b[3]);
+    double lo = -INFINITY, hi = INFINITY;
+    bool empty = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (b[i] * b[i] <= P.par2[i]) empty = empty || (P.a[i] < -kParD);
+        else if (b[i] > 0.0) lo = fmax(lo, -P.a[i] / b[i]);
+        else hi = fmin(hi, -P.a[i] / b[i]);
+    }
+    if (empty || !(hi - lo > P.tau_h)) return false;
+    const V3<double> *w = P.w;
+    const V3<double> Wb = mk(b[0] * w[0].x + b[1] * w[1].x + b[2] * w[2].x + b[3] * w[3].x,
+                             b[0] * w[0].y + b[1] * w[1].y + b[2] * w[2].y + b[3] * w[3].y,
+                             b[0] * w[0].z + b[1] * w[1].z + b[2] * w[2].z + b[3] * w[3].z);
+    const double f1 = fabs(hi) - fabs(lo);
+    const double f2 = 0.5 * (hi * fabs(hi) - lo * fabs(lo));
+    const V3<double> J = mk(f1 * P.Wa.x + f2 * Wb.x, f1 * P.Wa.y + f2 * Wb.y, f1 * P.Wa.z + f2 * Wb.z);
+    acc.x += ln.w * (s.y * J.z - s.z * J.y);
+    acc.y += ln.w * (s.z * J.x - s.x * J.z);
+    acc.z += ln.w * (s.x * J.y - s.y * J.x);
+    return true;
+}
+
+// One line in float64 with the record read from memory as it is needed (a
+// small register footprint: used for the rare float64 steps of the float32
+// path).  vk = vertex index of x in the tet or -1.
+__device__ __noinline__ bool line_f64_lean(V3<double> x, const double *__restrict__ r, int vk, const dbl4 ln,
+                                           V3<double> &acc)
+{
+    const V3<double> s = mk(ln.x, ln.y, ln.z);
+    {
+        const V3<double> rc = mk(r[nf64::C] - x.x, r[nf64::C + 1] - x.y, r[nf64::C + 2] - x.z);
+        const double rs = dot3(rc, s);
+        if (dot3(rc, rc) - rs * rs > r[nf64::RB2] * (1.0 + kBoundPadD)) return false;
+    }
+    double a[4], b[4];
+    {
+        const V3<double> d0 = mk(x.x - r[nf64::V], x.y - r[nf64::V + 1], x.z - r[nf64::V + 2]);
+        double sa = 0.0, sb = 0.0;
+        for (int i = 1; i < 4; ++i) {
+            const V3<double> g = mk(r[nf64::G + 3 * i - 3], r[nf64::G + 3 * i - 2], r[nf64::G + 3 * i - 1]);
+            a[i] = dot3(g, d0);
+            b[i] = dot3(g, s);
+            sa += a[i];
+            sb += b[i];
+        }
+        a[0] = 1.0 - sa;
+        b[0] = -sb;
+        if (vk >= 0)
+            for (int i = 0; i < 4; ++i) a[i] = (i == vk) ? 1.0 : 0.0;
+    }
+    double lo = -INFINITY, hi = INFINITY;
+    bool empty = false;
+    for (int i = 0; i < 4; ++i) {
+        V3<double> g;
+        if (i == 0) {
+            g = mk(0.0, 0.0, 0.0);
+            for (int j = 1; j < 4; ++j) {
+                g.x -= r[nf64::G + 3 * j - 3];
+                g.y -= r[nf64::G + 3 * j - 2];
+                g.z -= r[nf64::G + 3 * j - 1];
+            }
+        } else {
+            g = mk(r[nf64::G + 3 * i - 3], r[nf64::G + 3 * i - 2], r[nf64::G + 3 * i - 1]);
+        }
+        if (b[i] * b[i] <= kParD * kParD * dot3(g, g)) empty = empty || (a[i] < -kParD);
+        else if (b[i] > 0.0) lo = fmax(lo, -a[i] / b[i]);
+        else hi = fmin(hi, -a[i] / b[i]);
+    }
+    if (empty || !(hi - lo > kTau * r[nf64::H])) return false;
+    const double f1 = fabs(hi) - fabs(lo);
+    const double f2 = 0.5 * (hi * fabs(hi) - lo * fabs(lo));
+    V3<double> J = mk(0.0, 0.0, 0.0);
+    for (int i = 0; i < 4; ++i) {
+        const double c = f1 * a[i] + f2 * b[i];
+        J.x += c * r[nf64::W + 3 * i];
+        J.y += c * r[nf64::W + 3 * i + 1];
+        J.z += c * r[nf64::W + 3 * i + 2];
+    }
+    acc.x += ln.w * (s.y * J.z - s.z * J.y);
+    acc.y += ln.w * (s.z * J.x - s.x * J.z);
+    acc.z += ln.w * (s.x * J.y - s.y * J.x);
+    return true;
+}
+
+}  // namespace
+}  // namespace bs
