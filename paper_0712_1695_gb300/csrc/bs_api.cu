@@ -402,9 +402,10 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
     const int L = p->n_phi * p->n_theta;
     BS_CUDA(ensure_lines(h, p->n_phi, p->n_theta, st));
     // far_ratio = +inf: every pair takes the ray rule, in the all-ray kernel (one point per thread,
-    // direction windows); BS_ALLRAY_GENERIC=1 keeps such calls on the velocity kernel
+    // direction windows, the direction table in shared memory: up to kRayLinesSmemMax lines);
+    // BS_ALLRAY_GENERIC=1 keeps such calls on the velocity kernel
     const char *generic_env = getenv("BS_ALLRAY_GENERIC");
-    const bool ray = isinf(p->far_ratio) && !(generic_env && atoi(generic_env) != 0);
+    const bool ray = isinf(p->far_ratio) && L <= kRayLinesSmemMax && !(generic_env && atoi(generic_env) != 0);
     if (!ray) BS_CUDA(ensure_far(h, Q, st));
 
     int variant = h->variant[p->precision][Q];

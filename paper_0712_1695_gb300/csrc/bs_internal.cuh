@@ -165,7 +165,8 @@ cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cuda
 cudaError_t launch_reduce(const VelocityArgs &a, cudaStream_t st);
 // all-ray kernel (bs_ray.cu): one point per thread, near records streamed in tiles of ray_shape().tile;
 // single-mesh launches (a.meshes == nullptr); the partial sums and the reduction are those of the
-// velocity kernel.  Direction tables of up to kRayLinesSmemMax lines are staged in shared memory.
+// velocity kernel.  The float32 direction table is staged in shared memory: the host uses this kernel
+// for tables of up to kRayLinesSmemMax lines only.
 constexpr int kRayLinesSmemMax = 4096;
 LaunchShape ray_shape();
 int ray_ctas_per_sm(int precision, int L);

@@ -13,12 +13,15 @@
 // Direction window.  A line x + t s can reach the tet only if it passes within Rb of the
 // centroid c (the bounding-sphere test of the ray rule); with u the direction of c - x and
 // sin(alpha) = Rb / |c - x|, that needs s within alpha of u or of -u, so its polar angle
-// phi lies within alpha of phi(u) or of pi - phi(u).  Only the phi-rings of the direction
-// table (Eq. 3: l = n * n_theta + m, phi ascending in n) inside those two windows are
+// phi lies within alpha of phi(u) or of pi - phi(u).  The warp's 32 points lie in a small
+// ball (they are consecutive in the spatial order), so one window, widened by the angle the
+// ball subtends, serves the warp: its lanes take the same lines in lock step (broadcast
+// reads of the direction table, no divergence between lanes' loops).  Only the phi-rings of
+// the direction table (Eq. 3: l = n * n_theta + m, phi ascending in n) inside the window are
 // visited, padded by more than the rounding of the float32 test; every visited line still
-// takes the exact bounding-sphere test, so the set of lines that contribute is the one of
-// the dense loop over all n_phi * n_theta lines.  For a tet a few sizes away this visits one
-// or two rings instead of all of them.
+// takes each lane's exact bounding-sphere test, so the set of lines that contribute is the
+// one of the dense loop over all n_phi * n_theta lines.  For a tet a few warp sizes away this
+// visits a few rings instead of all of them.
 //
 // Per line the arithmetic is the velocity kernel's (barycentric clipping of the line,
 // Eq. 5 with sign(t)); float64 steps for the same degenerate cases: x a vertex of the tet
@@ -64,34 +67,35 @@ __device__ inline int ring_bound(const T *z, int n, T v, bool upper)
     return lo;
 }
 
-// Rings [a0, a1) and [b0, b1) (ascending, disjoint) whose lines can pass the bounding-sphere
-// test for a centroid offset rc (|rc|^2 = rc2) and the test's radius^2 bound.  With
-// sin(alpha) = sqrt(bound / rc2), a passing line has |s.u| >= cos(alpha) (u = rc/|rc|), so its
-// polar angle is within alpha of phi(u) or of pi - phi(u).  The window is widened to alpha' =
-// alpha + pad with pad = 2e-3 + 1e-6 / sin(alpha) radians: the float32 test decides
-// |rc|^2 - (rc.s)^2 <= bound with an absolute error of about 1.1e-6 |rc|^2, which can admit lines
-// up to sqrt(sin^2 alpha + 1.1e-6) - sin alpha <= min(1.05e-3, 5.5e-7 / sin alpha) radians
-// outside the cone, and the pad also covers the rounding of the window and of the table's z_n.
-// sin(alpha') and cos(alpha') are bounded (not evaluated): sin(alpha') <= sin(alpha) +
-// cos(alpha) pad and cos(alpha') >= cos(alpha)(1 - pad^2/2) - sin(alpha) pad, which can only
-// widen the window.  The windows are intervals of z = cos(phi): [zlo, zhi] for u, [-zhi, -zlo]
-// for -u.
+// Rings [a0, a1) and [b0, b1) (ascending, disjoint) holding every line that can pass the
+// bounding-sphere test of a tet (centroid c, test radius^2 bound, R = sqrt(bound)) for any point
+// of a ball (centre cw, radius rw; D = c - cw, d = |D|).  For a point x of the ball a passing line
+// has its direction within alpha_x of +-u_x (u_x = (c - x)/|c - x|, sin alpha_x = R/|c - x|),
+// and u_x is within beta of u = D/d (sin beta = rw/d, the largest angle the ball subtends from
+// c); with |c - x| >= d - rw, every such line is within alpha + beta of +-u, sin alpha =
+// R/(d - rw).  The angle is padded by 2e-3 + 1e-6 (d + rw)/R radians: the float32 test decides
+// |rc|^2 - (rc.s)^2 <= bound with an absolute error of about 1.1e-6 |rc|^2, which admits lines at
+// most min(1.05e-3, 5.5e-7 |rc|/R) radians outside the exact cone, and the pad also covers the
+// rounding of the window and of the table's z_n.  The sine and cosine of the padded angle are
+// bounded (the pad's sine by the pad, its cosine by 1 - pad^2/2), which can only widen the
+// window.  The windows are intervals of z = cos(phi): [zlo, zhi] around u, [-zhi, -zlo] around -u.
 template <typename T>
-__device__ inline void ring_window(const T *z, int N, V3<T> rc, T rc2, T bound, int &a0, int &a1, int &b0, int &b1)
+__device__ inline void ring_window(const T *z, int N, V3<T> D, T rw, T bound, int &a0, int &a1, int &b0, int &b1)
 {
     a0 = 0;
     a1 = N;
     b0 = b1 = 0;
-    const T sa2 = bound / rc2;
-    if (!(sa2 < (T)0.99)) return;  // x inside or near the bounding sphere: every ring
-    const T sa = sqrt(sa2), ca = sqrt((T)1 - sa2);
-    const T pad = (T)2e-3 + (T)1e-6 / sa;
-    if (pad > (T)0.25) return;
-    const T sA = min((T)1, sa + ca * pad);
-    const T cA = ca * ((T)1 - (T)0.5 * pad * pad) - sa * pad;
+    const T d = sqrt(dot3(D, D)), R = sqrt(bound);
+    if (!(d - rw > (T)1.01 * R)) return;  // the ball reaches the tet's bounding sphere: every ring
+    const T s1 = R / (d - rw), s2 = rw / d;
+    const T c1 = sqrt((T)1 - s1 * s1), c2 = sqrt((T)1 - s2 * s2);
+    const T sab = s1 * c2 + c1 * s2, cab = c1 * c2 - s1 * s2;  // sin, cos of alpha + beta
+    const T pad = (T)2e-3 + (T)1e-6 * (d + rw) / R;
+    if (!(pad < (T)0.25) || !(cab > (T)0)) return;
+    const T sA = min((T)1, sab + cab * pad);
+    const T cA = cab * ((T)1 - (T)0.5 * pad * pad) - sab * pad;
     if (!(cA > (T)0)) return;
-    const T ir = (T)1 / sqrt(rc2);
-    const T uz = rc.z * ir, su = sqrt(rc.x * rc.x + rc.y * rc.y) * ir;
+    const T uz = D.z / d, su = sqrt(D.x * D.x + D.y * D.y) / d;
     const T zhi = uz <= cA ? uz * cA + su * sA : (T)1;   // cos(max(phi_u - alpha', 0))
     const T zlo = uz >= -cA ? uz * cA - su * sA : (T)-1;  // cos(min(phi_u + alpha', pi))
     a0 = ring_bound(z, N, zhi, false);
@@ -111,96 +115,93 @@ __device__ inline void ring_window(const T *z, int N, V3<T> rc, T rc2, T bound, 
     }
 }
 
-// First line of the windows that passes the bounding-sphere test, or -1.
-template <typename T, typename LN>
-__device__ inline int first_passing(const LN *lines, int M, V3<T> rc, T rc2, T bound, int a0, int a1, int b0, int b1)
-{
-#pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
-        const int l0 = (pass ? b0 : a0) * M, l1 = (pass ? b1 : a1) * M;
-#pragma unroll 1
-        for (int l = l0; l < l1; ++l) {
-            const LN ln = lines[l];
-            const T rs = rc.x * (T)ln.x + rc.y * (T)ln.y + rc.z * (T)ln.z;
-            if (!(rc2 - rs * rs > bound)) return l;
-        }
-    }
-    return -1;
-}
-
-// float32 ray rule for one (point, tet) pair, one thread.  xs: the point as float splits
-// [component][hi, mid, lo]; r32: the near record (shared memory); r64: its float64 copy
-// (global, read only by the float64 steps); z: cos(phi_n) of the rings.  Adds the pair's
-// k s x J to (ax, ay, az).  The line-independent set-up runs once, after the first line that
-// passes the bounding-sphere test is found (all lanes of the warp that need it run it together).
-__device__ __forceinline__ void ray_pair_f32(const float *__restrict__ xs, const float4 *__restrict__ r32,
-                                             const double *__restrict__ r64, const float4 *__restrict__ lines,
-                                             const dbl4 *__restrict__ lines64, const float *__restrict__ z, int N,
-                                             int M, float &ax, float &ay, float &az, int &hits)
+// float32 ray rule for one tet against the 32 points of a warp (one per lane).  The warp
+// tests the window's lines in lock step, 32 at a time (broadcast reads of the direction
+// table in shared memory), each lane keeping a mask of the lines its own point passes; the
+// line-independent set-up then runs once for the warp, and each lane clips only its own
+// passing lines.  xs: the lane's point as float splits [component][hi, mid, lo]; r32: the
+// near record (shared memory); r64: its float64 copy (global, read only by the float64
+// steps); [a0, a1), [b0, b1): the warp's rings.  Adds the pair's k s x J to (ax, ay, az).
+__device__ __forceinline__ void ray_tet_f32(const float *__restrict__ xs, const float4 *__restrict__ r32,
+                                            const double *__restrict__ r64, const float4 *__restrict__ lines,
+                                            const dbl4 *__restrict__ lines64, int M, int a0, int a1, int b0, int b1,
+                                            float &ax, float &ay, float &az, int &hits)
 {
     const float xh0 = xs[0], xm0 = xs[1], xh1 = xs[3], xm1 = xs[4], xh2 = xs[6], xm2 = xs[7];
     const float4 ch = r32[nf32::CH], cm = r32[nf32::CM];
     const V3<float> rc = mk((ch.x - xh0) + (cm.x - xm0), (ch.y - xh1) + (cm.y - xm1), (ch.z - xh2) + (cm.z - xm2));
     const float rc2 = dot3(rc, rc);
     const float bound = r32[nf32::G2].w * (1.0f + kBoundPadF);
-    int a0, a1, b0, b1;
-    ring_window<float>(z, N, rc, rc2, bound, a0, a1, b0, b1);
-    const int lf = first_passing<float>(lines, M, rc, rc2, bound, a0, a1, b0, b1);
-    if (lf < 0) return;
+    // window position w -> line l: the rings [a0, a1) then [b0, b1), n_theta lines each
+    const int nA = (a1 - a0) * M, nW = nA + (b1 - b0) * M;
+    const int lA = a0 * M, lB = b0 * M - nA;
 
-    // line-independent state
+    bool ready = false;  // warp-uniform
     int vk = -1;
     bool whole_f64 = false;
-    float a[4], par2[4], fb2[4];
-    V3<float> g[4], w[4];
-    const float *vh = reinterpret_cast<const float *>(r32 + nf32::VH);
-    const float *vm = reinterpret_cast<const float *>(r32 + nf32::VM);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-        if (vk < 0 && vh[3 * i] == xh0 && vm[3 * i] == xm0 && vh[3 * i + 1] == xh1 && vm[3 * i + 1] == xm1 &&
-            vh[3 * i + 2] == xh2 && vm[3 * i + 2] == xm2)
-            vk = i;
-    const float4 q0 = r32[nf32::G1], q1 = r32[nf32::G2], q2 = r32[nf32::G3];
-    g[1] = mk(q0.x, q0.y, q0.z);
-    g[2] = mk(q1.x, q1.y, q1.z);
-    g[3] = mk(q2.x, q2.y, q2.z);
-    g[0] = mk(-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z));
-    if (vk >= 0) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = (i == vk) ? 1.0f : 0.0f;
-    } else {
-        const V3<float> d0 =
-            mk((xh0 - vh[0]) + (xm0 - vm[0]), (xh1 - vh[1]) + (xm1 - vm[1]), (xh2 - vh[2]) + (xm2 - vm[2]));
-        a[1] = dot3(g[1], d0);
-        a[2] = dot3(g[2], d0);
-        a[3] = dot3(g[3], d0);
-        a[0] = 1.0f - a[1] - a[2] - a[3];
-        const float amin = fminf(fminf(a[0], a[1]), fminf(a[2], a[3]));
-        const float aabs = fminf(fminf(fabsf(a[0]), fabsf(a[1])), fminf(fabsf(a[2]), fabsf(a[3])));
-        whole_f64 = amin > -kDegenA && aabs < kDegenA;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 t = r32[nf32::W + i];
-        w[i] = mk(t.x, t.y, t.z);
-        const float gg = dot3(g[i], g[i]);
-        par2[i] = kParF * kParF * gg;
-        fb2[i] = (vk >= 0 && i != vk) ? kVertexFallback * kVertexFallback * gg : -1.0f;
-    }
-    const V3<float> Wa = mk(a[0] * w[0].x + a[1] * w[1].x + a[2] * w[2].x + a[3] * w[3].x,
-                            a[0] * w[0].y + a[1] * w[1].y + a[2] * w[2].y + a[3] * w[3].y,
-                            a[0] * w[0].z + a[1] * w[1].z + a[2] * w[2].z + a[3] * w[3].z);
-    const float tau_h = (float)kTau * q0.w;
-
+    float a[4], par2[4], fb2[4], tau_h = 0.f;
+    V3<float> g[4], w[4], Wa = mk(0.f, 0.f, 0.f);
 #pragma unroll 1
-    for (int pass = 0; pass < 2; ++pass) {
-        const int l1 = (pass ? b1 : a1) * M;
+    for (int w0 = 0; w0 < nW; w0 += 32) {
+        const int nw = min(32, nW - w0);
+        uint32_t mine = 0u;  // lines of this group that this lane's point passes
+#pragma unroll 4
+        for (int i = 0; i < nw; ++i) {
+            const int wi = w0 + i;
+            const float4 ln = lines[wi < nA ? lA + wi : lB + wi];
+            const float rs = rc.x * ln.x + rc.y * ln.y + rc.z * ln.z;
+            if (!(rc2 - rs * rs > bound)) mine |= 1u << i;
+        }
+        if (!__any_sync(0xffffffffu, mine != 0u)) continue;
+        if (!ready) {
+            ready = true;
+            const float *vh = reinterpret_cast<const float *>(r32 + nf32::VH);
+            const float *vm = reinterpret_cast<const float *>(r32 + nf32::VM);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (vk < 0 && vh[3 * i] == xh0 && vm[3 * i] == xm0 && vh[3 * i + 1] == xh1 && vm[3 * i + 1] == xm1 &&
+                    vh[3 * i + 2] == xh2 && vm[3 * i + 2] == xm2)
+                    vk = i;
+            const float4 q0 = r32[nf32::G1], q1 = r32[nf32::G2], q2 = r32[nf32::G3];
+            g[1] = mk(q0.x, q0.y, q0.z);
+            g[2] = mk(q1.x, q1.y, q1.z);
+            g[3] = mk(q2.x, q2.y, q2.z);
+            g[0] = mk(-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z));
+            if (vk >= 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = (i == vk) ? 1.0f : 0.0f;
+            } else {
+                const V3<float> d0 =
+                    mk((xh0 - vh[0]) + (xm0 - vm[0]), (xh1 - vh[1]) + (xm1 - vm[1]), (xh2 - vh[2]) + (xm2 - vm[2]));
+                a[1] = dot3(g[1], d0);
+                a[2] = dot3(g[2], d0);
+                a[3] = dot3(g[3], d0);
+                a[0] = 1.0f - a[1] - a[2] - a[3];
+                const float amin = fminf(fminf(a[0], a[1]), fminf(a[2], a[3]));
+                const float aabs = fminf(fminf(fabsf(a[0]), fabsf(a[1])), fminf(fabsf(a[2]), fabsf(a[3])));
+                whole_f64 = amin > -kDegenA && aabs < kDegenA;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 t = r32[nf32::W + i];
+                w[i] = mk(t.x, t.y, t.z);
+                const float gg = dot3(g[i], g[i]);
+                par2[i] = kParF * kParF * gg;
+                fb2[i] = (vk >= 0 && i != vk) ? kVertexFallback * kVertexFallback * gg : -1.0f;
+            }
+            Wa = mk(a[0] * w[0].x + a[1] * w[1].x + a[2] * w[2].x + a[3] * w[3].x,
+                    a[0] * w[0].y + a[1] * w[1].y + a[2] * w[2].y + a[3] * w[3].y,
+                    a[0] * w[0].z + a[1] * w[1].z + a[2] * w[2].z + a[3] * w[3].z);
+            tau_h = (float)kTau * q0.w;
+        }
 #pragma unroll 1
-        for (int l = max((pass ? b0 : a0) * M, lf); l < l1; ++l) {
+        while (mine) {
+            const int i = __ffs(mine) - 1;
+            mine &= mine - 1u;
+            const int wi = w0 + i;
+            const int l = wi < nA ? lA + wi : lB + wi;
             const float4 ln = lines[l];
             const V3<float> s = mk(ln.x, ln.y, ln.z);
-            const float rs = dot3(rc, s);
-            if (rc2 - rs * rs > bound) continue;
             float b[4];
             b[1] = dot3(g[1], s);
             b[2] = dot3(g[2], s);
@@ -208,7 +209,7 @@ __device__ __forceinline__ void ray_pair_f32(const float *__restrict__ xs, const
             b[0] = -(b[1] + b[2] + b[3]);
             bool redo = whole_f64;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) redo = redo || (b[i] * b[i] <= fb2[i]);
+            for (int k = 0; k < 4; ++k) redo = redo || (b[k] * b[k] <= fb2[k]);
             if (redo) {
                 // rare: this line in float64 (the point's exact coordinates from its splits)
                 const V3<double> xd =
@@ -223,10 +224,10 @@ __device__ __forceinline__ void ray_pair_f32(const float *__restrict__ xs, const
             float lo = -INFINITY, hi = INFINITY;
             bool empty = false;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (b[i] * b[i] <= par2[i]) empty = empty || (a[i] < -kParF);
-                else if (b[i] > 0.f) lo = fmaxf(lo, -a[i] / b[i]);
-                else hi = fminf(hi, -a[i] / b[i]);
+            for (int k = 0; k < 4; ++k) {
+                if (b[k] * b[k] <= par2[k]) empty = empty || (a[k] < -kParF);
+                else if (b[k] > 0.f) lo = fmaxf(lo, -a[k] / b[k]);
+                else hi = fminf(hi, -a[k] / b[k]);
             }
             if (empty || !(hi - lo > tau_h)) continue;
             const V3<float> Wb = mk(b[0] * w[0].x + b[1] * w[1].x + b[2] * w[2].x + b[3] * w[3].x,
@@ -243,26 +244,31 @@ __device__ __forceinline__ void ray_pair_f32(const float *__restrict__ xs, const
     }
 }
 
-// float64 ray rule for one pair, one thread (the velocity kernel's line_f64 per line).
-__device__ __forceinline__ void ray_pair_f64(V3<double> x, const double *__restrict__ r,
-                                             const dbl4 *__restrict__ lines64, const double *__restrict__ z, int N,
-                                             int M, V3<double> &acc, int &hits)
+// float64 form of ray_tet_f32 (the velocity kernel's line_f64 per line); r: the near record.
+__device__ __forceinline__ void ray_tet_f64(V3<double> x, const double *__restrict__ r,
+                                            const dbl4 *__restrict__ lines64, int M, int a0, int a1, int b0, int b1,
+                                            V3<double> &acc, int &hits)
 {
     const V3<double> rc = mk(r[nf64::C] - x.x, r[nf64::C + 1] - x.y, r[nf64::C + 2] - x.z);
     const double rc2 = dot3(rc, rc);
     const double bound = r[nf64::RB2] * (1.0 + kBoundPadD);
-    int a0, a1, b0, b1;
-    ring_window<double>(z, N, rc, rc2, bound, a0, a1, b0, b1);
-    const int lf = first_passing<double>(lines64, M, rc, rc2, bound, a0, a1, b0, b1);
-    if (lf < 0) return;
     PairF64 P;
-    pair_setup_f64(P, x, r, vertex_index(x, r));
+    bool ready = false;  // warp-uniform
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
         const int l1 = (pass ? b1 : a1) * M;
 #pragma unroll 1
-        for (int l = max((pass ? b0 : a0) * M, lf); l < l1; ++l)
-            if (line_f64(P, lines64[l], acc)) ++hits;
+        for (int l = (pass ? b0 : a0) * M; l < l1; ++l) {
+            const dbl4 ln = lines64[l];
+            const double rs = rc.x * ln.x + rc.y * ln.y + rc.z * ln.z;
+            const bool near_line = !(rc2 - rs * rs > bound);
+            if (!__any_sync(0xffffffffu, near_line)) continue;
+            if (!ready) {
+                pair_setup_f64(P, x, r, vertex_index(x, r));
+                ready = true;
+            }
+            if (near_line && line_f64(P, ln, acc)) ++hits;
+        }
     }
 }
 
@@ -287,11 +293,9 @@ __global__ void __launch_bounds__(kRayThreads) ray_kernel(const VelocityArgs a)
     const int N = a.lines.n_phi, M = a.lines.n_theta;
     // cos(phi_n) of each ring (descending in n) and, for float32, the direction table
     for (int n = tid; n < N; n += kRayThreads) sz[n] = (T)a.lines.f64[n * M].z;
-    const float4 *slines = a.lines.f32;
-    if (F32 && a.smem_lines) {
+    // the float32 direction table in shared memory (the host sends larger tables to the velocity kernel)
+    if (F32)
         for (int l = tid; l < a.L; l += kRayThreads) sdir[l] = a.lines.f32[l];
-        slines = sdir;
-    }
     if (tid == 0) {
         for (int st = 0; st < kRayStages; ++st) {
             mbar_init(&pipe->full[st], 1);
@@ -346,6 +350,25 @@ __global__ void __launch_bounds__(kRayThreads) ray_kernel(const VelocityArgs a)
 #pragma unroll
         for (int j = 0; j < 3; ++j) split3(md.pts[3 * src + j], xs[3 * j], xs[3 * j + 1], xs[3 * j + 2]);
         const V3<double> xd = mk(md.pts[3 * src], md.pts[3 * src + 1], md.pts[3 * src + 2]);
+        // bounding ball of the warp's 32 points (float, padded): the direction windows are the warp's
+        float cwx, cwy, cwz, rw;
+        {
+            float mnx = xs[0], mxx = mnx, mny = xs[3], mxy = mny, mnz = xs[6], mxz = mnz;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+                mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+                mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+                mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+                mnz = fminf(mnz, __shfl_xor_sync(0xffffffffu, mnz, o));
+                mxz = fmaxf(mxz, __shfl_xor_sync(0xffffffffu, mxz, o));
+            }
+            cwx = 0.5f * (mnx + mxx);
+            cwy = 0.5f * (mny + mxy);
+            cwz = 0.5f * (mnz + mxz);
+            const float ex = mxx - mnx, ey = mxy - mny, ez = mxz - mnz;
+            rw = 0.5f * sqrtf(ex * ex + ey * ey + ez * ez) * 1.001f + 1e-6f;
+        }
 
         float ks[3] = {0.f, 0.f, 0.f}, kc[3] = {0.f, 0.f, 0.f};  // float32: Kahan sum across tiles
         V3<double> acc64 = mk(0.0, 0.0, 0.0);                    // float64: plain sum
@@ -365,10 +388,15 @@ __global__ void __launch_bounds__(kRayThreads) ray_kernel(const VelocityArgs a)
             if constexpr (F32) {
                 float ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll 1
-                for (int j = 0; j < cnt; ++j)
-                    ray_pair_f32(xs, reinterpret_cast<const float4 *>(tb) + j * kNearF32Vec4,
-                                 md.near64 + (t * kRayTile + j) * kNearF64, slines, a.lines.f64, sz, N, M, ax, ay,
-                                 az, hits);
+                for (int j = 0; j < cnt; ++j) {
+                    const float4 *r32 = reinterpret_cast<const float4 *>(tb) + j * kNearF32Vec4;
+                    const float4 ch = r32[nf32::CH];
+                    int a0, a1, b0, b1;
+                    ring_window<float>(sz, N, mk(ch.x - cwx, ch.y - cwy, ch.z - cwz), rw,
+                                       r32[nf32::G2].w * (1.0f + kBoundPadF), a0, a1, b0, b1);
+                    ray_tet_f32(xs, r32, md.near64 + (t * kRayTile + j) * kNearF64, sdir, a.lines.f64, M, a0, a1, b0,
+                                b1, ax, ay, az, hits);
+                }
                 const float v[3] = {ax, ay, az};
 #pragma unroll
                 for (int jj = 0; jj < 3; ++jj) {
@@ -379,9 +407,13 @@ __global__ void __launch_bounds__(kRayThreads) ray_kernel(const VelocityArgs a)
                 }
             } else {
 #pragma unroll 1
-                for (int j = 0; j < cnt; ++j)
-                    ray_pair_f64(xd, reinterpret_cast<const double *>(tb) + j * kNearF64, a.lines.f64, sz, N, M,
-                                 acc64, hits);
+                for (int j = 0; j < cnt; ++j) {
+                    const double *r = reinterpret_cast<const double *>(tb) + j * kNearF64;
+                    int a0, a1, b0, b1;
+                    ring_window<double>(sz, N, mk(r[nf64::C] - cwx, r[nf64::C + 1] - cwy, r[nf64::C + 2] - cwz),
+                                        (double)rw, r[nf64::RB2] * (1.0 + kBoundPadD), a0, a1, b0, b1);
+                    ray_tet_f64(xd, r, a.lines.f64, M, a0, a1, b0, b1, acc64, hits);
+                }
             }
             // this warp is done with stage st; the last warp to finish refills it
             __syncwarp();
@@ -437,7 +469,7 @@ template <typename T>
 cudaError_t ray_launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out, int *occ_out, bool query)
 {
     auto kern = ray_kernel<T>;
-    const size_t sm = ray_smem_bytes<T>(sizeof(T) == 4 && a.smem_lines ? a.L : 0);
+    const size_t sm = ray_smem_bytes<T>(sizeof(T) == 4 ? a.L : 0);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int occ = 0;
