@@ -153,3 +153,16 @@ def test_ring_mesh_full_size_sampled_against_oracle(orc):
     assert np.array_equal(c[idx, :2], co[:, :2])
     v64, _ = gpu_velocity(h, m.nodes[idx], bs.BS_FP64, **ALLRAY)
     assert rel_l2(v64, vo) <= TOL_FP64_REL_L2
+
+
+def test_direction_tables_beyond_shared_memory_use_the_dense_path(orc):
+    """n_phi * n_theta > 4096: the call goes to the velocity kernel's all-ray path and still matches."""
+    m = config1_plain()
+    tets = m.tets[:40]
+    h = bs.Mesh(m.nodes, tets, m.omega)
+    pts = m.nodes[::37]
+    p = dict(far_ratio=np.inf, tet_gauss_order=4, n_theta=64, n_phi=80)
+    v, c = gpu_velocity(h, pts, bs.BS_FP64, **p)
+    vo, co = orc.velocity(m.nodes, tets, m.omega, pts, counts=True, **_op(p))
+    assert rel_l2(v, vo) <= TOL_FP64_REL_L2
+    assert np.array_equal(c[:, :2], co[:, :2])
