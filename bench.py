@@ -117,6 +117,23 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest of the ranks' values (all-reduce MAX; NCCL wants a device tensor, gloo a host one)."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Units per second of the whole job: every rank processes units_per_rank (one replica of the
+    workload each, weak scaling), the job takes as long as its slowest rank."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def run_oracle_sample(mesh, count: int, seed_offset: int = 0):
     import oracle
 
@@ -426,11 +443,8 @@ def main():
     h.bs_profile(False)
     h.bs_status()
     ms = ev0.elapsed_time(ev1) / args.steps
-    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    value = world * pairs / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = whole_job_rate(pairs, world, ms_max)
 
     # end to end through the public API: pinned host inputs of a Lagrangian step (node
     # positions and vorticity) -> device, bs_update, bs_velocity at all nodes, velocities -> host
@@ -458,11 +472,8 @@ def main():
             e2e_step()
         barrier()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
-        t_e2e = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * pairs / float(t_e2e.item()), "unit": UNIT, "h2d_bytes_per_step": 2 * k * 24,
-               "d2h_bytes_per_step": k * 24}
+        e2e = {"value": whole_job_rate(pairs, world, 1e3 * max_over_ranks(e2e_s, dist, "cuda")), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * k * 24, "d2h_bytes_per_step": k * 24}
 
     if rank != 0:
         if dist is not None:
