@@ -281,8 +281,10 @@ def rings_workload(args):
 
 def allray_workload(args):
     """All-ray evaluation (far_ratio = inf: the ray rule for every pair, the paper's own method) on the
-    32^3 Gaussian-ring mesh, velocity at all 32768 nodes, 8x16 directions, FP32: the all-ray kernel
-    (direction windows) against the velocity kernel's dense all-ray path."""
+    32^3 Gaussian-ring mesh, velocity at all 32768 nodes, 8x16 directions, FP32: bs_velocity_nodes (lines
+    traced through face neighbours), against the all-ray kernel (direction windows) and the velocity
+    kernel's dense all-ray path.  With --points, a seeded subset of the nodes through the all-ray kernel
+    only (profiling case)."""
     import torch
 
     import paper_0712_1695_gb300 as bs
@@ -300,30 +302,47 @@ def allray_workload(args):
     pts = torch.from_numpy(nodes).cuda()
     out = torch.empty_like(pts)
 
-    def timeit(steps, generic):
-        os.environ["BS_ALLRAY_GENERIC"] = "1" if generic else "0"
-        for _ in range(args.warmup if not generic else 1):
-            h.bs_velocity(pts, out_dev=out, **P)
+    def timeit(steps, fn, warm):
+        for _ in range(warm):
+            fn()
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(steps):
-            h.bs_velocity(pts, out_dev=out, **P)
+            fn()
         ev1.record(stream)
         torch.cuda.synchronize()
         h.bs_status()
         return ev0.elapsed_time(ev1) / steps
 
-    with ClockSampler(0) as clk:
-        ms = timeit(args.steps, False)
+    def ray():
+        h.bs_velocity(pts, out_dev=out, **P)
+
+    def walk():
+        h.bs_velocity_nodes(out_dev=out, **P)
+
+    os.environ["BS_ALLRAY_GENERIC"] = "0"
+    ms_walk = None
+    if not args.points:
+        with ClockSampler(0) as clk:
+            ms_walk = timeit(args.steps, walk, args.warmup)
+        v_walk = out.cpu().numpy()
+        ms_ray = timeit(args.steps, ray, 1)
+    else:
+        with ClockSampler(0) as clk:
+            ms_ray = timeit(args.steps, ray, args.warmup)
     v32 = out.cpu().numpy()
-    ms_dense = timeit(1, True)
+    os.environ["BS_ALLRAY_GENERIC"] = "1"
+    ms_dense = timeit(1, ray, 1)
     os.environ["BS_ALLRAY_GENERIC"] = "0"
     # FP32 against the FP64 all-ray kernel on 512 seeded nodes
     idx = np.random.default_rng(2002).choice(len(nodes), size=min(512, len(nodes)), replace=False)
     v64 = h.bs_velocity(torch.from_numpy(nodes[idx]).cuda(), **dict(P, precision=bs.BS_FP64)).cpu().numpy()
     h.bs_status()
-    err = float(np.linalg.norm(v32[idx] - v64) / (np.sqrt(len(idx)) * np.linalg.norm(v64, axis=1).max()))
+
+    def err(v):
+        return float(np.linalg.norm(v[idx] - v64) / (np.sqrt(len(idx)) * np.linalg.norm(v64, axis=1).max()))
+
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -336,16 +355,22 @@ def allray_workload(args):
         dt = time.perf_counter() - t
         cpu = {"value": len(sel) * m.n_tets / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                "sample": f"{len(sel)} seeded nodes x all {m.n_tets} tets, all-ray ({dt:.1f} s)"}
+    ms = ms_walk if ms_walk is not None else ms_ray
     line = {"metric": "node-tet interactions/s (all-ray: ray rule for every pair, FP32 path)",
             "value": pairs / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"gaussian ring 32^3: {len(nodes)} of {m.n_nodes} nodes x {m.n_tets} tets",
-                       **dict(PARAMS, far_ratio="inf"), "precision": "fp32"},
+                       **dict(PARAMS, far_ratio="inf"), "precision": "fp32",
+                       "path": "mesh walk (bs_velocity_nodes)" if ms_walk is not None else "all-ray kernel"},
             "line_tests_per_s_dense_equivalent": pairs * L / (ms * 1e-3),
+            "ray_kernel": {"ms_per_step": ms_ray, "value": pairs / (ms_ray * 1e-3),
+                           "fp32_vs_fp64_rms_over_max": err(v32)},
             "dense_loop": {"ms_per_step": ms_dense, "value": pairs / (ms_dense * 1e-3)},
-            "window_over_dense": ms_dense / ms,
-            "fp32_vs_fp64_rms_over_max": err, "cpu_baseline": cpu, "clocks": clk.summary()}
+            "cpu_baseline": cpu, "clocks": clk.summary()}
+    if ms_walk is not None:
+        line["walk_fp32_vs_fp64_rms_over_max"] = err(v_walk)
+        line["walk_over_ray_kernel"] = ms_ray / ms_walk
     print(json.dumps(line), flush=True)
     return 0
 

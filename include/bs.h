@@ -98,11 +98,33 @@ BS_API int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const
 BS_API int bs_velocity_host(bs_handle h, const double *eval_pts_host, int64_t k, const bs_params *p, double *out_host,
                      void *stream);
 
+/* Velocity at the handle's own nodes (the evaluation points of the Lagrangian
+ * method, Section 1): out_dev [n_nodes][3] (device, overwritten), p->counts
+ * optional ([n_nodes][3]).  Same result as bs_velocity at the nodes.  With
+ * far_ratio = +inf (every pair by the ray rule, Eq. 2-5) and at most 4096
+ * directions, every line through a node is traced through the mesh by face
+ * neighbours (the tracing through the mesh that the paper's conclusion, §4,
+ * proposes): from the node, each half-line crosses the tets it meets one after
+ * the other until it leaves the mesh, each tet adding its chord of Eq. 5.
+ * That is exact when every line leaves the mesh once: the walk is used when the
+ * mesh is conforming (a face belongs to at most two tets, every node to some
+ * tet) and its domain convex (checked on the device after each change of the
+ * node positions: every boundary node on the inner side of every boundary face
+ * plane, within 1e-9 of the face size); otherwise the call evaluates the nodes
+ * as bs_velocity does.  The first such call builds the face adjacency and the
+ * node-to-tet incidence on the host (synchronous, once per handle; about
+ * 24 bytes per tet of device memory, owned by the handle); later calls are
+ * asynchronous on `stream`.  A walk that exceeds max(4096, 64 n_tets^(1/3))
+ * tets (impossible on a valid mesh) stops and raises BS_ERR_TIMEOUT at the next
+ * bs_status.  Setting the environment variable BS_WALK=0 disables the walk.
+ * Errors: BS_ERR_ARG, BS_ERR_ORDER, BS_ERR_CUDA. */
+BS_API int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, void *stream);
+
 /* One Heun (RK2) step of the Lagrangian vortex method (Section 1: the nodes
  * move with the flow and the velocity is re-evaluated on the moved mesh):
  *   v0 = v(x0) at the nodes;  x* = x0 + dt v0;  v1 = v(x*) at the moved nodes;
  *   x1 = x0 + dt (v0 + v1) / 2.
- * Every velocity evaluation is bs_velocity at all nodes with parameters p
+ * Every velocity evaluation is bs_velocity_nodes with parameters p
  * (p->counts must be NULL); the connectivity and the nodal vorticity stay
  * fixed (no vortex stretching: the paper gives no vorticity update).  The
  * handle's node positions become x1.  Asynchronous on `stream`; a tet that

@@ -22,7 +22,7 @@ BS_FP64, BS_FP32 = 0, 1
 EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_status", "bs_destroy",
             "bs_mesh_size", "bs_last_error", "bs_direction_table", "bs_tet_rule", "bs_batch_create",
             "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read",
-            "bs_velocity_noalloc", "bs_tuned_variant", "bs_rk2_step", "bs_nodes")
+            "bs_velocity_noalloc", "bs_tuned_variant", "bs_rk2_step", "bs_nodes", "bs_velocity_nodes")
 
 
 class BSError(RuntimeError):
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH):
                                             ctypes.POINTER(bs_params), _P, _P]
         lib.bs_rk2_step.argtypes = [_P, ctypes.c_double, ctypes.POINTER(bs_params), _P]
         lib.bs_nodes.argtypes = [_P, _P, _P]
+        lib.bs_velocity_nodes.argtypes = [_P, ctypes.POINTER(bs_params), _P, _P]
         lib.bs_tuned_variant.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         lib.bs_profile.argtypes = [_P, ctypes.c_int]
         lib.bs_profile_read.argtypes = [_P, _D, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -160,6 +161,21 @@ class Mesh:
         p = make_params(counts=counts_dev, **params)
         _check(load().bs_velocity(self.handle, pts_dev.data_ptr(), k, ctypes.byref(p), out_dev.data_ptr(),
                                   _stream_ptr(stream)))
+        return out_dev
+
+    def bs_velocity_nodes(self, out_dev=None, counts_dev=None, stream=None, **params):
+        """Velocity at the mesh's own nodes (torch float64 [n_nodes, 3] on the device); returns the output."""
+        import torch
+
+        n = self.n_nodes
+        if out_dev is None:
+            out_dev = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        _require_dev(out_dev, (n, 3))
+        if counts_dev is not None:
+            if counts_dev.dtype != torch.int32 or tuple(counts_dev.shape) != (n, 3) or not counts_dev.is_contiguous():
+                raise ValueError("counts must be a contiguous int32 [n_nodes, 3] CUDA tensor")
+        p = make_params(counts=counts_dev, **params)
+        _check(load().bs_velocity_nodes(self.handle, ctypes.byref(p), out_dev.data_ptr(), _stream_ptr(stream)))
         return out_dev
 
     def bs_velocity_host(self, pts, stream=None, out=None, **params):

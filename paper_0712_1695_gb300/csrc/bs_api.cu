@@ -101,6 +101,14 @@ struct bs_ctx {
     int ray_occ[2] = {};                // cached CTAs per SM of the all-ray kernel by [precision]
     int ray_occ_L[2] = {};              // ... for this many directions
     int variant[2][65] = {};  // chosen kernel variant by [precision][Q] (bs_autotune, or BS_VARIANT)
+    // mesh walk of the all-ray velocity at the nodes (built on first use)
+    bool walk_built = false;
+    bool walk_conforming = false;
+    int32_t *walk_nbr = nullptr, *walk_inc_off = nullptr, *walk_inc = nullptr, *walk_bface = nullptr,
+            *walk_bnode = nullptr;
+    int64_t walk_n_bface = 0, walk_n_bnode = 0;
+    int *walk_mode = nullptr;      // device: the walk is valid for the current node positions
+    uint64_t walk_version = 0;     // mesh version when walk_mode was computed
     // kernel timing (bs_profile)
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
@@ -125,7 +133,8 @@ void free_ctx(bs_ctx *h)
     void *bufs[] = {h->nodes, h->tets,  h->omega,     h->near32,   h->near64,  h->rho2,         h->flag,
                     h->first_bad, h->work_counter, h->rule.bary, h->rule.w, h->far32, h->far64, h->lines.f32,
                     h->lines.f64, h->partial, h->stage, h->rk, h->tile_hdr, h->perm, h->keys,
-                    h->cell_count, h->box};
+                    h->cell_count, h->box, h->walk_nbr, h->walk_inc_off, h->walk_inc, h->walk_bface,
+                    h->walk_bnode, h->walk_mode};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete h;
@@ -345,10 +354,10 @@ int bs_rk2_step(bs_handle h, double dt, const bs_params *p, void *stream)
     if (!h->rk) BS_CUDA(cudaMallocAsync((void **)&h->rk, sizeof(double) * 3 * nv, st));
     double *x0 = h->rk, *v0 = h->rk + nv, *v1 = h->rk + 2 * nv;
     BS_CUDA(cudaMemcpyAsync(x0, h->nodes, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
-    if ((rc = bs_velocity(h, x0, n, p, v0, stream))) return rc;
+    if ((rc = bs_velocity_nodes(h, p, v0, stream))) return rc;
     BS_CUDA(launch_euler(x0, v0, dt, nv, h->nodes, st));  // the mesh moves to x*
     if ((rc = bs_update(h, nullptr, nullptr, stream))) return rc;
-    if ((rc = bs_velocity(h, h->nodes, n, p, v1, stream))) return rc;
+    if ((rc = bs_velocity_nodes(h, p, v1, stream))) return rc;
     BS_CUDA(launch_heun(x0, v0, v1, dt, nv, h->nodes, st));  // and on to x1
     if ((rc = bs_update(h, nullptr, nullptr, stream))) return rc;
     if (h->prof) h->prof_all += 2;
@@ -371,6 +380,7 @@ int bs_status(bs_handle h, void *stream)
     BS_CUDA(cudaMemcpy(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost));
     BS_CUDA(cudaMemset(h->flag, 0, sizeof(int)));
     if (flag & kFlagTimeout) return fail(BS_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (flag & kFlagWalk) return fail(BS_ERR_TIMEOUT, "a mesh walk did not leave the mesh within its step limit");
     if (flag & (kFlagMeshIndex | kFlagMeshVolume)) return fail(BS_ERR_MESH, "degenerate tet after bs_update");
     return BS_OK;
 }
@@ -383,8 +393,114 @@ int bs_mesh_size(bs_handle h, int64_t *n_nodes, int64_t *n_tets)
     return BS_OK;
 }
 
+namespace {
+int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_params *p, double *out_dev,
+                  void *stream, const int *skip);
+}
+
 int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_params *p, double *out_dev,
                 void *stream)
+{
+    return velocity_impl(h, eval_pts_dev, k, p, out_dev, stream, nullptr);
+}
+
+namespace {
+
+// The mesh walk's connectivity (host build, synchronous, once per handle) and device arrays.
+cudaError_t ensure_walk(bs_ctx *h)
+{
+    if (h->walk_built) return cudaSuccess;
+    std::vector<int32_t> tets((size_t)4 * h->n_tets);
+    cudaError_t e = cudaMemcpy(tets.data(), h->tets, sizeof(int32_t) * tets.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return e;
+    WalkMesh w;
+    build_walk_mesh(tets.data(), h->n_nodes, h->n_tets, w);
+    auto up = [](int32_t **dst, const std::vector<int32_t> &v) -> cudaError_t {
+        cudaError_t r = cudaMalloc((void **)dst, sizeof(int32_t) * std::max<size_t>(v.size(), 1));
+        if (r != cudaSuccess || v.empty()) return r;
+        return cudaMemcpy(*dst, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice);
+    };
+    if ((e = up(&h->walk_nbr, w.nbr)) != cudaSuccess) return e;
+    if ((e = up(&h->walk_inc_off, w.inc_off)) != cudaSuccess) return e;
+    if ((e = up(&h->walk_inc, w.inc)) != cudaSuccess) return e;
+    if ((e = up(&h->walk_bface, w.bface)) != cudaSuccess) return e;
+    if ((e = up(&h->walk_bnode, w.bnode)) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&h->walk_mode, sizeof(int))) != cudaSuccess) return e;
+    h->walk_n_bface = (int64_t)w.bface.size();
+    h->walk_n_bnode = (int64_t)w.bnode.size();
+    h->walk_conforming = w.conforming && 4 * h->n_tets < INT32_MAX;
+    h->walk_built = true;
+    h->walk_version = 0;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, void *stream)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!out_dev) return fail(BS_ERR_ARG, "NULL output");
+    const int L = p->n_phi * p->n_theta;
+    const char *env = getenv("BS_WALK");
+    const bool walk = isinf(p->far_ratio) && L <= kRayLinesSmemMax && h->n_tets > 0 && !(env && atoi(env) == 0);
+    if (!walk) return velocity_impl(h, h->nodes, h->n_nodes, p, out_dev, stream, nullptr);
+    cudaStream_t st = (cudaStream_t)stream;
+    BS_CUDA(ensure_walk(h));
+    BS_CUDA(ensure_lines(h, p->n_phi, p->n_theta, st));
+    if (h->walk_version != h->version) {  // node positions changed: is the domain still convex?
+        BS_CUDA(launch_convex_check(h->nodes, h->tets, h->walk_bface, h->walk_n_bface, h->walk_bnode,
+                                    h->walk_n_bnode, h->walk_conforming ? 1 : 0, h->walk_mode, st));
+        h->walk_version = h->version;
+        if (h->prof) h->prof_all += 1 + (h->walk_conforming && h->walk_n_bface > 0 ? (h->walk_n_bface + 65534) / 65535 : 0);
+    }
+    WalkArgs w;
+    w.nodes = h->nodes;
+    w.n_nodes = h->n_nodes;
+    w.n_tets = h->n_tets;
+    w.near32 = h->near32;
+    w.near64 = h->near64;
+    w.nbr = h->walk_nbr;
+    w.inc_off = h->walk_inc_off;
+    w.inc = h->walk_inc;
+    w.lines32 = h->lines.f32;
+    w.lines64 = h->lines.f64;
+    w.L = L;
+    w.out = out_dev;
+    w.counts = p->counts;
+    w.mode = h->walk_mode;
+    w.flag = h->flag;
+    // no valid mesh needs more steps than tets; a small cap keeps a broken walk short
+    w.max_steps = (int)std::min<int64_t>(h->n_tets, std::max<int64_t>(4096, 64 * (int64_t)std::cbrt((double)h->n_tets)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->prof) {
+        if (h->ev_free.empty()) {
+            BS_CUDA(cudaEventCreate(&e0));
+            BS_CUDA(cudaEventCreate(&e1));
+        } else {
+            e0 = h->ev_free.back().first;
+            e1 = h->ev_free.back().second;
+            h->ev_free.pop_back();
+        }
+        h->ev_used.push_back({e0, e1});
+        h->prof_kernel += 1;
+        h->prof_all += 1;
+    }
+    BS_CUDA(launch_walk(p->precision, w, st, e0, e1));
+    // the all-ray kernel for a domain the walk cannot serve (returns at once otherwise)
+    const bool prof = h->prof;
+    h->prof = false;  // the walk's events time this call
+    rc = velocity_impl(h, h->nodes, h->n_nodes, p, out_dev, stream, h->walk_mode);
+    h->prof = prof;
+    if (prof) h->prof_all += 5 + 3;
+    return rc;
+}
+
+namespace {
+
+int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_params *p, double *out_dev,
+                  void *stream, const int *skip)
 {
     if (!h) return fail(BS_ERR_ARG, "handle is NULL");
     int rc = check_params(p);
@@ -460,6 +576,7 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
     a.m.tiles_per_chunk = (int)per;
     a.m.partial = h->partial;
     a.variant = variant;
+    a.skip = skip;
     a.n_items = n_blocks * n_chunks;
     int grid = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -483,6 +600,8 @@ int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_par
     }
     return BS_OK;
 }
+
+}  // namespace
 
 int bs_velocity_host(bs_handle h, const double *eval_pts_host, int64_t k, const bs_params *p, double *out_host,
                      void *stream)

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/bs.h"
 
@@ -88,6 +89,7 @@ struct TetRule {
 constexpr int kFlagMeshIndex = 1;
 constexpr int kFlagMeshVolume = 2;
 constexpr int kFlagTimeout = 4;
+constexpr int kFlagWalk = 8;  // a mesh walk hit its step limit or a tet with no face ahead
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).
@@ -142,6 +144,7 @@ struct VelocityArgs {
     int *flag = nullptr;
     int *work_counter = nullptr;  // device int, zeroed by launch_velocity
     int variant = 0;  // kernel variant (points per thread / registers) for this precision and rule
+    const int *skip = nullptr;  // device flag: when set, the all-ray and reduce kernels return at once
 };
 
 constexpr int64_t kMinTilesPerItem = 2;  // work items shorter than this are dominated by their set-up
@@ -172,6 +175,38 @@ LaunchShape ray_shape();
 int ray_ctas_per_sm(int precision, int L);
 cudaError_t launch_ray(int precision, const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
                        cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);
+
+// Mesh walk (bs_walk.cu): the all-ray velocity at the mesh nodes by tracing every line through
+// face neighbours.  Host-side connectivity, built once per handle from the tets:
+struct WalkMesh {
+    std::vector<int32_t> nbr;      // [n_tets][4] tet across the face opposite vertex i, or -1
+    std::vector<int32_t> inc_off;  // [n_nodes + 1] CSR offsets of the node -> tet incidence
+    std::vector<int32_t> inc;      // [4 n_tets] (tet << 2) | vertex index of the node in the tet
+    std::vector<int32_t> bface;    // boundary faces as (tet << 2) | opposite vertex
+    std::vector<int32_t> bnode;    // nodes on a boundary face
+    bool conforming = false;       // every face shared by at most two tets, every node in some tet
+};
+bool build_walk_mesh(const int32_t *tets_host, int64_t n_nodes, int64_t n_tets, WalkMesh &w);
+struct WalkArgs {
+    const double *nodes = nullptr;  // [n_nodes][3], also the evaluation points
+    int64_t n_nodes = 0, n_tets = 0;
+    const float4 *near32 = nullptr;
+    const double *near64 = nullptr;
+    const int32_t *nbr = nullptr, *inc_off = nullptr, *inc = nullptr;
+    const float4 *lines32 = nullptr;
+    const dbl4 *lines64 = nullptr;
+    int L = 0;
+    double *out = nullptr;       // [n_nodes][3]
+    int32_t *counts = nullptr;   // [n_nodes][3] or null
+    const int *mode = nullptr;   // device flag: the walk is valid (convex conforming mesh)
+    int *flag = nullptr;
+    int max_steps = 0;           // tets per half-line before the walk gives up (error flag)
+};
+// mode := conforming, then cleared if a boundary node lies outside a boundary face's plane
+cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const int32_t *bface, int64_t n_bface,
+                                const int32_t *bnode, int64_t n_bnode, int conforming, int *mode, cudaStream_t st);
+cudaError_t launch_walk(int precision, const WalkArgs &a, cudaStream_t st, cudaEvent_t ev_start = nullptr,
+                        cudaEvent_t ev_stop = nullptr);
 // Heun step position updates (n_values = 3 * nodes)
 cudaError_t launch_euler(const double *x0, const double *v0, double dt, int64_t n_values, double *x, cudaStream_t st);
 cudaError_t launch_heun(const double *x0, const double *v0, const double *v1, double dt, int64_t n_values, double *x,

@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(kRayThreads) ray_kernel(const VelocityArgs a)
     T *sz = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(s_item) + 16);  // [n_phi] cos(phi_n)
     float4 *sdir = reinterpret_cast<float4 *>(reinterpret_cast<unsigned char *>(sz) + 16 * ((sizeof(T) * 256 + 15) / 16));
 
+    if (a.skip && *a.skip) return;  // the mesh walk evaluated these points
     const int tid = threadIdx.x, lane = tid & 31;
     const int N = a.lines.n_phi, M = a.lines.n_theta;
     // cos(phi_n) of each ring (descending in n) and, for float32, the direction table
@@ -451,8 +452,9 @@ __global__ void __launch_bounds__(kRayThreads) ray_kernel(const VelocityArgs a)
     }
 }
 
-__global__ void ray_zero_kernel(int32_t *counts, int64_t n, int *work_counter)
+__global__ void ray_zero_kernel(int32_t *counts, int64_t n, int *work_counter, const int *skip)
 {
+    if (skip && *skip) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i == 0) *reinterpret_cast<unsigned long long *>(work_counter) = 0ull;
     if (counts && i < n) counts[i] = 0;
@@ -510,7 +512,7 @@ cudaError_t launch_ray(int precision, const VelocityArgs &a, int n_sm, cudaStrea
                        cudaEvent_t ev_start, cudaEvent_t ev_stop)
 {
     const int64_t nc = a.counts ? 3 * a.m.k : 0;
-    ray_zero_kernel<<<(unsigned)((nc + 255) / 256 + 1), 256, 0, st>>>(a.counts, nc, a.work_counter);
+    ray_zero_kernel<<<(unsigned)((nc + 255) / 256 + 1), 256, 0, st>>>(a.counts, nc, a.work_counter, a.skip);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev_start && (e = cudaEventRecord(ev_start, st)) != cudaSuccess) return e;

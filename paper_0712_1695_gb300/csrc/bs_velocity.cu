@@ -337,6 +337,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
     constexpr int NACC = F32 ? 6 : 3;  // float: (sum, compensation) per component; double: sum
     static_assert(TILE <= 256, "tet index in the near queue is 8 bits");
 
+    if (a.skip && *a.skip) return;  // the mesh walk evaluated these points
     extern __shared__ __align__(128) unsigned char smem[];
     // shared-memory regions, each rounded up to 16 bytes (the same rule as smem_bytes below)
     SmemCarve carve{smem};
@@ -782,6 +783,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
 // batch: one thread per point of all meshes, the mesh found from point_begin.
 __global__ void reduce_kernel(const VelocityArgs a)
 {
+    if (a.skip && *a.skip) return;  // the mesh walk wrote the output
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const MeshDesc *m = &a.m;
     int64_t i = g;
@@ -811,8 +813,9 @@ __global__ void reduce_kernel(const VelocityArgs a)
     m->out[3 * o + 2] = s2;
 }
 
-__global__ void zero_kernel(int32_t *counts, int64_t n, int *work_counter)
+__global__ void zero_kernel(int32_t *counts, int64_t n, int *work_counter, const int *skip)
 {
+    if (skip && *skip) return;  // the mesh walk evaluated these points
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i == 0) *reinterpret_cast<unsigned long long *>(work_counter) = 0ull;
     if (counts && i < n) counts[i] = 0;
@@ -941,7 +944,7 @@ cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cuda
                             cudaEvent_t ev_start, cudaEvent_t ev_stop)
 {
     const int64_t nc = a.counts ? 3 * a.m.k : 0;
-    zero_kernel<<<(unsigned)((nc + 255) / 256 + 1), 256, 0, st>>>(a.counts, nc, a.work_counter);
+    zero_kernel<<<(unsigned)((nc + 255) / 256 + 1), 256, 0, st>>>(a.counts, nc, a.work_counter, a.skip);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (ev_start && (e = cudaEventRecord(ev_start, st)) != cudaSuccess) return e;
