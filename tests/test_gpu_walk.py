@@ -162,3 +162,15 @@ def test_heun_step_all_ray_uses_the_walk(orc, c1):
     x1 = h.bs_nodes().cpu().numpy()
     ref = oracle.heun_step(orc, m.nodes, m.tets, m.omega, dt, **_op(ALLRAY))
     assert np.abs(x1 - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_hybrid_rule_at_the_nodes_is_bs_velocity(c1):
+    """With a finite far ratio bs_velocity_nodes is bs_velocity at the nodes, bit for bit."""
+    m, h = c1
+    p = dict(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16)
+    for prec in (bs.BS_FP64, bs.BS_FP32):
+        v, c = nodes_velocity(h, m.n_nodes, prec, **p)
+        cnt = torch.zeros((m.n_nodes, 3), dtype=torch.int32, device="cuda")
+        vr = h.bs_velocity(torch.from_numpy(m.nodes).cuda(), counts_dev=cnt, precision=prec, **p).cpu().numpy()
+        h.bs_status()
+        assert np.array_equal(v, vr) and np.array_equal(c, cnt.cpu().numpy())
