@@ -290,7 +290,8 @@ def allray_workload(args):
     import paper_0712_1695_gb300 as bs
 
     bs.load()
-    m = config2_ring()
+    big = args.allray_mesh == "fourier64"  # the headline mesh: the walk alone (the other paths take minutes)
+    m = config3_fourier() if big else config2_ring()
     h = bs.Mesh(m.nodes, m.tets, m.omega)
     P = dict(PARAMS, far_ratio=float("inf"), precision=bs.BS_FP32)
     L = P["n_theta"] * P["n_phi"]
@@ -322,19 +323,22 @@ def allray_workload(args):
         h.bs_velocity_nodes(out_dev=out, **P)
 
     os.environ["BS_ALLRAY_GENERIC"] = "0"
-    ms_walk = None
+    ms_walk = ms_ray = ms_dense = None
+    v32 = None
     if not args.points:
         with ClockSampler(0) as clk:
             ms_walk = timeit(args.steps, walk, args.warmup)
         v_walk = out.cpu().numpy()
-        ms_ray = timeit(args.steps, ray, 1)
+        if not big:
+            ms_ray = timeit(args.steps, ray, 1)
     else:
         with ClockSampler(0) as clk:
             ms_ray = timeit(args.steps, ray, args.warmup)
-    v32 = out.cpu().numpy()
-    os.environ["BS_ALLRAY_GENERIC"] = "1"
-    ms_dense = timeit(1, ray, 1)
-    os.environ["BS_ALLRAY_GENERIC"] = "0"
+    if ms_ray is not None:
+        v32 = out.cpu().numpy()
+        os.environ["BS_ALLRAY_GENERIC"] = "1"
+        ms_dense = timeit(1, ray, 1)
+        os.environ["BS_ALLRAY_GENERIC"] = "0"
     # FP32 against the FP64 all-ray kernel on 512 seeded nodes
     idx = np.random.default_rng(2002).choice(len(nodes), size=min(512, len(nodes)), replace=False)
     v64 = h.bs_velocity(torch.from_numpy(nodes[idx]).cuda(), **dict(P, precision=bs.BS_FP64)).cpu().numpy()
@@ -348,7 +352,7 @@ def allray_workload(args):
         import oracle
 
         oracle.build()
-        sel = idx[:256]
+        sel = idx[:32] if big else idx[:256]
         t = time.perf_counter()
         oracle.velocity(m.nodes, m.tets, m.omega, nodes[sel], far_ratio=float("inf"),
                         tet_order=PARAMS["tet_gauss_order"], n_theta=PARAMS["n_theta"], n_phi=PARAMS["n_phi"])
@@ -360,17 +364,19 @@ def allray_workload(args):
             "value": pairs / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": f"gaussian ring 32^3: {len(nodes)} of {m.n_nodes} nodes x {m.n_tets} tets",
+            "config": {"workload": (f"fourier-64^3: {len(nodes)} nodes x {m.n_tets} tets" if big else
+                                    f"gaussian ring 32^3: {len(nodes)} of {m.n_nodes} nodes x {m.n_tets} tets"),
                        **dict(PARAMS, far_ratio="inf"), "precision": "fp32",
                        "path": "mesh walk (bs_velocity_nodes)" if ms_walk is not None else "all-ray kernel"},
             "line_tests_per_s_dense_equivalent": pairs * L / (ms * 1e-3),
-            "ray_kernel": {"ms_per_step": ms_ray, "value": pairs / (ms_ray * 1e-3),
-                           "fp32_vs_fp64_rms_over_max": err(v32)},
-            "dense_loop": {"ms_per_step": ms_dense, "value": pairs / (ms_dense * 1e-3)},
+            "ray_kernel": None if ms_ray is None else {"ms_per_step": ms_ray, "value": pairs / (ms_ray * 1e-3),
+                                                       "fp32_vs_fp64_rms_over_max": err(v32)},
+            "dense_loop": None if ms_dense is None else {"ms_per_step": ms_dense, "value": pairs / (ms_dense * 1e-3)},
             "cpu_baseline": cpu, "clocks": clk.summary()}
     if ms_walk is not None:
         line["walk_fp32_vs_fp64_rms_over_max"] = err(v_walk)
-        line["walk_over_ray_kernel"] = ms_ray / ms_walk
+        if ms_ray is not None:
+            line["walk_over_ray_kernel"] = ms_ray / ms_walk
     print(json.dumps(line), flush=True)
     return 0
 
@@ -386,6 +392,9 @@ def main():
                          "launches; rings: Heun steps of two colliding rings; allray: the ray rule for every "
                          "pair on the 32^3 ring mesh")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
+    ap.add_argument("--allray-mesh", default="ring32", choices=["ring32", "fourier64"],
+                    help="allray workload: the 32^3 ring mesh (walk, all-ray kernel, dense path) or the 64^3 "
+                         "Fourier mesh (the walk alone)")
     ap.add_argument("--batch-count", type=int, default=256, help="meshes in the batch workload")
     ap.add_argument("--batch-only", action="store_true", help="batch workload: skip the separate-launch timing")
     ap.add_argument("--cpu-sample", type=int, default=640, help="oracle sample nodes for cpu_baseline")

@@ -108,6 +108,7 @@ struct bs_ctx {
             *walk_bnode = nullptr;
     int64_t walk_n_bface = 0, walk_n_bnode = 0;
     int *walk_mode = nullptr;      // device: the walk is valid for the current node positions
+    float4 *walk_rec = nullptr;    // float32 walk records [n_tets][kWalkRecVec4]
     uint64_t walk_version = 0;     // mesh version when walk_mode was computed
     // kernel timing (bs_profile)
     bool prof = false;
@@ -134,7 +135,7 @@ void free_ctx(bs_ctx *h)
                     h->first_bad, h->work_counter, h->rule.bary, h->rule.w, h->far32, h->far64, h->lines.f32,
                     h->lines.f64, h->partial, h->stage, h->rk, h->tile_hdr, h->perm, h->keys,
                     h->cell_count, h->box, h->walk_nbr, h->walk_inc_off, h->walk_inc, h->walk_bface,
-                    h->walk_bnode, h->walk_mode};
+                    h->walk_bnode, h->walk_mode, h->walk_rec};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete h;
@@ -426,6 +427,9 @@ cudaError_t ensure_walk(bs_ctx *h)
     if ((e = up(&h->walk_bface, w.bface)) != cudaSuccess) return e;
     if ((e = up(&h->walk_bnode, w.bnode)) != cudaSuccess) return e;
     if ((e = cudaMalloc((void **)&h->walk_mode, sizeof(int))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&h->walk_rec, sizeof(float4) * kWalkRecVec4 * std::max<int64_t>(h->n_tets, 1))) !=
+        cudaSuccess)
+        return e;
     h->walk_n_bface = (int64_t)w.bface.size();
     h->walk_n_bnode = (int64_t)w.bnode.size();
     h->walk_conforming = w.conforming && 4 * h->n_tets < INT32_MAX;
@@ -449,11 +453,13 @@ int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, void *st
     cudaStream_t st = (cudaStream_t)stream;
     BS_CUDA(ensure_walk(h));
     BS_CUDA(ensure_lines(h, p->n_phi, p->n_theta, st));
-    if (h->walk_version != h->version) {  // node positions changed: is the domain still convex?
+    if (h->walk_version != h->version) {  // the mesh changed: walk records, and is the domain still convex?
+        BS_CUDA(launch_walk_records(h->near32, h->walk_nbr, h->n_tets, h->walk_rec, st));
         BS_CUDA(launch_convex_check(h->nodes, h->tets, h->walk_bface, h->walk_n_bface, h->walk_bnode,
                                     h->walk_n_bnode, h->walk_conforming ? 1 : 0, h->walk_mode, st));
         h->walk_version = h->version;
-        if (h->prof) h->prof_all += 1 + (h->walk_conforming && h->walk_n_bface > 0 ? (h->walk_n_bface + 65534) / 65535 : 0);
+        if (h->prof)
+            h->prof_all += 2 + (h->walk_conforming && h->walk_n_bface > 0 ? (h->walk_n_bface + 65534) / 65535 : 0);
     }
     WalkArgs w;
     w.nodes = h->nodes;
@@ -461,6 +467,7 @@ int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, void *st
     w.n_tets = h->n_tets;
     w.near32 = h->near32;
     w.near64 = h->near64;
+    w.wrec = h->walk_rec;
     w.nbr = h->walk_nbr;
     w.inc_off = h->walk_inc_off;
     w.inc = h->walk_inc;

@@ -192,6 +192,7 @@ struct WalkArgs {
     int64_t n_nodes = 0, n_tets = 0;
     const float4 *near32 = nullptr;
     const double *near64 = nullptr;
+    const float4 *wrec = nullptr;  // float32 walk records [n_tets][kWalkRecVec4] (see bs_walk.cu)
     const int32_t *nbr = nullptr, *inc_off = nullptr, *inc = nullptr;
     const float4 *lines32 = nullptr;
     const dbl4 *lines64 = nullptr;
@@ -202,6 +203,10 @@ struct WalkArgs {
     int *flag = nullptr;
     int max_steps = 0;           // tets per half-line before the walk gives up (error flag)
 };
+constexpr int kWalkRecVec4 = 8;  // float4 per float32 walk record (one 128-byte line)
+// float32 walk records from the near records and the face neighbours (after every mesh update)
+cudaError_t launch_walk_records(const float4 *near32, const int32_t *nbr, int64_t n_tets, float4 *wrec,
+                                cudaStream_t st);
 // mode := conforming, then cleared if a boundary node lies outside a boundary face's plane
 cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const int32_t *bface, int64_t n_bface,
                                 const int32_t *bnode, int64_t n_bnode, int conforming, int *mode, cudaStream_t st);

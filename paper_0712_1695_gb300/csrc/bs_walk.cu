@@ -19,7 +19,9 @@
 // on the host.
 //
 // One warp per node, the lanes over the lines; per-node sums by warp reduction (no atomics,
-// deterministic).  A walk that has not left the mesh after max_steps tets (it cannot happen on
+// deterministic).  The float32 walk reads one 128-byte record per tet step (gradients, longest
+// edge, vertex 0 as float splits, nodal vorticity, the four face neighbours: everything a step
+// needs in one cache line), rebuilt from the near records after every mesh update.  A walk that has not left the mesh after max_steps tets (it cannot happen on
 // a valid mesh) sets the error flag and stops.
 #include <math.h>
 
@@ -50,8 +52,8 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, const float xh[3]
     for (int e = a.inc_off[node]; e < a.inc_off[node + 1]; ++e) {
         const int code = a.inc[e];
         const int t = code >> 2, k = code & 3;
-        const float4 *r = a.near32 + (int64_t)t * kNearF32Vec4;
-        const float4 q0 = __ldg(r + nf32::G1), q1 = __ldg(r + nf32::G2), q2 = __ldg(r + nf32::G3);
+        const float4 *r = a.wrec + (int64_t)t * kWalkRecVec4;
+        const float4 q0 = __ldg(r), q1 = __ldg(r + 1), q2 = __ldg(r + 2);
         const V3<float> g1 = mk(q0.x, q0.y, q0.z), g2 = mk(q1.x, q1.y, q1.z), g3 = mk(q2.x, q2.y, q2.z);
         const V3<float> g0 = mk(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
         float m = INFINITY;
@@ -71,8 +73,8 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, const float xh[3]
             atomicOr(a.flag, kFlagWalk);
             break;
         }
-        const float4 *r = a.near32 + (int64_t)T * kNearF32Vec4;
-        const float4 q0 = __ldg(r + nf32::G1), q1 = __ldg(r + nf32::G2), q2 = __ldg(r + nf32::G3);
+        const float4 *r = a.wrec + (int64_t)T * kWalkRecVec4;
+        const float4 q0 = __ldg(r), q1 = __ldg(r + 1), q2 = __ldg(r + 2), q3 = __ldg(r + 3);
         V3<float> g[4];
         g[1] = mk(q0.x, q0.y, q0.z);
         g[2] = mk(q1.x, q1.y, q1.z);
@@ -83,9 +85,9 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, const float xh[3]
 #pragma unroll
             for (int i = 0; i < 4; ++i) av[i] = (i == kk) ? 1.0f : 0.0f;
         } else {
-            const float4 vh = __ldg(r + nf32::VH), vm = __ldg(r + nf32::VM);  // vertex 0 (xyz)
-            const V3<float> d0 =
-                mk((xh[0] - vh.x) + (xm[0] - vm.x), (xh[1] - vh.y) + (xm[1] - vm.y), (xh[2] - vh.z) + (xm[2] - vm.z));
+            // vertex 0 as float splits: hi = (q1.w, q2.w, q3.x), mid = (q3.y, q3.z, q3.w)
+            const V3<float> d0 = mk((xh[0] - q1.w) + (xm[0] - q3.y), (xh[1] - q2.w) + (xm[1] - q3.z),
+                                    (xh[2] - q3.x) + (xm[2] - q3.w));
             av[1] = dot3(g[1], d0);
             av[2] = dot3(g[2], d0);
             av[3] = dot3(g[3], d0);
@@ -117,20 +119,20 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, const float xh[3]
             atomicOr(a.flag, kFlagWalk);
             break;
         }
+        // omega at the vertices (w0 w1 w2 w3, 12 floats) and the face neighbours (4 ints)
+        const float4 q4 = __ldg(r + 4), q5 = __ldg(r + 5), q6 = __ldg(r + 6);
+        const int4 nb = __ldg(reinterpret_cast<const int4 *>(r + 7));
         if (!empty && hi - lo > (float)kTau * q0.w) {
-            float4 w4[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) w4[i] = __ldg(r + nf32::W + i);
             const float l0 = fmaxf(lo, 0.f);
             const float f1 = hi - l0, f2 = 0.5f * (hi * hi - l0 * l0);
             const float c0 = f1 * av[0] + f2 * b[0], c1 = f1 * av[1] + f2 * b[1];
             const float c2 = f1 * av[2] + f2 * b[2], c3 = f1 * av[3] + f2 * b[3];
-            I.x += c0 * w4[0].x + c1 * w4[1].x + c2 * w4[2].x + c3 * w4[3].x;
-            I.y += c0 * w4[0].y + c1 * w4[1].y + c2 * w4[2].y + c3 * w4[3].y;
-            I.z += c0 * w4[0].z + c1 * w4[1].z + c2 * w4[2].z + c3 * w4[3].z;
+            I.x += c0 * q4.x + c1 * q4.w + c2 * q5.z + c3 * q6.y;
+            I.y += c0 * q4.y + c1 * q5.x + c2 * q5.w + c3 * q6.z;
+            I.z += c0 * q4.z + c1 * q5.y + c2 * q6.x + c3 * q6.w;
             ++hits;
         }
-        T = a.nbr[4 * (int64_t)T + exitf];
+        T = exitf == 0 ? nb.x : exitf == 1 ? nb.y : exitf == 2 ? nb.z : nb.w;
     }
     return I;
 }
@@ -273,6 +275,29 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a)
 
 __global__ void set_int_kernel(int *p, int v) { *p = v; }
 
+// float32 walk record of a tet, one 128-byte line:
+//   [g1 h] [g2 v0hi.x] [g3 v0hi.y] [v0hi.z v0mid.xyz] [w0.xyz w1.x] [w1.yz w2.xy] [w2.z w3.xyz] [nbr0..3]
+__global__ void walk_records_kernel(const float4 *__restrict__ near32, const int32_t *__restrict__ nbr,
+                                    int64_t n_tets, float4 *__restrict__ wrec)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n_tets) return;
+    const float4 *r = near32 + t * kNearF32Vec4;
+    const float4 g1 = r[nf32::G1], g2 = r[nf32::G2], g3 = r[nf32::G3];
+    const float4 w0 = r[nf32::W], w1 = r[nf32::W + 1], w2 = r[nf32::W + 2], w3 = r[nf32::W + 3];
+    const float4 vh = r[nf32::VH], vm = r[nf32::VM];  // vertex 0 in .xyz
+    float4 *o = wrec + t * kWalkRecVec4;
+    o[0] = make_float4(g1.x, g1.y, g1.z, g1.w);
+    o[1] = make_float4(g2.x, g2.y, g2.z, vh.x);
+    o[2] = make_float4(g3.x, g3.y, g3.z, vh.y);
+    o[3] = make_float4(vh.z, vm.x, vm.y, vm.z);
+    o[4] = make_float4(w0.x, w0.y, w0.z, w1.x);
+    o[5] = make_float4(w1.y, w1.z, w2.x, w2.y);
+    o[6] = make_float4(w2.z, w3.x, w3.y, w3.z);
+    o[7] = make_float4(__int_as_float(nbr[4 * t]), __int_as_float(nbr[4 * t + 1]), __int_as_float(nbr[4 * t + 2]),
+                       __int_as_float(nbr[4 * t + 3]));
+}
+
 // mode = 1 iff every boundary node lies on the inner side of every boundary face's plane
 // (within 1e-9 of the face's longest edge); mode must be set to the mesh's conformity (1 or 0)
 // before the launch; a violation clears it.
@@ -378,6 +403,14 @@ cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_walk_records(const float4 *near32, const int32_t *nbr, int64_t n_tets, float4 *wrec,
+                                cudaStream_t st)
+{
+    if (n_tets == 0) return cudaSuccess;
+    walk_records_kernel<<<(unsigned)((n_tets + 255) / 256), 256, 0, st>>>(near32, nbr, n_tets, wrec);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_walk(int precision, const WalkArgs &a, cudaStream_t st, cudaEvent_t ev_start, cudaEvent_t ev_stop)
