@@ -268,13 +268,30 @@ def rings_workload(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     pairs_per_step = 2 * m.n_nodes * m.n_tets
     x = h.bs_nodes().cpu().numpy()
+    # drift of the FP32 trajectory against the FP64 one: 20 Heun steps (t = 0.2) on a smaller grid (the FP64
+    # trajectory of the 80^3 grid would take hours at the FP64 rate)
+    drift = None
+    if args.rings_drift_n > 0:
+        md = config5_rings(n=args.rings_drift_n)
+        traj = {}
+        for prec in (bs.BS_FP64, bs.BS_FP32):
+            hd = bs.Mesh(md.nodes, md.tets, md.omega)
+            for _ in range(20):
+                hd.bs_rk2_step(0.01, **dict(PARAMS, precision=prec))
+            hd.bs_status()
+            traj[prec] = hd.bs_nodes().cpu().numpy()
+        dd = np.linalg.norm(traj[bs.BS_FP32] - traj[bs.BS_FP64], axis=1)
+        drift = {"grid": f"{args.rings_drift_n}^3", "steps": 20, "dt": 0.01, "max": float(dd.max()),
+                 "rms": float(np.sqrt(np.mean(dd ** 2))),
+                 "max_displacement_fp64": float(np.abs(traj[bs.BS_FP64] - md.nodes).max())}
     line = {"metric": "node-tet interactions/s (RK2 steps of two colliding rings, FP32 path)",
             "value": pairs_per_step / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"two rings {args.rings_n}^3: {m.n_nodes} nodes, {m.n_tets} tets, Heun dt=0.01",
                        **PARAMS, "precision": "fp32"},
-            "max_displacement": float(np.abs(x - m.nodes).max()), "clocks": clk.summary()}
+            "max_displacement": float(np.abs(x - m.nodes).max()), "fp32_vs_fp64_drift": drift,
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -392,6 +409,8 @@ def main():
                          "launches; rings: Heun steps of two colliding rings; allray: the ray rule for every "
                          "pair on the 32^3 ring mesh")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
+    ap.add_argument("--rings-drift-n", type=int, default=32,
+                    help="rings workload: grid of the FP32-vs-FP64 drift run (20 Heun steps; 0 to skip)")
     ap.add_argument("--allray-mesh", default="ring32", choices=["ring32", "fourier64"],
                     help="allray workload: the 32^3 ring mesh (walk, all-ray kernel, dense path) or the 64^3 "
                          "Fourier mesh (the walk alone)")
