@@ -68,6 +68,8 @@ class OracleLib:
         lib.orc_velocity.argtypes = [_D, ctypes.c_int64, _I32, ctypes.c_int64, _D, _D, ctypes.c_int64,
                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_double, ctypes.c_double, _D, _I32]
+        lib.orc_velocity_dderiv.argtypes = [_D, ctypes.c_int64, _I32, ctypes.c_int64, _D, _D, _D, ctypes.c_int64,
+                                            ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
         lib.orc_num_threads.argtypes = []
         self.lib = lib
         self.path = path
@@ -146,6 +148,26 @@ class OracleLib:
         return (vel, cnt) if counts else vel
 
 
+    def velocity_dderiv(self, nodes, tets, omega, pts, dirs, n_theta=8, n_phi=16, eps_b=1e-12, tau=1e-9):
+        """All-ray velocity [n_pts, 3] and its derivative along dirs [n_pts, 3] (the stretching term
+        (omega . grad) v when dirs = omega at the points)."""
+        nodes = _f64(nodes).reshape(-1, 3)
+        omega = _f64(omega).reshape(-1, 3)
+        pts = _f64(pts).reshape(-1, 3)
+        dirs = _f64(dirs).reshape(-1, 3)
+        if dirs.shape != pts.shape:
+            raise ValueError("one direction per point")
+        tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+        vel = np.zeros((len(pts), 3))
+        dvel = np.zeros((len(pts), 3))
+        rc = self.lib.orc_velocity_dderiv(_dp(nodes), len(nodes), tets.ctypes.data_as(_I32), len(tets), _dp(omega),
+                                          _dp(pts), _dp(dirs), len(pts), int(n_theta), int(n_phi), float(eps_b),
+                                          float(tau), _dp(vel), _dp(dvel))
+        if rc != 0:
+            raise ValueError(f"oracle rejected arguments (code {rc})")
+        return vel, dvel
+
+
 def heun_step(orc, nodes, tets, omega, dt, **params):
     """One Heun (RK2) step of the node positions with the oracle's velocity (plain numpy arithmetic).
 
@@ -202,3 +224,7 @@ def line_tet(*args, **kw):
 
 def velocity(*args, **kw):
     return _load().velocity(*args, **kw)
+
+
+def velocity_dderiv(*args, **kw):
+    return _load().velocity_dderiv(*args, **kw)

@@ -496,6 +496,171 @@ int orc_velocity(const double *nodes, int64_t n_nodes, const int32_t *tets, int6
     return ORC_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Derivative of the all-ray velocity (every tet by the ray rule) at points  */
+/* x along directions e.  The paper gives no vorticity update; the stretching */
+/* term (omega . grad) v of the Lagrangian method is this derivative with     */
+/* e = omega(x).  Along one line the rule integrates                          */
+/*   J(x) = int sign(R) omega_h(x + R s) dR                                   */
+/* (omega_h: the piecewise-linear vorticity, zero outside the mesh), so       */
+/*   dJ/de = int sign(R) (e . grad omega_h) dR                                */
+/*           + [sign(R) omega_h(R) dR/de] at the mesh boundary crossings,    */
+/* the second term from the jump of omega_h to zero where the line leaves    */
+/* the mesh (inside, omega_h is continuous and the chord ends of neighbouring */
+/* tets cancel).  Per tet the first term is (|R1| - |R0|) (e . grad omega_T); */
+/* for a chord end on a boundary face with normal n, dR/de = -(n . e)/(n . s) */
+/* (moving x by e moves the line's crossing of the face plane), entering with */
+/* the sign - at R0 and + at R1; sign(R) = 0 for |R| <= 1e-12 h (the point    */
+/* itself).  dv/de = sum over lines k s x dJ/de.                              */
+/*   pts, dirs [n_pts][3]; vel, dvel [n_pts][3] overwritten (vel: as          */
+/*   orc_velocity with far_ratio = INFINITY).                                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t a, b, c;
+    int64_t slot; /* 4 * tet + face */
+} orc_face;
+
+static int face_cmp(const void *x, const void *y)
+{
+    const orc_face *p = (const orc_face *)x, *q = (const orc_face *)y;
+    if (p->a != q->a) return p->a < q->a ? -1 : 1;
+    if (p->b != q->b) return p->b < q->b ? -1 : 1;
+    if (p->c != q->c) return p->c < q->c ? -1 : 1;
+    return p->slot < q->slot ? -1 : (p->slot > q->slot);
+}
+
+static void sort3i(int32_t *v)
+{
+    int32_t t;
+    if (v[0] > v[1]) { t = v[0]; v[0] = v[1]; v[1] = t; }
+    if (v[1] > v[2]) { t = v[1]; v[1] = v[2]; v[2] = t; }
+    if (v[0] > v[1]) { t = v[0]; v[0] = v[1]; v[1] = t; }
+}
+
+int orc_velocity_dderiv(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                        const double *omega, const double *pts, const double *dirs, int64_t n_pts, int n_theta,
+                        int n_phi, double eps_b, double tau, double *vel, double *dvel)
+{
+    if (!nodes || !tets || !omega || !pts || !dirs || !vel || !dvel || n_pts < 0 || n_tets < 0 || n_nodes < 0)
+        return ORC_ERR_ARG;
+    if (n_theta < 1 || n_phi < 1 || n_theta > 512 || n_phi > 512) return ORC_ERR_ARG;
+    int rc = orc_velocity(nodes, n_nodes, tets, n_tets, omega, pts, n_pts, INFINITY, 1, n_theta, n_phi, 0, eps_b,
+                          tau, vel, NULL);
+    if (rc) return rc;
+    const int L = n_theta * n_phi;
+    double *S = (double *)malloc(sizeof(double) * 3 * L);
+    double *K = (double *)malloc(sizeof(double) * L);
+    char *bnd = (char *)calloc((size_t)(n_tets > 0 ? 4 * n_tets : 1), 1); /* face on the mesh boundary */
+    orc_face *F = (orc_face *)malloc(sizeof(orc_face) * (size_t)(n_tets > 0 ? 4 * n_tets : 1));
+    if (!S || !K || !bnd || !F) {
+        free(S); free(K); free(bnd); free(F);
+        return ORC_ERR_ARG;
+    }
+    orc_directions(n_phi, n_theta, S, K);
+    /* boundary faces: faces that belong to one tet only */
+    for (int64_t e = 0; e < n_tets; e++)
+        for (int f = 0; f < 4; f++) {
+            int32_t v[3] = {tets[4 * e + FACE_VERTS[f][0]], tets[4 * e + FACE_VERTS[f][1]], tets[4 * e + FACE_VERTS[f][2]]};
+            sort3i(v);
+            F[4 * e + f].a = v[0];
+            F[4 * e + f].b = v[1];
+            F[4 * e + f].c = v[2];
+            F[4 * e + f].slot = 4 * e + f;
+        }
+    qsort(F, (size_t)(4 * n_tets), sizeof(orc_face), face_cmp);
+    for (int64_t i = 0; i < 4 * n_tets;) {
+        int64_t j = i + 1;
+        while (j < 4 * n_tets && F[j].a == F[i].a && F[j].b == F[i].b && F[j].c == F[i].c) j++;
+        if (j - i == 1) bnd[F[i].slot] = 1;
+        i = j;
+    }
+    free(F);
+
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t p = 0; p < n_pts; p++) {
+        const double *x = pts + 3 * p, *ed = dirs + 3 * p;
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int64_t e = 0; e < n_tets; e++) {
+            double v[12], om[12];
+            for (int i = 0; i < 4; i++)
+                for (int j = 0; j < 3; j++) {
+                    v[3 * i + j] = nodes[3 * (int64_t)tets[4 * e + i] + j];
+                    om[3 * i + j] = omega[3 * (int64_t)tets[4 * e + i] + j];
+                }
+            /* barycentric gradients (face planes) and e . grad omega_T */
+            double e1[3], e2[3], e3[3], gl[4][3], c23[3], c31[3], c12[3];
+            sub3(v + 3, v, e1);
+            sub3(v + 6, v, e2);
+            sub3(v + 9, v, e3);
+            cross3(e2, e3, c23);
+            cross3(e3, e1, c31);
+            cross3(e1, e2, c12);
+            double V6 = dot3(e1, c23);
+            for (int j = 0; j < 3; j++) {
+                gl[1][j] = c23[j] / V6;
+                gl[2][j] = c31[j] / V6;
+                gl[3][j] = c12[j] / V6;
+                gl[0][j] = -(gl[1][j] + gl[2][j] + gl[3][j]);
+            }
+            double gw[3] = {0.0, 0.0, 0.0};
+            for (int i = 0; i < 4; i++) {
+                double ge = dot3(gl[i], ed);
+                for (int j = 0; j < 3; j++) gw[j] += om[3 * i + j] * ge;
+            }
+            double hmax2 = 0.0;
+            for (int a = 0; a < 4; a++)
+                for (int b = a + 1; b < 4; b++) {
+                    double d[3];
+                    sub3(v + 3 * b, v + 3 * a, d);
+                    if (dot3(d, d) > hmax2) hmax2 = dot3(d, d);
+                }
+            const double hmax = sqrt(hmax2);
+            for (int l = 0; l < L; l++) {
+                const double *s = S + 3 * l;
+                int nh = 0, f0 = -1, f1 = -1;
+                double R0 = 0.0, R1 = 0.0, w0[3] = {0, 0, 0}, w1[3] = {0, 0, 0};
+                for (int f = 0; f < 4; f++) {
+                    int a = FACE_VERTS[f][0], b = FACE_VERTS[f][1], c = FACE_VERTS[f][2];
+                    double t, u, vv;
+                    if (!orc_moller_trumbore(x, s, v + 3 * a, v + 3 * b, v + 3 * c, 1e-12, eps_b, &t, &u, &vv)) continue;
+                    double w[3]; /* omega at the hit from the face's area coordinates */
+                    for (int j = 0; j < 3; j++)
+                        w[j] = om[3 * a + j] + u * (om[3 * b + j] - om[3 * a + j]) + vv * (om[3 * c + j] - om[3 * a + j]);
+                    if (nh == 0 || t < R0) { R0 = t; f0 = f; memcpy(w0, w, sizeof w); }
+                    if (nh == 0 || t > R1) { R1 = t; f1 = f; memcpy(w1, w, sizeof w); }
+                    nh++;
+                }
+                if (nh < 2 || !(R1 - R0 > 0.0)) continue;
+                double dJ[3];
+                for (int j = 0; j < 3; j++) dJ[j] = (fabs(R1) - fabs(R0)) * gw[j];
+                const int ends[2] = {f0, f1};
+                const double Rs[2] = {R0, R1}, sgn_end[2] = {-1.0, 1.0};
+                const double *ws[2] = {w0, w1};
+                for (int k = 0; k < 2; k++) {
+                    if (!bnd[4 * e + ends[k]]) continue;
+                    const double R = Rs[k];
+                    const double sg = fabs(R) <= 1e-12 * hmax ? 0.0 : (R > 0.0 ? 1.0 : -1.0);
+                    if (sg == 0.0) continue;
+                    /* normal of the end's face plane and dR/de = -(n . e)/(n . s) */
+                    int a = FACE_VERTS[ends[k]][0], b = FACE_VERTS[ends[k]][1], c = FACE_VERTS[ends[k]][2];
+                    double ea[3], eb[3], n[3];
+                    sub3(v + 3 * b, v + 3 * a, ea);
+                    sub3(v + 3 * c, v + 3 * a, eb);
+                    cross3(ea, eb, n);
+                    const double dR = -dot3(n, ed) / dot3(n, s);
+                    for (int j = 0; j < 3; j++) dJ[j] += sgn_end[k] * sg * ws[k][j] * dR;
+                }
+                double sxd[3];
+                cross3(s, dJ, sxd);
+                for (int j = 0; j < 3; j++) acc[j] += K[l] * sxd[j];
+            }
+        }
+        for (int j = 0; j < 3; j++) dvel[3 * p + j] = acc[j];
+    }
+    free(S); free(K); free(bnd);
+    return ORC_OK;
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP

@@ -13,6 +13,10 @@ mistake) and returns the numbers the tests compare with their bounds.
   hill         Hill's spherical vortex (Section 3.1), with the velocity
                re-derived from the Stokes stream function (the printed
                formula is garbled, see ``hill_velocity``).
+  dderiv       derivative of the all-ray velocity along a direction (the
+               stretching term): central differences of the oracle's own
+               velocity at interior points and nodes, and the uniform ball's
+               exact derivative omega x e / 3.
 """
 from __future__ import annotations
 
@@ -161,3 +165,30 @@ def divergence(orc, N=64, far_ratio=np.inf, count=4, seed=3):
     grad = (v[:, :, 0, :] - v[:, :, 1, :]) / (2 * d)  # [pt, j (d/dx_j), component]
     div = np.einsum("pjj->p", grad)
     return float(np.abs(div).max() / np.abs(grad).max())
+
+
+def dderiv(orc, n=5, count=20, ball_n=7):
+    """Largest errors (relative to the largest derivative) of orc.velocity_dderiv against central differences
+    of orc.velocity (all-ray, 8 x 16 directions) at interior off-node points (step 1e-5) and interior nodes
+    (step 1e-6), and against the uniform ball's exact derivative omega x e / 3 inside (16 x 32 directions)."""
+    rng = np.random.default_rng(23)
+    nodes, tets = jittered_grid(n, 0.0, 1.0, rng)
+    om = np.array([0.0, 0.0, 1.0]) + 0.3 * rng.standard_normal(nodes.shape)
+    P = dict(n_theta=8, n_phi=16)
+    inner = np.all((nodes > 1e-9) & (nodes < 1 - 1e-9), axis=1)
+    out = {}
+    for name, pts, d in (("points", rng.uniform(0.15, 0.85, (count, 3)), 1e-5),
+                         ("nodes", nodes[inner][:count], 1e-6)):
+        e = rng.standard_normal(pts.shape)
+        _, dv = orc.velocity_dderiv(nodes, tets, om, pts, e, **P)
+        vp = orc.velocity(nodes, tets, om, pts + d * e, far_ratio=np.inf, **P)
+        vm = orc.velocity(nodes, tets, om, pts - d * e, far_ratio=np.inf, **P)
+        out[name] = float(np.abs((vp - vm) / (2 * d) - dv).max() / np.abs(dv).max())
+    m = ball_mesh(ball_n)
+    w0 = np.array([0.3, -0.2, 1.0])
+    pts = rng.uniform(-0.4, 0.4, (count, 3))
+    e = rng.standard_normal((count, 3))
+    _, dv = orc.velocity_dderiv(m.nodes, m.tets, np.tile(w0, (len(m.nodes), 1)), pts, e, n_theta=16, n_phi=32)
+    ex = np.cross(w0, e) / 3.0
+    out["ball"] = float(np.abs(dv - ex).max() / np.abs(ex).max())
+    return out

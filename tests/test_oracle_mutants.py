@@ -43,6 +43,11 @@ MUTANTS = {
     "circumradius halved": ("*circumradius = sqrt(dot3(dp, dp));", "*circumradius = 0.5 * sqrt(dot3(dp, dp));"),
     "far rule volume factor dropped": ("double f = -inv4pi * wq[q] * vol[e] / (R * R * R);",
                                        "double f = -inv4pi * wq[q] / (R * R * R);"),
+    "derivative: boundary term dropped": ("if (!bnd[4 * e + ends[k]]) continue;", "if (1) continue;"),
+    "derivative: face-crossing shift sign": ("const double dR = -dot3(n, ed) / dot3(n, s);",
+                                             "const double dR = dot3(n, ed) / dot3(n, s);"),
+    "derivative: signed chord length": ("dJ[j] = (fabs(R1) - fabs(R0)) * gw[j];", "dJ[j] = (R1 - R0) * gw[j];"),
+    "derivative: vorticity gradient index": ("gw[j] += om[3 * i + j] * ge;", "gw[j] += om[3 * ((i + 1) % 4) + j] * ge;"),
 }
 
 
@@ -98,6 +103,10 @@ def battery(orc):
         failed.append("ball outside")
     if pins.hill(orc, ns=(9,), count=8)[0] > 2e-2:
         failed.append("hill")
+    # derivative along a direction (stretching term) against central differences and the ball
+    d = pins.dderiv(orc, count=10)
+    if d["points"] > 1e-4 or d["nodes"] > 2e-3 or d["ball"] > 2.5e-2:
+        failed.append("derivative")
     return failed
 
 
