@@ -106,19 +106,50 @@ BS_API int bs_velocity_host(bs_handle h, const double *eval_pts_host, int64_t k,
  * neighbours (the tracing through the mesh that the paper's conclusion, §4,
  * proposes): from the node, each half-line crosses the tets it meets one after
  * the other until it leaves the mesh, each tet adding its chord of Eq. 5.
- * That is exact when every line leaves the mesh once: the walk is used when the
- * mesh is conforming (a face belongs to at most two tets, every node to some
- * tet) and its domain convex (checked on the device after each change of the
- * node positions: every boundary node on the inner side of every boundary face
- * plane, within 1e-9 of the face size); otherwise the call evaluates the nodes
- * as bs_velocity does.  The first such call builds the face adjacency and the
- * node-to-tet incidence on the host (synchronous, once per handle; about
- * 24 bytes per tet of device memory, owned by the handle); later calls are
- * asynchronous on `stream`.  A walk that exceeds max(4096, 64 n_tets^(1/3))
+ * The walk is used when the mesh is conforming (a face belongs to at most two
+ * tets, every node to some tet); otherwise the call evaluates the nodes as
+ * bs_velocity does.  On a convex domain every line leaves the mesh once; on a
+ * non-convex one (checked on the device after each change of the node
+ * positions: some boundary node outside some boundary face's plane) a line
+ * that leaves is followed through a uniform grid of the boundary faces to
+ * where it comes back in, if it does.  The first such call builds the face
+ * adjacency and the node-to-tet incidence on the host (synchronous, once per
+ * handle; about 200 bytes per tet and 100 per boundary face of device memory,
+ * owned by the handle); later calls are asynchronous on `stream`.  A walk that exceeds max(4096, 64 n_tets^(1/3))
  * tets (impossible on a valid mesh) stops and raises BS_ERR_TIMEOUT at the next
  * bs_status.  Setting the environment variable BS_WALK=0 disables the walk.
  * Errors: BS_ERR_ARG, BS_ERR_ORDER, BS_ERR_CUDA. */
 BS_API int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, void *stream);
+
+/* Velocity at the nodes (as bs_velocity_nodes) and its derivative along a
+ * direction per node: dout_dev[i] = (e_i . grad) v at node i, with e_i =
+ * dirs_dev[i] ([n_nodes][3] device, or NULL for the nodal vorticity, which
+ * makes dout the stretching term (omega . grad) v of the vorticity equation;
+ * the paper gives no vorticity update).  Defined for the all-ray method
+ * (far_ratio = +inf, at most 4096 directions): along each line the rule
+ * integrates the piecewise-linear vorticity omega_h (zero outside the mesh),
+ * and the derivative is the chord length in each tet the line crosses times
+ * e . grad omega in that tet, plus the jump of omega to zero where the line
+ * leaves the mesh (omega there times the shift of the exit point), computed
+ * during the mesh walk.  At a node on the mesh boundary the rule is not
+ * differentiable (omega jumps at the node itself); the value returned there
+ * leaves out the jump at the node.  Other parameters return BS_ERR_ARG; a mesh
+ * the walk cannot serve (not conforming) gets the velocity but no derivative,
+ * reported as BS_ERR_MESH by the next bs_status.
+ * Asynchronous on `stream` after the first call (see bs_velocity_nodes). */
+BS_API int bs_velocity_nodes_dderiv(bs_handle h, const bs_params *p, const double *dirs_dev, double *out_dev,
+                                    double *dout_dev, void *stream);
+
+/* One Heun step of the node positions and the nodal vorticity with vortex
+ * stretching: dx/dt = v, d omega/dt = (omega . grad) v at the nodes, both from
+ * bs_velocity_nodes_dderiv (all-ray method only, see there):
+ *   (v0, s0) at (x0, omega0); x* = x0 + dt v0, omega* = omega0 + dt s0;
+ *   (v1, s1) at (x*, omega*); x1 = x0 + dt (v0 + v1)/2,
+ *   omega1 = omega0 + dt (s0 + s1)/2.
+ * The handle's nodes and vorticity become (x1, omega1).  p->counts must be
+ * NULL.  The first call allocates six [n_nodes][3] work arrays owned by the
+ * handle.  Asynchronous on `stream`. */
+BS_API int bs_rk2_step_stretch(bs_handle h, double dt, const bs_params *p, void *stream);
 
 /* One Heun (RK2) step of the Lagrangian vortex method (Section 1: the nodes
  * move with the flow and the velocity is re-evaluated on the moved mesh):
@@ -134,6 +165,10 @@ BS_API int bs_rk2_step(bs_handle h, double dt, const bs_params *p, void *stream)
 
 /* Copy the handle's current node positions to device array nodes_dev [n_nodes][3]. */
 BS_API int bs_nodes(bs_handle h, double *nodes_dev, void *stream);
+
+/* Copy the handle's current nodal vorticity to device array omega_dev [n_nodes][3]
+ * (it changes under bs_update and bs_rk2_step_stretch). */
+BS_API int bs_omega(bs_handle h, double *omega_dev, void *stream);
 
 /* Synchronise `stream` and return BS_ERR_MESH / BS_ERR_TIMEOUT if a kernel of
  * this handle raised its device error flag since the last call (clears it). */

@@ -182,6 +182,18 @@ def heun_step(orc, nodes, tets, omega, dt, **params):
     return x0 + 0.5 * dt * (v0 + v1)
 
 
+def heun_step_stretch(orc, nodes, tets, omega, dt, n_theta=8, n_phi=16):
+    """One Heun step of node positions and nodal vorticity with vortex stretching (plain numpy arithmetic),
+    all-ray velocity: dx/dt = v, d omega/dt = (omega . grad) v at the nodes (orc.velocity_dderiv with the
+    nodal vorticity as the directions).  Returns (x1, omega1)."""
+    x0 = np.ascontiguousarray(nodes, dtype=np.float64)
+    w0 = np.ascontiguousarray(omega, dtype=np.float64)
+    v0, s0 = orc.velocity_dderiv(x0, tets, w0, x0, w0, n_theta=n_theta, n_phi=n_phi)
+    xs, ws = x0 + dt * v0, w0 + dt * s0
+    v1, s1 = orc.velocity_dderiv(xs, tets, ws, xs, ws, n_theta=n_theta, n_phi=n_phi)
+    return x0 + 0.5 * dt * (v0 + v1), w0 + 0.5 * dt * (s0 + s1)
+
+
 def _load() -> OracleLib:
     global _lib
     with _lock:

@@ -22,7 +22,8 @@ BS_FP64, BS_FP32 = 0, 1
 EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_status", "bs_destroy",
             "bs_mesh_size", "bs_last_error", "bs_direction_table", "bs_tet_rule", "bs_batch_create",
             "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read",
-            "bs_velocity_noalloc", "bs_tuned_variant", "bs_rk2_step", "bs_nodes", "bs_velocity_nodes")
+            "bs_velocity_noalloc", "bs_tuned_variant", "bs_rk2_step", "bs_nodes", "bs_velocity_nodes",
+            "bs_velocity_nodes_dderiv", "bs_rk2_step_stretch", "bs_omega")
 
 
 class BSError(RuntimeError):
@@ -72,6 +73,9 @@ def load(path: str = LIB_PATH):
         lib.bs_rk2_step.argtypes = [_P, ctypes.c_double, ctypes.POINTER(bs_params), _P]
         lib.bs_nodes.argtypes = [_P, _P, _P]
         lib.bs_velocity_nodes.argtypes = [_P, ctypes.POINTER(bs_params), _P, _P]
+        lib.bs_velocity_nodes_dderiv.argtypes = [_P, ctypes.POINTER(bs_params), _P, _P, _P, _P]
+        lib.bs_rk2_step_stretch.argtypes = [_P, ctypes.c_double, ctypes.POINTER(bs_params), _P]
+        lib.bs_omega.argtypes = [_P, _P, _P]
         lib.bs_tuned_variant.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         lib.bs_profile.argtypes = [_P, ctypes.c_int]
         lib.bs_profile_read.argtypes = [_P, _D, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -177,6 +181,39 @@ class Mesh:
         p = make_params(counts=counts_dev, **params)
         _check(load().bs_velocity_nodes(self.handle, ctypes.byref(p), out_dev.data_ptr(), _stream_ptr(stream)))
         return out_dev
+
+    def bs_velocity_nodes_dderiv(self, dirs_dev=None, out_dev=None, dout_dev=None, stream=None, **params):
+        """Velocity at the nodes and its derivative along dirs ([n_nodes, 3] CUDA float64, or None for the
+        nodal vorticity: the stretching term); returns (velocity, derivative)."""
+        import torch
+
+        n = self.n_nodes
+        if out_dev is None:
+            out_dev = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        if dout_dev is None:
+            dout_dev = torch.empty((n, 3), dtype=torch.float64, device="cuda")
+        _require_dev(out_dev, (n, 3))
+        _require_dev(dout_dev, (n, 3))
+        if dirs_dev is not None:
+            _require_dev(dirs_dev, (n, 3))
+        p = make_params(**params)
+        _check(load().bs_velocity_nodes_dderiv(self.handle, ctypes.byref(p),
+                                               None if dirs_dev is None else dirs_dev.data_ptr(),
+                                               out_dev.data_ptr(), dout_dev.data_ptr(), _stream_ptr(stream)))
+        return out_dev, dout_dev
+
+    def bs_rk2_step_stretch(self, dt: float, stream=None, **params):
+        """One Heun step of the nodes and the nodal vorticity with vortex stretching (all-ray method)."""
+        p = make_params(**params)
+        _check(load().bs_rk2_step_stretch(self.handle, float(dt), ctypes.byref(p), _stream_ptr(stream)))
+
+    def bs_omega(self):
+        """Current nodal vorticity as a float64 [n_nodes, 3] CUDA tensor."""
+        import torch
+
+        out = torch.empty((self.n_nodes, 3), dtype=torch.float64, device="cuda")
+        _check(load().bs_omega(self.handle, out.data_ptr(), None))
+        return out
 
     def bs_velocity_host(self, pts, stream=None, out=None, **params):
         """Velocity at host points (numpy float64 [k, 3]) through host buffers."""

@@ -95,8 +95,9 @@ struct bs_ctx {
     // staging for bs_velocity_host
     double *stage = nullptr;
     size_t stage_cap = 0;
-    // work arrays of bs_rk2_step: x0, v0, v1 (each [n_nodes][3])
+    // work arrays of bs_rk2_step: x0, v0, v1 (each [n_nodes][3]); of bs_rk2_step_stretch also w0, s0, s1
     double *rk = nullptr;
+    double *rk_w = nullptr;
     int occ[2][65][kMaxVariants] = {};  // cached CTAs per SM by [precision][Q][variant]
     int ray_occ[2] = {};                // cached CTAs per SM of the all-ray kernel by [precision]
     int ray_occ_L[2] = {};              // ... for this many directions
@@ -109,6 +110,7 @@ struct bs_ctx {
     int64_t walk_n_bface = 0, walk_n_bnode = 0;
     int *walk_mode = nullptr;      // device: the walk is valid for the current node positions
     float4 *walk_rec = nullptr;    // float32 walk records [n_tets][kWalkRecVec4]
+    WalkGridArrays walk_grid;      // boundary faces on a uniform grid (re-entries into a non-convex mesh)
     uint64_t walk_version = 0;     // mesh version when walk_mode was computed
     // kernel timing (bs_profile)
     bool prof = false;
@@ -135,7 +137,8 @@ void free_ctx(bs_ctx *h)
                     h->first_bad, h->work_counter, h->rule.bary, h->rule.w, h->far32, h->far64, h->lines.f32,
                     h->lines.f64, h->partial, h->stage, h->rk, h->tile_hdr, h->perm, h->keys,
                     h->cell_count, h->box, h->walk_nbr, h->walk_inc_off, h->walk_inc, h->walk_bface,
-                    h->walk_bnode, h->walk_mode, h->walk_rec};
+                    h->walk_bnode, h->walk_mode, h->walk_rec, h->rk_w, h->walk_grid.grid,
+                    h->walk_grid.cell_off, h->walk_grid.cell_cnt, h->walk_grid.cell_face, h->walk_grid.geo};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete h;
@@ -365,6 +368,14 @@ int bs_rk2_step(bs_handle h, double dt, const bs_params *p, void *stream)
     return BS_OK;
 }
 
+int bs_omega(bs_handle h, double *omega_dev, void *stream)
+{
+    if (!h || !omega_dev) return fail(BS_ERR_ARG, "NULL argument");
+    BS_CUDA(cudaMemcpyAsync(omega_dev, h->omega, sizeof(double) * 3 * h->n_nodes, cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
+    return BS_OK;
+}
+
 int bs_nodes(bs_handle h, double *nodes_dev, void *stream)
 {
     if (!h || !nodes_dev) return fail(BS_ERR_ARG, "NULL argument");
@@ -382,6 +393,9 @@ int bs_status(bs_handle h, void *stream)
     BS_CUDA(cudaMemset(h->flag, 0, sizeof(int)));
     if (flag & kFlagTimeout) return fail(BS_ERR_TIMEOUT, "a bounded device wait gave up");
     if (flag & kFlagWalk) return fail(BS_ERR_TIMEOUT, "a mesh walk did not leave the mesh within its step limit");
+    if (flag & kFlagNoWalk)
+        return fail(BS_ERR_MESH, "the derivative along directions needs a conforming mesh with a convex domain "
+                                 "(the mesh walk); the velocity was computed, the derivative was not");
     if (flag & (kFlagMeshIndex | kFlagMeshVolume)) return fail(BS_ERR_MESH, "degenerate tet after bs_update");
     return BS_OK;
 }
@@ -432,6 +446,18 @@ cudaError_t ensure_walk(bs_ctx *h)
         return e;
     h->walk_n_bface = (int64_t)w.bface.size();
     h->walk_n_bnode = (int64_t)w.bnode.size();
+    // face grid: about two boundary faces per cell of a G^3 grid; lists of up to 16 cells per face
+    WalkGridArrays &g = h->walk_grid;
+    g.G = (int)std::min<double>(128.0, std::max(4.0, std::round(std::cbrt(0.5 * (double)h->walk_n_bface))));
+    const int64_t cells = (int64_t)g.G * g.G * g.G;
+    g.cap = 16 * std::max<int64_t>(h->walk_n_bface, 1);
+    if ((e = cudaMalloc((void **)&g.grid, sizeof(WalkGrid))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&g.cell_off, sizeof(int32_t) * (cells + 1))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&g.cell_cnt, sizeof(int32_t) * cells)) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&g.cell_face, sizeof(int32_t) * g.cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void **)&g.geo, sizeof(double) * kBFaceGeo * std::max<int64_t>(h->walk_n_bface, 1))) !=
+        cudaSuccess)
+        return e;
     h->walk_conforming = w.conforming && 4 * h->n_tets < INT32_MAX;
     h->walk_built = true;
     h->walk_version = 0;
@@ -440,7 +466,11 @@ cudaError_t ensure_walk(bs_ctx *h)
 
 }  // namespace
 
-int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, void *stream)
+namespace {
+
+// Velocity at the nodes (and, with dout, its derivative along dirs or the nodal vorticity): the mesh walk
+// in all-ray mode, else bs_velocity at the nodes.
+int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *dirs, double *dout, void *stream)
 {
     if (!h) return fail(BS_ERR_ARG, "handle is NULL");
     int rc = check_params(p);
@@ -449,6 +479,9 @@ int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, void *st
     const int L = p->n_phi * p->n_theta;
     const char *env = getenv("BS_WALK");
     const bool walk = isinf(p->far_ratio) && L <= kRayLinesSmemMax && h->n_tets > 0 && !(env && atoi(env) == 0);
+    if (dout && !walk)
+        return fail(BS_ERR_ARG, "the derivative along directions is the all-ray method's (far_ratio = +inf, at most "
+                                "4096 directions) computed by the mesh walk");
     if (!walk) return velocity_impl(h, h->nodes, h->n_nodes, p, out_dev, stream, nullptr);
     cudaStream_t st = (cudaStream_t)stream;
     BS_CUDA(ensure_walk(h));
@@ -457,6 +490,12 @@ int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, void *st
         BS_CUDA(launch_walk_records(h->near32, h->walk_nbr, h->n_tets, h->walk_rec, st));
         BS_CUDA(launch_convex_check(h->nodes, h->tets, h->walk_bface, h->walk_n_bface, h->walk_bnode,
                                     h->walk_n_bnode, h->walk_conforming ? 1 : 0, h->walk_mode, st));
+        if (h->walk_conforming) {
+            BS_CUDA(launch_walk_grid(h->nodes, h->tets, h->walk_bface, h->walk_n_bface, h->walk_bnode,
+                                     h->walk_n_bnode, h->walk_grid, st));
+            BS_CUDA(launch_walk_finalize(h->walk_grid.grid, h->walk_mode, st));
+            if (h->prof) h->prof_all += 5;
+        }
         h->walk_version = h->version;
         if (h->prof)
             h->prof_all += 2 + (h->walk_conforming && h->walk_n_bface > 0 ? (h->walk_n_bface + 65534) / 65535 : 0);
@@ -476,7 +515,15 @@ int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, void *st
     w.L = L;
     w.out = out_dev;
     w.counts = p->counts;
+    w.omega = h->omega;
+    w.dirs = dirs;
+    w.dout = dout;
     w.mode = h->walk_mode;
+    w.grid = h->walk_grid.grid;
+    w.cell_off = h->walk_grid.cell_off;
+    w.cell_face = h->walk_grid.cell_face;
+    w.bface = h->walk_bface;
+    w.bgeo = h->walk_grid.geo;
     w.flag = h->flag;
     // no valid mesh needs more steps than tets; a small cap keeps a broken walk short
     w.max_steps = (int)std::min<int64_t>(h->n_tets, std::max<int64_t>(4096, 64 * (int64_t)std::cbrt((double)h->n_tets)));
@@ -502,6 +549,49 @@ int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, void *st
     h->prof = prof;
     if (prof) h->prof_all += 5 + 3;
     return rc;
+}
+
+}  // namespace
+
+int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, void *stream)
+{
+    return nodes_impl(h, p, out_dev, nullptr, nullptr, stream);
+}
+
+int bs_velocity_nodes_dderiv(bs_handle h, const bs_params *p, const double *dirs_dev, double *out_dev,
+                             double *dout_dev, void *stream)
+{
+    if (!dout_dev) return fail(BS_ERR_ARG, "NULL derivative output");
+    return nodes_impl(h, p, out_dev, dirs_dev, dout_dev, stream);
+}
+
+int bs_rk2_step_stretch(bs_handle h, double dt, const bs_params *p, void *stream)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (p->counts) return fail(BS_ERR_ARG, "bs_rk2_step_stretch: counts are not supported (set p->counts = NULL)");
+    if (!std::isfinite(dt)) return fail(BS_ERR_ARG, "bs_rk2_step_stretch: dt must be finite");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = h->n_nodes, nv = 3 * n;
+    if (!h->rk) BS_CUDA(cudaMallocAsync((void **)&h->rk, sizeof(double) * 3 * nv, st));
+    if (!h->rk_w) BS_CUDA(cudaMallocAsync((void **)&h->rk_w, sizeof(double) * 3 * nv, st));
+    double *x0 = h->rk, *v0 = h->rk + nv, *v1 = h->rk + 2 * nv;
+    double *w0 = h->rk_w, *s0 = h->rk_w + nv, *s1 = h->rk_w + 2 * nv;
+    BS_CUDA(cudaMemcpyAsync(x0, h->nodes, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+    BS_CUDA(cudaMemcpyAsync(w0, h->omega, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+    // stage 1: v0 and the stretching s0 = (omega . grad) v at (x0, w0)
+    if ((rc = nodes_impl(h, p, v0, nullptr, s0, stream))) return rc;
+    BS_CUDA(launch_euler(x0, v0, dt, nv, h->nodes, st));  // x* = x0 + dt v0
+    BS_CUDA(launch_euler(w0, s0, dt, nv, h->omega, st));  // w* = w0 + dt s0
+    if ((rc = bs_update(h, nullptr, nullptr, stream))) return rc;
+    // stage 2 at (x*, w*), then the Heun average
+    if ((rc = nodes_impl(h, p, v1, nullptr, s1, stream))) return rc;
+    BS_CUDA(launch_heun(x0, v0, v1, dt, nv, h->nodes, st));
+    BS_CUDA(launch_heun(w0, s0, s1, dt, nv, h->omega, st));
+    if ((rc = bs_update(h, nullptr, nullptr, stream))) return rc;
+    if (h->prof) h->prof_all += 4;
+    return BS_OK;
 }
 
 namespace {

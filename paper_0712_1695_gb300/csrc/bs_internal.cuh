@@ -89,7 +89,8 @@ struct TetRule {
 constexpr int kFlagMeshIndex = 1;
 constexpr int kFlagMeshVolume = 2;
 constexpr int kFlagTimeout = 4;
-constexpr int kFlagWalk = 8;  // a mesh walk hit its step limit or a tet with no face ahead
+constexpr int kFlagWalk = 8;     // a mesh walk hit its step limit or a tet with no face ahead
+constexpr int kFlagNoWalk = 16;  // a derivative along directions was asked of a mesh the walk cannot serve
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).
@@ -187,6 +188,23 @@ struct WalkMesh {
     bool conforming = false;       // every face shared by at most two tets, every node in some tet
 };
 bool build_walk_mesh(const int32_t *tets_host, int64_t n_nodes, int64_t n_tets, WalkMesh &w);
+// Uniform grid of the boundary faces (device), for finding where a line re-enters a non-convex mesh.
+struct WalkGrid {
+    double lo[3], cell[3], inv[3];  // origin, cell size and its inverse per axis
+    int G;                          // cells per axis (G^3 cells)
+    int ok;                         // 0 when the face lists overflowed their capacity
+};
+// Per boundary face (double, outward normal e1 x e2): vertex p0, edges e1, e2; and the face's (tet << 2) | face.
+constexpr int kBFaceGeo = 9;
+struct WalkGridArrays {
+    WalkGrid *grid = nullptr;
+    int32_t *cell_off = nullptr;   // [G^3 + 1]
+    int32_t *cell_cnt = nullptr;   // [G^3] scratch
+    int32_t *cell_face = nullptr;  // [cap] boundary-face indices
+    double *geo = nullptr;         // [n_bface][kBFaceGeo]
+    int G = 0;
+    int64_t cap = 0;
+};
 struct WalkArgs {
     const double *nodes = nullptr;  // [n_nodes][3], also the evaluation points
     int64_t n_nodes = 0, n_tets = 0;
@@ -199,7 +217,14 @@ struct WalkArgs {
     int L = 0;
     double *out = nullptr;       // [n_nodes][3]
     int32_t *counts = nullptr;   // [n_nodes][3] or null
-    const int *mode = nullptr;   // device flag: the walk is valid (convex conforming mesh)
+    // derivative of the velocity along directions e (the stretching term (omega . grad) v when e = omega):
+    const double *omega = nullptr;  // [n_nodes][3] nodal vorticity (the directions when dirs is null)
+    const double *dirs = nullptr;   // [n_nodes][3] or null
+    double *dout = nullptr;         // [n_nodes][3] or null (no derivative)
+    const int *mode = nullptr;   // device: 0 no walk, 1 walk (convex domain), 2 walk with re-entries
+    const WalkGrid *grid = nullptr;
+    const int32_t *cell_off = nullptr, *cell_face = nullptr, *bface = nullptr;
+    const double *bgeo = nullptr;
     int *flag = nullptr;
     int max_steps = 0;           // tets per half-line before the walk gives up (error flag)
 };
@@ -207,7 +232,12 @@ constexpr int kWalkRecVec4 = 8;  // float4 per float32 walk record (one 128-byte
 // float32 walk records from the near records and the face neighbours (after every mesh update)
 cudaError_t launch_walk_records(const float4 *near32, const int32_t *nbr, int64_t n_tets, float4 *wrec,
                                 cudaStream_t st);
-// mode := conforming, then cleared if a boundary node lies outside a boundary face's plane
+cudaError_t launch_walk_grid(const double *nodes, const int32_t *tets, const int32_t *bface, int64_t n_bface,
+                             const int32_t *bnode, int64_t n_bnode, const WalkGridArrays &g, cudaStream_t st);
+// after the convexity check and the grid: a non-convex mesh whose face grid overflowed gets mode 0
+cudaError_t launch_walk_finalize(const WalkGrid *g, int *mode, cudaStream_t st);
+// mode := 1 if conforming (else 0), then 2 if a boundary node lies outside a boundary face's plane
+// (a non-convex domain: the walk then looks for re-entries through the grid)
 cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const int32_t *bface, int64_t n_bface,
                                 const int32_t *bnode, int64_t n_bnode, int conforming, int *mode, cudaStream_t st);
 cudaError_t launch_walk(int precision, const WalkArgs &a, cudaStream_t st, cudaEvent_t ev_start = nullptr,

@@ -10,13 +10,21 @@
 // attains hi, and the next tet is the face neighbour across it, until the line leaves the
 // mesh.  Each visited tet contributes its chord on the half-line, so the sum over both
 // half-lines is the ray rule's sum over all tets (Eq. 5 with sign(t)): with I(d) the integral
-// of omega along the half-line in direction d, J = I(s) - I(-s).  That holds when every line
-// leaves the mesh once, i.e. on a convex domain: the library checks, after every change of
-// the node positions, that every boundary node lies on the inner side of every boundary
-// face's plane, and uses the walk only then (and only on a conforming mesh whose nodes all
-// belong to some tet); otherwise the all-ray kernel evaluates the nodes.  The two paths are
-// both queued and each returns at once when the other one is in charge, so nothing waits
-// on the host.
+// of omega along the half-line in direction d, J = I(s) - I(-s).  On a convex domain every line
+// leaves the mesh once.  After every change of the node positions the library checks that every
+// boundary node lies on the inner side of every boundary face's plane; where that fails (a
+// non-convex domain) a line that leaves the mesh is followed through a uniform grid of the
+// boundary faces to the face where it comes back in, if any, and the walk goes on from there.
+// The walk needs a conforming mesh whose nodes all belong to some tet; otherwise the all-ray
+// kernel evaluates the nodes.  The paths are all queued and each returns at once when another
+// one is in charge, so nothing waits on the host.
+//
+// Derivative along a direction e (the stretching term (omega . grad) v of the Lagrangian method with
+// e = omega): per half-line dI/de = sum over the tets it crosses of the chord length on the
+// half-line times e . grad omega_T, plus omega(exit) dT/de where the line leaves the mesh
+// (omega jumps to zero there; T is the exit parameter, dT/de = -(g_f . e)/(g_f . d) for the
+// boundary face f with barycentric gradient g_f); inside the mesh omega is continuous and the
+// chord ends of neighbouring tets cancel.  dv/de = sum over lines k s x (dI(s) - dI(-s)).
 //
 // One warp per node, the lanes over the lines; per-node sums by warp reduction (no atomics,
 // deterministic).  The float32 walk reads one 128-byte record per tet step (gradients, longest
@@ -40,10 +48,109 @@ constexpr int kWalkThreads = 128;     // 4 nodes per CTA
 constexpr float kStartTolF = 1e-6f;   // a half-line whose best start margin is below -tol leaves the mesh at x
 constexpr double kStartTolD = 1e-12;
 
+// First boundary face through which the line x + t d enters the mesh at some t > t0 (the line is
+// outside the mesh just after t0), or -1.  A 3-D DDA over the uniform grid of boundary faces from
+// where the line enters the grid's box; in each cell, Moller-Trumbore against the cell's faces
+// (a face is an entry when d points against its outward normal); the nearest entry within the
+// cells visited so far ends the search once the line has left the cell holding it.  The search
+// visits at most 3G + 3 cells.
+// Clip of the line to the slab [lo, hi] of one axis (tin, tout narrowed); false when the line misses it.
+__device__ __forceinline__ bool slab(double x, double d, double lo, double hi, double &tin, double &tout)
+{
+    if (d == 0.0) return x >= lo && x <= hi;
+    const double t1 = (lo - x) / d, t2 = (hi - x) / d;
+    tin = fmax(tin, fmin(t1, t2));
+    tout = fmin(tout, fmax(t1, t2));
+    return true;
+}
+
+// DDA set-up along one axis: cell index, step, parameter of the next cell boundary and per-cell increment.
+__device__ __forceinline__ void dda_axis(double x, double d, double tin, double lo, double cell, double inv, int G,
+                                        int &i, int &st, double &tmax, double &tdelta)
+{
+    i = min(G - 1, max(0, (int)floor((x + tin * d - lo) * inv)));
+    if (d > 0.0) {
+        st = 1;
+        tmax = (lo + (i + 1) * cell - x) / d;
+        tdelta = cell / d;
+    } else if (d < 0.0) {
+        st = -1;
+        tmax = (lo + i * cell - x) / d;
+        tdelta = -cell / d;
+    } else {
+        st = 0;
+        tmax = INFINITY;
+        tdelta = INFINITY;
+    }
+}
+
+__device__ __forceinline__ int walk_reenter(const WalkArgs &a, V3<double> x, V3<double> d, double t0, double &t_hit)
+{
+    const WalkGrid &g = *a.grid;
+    const int G = g.G;
+    double tin = t0, tout = INFINITY;
+    if (!slab(x.x, d.x, g.lo[0], g.lo[0] + G * g.cell[0], tin, tout) ||
+        !slab(x.y, d.y, g.lo[1], g.lo[1] + G * g.cell[1], tin, tout) ||
+        !slab(x.z, d.z, g.lo[2], g.lo[2] + G * g.cell[2], tin, tout) || !(tin <= tout))
+        return -1;
+    int ix, iy, iz, sx, sy, sz;
+    double mx, my, mz, dx, dy, dz;
+    dda_axis(x.x, d.x, tin, g.lo[0], g.cell[0], g.inv[0], G, ix, sx, mx, dx);
+    dda_axis(x.y, d.y, tin, g.lo[1], g.cell[1], g.inv[1], G, iy, sy, my, dy);
+    dda_axis(x.z, d.z, tin, g.lo[2], g.cell[2], g.inv[2], G, iz, sz, mz, dz);
+    const double tmin = t0 + 1e-14 * fmax(1.0, fabs(t0));
+    double best = INFINITY;
+    int bf = -1;
+    for (int it = 0; it < 3 * G + 3; ++it) {
+        const int c = (iz * G + iy) * G + ix;
+        for (int j = a.cell_off[c]; j < a.cell_off[c + 1]; ++j) {
+            const int f = a.cell_face[j];
+            const double *q = a.bgeo + (int64_t)f * kBFaceGeo;
+            const V3<double> p0 = mk(q[0], q[1], q[2]), e1 = mk(q[3], q[4], q[5]), e2 = mk(q[6], q[7], q[8]);
+            const V3<double> n = mk(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
+            if (!(dot3(n, d) < 0.0)) continue;  // not an entry (outward normal e1 x e2)
+            const V3<double> P = mk(d.y * e2.z - d.z * e2.y, d.z * e2.x - d.x * e2.z, d.x * e2.y - d.y * e2.x);
+            const double det = dot3(e1, P);
+            if (fabs(det) <= 1e-14 * sqrt(dot3(e1, e1) * dot3(e2, e2))) continue;
+            const double inv = 1.0 / det;
+            const V3<double> Tv = mk(x.x - p0.x, x.y - p0.y, x.z - p0.z);
+            const double u = dot3(Tv, P) * inv;
+            if (u < -1e-12 || u > 1.0 + 1e-12) continue;
+            const V3<double> Qv = mk(Tv.y * e1.z - Tv.z * e1.y, Tv.z * e1.x - Tv.x * e1.z, Tv.x * e1.y - Tv.y * e1.x);
+            const double v = dot3(d, Qv) * inv;
+            if (v < -1e-12 || u + v > 1.0 + 1e-12) continue;
+            const double t = dot3(e2, Qv) * inv;
+            if (t > tmin && t < best) {
+                best = t;
+                bf = f;
+            }
+        }
+        const double tnext = fmin(mx, fmin(my, mz));
+        if (bf >= 0 && best <= tnext) break;  // nothing nearer can lie in a later cell
+        if (tnext > tout) break;
+        if (mx <= my && mx <= mz) {
+            ix += sx;
+            mx += dx;
+            if (ix < 0 || ix >= G) break;
+        } else if (my <= mz) {
+            iy += sy;
+            my += dy;
+            if (iy < 0 || iy >= G) break;
+        } else {
+            iz += sz;
+            mz += dz;
+            if (iz < 0 || iz >= G) break;
+        }
+    }
+    t_hit = best;
+    return bf;
+}
+
 // The integral of omega along one half-line x + t d, t > 0, walking the tets from node `node`.
 // float32: the point as float splits (xh, xm); records from near32.
-__device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, const float xh[3], const float xm[3], V3<float> d,
-                              int &hits)
+template <bool GRAD, bool RE>
+__device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, const float xh[3],
+                              const float xm[3], V3<float> d, V3<float> e, V3<float> &dI, int &hits)
 {
     V3<float> I = mk(0.f, 0.f, 0.f);
     // start tet: the incident tet whose face planes through x the half-line enters (largest margin)
@@ -67,7 +174,17 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, const float xh[3]
             kk = k;
         }
     }
-    if (T < 0 || best < -kStartTolF) return I;  // the half-line leaves the mesh at x
+    bool exact = true;  // x is vertex kk of T
+    int entf = -1;      // face of T through which the line came in from outside the mesh
+    if (T < 0 || best < -kStartTolF) {  // the half-line leaves the mesh at x
+        if constexpr (!RE) return I;
+        double th;  // a non-convex mesh: the line may come back
+        const int f = walk_reenter(a, xd, mk((double)d.x, (double)d.y, (double)d.z), 0.0, th);
+        if (f < 0) return I;
+        T = a.bface[f] >> 2;
+        entf = a.bface[f] & 3;
+        exact = false;
+    }
     for (int step = 0; T >= 0; ++step) {
         if (step >= a.max_steps) {
             atomicOr(a.flag, kFlagWalk);
@@ -81,7 +198,7 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, const float xh[3]
         g[3] = mk(q2.x, q2.y, q2.z);
         g[0] = mk(-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z));
         float av[4];
-        if (step == 0) {
+        if (exact) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) av[i] = (i == kk) ? 1.0f : 0.0f;
         } else {
@@ -122,6 +239,13 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, const float xh[3]
         // omega at the vertices (w0 w1 w2 w3, 12 floats) and the face neighbours (4 ints)
         const float4 q4 = __ldg(r + 4), q5 = __ldg(r + 5), q6 = __ldg(r + 6);
         const int4 nb = __ldg(reinterpret_cast<const int4 *>(r + 7));
+        float ge[4];  // g_i . e
+        if constexpr (GRAD) {
+            ge[1] = dot3(g[1], e);
+            ge[2] = dot3(g[2], e);
+            ge[3] = dot3(g[3], e);
+            ge[0] = -(ge[1] + ge[2] + ge[3]);
+        }
         if (!empty && hi - lo > (float)kTau * q0.w) {
             const float l0 = fmaxf(lo, 0.f);
             const float f1 = hi - l0, f2 = 0.5f * (hi * hi - l0 * l0);
@@ -130,15 +254,54 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, const float xh[3]
             I.x += c0 * q4.x + c1 * q4.w + c2 * q5.z + c3 * q6.y;
             I.y += c0 * q4.y + c1 * q5.x + c2 * q5.w + c3 * q6.z;
             I.z += c0 * q4.z + c1 * q5.y + c2 * q6.x + c3 * q6.w;
+            if constexpr (GRAD) {  // chord length times e . grad omega_T
+                dI.x += f1 * (ge[0] * q4.x + ge[1] * q4.w + ge[2] * q5.z + ge[3] * q6.y);
+                dI.y += f1 * (ge[0] * q4.y + ge[1] * q5.x + ge[2] * q5.w + ge[3] * q6.z);
+                dI.z += f1 * (ge[0] * q4.z + ge[1] * q5.y + ge[2] * q6.x + ge[3] * q6.w);
+            }
             ++hits;
         }
-        T = exitf == 0 ? nb.x : exitf == 1 ? nb.y : exitf == 2 ? nb.z : nb.w;
+        const int next = exitf == 0 ? nb.x : exitf == 1 ? nb.y : exitf == 2 ? nb.z : nb.w;
+        if constexpr (GRAD) {
+            // where omega jumps (the line enters from outside at lo, or leaves at hi): omega there times the
+            // shift of that point, dT/de = -(g_f . e)/b_f; the face's g . e and b picked without indexing the
+            // arrays (they stay in registers)
+            for (int side = 0; side < 2; ++side) {
+                const int f = side == 0 ? entf : (next < 0 ? exitf : -1);
+                if (f < 0) continue;
+                const float tt = side == 0 ? lo : hi;
+                const float c0 = av[0] + b[0] * tt, c1 = av[1] + b[1] * tt;
+                const float c2 = av[2] + b[2] * tt, c3 = av[3] + b[3] * tt;
+                const float gef = f == 0 ? ge[0] : f == 1 ? ge[1] : f == 2 ? ge[2] : ge[3];
+                const float bf = f == 0 ? b[0] : f == 1 ? b[1] : f == 2 ? b[2] : b[3];
+                const float dT = (side == 0 ? gef : -gef) / bf;  // entry: -omega dT/de; exit: +omega dT/de
+                dI.x += dT * (c0 * q4.x + c1 * q4.w + c2 * q5.z + c3 * q6.y);
+                dI.y += dT * (c0 * q4.y + c1 * q5.x + c2 * q5.w + c3 * q6.z);
+                dI.z += dT * (c0 * q4.z + c1 * q5.y + c2 * q6.x + c3 * q6.w);
+            }
+        }
+        exact = false;
+        entf = -1;
+        if constexpr (RE) {
+            if (next < 0) {  // left a non-convex mesh: does the line come back?
+                double th;
+                const int f = walk_reenter(a, xd, mk((double)d.x, (double)d.y, (double)d.z), (double)hi, th);
+                if (f >= 0) {
+                    T = a.bface[f] >> 2;
+                    entf = a.bface[f] & 3;
+                    continue;
+                }
+            }
+        }
+        T = next;
     }
     return I;
 }
 
 // float64 form: records from near64.
-__device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3<double> d, int &hits)
+template <bool GRAD, bool RE>
+__device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3<double> d, V3<double> e,
+                               V3<double> &dI, int &hits)
 {
     V3<double> I = mk(0.0, 0.0, 0.0);
     int T = -1, kk = -1;
@@ -159,7 +322,17 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
             kk = k;
         }
     }
-    if (T < 0 || best < -kStartTolD) return I;
+    bool exact = true;  // x is vertex kk of T
+    int entf = -1;      // face of T through which the line came in from outside the mesh
+    if (T < 0 || best < -kStartTolD) {
+        if constexpr (!RE) return I;
+        double th;
+        const int f = walk_reenter(a, x, d, 0.0, th);
+        if (f < 0) return I;
+        T = a.bface[f] >> 2;
+        entf = a.bface[f] & 3;
+        exact = false;
+    }
     for (int step = 0; T >= 0; ++step) {
         if (step >= a.max_steps) {
             atomicOr(a.flag, kFlagWalk);
@@ -170,7 +343,7 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
         for (int i = 1; i < 4; ++i) g[i] = mk(r[nf64::G + 3 * i - 3], r[nf64::G + 3 * i - 2], r[nf64::G + 3 * i - 1]);
         g[0] = mk(-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z));
         double av[4];
-        if (step == 0) {
+        if (exact) {
             for (int i = 0; i < 4; ++i) av[i] = (i == kk) ? 1.0 : 0.0;
         } else {
             const V3<double> d0 = mk(x.x - r[nf64::V], x.y - r[nf64::V + 1], x.z - r[nf64::V + 2]);
@@ -204,6 +377,13 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
             atomicOr(a.flag, kFlagWalk);
             break;
         }
+        double ge[4];  // g_i . e
+        if constexpr (GRAD) {
+            ge[1] = dot3(g[1], e);
+            ge[2] = dot3(g[2], e);
+            ge[3] = dot3(g[3], e);
+            ge[0] = -(ge[1] + ge[2] + ge[3]);
+        }
         if (!empty && hi - lo > kTau * r[nf64::H]) {
             const double l0 = fmax(lo, 0.0);
             const double f1 = hi - l0, f2 = 0.5 * (hi * hi - l0 * l0);
@@ -212,59 +392,128 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
                 I.x += c * r[nf64::W + 3 * i];
                 I.y += c * r[nf64::W + 3 * i + 1];
                 I.z += c * r[nf64::W + 3 * i + 2];
+                if constexpr (GRAD) {
+                    dI.x += f1 * ge[i] * r[nf64::W + 3 * i];
+                    dI.y += f1 * ge[i] * r[nf64::W + 3 * i + 1];
+                    dI.z += f1 * ge[i] * r[nf64::W + 3 * i + 2];
+                }
             }
             ++hits;
         }
-        T = a.nbr[4 * (int64_t)T + exitf];
+        const int next = a.nbr[4 * (int64_t)T + exitf];
+        if constexpr (GRAD) {
+            for (int side = 0; side < 2; ++side) {  // omega jumps where the line enters or leaves the mesh
+                const int f = side == 0 ? entf : (next < 0 ? exitf : -1);
+                if (f < 0) continue;
+                const double tt = side == 0 ? lo : hi;
+                const double gef = f == 0 ? ge[0] : f == 1 ? ge[1] : f == 2 ? ge[2] : ge[3];
+                const double bf = f == 0 ? b[0] : f == 1 ? b[1] : f == 2 ? b[2] : b[3];
+                const double dT = (side == 0 ? gef : -gef) / bf;
+                for (int i = 0; i < 4; ++i) {
+                    const double c = dT * (av[i] + b[i] * tt);
+                    dI.x += c * r[nf64::W + 3 * i];
+                    dI.y += c * r[nf64::W + 3 * i + 1];
+                    dI.z += c * r[nf64::W + 3 * i + 2];
+                }
+            }
+        }
+        exact = false;
+        entf = -1;
+        if constexpr (RE) {
+            if (next < 0) {
+                double th;
+                const int f = walk_reenter(a, x, d, hi, th);
+                if (f >= 0) {
+                    T = a.bface[f] >> 2;
+                    entf = a.bface[f] & 3;
+                    continue;
+                }
+            }
+        }
+        T = next;
     }
     return I;
 }
 
-template <typename T>
+// RE: the instance for a non-convex domain (mode 2), with the re-entry search; the other one serves convex
+// domains (mode 1).  Both are queued; the one not in charge returns at once.
+template <typename T, bool GRAD, bool RE>
 __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a)
 {
-    if (!*a.mode) return;  // not a convex conforming mesh: the all-ray kernel takes the nodes
+    const int mode = *a.mode;
+    if (!mode) {  // not a conforming mesh: the all-ray kernel takes the nodes
+        if (GRAD && !RE && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.flag, kFlagNoWalk);  // no derivative
+        return;
+    }
+    if ((mode == 2) != RE) return;
     const int lane = threadIdx.x & 31;
     const int64_t node = (int64_t)blockIdx.x * (kWalkThreads / 32) + (threadIdx.x >> 5);
     if (node >= a.n_nodes) return;  // whole warps
     const V3<double> xd = mk(a.nodes[3 * node], a.nodes[3 * node + 1], a.nodes[3 * node + 2]);
-    T ax = 0, ay = 0, az = 0;
+    const double *ep = a.dirs ? a.dirs + 3 * node : a.omega + 3 * node;
+    const V3<double> ed = GRAD ? mk(ep[0], ep[1], ep[2]) : mk(0.0, 0.0, 0.0);
+    T ax = 0, ay = 0, az = 0, gx = 0, gy = 0, gz = 0;
     int hits = 0;
     if constexpr (sizeof(T) == 4) {
         float xh[3], xm[3], xl;
         split3(xd.x, xh[0], xm[0], xl);
         split3(xd.y, xh[1], xm[1], xl);
         split3(xd.z, xh[2], xm[2], xl);
+        const V3<float> e = mk((float)ed.x, (float)ed.y, (float)ed.z);
         for (int l = lane; l < a.L; l += 32) {
             const float4 ln = __ldg(a.lines32 + l);
             const V3<float> s = mk(ln.x, ln.y, ln.z);
-            const V3<float> Ip = walk_f32(a, node, xh, xm, s, hits);
-            const V3<float> Im = walk_f32(a, node, xh, xm, mk(-s.x, -s.y, -s.z), hits);
+            V3<float> dp = mk(0.f, 0.f, 0.f), dm = mk(0.f, 0.f, 0.f);
+            const V3<float> Ip = walk_f32<GRAD, RE>(a, node, xd, xh, xm, s, e, dp, hits);
+            const V3<float> Im = walk_f32<GRAD, RE>(a, node, xd, xh, xm, mk(-s.x, -s.y, -s.z), e, dm, hits);
             const V3<float> J = mk(Ip.x - Im.x, Ip.y - Im.y, Ip.z - Im.z);
             ax += ln.w * (s.y * J.z - s.z * J.y);
             ay += ln.w * (s.z * J.x - s.x * J.z);
             az += ln.w * (s.x * J.y - s.y * J.x);
+            if constexpr (GRAD) {
+                const V3<float> D = mk(dp.x - dm.x, dp.y - dm.y, dp.z - dm.z);
+                gx += ln.w * (s.y * D.z - s.z * D.y);
+                gy += ln.w * (s.z * D.x - s.x * D.z);
+                gz += ln.w * (s.x * D.y - s.y * D.x);
+            }
         }
     } else {
         for (int l = lane; l < a.L; l += 32) {
             const dbl4 ln = a.lines64[l];
             const V3<double> s = mk(ln.x, ln.y, ln.z);
-            const V3<double> Ip = walk_f64(a, node, xd, s, hits);
-            const V3<double> Im = walk_f64(a, node, xd, mk(-s.x, -s.y, -s.z), hits);
+            V3<double> dp = mk(0.0, 0.0, 0.0), dm = mk(0.0, 0.0, 0.0);
+            const V3<double> Ip = walk_f64<GRAD, RE>(a, node, xd, s, ed, dp, hits);
+            const V3<double> Im = walk_f64<GRAD, RE>(a, node, xd, mk(-s.x, -s.y, -s.z), ed, dm, hits);
             const V3<double> J = mk(Ip.x - Im.x, Ip.y - Im.y, Ip.z - Im.z);
             ax += ln.w * (s.y * J.z - s.z * J.y);
             ay += ln.w * (s.z * J.x - s.x * J.z);
             az += ln.w * (s.x * J.y - s.y * J.x);
+            if constexpr (GRAD) {
+                const V3<double> D = mk(dp.x - dm.x, dp.y - dm.y, dp.z - dm.z);
+                gx += ln.w * (s.y * D.z - s.z * D.y);
+                gy += ln.w * (s.z * D.x - s.x * D.z);
+                gz += ln.w * (s.x * D.y - s.y * D.x);
+            }
         }
     }
     ax = warp_sum(ax);
     ay = warp_sum(ay);
     az = warp_sum(az);
     hits = warp_sum(hits);
+    if constexpr (GRAD) {
+        gx = warp_sum(gx);
+        gy = warp_sum(gy);
+        gz = warp_sum(gz);
+    }
     if (lane == 0) {
         a.out[3 * node] = (double)ax;
         a.out[3 * node + 1] = (double)ay;
         a.out[3 * node + 2] = (double)az;
+        if constexpr (GRAD) {
+            a.dout[3 * node] = (double)gx;
+            a.dout[3 * node + 1] = (double)gy;
+            a.dout[3 * node + 2] = (double)gz;
+        }
         if (a.counts) {
             a.counts[3 * node] = (int32_t)min(a.n_tets, (int64_t)INT32_MAX);
             a.counts[3 * node + 1] = 0;
@@ -274,6 +523,137 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a)
 }
 
 __global__ void set_int_kernel(int *p, int v) { *p = v; }
+
+// Box of the boundary nodes (one block), padded by 1e-6 of its largest extent, and a G^3 grid over it.
+__global__ void grid_box_kernel(const double *__restrict__ nodes, const int32_t *__restrict__ bnode, int64_t n_bnode,
+                                int G, WalkGrid *g)
+{
+    __shared__ double smn[3][256], smx[3][256];
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = threadIdx.x; i < n_bnode; i += blockDim.x) {
+        const int64_t q = bnode[i];
+        for (int k = 0; k < 3; ++k) {
+            mn[k] = fmin(mn[k], nodes[3 * q + k]);
+            mx[k] = fmax(mx[k], nodes[3 * q + k]);
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        smn[k][threadIdx.x] = mn[k];
+        smx[k][threadIdx.x] = mx[k];
+    }
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 3; ++k) {
+                smn[k][threadIdx.x] = fmin(smn[k][threadIdx.x], smn[k][threadIdx.x + o]);
+                smx[k][threadIdx.x] = fmax(smx[k][threadIdx.x], smx[k][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double ext = 0.0;
+        for (int k = 0; k < 3; ++k) ext = fmax(ext, smx[k][0] - smn[k][0]);
+        const double pad = 1e-6 * ext + 1e-300;
+        for (int k = 0; k < 3; ++k) {
+            g->lo[k] = smn[k][0] - pad;
+            g->cell[k] = (smx[k][0] - smn[k][0] + 2.0 * pad) / G;
+            g->inv[k] = 1.0 / g->cell[k];
+        }
+        g->G = G;
+        g->ok = 1;
+    }
+}
+
+// Per boundary face: its cells (those its bounding box overlaps).  Pass 0 counts the faces per cell and writes
+// the face's record (vertex p0 and edges e1, e2 ordered so that e1 x e2 points out of the mesh); pass 1 fills
+// the cells' face lists from the offsets (cell_cnt zeroed again in between).
+template <int PASS>
+__global__ void grid_faces_kernel(const double *__restrict__ nodes, const int32_t *__restrict__ tets,
+                                  const int32_t *__restrict__ bface, int64_t n_bface, const WalkGrid *g,
+                                  int32_t *cell_cnt, const int32_t *__restrict__ cell_off, int32_t *cell_face,
+                                  int64_t cap, double *geo)
+{
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= n_bface) return;
+    const int slot = bface[f];
+    const int64_t t = slot >> 2;
+    const int opp = slot & 3;
+    int id[3], j = 0;
+    for (int i = 0; i < 4; ++i)
+        if (i != opp) id[j++] = tets[4 * t + i];
+    V3<double> p[3];
+    for (int i = 0; i < 3; ++i) p[i] = mk(nodes[3 * id[i]], nodes[3 * id[i] + 1], nodes[3 * id[i] + 2]);
+    if (PASS == 0) {
+        const int io = tets[4 * t + opp];
+        const V3<double> po = mk(nodes[3 * io], nodes[3 * io + 1], nodes[3 * io + 2]);
+        V3<double> e1 = mk(p[1].x - p[0].x, p[1].y - p[0].y, p[1].z - p[0].z);
+        V3<double> e2 = mk(p[2].x - p[0].x, p[2].y - p[0].y, p[2].z - p[0].z);
+        const V3<double> n = mk(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
+        if (n.x * (po.x - p[0].x) + n.y * (po.y - p[0].y) + n.z * (po.z - p[0].z) > 0.0) {
+            const V3<double> tmp = e1;
+            e1 = e2;
+            e2 = tmp;
+        }
+        double *q = geo + f * kBFaceGeo;
+        q[0] = p[0].x; q[1] = p[0].y; q[2] = p[0].z;
+        q[3] = e1.x; q[4] = e1.y; q[5] = e1.z;
+        q[6] = e2.x; q[7] = e2.y; q[8] = e2.z;
+    }
+    const int G = g->G;
+    int i0[3], i1[3];
+    const double c[3][3] = {{p[0].x, p[1].x, p[2].x}, {p[0].y, p[1].y, p[2].y}, {p[0].z, p[1].z, p[2].z}};
+    for (int k = 0; k < 3; ++k) {
+        const double a = fmin(c[k][0], fmin(c[k][1], c[k][2])), b = fmax(c[k][0], fmax(c[k][1], c[k][2]));
+        i0[k] = min(G - 1, max(0, (int)floor((a - g->lo[k]) * g->inv[k])));
+        i1[k] = min(G - 1, max(0, (int)floor((b - g->lo[k]) * g->inv[k])));
+    }
+    for (int z = i0[2]; z <= i1[2]; ++z)
+        for (int y = i0[1]; y <= i1[1]; ++y)
+            for (int x = i0[0]; x <= i1[0]; ++x) {
+                const int cell = (z * G + y) * G + x;
+                if (PASS == 0) {
+                    atomicAdd(&cell_cnt[cell], 1);
+                } else {
+                    const int64_t pos = (int64_t)cell_off[cell] + atomicAdd(&cell_cnt[cell], 1);
+                    if (pos < cap) cell_face[pos] = (int32_t)f;
+                }
+            }
+}
+
+// Exclusive scan of the G^3 cell counts into cell_off (one block: a serial scan of each thread's run, then
+// of the runs); the grid is not usable when the lists need more than cap entries.
+__global__ void grid_scan_kernel(const int32_t *__restrict__ cnt, int n, int32_t *off, int64_t cap, WalkGrid *g)
+{
+    __shared__ int64_t run[1024];
+    const int T = blockDim.x, tid = threadIdx.x;
+    const int per = (n + T - 1) / T, b = tid * per, e = min(n, b + per);
+    int64_t sum = 0;
+    for (int i = b; i < e; ++i) sum += cnt[i];
+    run[tid] = sum;
+    __syncthreads();
+    if (tid == 0) {
+        int64_t acc = 0;
+        for (int i = 0; i < T; ++i) {
+            const int64_t v = run[i];
+            run[i] = acc;
+            acc += v;
+        }
+        off[n] = (int32_t)min(acc, (int64_t)INT32_MAX);
+        if (acc > cap) g->ok = 0;
+    }
+    __syncthreads();
+    int64_t acc = run[tid];
+    for (int i = b; i < e; ++i) {
+        off[i] = (int32_t)min(acc, (int64_t)INT32_MAX);
+        acc += cnt[i];
+    }
+}
+
+// A non-convex mesh (mode 2) whose face grid overflowed is left to the all-ray kernel (mode 0).
+__global__ void grid_finalize_kernel(const WalkGrid *g, int *mode)
+{
+    if (*mode == 2 && !g->ok) *mode = 0;
+}
 
 // float32 walk record of a tet, one 128-byte line:
 //   [g1 h] [g2 v0hi.x] [g3 v0hi.y] [v0hi.z v0mid.xyz] [w0.xyz w1.x] [w1.yz w2.xy] [w2.z w3.xyz] [nbr0..3]
@@ -306,7 +686,7 @@ __global__ void convex_kernel(const double *__restrict__ nodes, const int32_t *_
                               int64_t n_bnode, int *mode)
 {
     const int64_t f = blockIdx.y;  // boundary face of this block row
-    if (f >= n_bface || !*mode) return;
+    if (f >= n_bface || *mode != 1) return;
     const int slot = bface[f];
     const int64_t t = slot >> 2;
     const int opp = slot & 3;
@@ -329,7 +709,7 @@ __global__ void convex_kernel(const double *__restrict__ nodes, const int32_t *_
         const int q = bnode[i];
         const double s = n.x * (nodes[3 * q] - p0.x) + n.y * (nodes[3 * q + 1] - p0.y) + n.z * (nodes[3 * q + 2] - p0.z);
         if (s > tol) {
-            atomicAnd(mode, 0);
+            atomicMax(mode, 2);  // not convex: the walk looks for re-entries
             return;
         }
     }
@@ -413,13 +793,47 @@ cudaError_t launch_walk_records(const float4 *near32, const int32_t *nbr, int64_
     return cudaGetLastError();
 }
 
+cudaError_t launch_walk_grid(const double *nodes, const int32_t *tets, const int32_t *bface, int64_t n_bface,
+                             const int32_t *bnode, int64_t n_bnode, const WalkGridArrays &g, cudaStream_t st)
+{
+    if (n_bface == 0 || n_bnode == 0) return cudaSuccess;
+    const int64_t cells = (int64_t)g.G * g.G * g.G;
+    grid_box_kernel<<<1, 256, 0, st>>>(nodes, bnode, n_bnode, g.G, g.grid);
+    cudaError_t e = cudaMemsetAsync(g.cell_cnt, 0, sizeof(int32_t) * cells, st);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((n_bface + 127) / 128);
+    grid_faces_kernel<0><<<blocks, 128, 0, st>>>(nodes, tets, bface, n_bface, g.grid, g.cell_cnt, g.cell_off,
+                                                 g.cell_face, g.cap, g.geo);
+    grid_scan_kernel<<<1, 1024, 0, st>>>(g.cell_cnt, (int)cells, g.cell_off, g.cap, g.grid);
+    if ((e = cudaMemsetAsync(g.cell_cnt, 0, sizeof(int32_t) * cells, st)) != cudaSuccess) return e;
+    grid_faces_kernel<1><<<blocks, 128, 0, st>>>(nodes, tets, bface, n_bface, g.grid, g.cell_cnt, g.cell_off,
+                                                 g.cell_face, g.cap, g.geo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_walk_finalize(const WalkGrid *g, int *mode, cudaStream_t st)
+{
+    grid_finalize_kernel<<<1, 1, 0, st>>>(g, mode);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_walk(int precision, const WalkArgs &a, cudaStream_t st, cudaEvent_t ev_start, cudaEvent_t ev_stop)
 {
     cudaError_t e;
     if (ev_start && (e = cudaEventRecord(ev_start, st)) != cudaSuccess) return e;
     const int64_t blocks = (a.n_nodes + kWalkThreads / 32 - 1) / (kWalkThreads / 32);
-    if (precision == BS_FP32) walk_kernel<float><<<(unsigned)blocks, kWalkThreads, 0, st>>>(a);
-    else walk_kernel<double><<<(unsigned)blocks, kWalkThreads, 0, st>>>(a);
+    // the convex-domain instance and the one with re-entries (only the one the mode selects does any work)
+#define BS_WALK_PAIR(T_, G_)                                                          \
+    walk_kernel<T_, G_, false><<<(unsigned)blocks, kWalkThreads, 0, st>>>(a);         \
+    walk_kernel<T_, G_, true><<<(unsigned)blocks, kWalkThreads, 0, st>>>(a)
+    if (a.dout) {
+        if (precision == BS_FP32) { BS_WALK_PAIR(float, true); }
+        else { BS_WALK_PAIR(double, true); }
+    } else {
+        if (precision == BS_FP32) { BS_WALK_PAIR(float, false); }
+        else { BS_WALK_PAIR(double, false); }
+    }
+#undef BS_WALK_PAIR
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev_stop) e = cudaEventRecord(ev_stop, st);
     return e;

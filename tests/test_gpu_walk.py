@@ -5,8 +5,8 @@ meets one after the other; the sum of their chords is the ray rule's sum over
 all tets.  The walk must match the CPU oracle's all-ray velocity at the nodes
 (float64: relative L2 <= 1e-12, counts bit-exact on stable nodes; float32: RMS
 error over max speed <= 1e-5) and the all-ray kernel.  On a non-convex domain
-(an L-shaped block) the library must not walk: the result is then the all-ray
-kernel's, and still the oracle's.  The Heun step uses the same path.
+(an L-shaped block) lines leave and come back; the walk finds the re-entries
+through a grid of the boundary faces.  The Heun step uses the same path.
 """
 import os
 
@@ -125,15 +125,25 @@ def _l_shaped():
     return nodes, tets, omega
 
 
-def test_non_convex_domain_is_not_walked(orc):
+def test_non_convex_domain_walks_with_re_entries(orc):
+    """An L-shaped block: lines that leave the mesh come back into it; the walk finds the re-entries through a
+    grid of boundary faces, and matches the oracle and the all-ray kernel (counts exactly)."""
     nodes, tets, omega = _l_shaped()
     h = bs.Mesh(nodes, tets, omega)
+    vo, co, stable = oracle_with_stability(orc, _Mesh(nodes, tets, omega), nodes, **_op(ALLRAY))
     v, c = nodes_velocity(h, len(nodes), bs.BS_FP64, **ALLRAY)
     vr, cr = nodes_velocity(h, len(nodes), bs.BS_FP64, walk=False, **ALLRAY)
-    # the all-ray kernel's result exactly (a walk would miss the lines that re-enter the L)
-    assert np.array_equal(v, vr) and np.array_equal(c, cr)
-    vo = orc.velocity(nodes, tets, omega, nodes, **_op(ALLRAY))
     assert rel_l2(v, vo) <= TOL_FP64_REL_L2
+    assert rel_l2(v, vr) <= 1e-13
+    assert np.array_equal(c, cr)
+    assert np.array_equal(c[stable], co[stable])
+    v32, _ = nodes_velocity(h, len(nodes), bs.BS_FP32, **ALLRAY)
+    assert rms_over_max(v32, vo) <= TOL_FP32_RMS_MAX
+
+
+class _Mesh:
+    def __init__(self, nodes, tets, omega):
+        self.nodes, self.tets, self.omega = nodes, tets, omega
 
 
 def test_ring_mesh_full_size(orc):
