@@ -249,19 +249,29 @@ def rings_workload(args):
     bs.load()
     m = config5_rings(n=args.rings_n)
     h = bs.Mesh(m.nodes, m.tets, m.omega)
-    P = dict(PARAMS, precision=bs.BS_FP32)
+    stretch = args.rings_mode == "allray-stretch"
+    # allray-stretch: the all-ray method (mesh walk) with the vortex-stretching term in the Heun step
+    base = dict(PARAMS, far_ratio=float("inf")) if stretch else dict(PARAMS)
+    P = dict(base, precision=bs.BS_FP32)
+
+    def step(hh, **kw):
+        (hh.bs_rk2_step_stretch if stretch else hh.bs_rk2_step)(0.01, **kw)
+
     stream = torch.cuda.current_stream()
     for _ in range(min(args.warmup, 1)):  # one warm-up step (a full step is seconds long)
-        h.bs_rk2_step(0.01, **P)
+        step(h, **P)
     h.bs_status()
     h = bs.Mesh(m.nodes, m.tets, m.omega)  # start the timed trajectory from t = 0
-    h.bs_velocity(torch.from_numpy(m.nodes).cuda(), **P)  # tables built outside the timed region
+    if stretch:
+        h.bs_velocity_nodes(**P)  # connectivity and tables built outside the timed region
+    else:
+        h.bs_velocity(torch.from_numpy(m.nodes).cuda(), **P)
     h.bs_status()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            h.bs_rk2_step(0.01, **P)
+            step(h, **P)
         ev1.record(stream)
         torch.cuda.synchronize()
     h.bs_status()
@@ -277,20 +287,24 @@ def rings_workload(args):
         for prec in (bs.BS_FP64, bs.BS_FP32):
             hd = bs.Mesh(md.nodes, md.tets, md.omega)
             for _ in range(20):
-                hd.bs_rk2_step(0.01, **dict(PARAMS, precision=prec))
+                step(hd, **dict(base, precision=prec))
             hd.bs_status()
             traj[prec] = hd.bs_nodes().cpu().numpy()
         dd = np.linalg.norm(traj[bs.BS_FP32] - traj[bs.BS_FP64], axis=1)
         drift = {"grid": f"{args.rings_drift_n}^3", "steps": 20, "dt": 0.01, "max": float(dd.max()),
                  "rms": float(np.sqrt(np.mean(dd ** 2))),
                  "max_displacement_fp64": float(np.abs(traj[bs.BS_FP64] - md.nodes).max())}
-    line = {"metric": "node-tet interactions/s (RK2 steps of two colliding rings, FP32 path)",
+    w_change = float(np.abs(h.bs_omega().cpu().numpy() - m.omega).max()) if stretch else 0.0
+    line = {"metric": "node-tet interactions/s (RK2 steps of two colliding rings, FP32 path)"
+                      + (", all-ray with vortex stretching" if stretch else ""),
             "value": pairs_per_step / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"two rings {args.rings_n}^3: {m.n_nodes} nodes, {m.n_tets} tets, Heun dt=0.01",
-                       **PARAMS, "precision": "fp32"},
-            "max_displacement": float(np.abs(x - m.nodes).max()), "fp32_vs_fp64_drift": drift,
+                       **{k: (str(v) if k == "far_ratio" else v) for k, v in base.items()}, "precision": "fp32",
+                       "mode": args.rings_mode},
+            "max_displacement": float(np.abs(x - m.nodes).max()), "max_vorticity_change": w_change,
+            "fp32_vs_fp64_drift": drift,
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     return 0
@@ -409,6 +423,9 @@ def main():
                          "launches; rings: Heun steps of two colliding rings; allray: the ray rule for every "
                          "pair on the 32^3 ring mesh")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
+    ap.add_argument("--rings-mode", default="hybrid", choices=["hybrid", "allray-stretch"],
+                    help="rings workload: the far/near rule with frozen vorticity, or the all-ray method with vortex "
+                         "stretching")
     ap.add_argument("--rings-drift-n", type=int, default=32,
                     help="rings workload: grid of the FP32-vs-FP64 drift run (20 Heun steps; 0 to skip)")
     ap.add_argument("--allray-mesh", default="ring32", choices=["ring32", "fourier64"],

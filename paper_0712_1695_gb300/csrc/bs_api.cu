@@ -138,7 +138,8 @@ void free_ctx(bs_ctx *h)
                     h->lines.f64, h->partial, h->stage, h->rk, h->tile_hdr, h->perm, h->keys,
                     h->cell_count, h->box, h->walk_nbr, h->walk_inc_off, h->walk_inc, h->walk_bface,
                     h->walk_bnode, h->walk_mode, h->walk_rec, h->rk_w, h->walk_grid.grid,
-                    h->walk_grid.cell_off, h->walk_grid.cell_cnt, h->walk_grid.cell_face, h->walk_grid.geo};
+                    h->walk_grid.cell_off, h->walk_grid.cell_cnt, h->walk_grid.cell_face, h->walk_grid.geo,
+                    h->walk_grid.geo32};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete h;
@@ -446,9 +447,10 @@ cudaError_t ensure_walk(bs_ctx *h)
         return e;
     h->walk_n_bface = (int64_t)w.bface.size();
     h->walk_n_bnode = (int64_t)w.bnode.size();
-    // face grid: about two boundary faces per cell of a G^3 grid; lists of up to 16 cells per face
+    // face grid: the boundary is a surface, about 6 G^2 of the G^3 cells hold its faces; G for a few faces per
+    // surface cell; lists of up to 16 cells per face
     WalkGridArrays &g = h->walk_grid;
-    g.G = (int)std::min<double>(128.0, std::max(4.0, std::round(std::cbrt(0.5 * (double)h->walk_n_bface))));
+    g.G = (int)std::min<double>(160.0, std::max(4.0, std::round(std::sqrt((double)h->walk_n_bface / 8.0))));
     const int64_t cells = (int64_t)g.G * g.G * g.G;
     g.cap = 16 * std::max<int64_t>(h->walk_n_bface, 1);
     if ((e = cudaMalloc((void **)&g.grid, sizeof(WalkGrid))) != cudaSuccess) return e;
@@ -456,6 +458,9 @@ cudaError_t ensure_walk(bs_ctx *h)
     if ((e = cudaMalloc((void **)&g.cell_cnt, sizeof(int32_t) * cells)) != cudaSuccess) return e;
     if ((e = cudaMalloc((void **)&g.cell_face, sizeof(int32_t) * g.cap)) != cudaSuccess) return e;
     if ((e = cudaMalloc((void **)&g.geo, sizeof(double) * kBFaceGeo * std::max<int64_t>(h->walk_n_bface, 1))) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMalloc((void **)&g.geo32, sizeof(float) * kBFaceGeo * std::max<int64_t>(h->walk_n_bface, 1))) !=
         cudaSuccess)
         return e;
     h->walk_conforming = w.conforming && 4 * h->n_tets < INT32_MAX;
@@ -489,7 +494,7 @@ int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *d
     if (h->walk_version != h->version) {  // the mesh changed: walk records, and is the domain still convex?
         BS_CUDA(launch_walk_records(h->near32, h->walk_nbr, h->n_tets, h->walk_rec, st));
         BS_CUDA(launch_convex_check(h->nodes, h->tets, h->walk_bface, h->walk_n_bface, h->walk_bnode,
-                                    h->walk_n_bnode, h->walk_conforming ? 1 : 0, h->walk_mode, st));
+                                    h->walk_n_bnode, h->walk_conforming ? 1 : 0, h->walk_mode, h->walk_rec, st));
         if (h->walk_conforming) {
             BS_CUDA(launch_walk_grid(h->nodes, h->tets, h->walk_bface, h->walk_n_bface, h->walk_bnode,
                                      h->walk_n_bnode, h->walk_grid, st));
@@ -524,6 +529,7 @@ int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *d
     w.cell_face = h->walk_grid.cell_face;
     w.bface = h->walk_bface;
     w.bgeo = h->walk_grid.geo;
+    w.bgeo32 = h->walk_grid.geo32;
     w.flag = h->flag;
     // no valid mesh needs more steps than tets; a small cap keeps a broken walk short
     w.max_steps = (int)std::min<int64_t>(h->n_tets, std::max<int64_t>(4096, 64 * (int64_t)std::cbrt((double)h->n_tets)));

@@ -191,6 +191,7 @@ bool build_walk_mesh(const int32_t *tets_host, int64_t n_nodes, int64_t n_tets, 
 // Uniform grid of the boundary faces (device), for finding where a line re-enters a non-convex mesh.
 struct WalkGrid {
     double lo[3], cell[3], inv[3];  // origin, cell size and its inverse per axis
+    float lo32[3], cell32[3], inv32[3];  // the same in float (the float32 walk's search)
     int G;                          // cells per axis (G^3 cells)
     int ok;                         // 0 when the face lists overflowed their capacity
 };
@@ -202,6 +203,7 @@ struct WalkGridArrays {
     int32_t *cell_cnt = nullptr;   // [G^3] scratch
     int32_t *cell_face = nullptr;  // [cap] boundary-face indices
     double *geo = nullptr;         // [n_bface][kBFaceGeo]
+    float *geo32 = nullptr;        // [n_bface][kBFaceGeo] float copy
     int G = 0;
     int64_t cap = 0;
 };
@@ -225,6 +227,7 @@ struct WalkArgs {
     const WalkGrid *grid = nullptr;
     const int32_t *cell_off = nullptr, *cell_face = nullptr, *bface = nullptr;
     const double *bgeo = nullptr;
+    const float *bgeo32 = nullptr;
     int *flag = nullptr;
     int max_steps = 0;           // tets per half-line before the walk gives up (error flag)
 };
@@ -239,7 +242,8 @@ cudaError_t launch_walk_finalize(const WalkGrid *g, int *mode, cudaStream_t st);
 // mode := 1 if conforming (else 0), then 2 if a boundary node lies outside a boundary face's plane
 // (a non-convex domain: the walk then looks for re-entries through the grid)
 cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const int32_t *bface, int64_t n_bface,
-                                const int32_t *bnode, int64_t n_bnode, int conforming, int *mode, cudaStream_t st);
+                                const int32_t *bnode, int64_t n_bnode, int conforming, int *mode, float4 *wrec,
+                                cudaStream_t st);
 cudaError_t launch_walk(int precision, const WalkArgs &a, cudaStream_t st, cudaEvent_t ev_start = nullptr,
                         cudaEvent_t ev_stop = nullptr);
 // Heun step position updates (n_values = 3 * nodes)

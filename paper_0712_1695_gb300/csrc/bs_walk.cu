@@ -55,77 +55,101 @@ constexpr double kStartTolD = 1e-12;
 // cells visited so far ends the search once the line has left the cell holding it.  The search
 // visits at most 3G + 3 cells.
 // Clip of the line to the slab [lo, hi] of one axis (tin, tout narrowed); false when the line misses it.
-__device__ __forceinline__ bool slab(double x, double d, double lo, double hi, double &tin, double &tout)
+template <typename T>
+__device__ __forceinline__ bool slab(T x, T d, T lo, T hi, T &tin, T &tout)
 {
-    if (d == 0.0) return x >= lo && x <= hi;
-    const double t1 = (lo - x) / d, t2 = (hi - x) / d;
-    tin = fmax(tin, fmin(t1, t2));
-    tout = fmin(tout, fmax(t1, t2));
+    if (d == (T)0) return x >= lo && x <= hi;
+    const T t1 = (lo - x) / d, t2 = (hi - x) / d;
+    tin = max(tin, min(t1, t2));
+    tout = min(tout, max(t1, t2));
     return true;
 }
 
 // DDA set-up along one axis: cell index, step, parameter of the next cell boundary and per-cell increment.
-__device__ __forceinline__ void dda_axis(double x, double d, double tin, double lo, double cell, double inv, int G,
-                                        int &i, int &st, double &tmax, double &tdelta)
+template <typename T>
+__device__ __forceinline__ void dda_axis(T x, T d, T tin, T lo, T cell, T inv, int G, int &i, int &st, T &tmax,
+                                        T &tdelta)
 {
     i = min(G - 1, max(0, (int)floor((x + tin * d - lo) * inv)));
-    if (d > 0.0) {
+    if (d > (T)0) {
         st = 1;
         tmax = (lo + (i + 1) * cell - x) / d;
         tdelta = cell / d;
-    } else if (d < 0.0) {
+    } else if (d < (T)0) {
         st = -1;
         tmax = (lo + i * cell - x) / d;
         tdelta = -cell / d;
     } else {
         st = 0;
-        tmax = INFINITY;
-        tdelta = INFINITY;
+        tmax = (T)INFINITY;
+        tdelta = (T)INFINITY;
     }
 }
 
-__device__ __forceinline__ int walk_reenter(const WalkArgs &a, V3<double> x, V3<double> d, double t0, double &t_hit)
+// T = float for the float32 walk (the float copy of the grid and the faces), double for the float64 walk.
+template <typename T>
+__device__ __forceinline__ int walk_reenter(const WalkArgs &a, V3<T> x, V3<T> d, T t0, T &t_hit)
 {
+    constexpr bool F = sizeof(T) == 4;
     const WalkGrid &g = *a.grid;
     const int G = g.G;
-    double tin = t0, tout = INFINITY;
-    if (!slab(x.x, d.x, g.lo[0], g.lo[0] + G * g.cell[0], tin, tout) ||
-        !slab(x.y, d.y, g.lo[1], g.lo[1] + G * g.cell[1], tin, tout) ||
-        !slab(x.z, d.z, g.lo[2], g.lo[2] + G * g.cell[2], tin, tout) || !(tin <= tout))
+    const T lo0 = F ? (T)g.lo32[0] : (T)g.lo[0], lo1 = F ? (T)g.lo32[1] : (T)g.lo[1], lo2 = F ? (T)g.lo32[2] : (T)g.lo[2];
+    const T c0 = F ? (T)g.cell32[0] : (T)g.cell[0], c1 = F ? (T)g.cell32[1] : (T)g.cell[1],
+            c2 = F ? (T)g.cell32[2] : (T)g.cell[2];
+    const T i0 = F ? (T)g.inv32[0] : (T)g.inv[0], i1 = F ? (T)g.inv32[1] : (T)g.inv[1], i2 = F ? (T)g.inv32[2] : (T)g.inv[2];
+    T tin = t0, tout = (T)INFINITY;
+    if (!slab<T>(x.x, d.x, lo0, lo0 + G * c0, tin, tout) || !slab<T>(x.y, d.y, lo1, lo1 + G * c1, tin, tout) ||
+        !slab<T>(x.z, d.z, lo2, lo2 + G * c2, tin, tout) || !(tin <= tout))
         return -1;
     int ix, iy, iz, sx, sy, sz;
-    double mx, my, mz, dx, dy, dz;
-    dda_axis(x.x, d.x, tin, g.lo[0], g.cell[0], g.inv[0], G, ix, sx, mx, dx);
-    dda_axis(x.y, d.y, tin, g.lo[1], g.cell[1], g.inv[1], G, iy, sy, my, dy);
-    dda_axis(x.z, d.z, tin, g.lo[2], g.cell[2], g.inv[2], G, iz, sz, mz, dz);
-    const double tmin = t0 + 1e-14 * fmax(1.0, fabs(t0));
-    double best = INFINITY;
+    T mx, my, mz, dx, dy, dz;
+    dda_axis<T>(x.x, d.x, tin, lo0, c0, i0, G, ix, sx, mx, dx);
+    dda_axis<T>(x.y, d.y, tin, lo1, c1, i1, G, iy, sy, my, dy);
+    dda_axis<T>(x.z, d.z, tin, lo2, c2, i2, G, iz, sz, mz, dz);
+    const T eps = F ? (T)1e-6 : (T)1e-14;  // relative: entries at or before t0 are not entries
+    const T tmin = t0 + eps * max((T)1, fabs(t0));
+    const T tol = F ? (T)1e-6 : (T)1e-12;  // area-coordinate tolerance
+    T best = (T)INFINITY;
     int bf = -1;
     for (int it = 0; it < 3 * G + 3; ++it) {
         const int c = (iz * G + iy) * G + ix;
         for (int j = a.cell_off[c]; j < a.cell_off[c + 1]; ++j) {
             const int f = a.cell_face[j];
-            const double *q = a.bgeo + (int64_t)f * kBFaceGeo;
-            const V3<double> p0 = mk(q[0], q[1], q[2]), e1 = mk(q[3], q[4], q[5]), e2 = mk(q[6], q[7], q[8]);
-            const V3<double> n = mk(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
-            if (!(dot3(n, d) < 0.0)) continue;  // not an entry (outward normal e1 x e2)
-            const V3<double> P = mk(d.y * e2.z - d.z * e2.y, d.z * e2.x - d.x * e2.z, d.x * e2.y - d.y * e2.x);
-            const double det = dot3(e1, P);
-            if (fabs(det) <= 1e-14 * sqrt(dot3(e1, e1) * dot3(e2, e2))) continue;
-            const double inv = 1.0 / det;
-            const V3<double> Tv = mk(x.x - p0.x, x.y - p0.y, x.z - p0.z);
-            const double u = dot3(Tv, P) * inv;
-            if (u < -1e-12 || u > 1.0 + 1e-12) continue;
-            const V3<double> Qv = mk(Tv.y * e1.z - Tv.z * e1.y, Tv.z * e1.x - Tv.x * e1.z, Tv.x * e1.y - Tv.y * e1.x);
-            const double v = dot3(d, Qv) * inv;
-            if (v < -1e-12 || u + v > 1.0 + 1e-12) continue;
-            const double t = dot3(e2, Qv) * inv;
+            V3<T> p0, e1, e2;
+            if constexpr (F) {
+                const float *q = a.bgeo32 + (int64_t)f * kBFaceGeo;
+                p0 = mk(q[0], q[1], q[2]);
+                e1 = mk(q[3], q[4], q[5]);
+                e2 = mk(q[6], q[7], q[8]);
+            } else {
+                const double *q = a.bgeo + (int64_t)f * kBFaceGeo;
+                p0 = mk(q[0], q[1], q[2]);
+                e1 = mk(q[3], q[4], q[5]);
+                e2 = mk(q[6], q[7], q[8]);
+            }
+            const V3<T> n = mk(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
+            const T nd = dot3(n, d);
+            if (!(nd < (T)0)) continue;  // not an entry (outward normal e1 x e2)
+            // the plane's crossing first: a face behind tmin or beyond the best entry so far needs no more
+            const T tp = (n.x * (p0.x - x.x) + n.y * (p0.y - x.y) + n.z * (p0.z - x.z)) / nd;
+            if (!(tp > tmin - tol * max((T)1, fabs(tmin))) || !(tp < best + tol * max((T)1, fabs(tp)))) continue;
+            const V3<T> P = mk(d.y * e2.z - d.z * e2.y, d.z * e2.x - d.x * e2.z, d.x * e2.y - d.y * e2.x);
+            const T det = dot3(e1, P);
+            if (fabs(det) <= (F ? (T)1e-7 : (T)1e-14) * sqrt(dot3(e1, e1) * dot3(e2, e2))) continue;
+            const T inv = (T)1 / det;
+            const V3<T> Tv = mk(x.x - p0.x, x.y - p0.y, x.z - p0.z);
+            const T u = dot3(Tv, P) * inv;
+            if (u < -tol || u > (T)1 + tol) continue;
+            const V3<T> Qv = mk(Tv.y * e1.z - Tv.z * e1.y, Tv.z * e1.x - Tv.x * e1.z, Tv.x * e1.y - Tv.y * e1.x);
+            const T v = dot3(d, Qv) * inv;
+            if (v < -tol || u + v > (T)1 + tol) continue;
+            const T t = dot3(e2, Qv) * inv;
             if (t > tmin && t < best) {
                 best = t;
                 bf = f;
             }
         }
-        const double tnext = fmin(mx, fmin(my, mz));
+        const T tnext = min(mx, min(my, mz));
         if (bf >= 0 && best <= tnext) break;  // nothing nearer can lie in a later cell
         if (tnext > tout) break;
         if (mx <= my && mx <= mz) {
@@ -176,14 +200,18 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, co
     }
     bool exact = true;  // x is vertex kk of T
     int entf = -1;      // face of T through which the line came in from outside the mesh
+    float tcur = 0.f;  // the farthest point reached: re-entries are looked for beyond it only, so that a line
+                       // grazing a fold, where the tet tests and the face search round differently, cannot cycle
+    const V3<float> xf = mk((float)xd.x, (float)xd.y, (float)xd.z);
     if (T < 0 || best < -kStartTolF) {  // the half-line leaves the mesh at x
         if constexpr (!RE) return I;
-        double th;  // a non-convex mesh: the line may come back
-        const int f = walk_reenter(a, xd, mk((double)d.x, (double)d.y, (double)d.z), 0.0, th);
+        float th;  // a non-convex mesh: the line may come back
+        const int f = walk_reenter<float>(a, xf, d, 0.f, th);
         if (f < 0) return I;
         T = a.bface[f] >> 2;
         entf = a.bface[f] & 3;
         exact = false;
+        tcur = th;
     }
     for (int step = 0; T >= 0; ++step) {
         if (step >= a.max_steps) {
@@ -283,12 +311,14 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, co
         exact = false;
         entf = -1;
         if constexpr (RE) {
-            if (next < 0) {  // left a non-convex mesh: does the line come back?
-                double th;
-                const int f = walk_reenter(a, xd, mk((double)d.x, (double)d.y, (double)d.z), (double)hi, th);
-                if (f >= 0) {
+            tcur = fmaxf(tcur, hi);
+            if (next == -2) {  // left through a face some boundary node lies beyond: does the line come back?
+                float th;
+                const int f = walk_reenter<float>(a, xf, d, tcur, th);
+                if (f >= 0) {  // a grazing entry may give the tet an empty chord: never find it twice
                     T = a.bface[f] >> 2;
                     entf = a.bface[f] & 3;
+                    tcur = fmaxf(tcur, th);
                     continue;
                 }
             }
@@ -324,14 +354,16 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
     }
     bool exact = true;  // x is vertex kk of T
     int entf = -1;      // face of T through which the line came in from outside the mesh
+    double tcur = 0.0;  // the farthest point reached (re-entries only beyond it)
     if (T < 0 || best < -kStartTolD) {
         if constexpr (!RE) return I;
         double th;
-        const int f = walk_reenter(a, x, d, 0.0, th);
+        const int f = walk_reenter<double>(a, x, d, 0.0, th);
         if (f < 0) return I;
         T = a.bface[f] >> 2;
         entf = a.bface[f] & 3;
         exact = false;
+        tcur = th;
     }
     for (int step = 0; T >= 0; ++step) {
         if (step >= a.max_steps) {
@@ -420,12 +452,14 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
         exact = false;
         entf = -1;
         if constexpr (RE) {
+            tcur = fmax(tcur, hi);
             if (next < 0) {
                 double th;
-                const int f = walk_reenter(a, x, d, hi, th);
+                const int f = walk_reenter<double>(a, x, d, tcur, th);
                 if (f >= 0) {
                     T = a.bface[f] >> 2;
                     entf = a.bface[f] & 3;
+                    tcur = fmax(tcur, th);
                     continue;
                 }
             }
@@ -558,6 +592,9 @@ __global__ void grid_box_kernel(const double *__restrict__ nodes, const int32_t 
             g->lo[k] = smn[k][0] - pad;
             g->cell[k] = (smx[k][0] - smn[k][0] + 2.0 * pad) / G;
             g->inv[k] = 1.0 / g->cell[k];
+            g->lo32[k] = (float)g->lo[k];
+            g->cell32[k] = (float)g->cell[k];
+            g->inv32[k] = 1.0f / g->cell32[k];
         }
         g->G = G;
         g->ok = 1;
@@ -571,7 +608,7 @@ template <int PASS>
 __global__ void grid_faces_kernel(const double *__restrict__ nodes, const int32_t *__restrict__ tets,
                                   const int32_t *__restrict__ bface, int64_t n_bface, const WalkGrid *g,
                                   int32_t *cell_cnt, const int32_t *__restrict__ cell_off, int32_t *cell_face,
-                                  int64_t cap, double *geo)
+                                  int64_t cap, double *geo, float *geo32)
 {
     const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= n_bface) return;
@@ -598,6 +635,7 @@ __global__ void grid_faces_kernel(const double *__restrict__ nodes, const int32_
         q[0] = p[0].x; q[1] = p[0].y; q[2] = p[0].z;
         q[3] = e1.x; q[4] = e1.y; q[5] = e1.z;
         q[6] = e2.x; q[7] = e2.y; q[8] = e2.z;
+        for (int i = 0; i < kBFaceGeo; ++i) geo32[f * kBFaceGeo + i] = (float)q[i];
     }
     const int G = g->G;
     int i0[3], i1[3];
@@ -681,12 +719,16 @@ __global__ void walk_records_kernel(const float4 *__restrict__ near32, const int
 // mode = 1 iff every boundary node lies on the inner side of every boundary face's plane
 // (within 1e-9 of the face's longest edge); mode must be set to the mesh's conformity (1 or 0)
 // before the launch; a violation clears it.
+// Every boundary face is checked (not only until the first violation): a face with a boundary node outside
+// its plane is marked in the float32 walk record (neighbour -2 instead of -1), since a line can re-enter the
+// mesh only after leaving it through such a face; a line that leaves through a face whose plane has the whole
+// mesh on its inner side never comes back.
 __global__ void convex_kernel(const double *__restrict__ nodes, const int32_t *__restrict__ tets,
                               const int32_t *__restrict__ bface, int64_t n_bface, const int32_t *__restrict__ bnode,
-                              int64_t n_bnode, int *mode)
+                              int64_t n_bnode, int *mode, float4 *wrec)
 {
     const int64_t f = blockIdx.y;  // boundary face of this block row
-    if (f >= n_bface || *mode != 1) return;
+    if (f >= n_bface || *mode == 0) return;
     const int slot = bface[f];
     const int64_t t = slot >> 2;
     const int opp = slot & 3;
@@ -705,11 +747,21 @@ __global__ void convex_kernel(const double *__restrict__ nodes, const int32_t *_
                                                                     (p2.y - p1.y) * (p2.y - p1.y) +
                                                                     (p2.z - p1.z) * (p2.z - p1.z))));
     const double tol = 1e-9 * e3 * sqrt(dot3(n, n));
+    // float screen of n . (q - p0) with a margin above its rounding; float64 only near the threshold
+    const float nxf = (float)n.x, nyf = (float)n.y, nzf = (float)n.z;
+    const float pxf = (float)p0.x, pyf = (float)p0.y, pzf = (float)p0.z;
+    const float nn = (float)sqrt(dot3(n, n));
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_bnode; i += (int64_t)gridDim.x * blockDim.x) {
         const int q = bnode[i];
+        const float qx = (float)nodes[3 * q], qy = (float)nodes[3 * q + 1], qz = (float)nodes[3 * q + 2];
+        const float dx = qx - pxf, dy = qy - pyf, dz = qz - pzf;
+        const float sf = nxf * dx + nyf * dy + nzf * dz;
+        const float margin = 1e-5f * nn * (fabsf(dx) + fabsf(dy) + fabsf(dz) + fabsf(pxf) + fabsf(pyf) + fabsf(pzf));
+        if (sf < (float)tol - margin) continue;  // inside the plane beyond doubt
         const double s = n.x * (nodes[3 * q] - p0.x) + n.y * (nodes[3 * q + 1] - p0.y) + n.z * (nodes[3 * q + 2] - p0.z);
         if (s > tol) {
             atomicMax(mode, 2);  // not convex: the walk looks for re-entries
+            reinterpret_cast<int *>(wrec + t * kWalkRecVec4 + 7)[opp] = -2;
             return;
         }
     }
@@ -771,7 +823,8 @@ bool build_walk_mesh(const int32_t *tets_host, int64_t n_nodes, int64_t n_tets, 
 }
 
 cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const int32_t *bface, int64_t n_bface,
-                                const int32_t *bnode, int64_t n_bnode, int conforming, int *mode, cudaStream_t st)
+                                const int32_t *bnode, int64_t n_bnode, int conforming, int *mode, float4 *wrec,
+                                cudaStream_t st)
 {
     set_int_kernel<<<1, 1, 0, st>>>(mode, conforming ? 1 : 0);
     cudaError_t e = cudaGetLastError();
@@ -779,7 +832,7 @@ cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const 
     const int64_t gx = std::min<int64_t>((n_bnode + 255) / 256, 8);
     for (int64_t f0 = 0; f0 < n_bface; f0 += 65535) {
         const dim3 grid((unsigned)gx, (unsigned)std::min<int64_t>(65535, n_bface - f0));
-        convex_kernel<<<grid, 256, 0, st>>>(nodes, tets, bface + f0, n_bface - f0, bnode, n_bnode, mode);
+        convex_kernel<<<grid, 256, 0, st>>>(nodes, tets, bface + f0, n_bface - f0, bnode, n_bnode, mode, wrec);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -803,11 +856,11 @@ cudaError_t launch_walk_grid(const double *nodes, const int32_t *tets, const int
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((n_bface + 127) / 128);
     grid_faces_kernel<0><<<blocks, 128, 0, st>>>(nodes, tets, bface, n_bface, g.grid, g.cell_cnt, g.cell_off,
-                                                 g.cell_face, g.cap, g.geo);
+                                                 g.cell_face, g.cap, g.geo, g.geo32);
     grid_scan_kernel<<<1, 1024, 0, st>>>(g.cell_cnt, (int)cells, g.cell_off, g.cap, g.grid);
     if ((e = cudaMemsetAsync(g.cell_cnt, 0, sizeof(int32_t) * cells, st)) != cudaSuccess) return e;
     grid_faces_kernel<1><<<blocks, 128, 0, st>>>(nodes, tets, bface, n_bface, g.grid, g.cell_cnt, g.cell_off,
-                                                 g.cell_face, g.cap, g.geo);
+                                                 g.cell_face, g.cap, g.geo, g.geo32);
     return cudaGetLastError();
 }
 
