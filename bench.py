@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import config2_ring, config3_fourier, config3_samples, config4_batch, config5_rings  # noqa: E402
+from workloads import ball_mesh, config2_ring, config3_fourier, config3_samples, config4_batch, config5_rings  # noqa: E402
 
 PARAMS = dict(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16)
 METRIC = "node-tet interactions/s (velocity at all nodes, FP32 path)"
@@ -50,7 +50,7 @@ def workload_config():
     return {"workload": "fourier-64^3: 262144 nodes x 1500282 tets, velocity at all nodes",
             "far_ratio": PARAMS["far_ratio"], "tet_gauss_order": PARAMS["tet_gauss_order"],
             "n_theta": PARAMS["n_theta"], "n_phi": PARAMS["n_phi"], "precision": "fp32",
-            "l2": "inputs larger than L2 (far records 168 MB, near records 192 MB per replica)"}
+            "l2": "inputs larger than L2 (far records 264 MB, near records 360 MB per replica)"}
 
 
 def kernel_source_hash() -> str:
@@ -412,16 +412,64 @@ def allray_workload(args):
     return 0
 
 
+def hill_workload(args):
+    """The paper's Table 1 experiment on this hardware: Hill's spherical vortex (Section 3.1) on a tetrahedralised
+    unit ball of N nodes, velocity at all nodes by the all-ray method (the mesh walk) with 4x4 and 16x16
+    directions, FP32; r.m.s. error against the closed-form velocity (the paper's epsilon, here over the largest
+    speed too) and the time per evaluation.  The paper's meshes are TETGEN meshes of N random points (not
+    published); jittered Kuhn grids mapped onto the ball stand in for them."""
+    import torch
+
+    import paper_0712_1695_gb300 as bs
+    from workloads import hill_velocity, hill_vorticity
+
+    bs.load()
+    rows = []
+    with ClockSampler(0) as clk:
+        for n in (10, 13, 16, 20, 25):  # 1000 .. 15625 nodes, the paper's N = 1000 .. 16000
+            b = ball_mesh(n, hill_vorticity, jitter=0.1)
+            h = bs.Mesh(b.nodes, b.tets, b.omega)
+            ex = hill_velocity(b.nodes)
+            for N in (4, 16):
+                P = dict(far_ratio=float("inf"), tet_gauss_order=4, n_theta=N, n_phi=N, precision=bs.BS_FP32)
+                out = h.bs_velocity_nodes(**P)  # connectivity, tables
+                h.bs_status()
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = max(3, args.steps)
+                ev0.record()
+                for _ in range(reps):
+                    h.bs_velocity_nodes(out_dev=out, **P)
+                ev1.record()
+                torch.cuda.synchronize()
+                h.bs_status()
+                v = out.cpu().numpy()
+                err = v - ex
+                rms = float(np.sqrt(np.mean(np.sum(err ** 2, axis=1))))
+                rows.append({"N": len(b.nodes), "tets": len(b.tets), "directions": f"{N}x{N}",
+                             "ms": ev0.elapsed_time(ev1) / reps, "eps_rms": rms,
+                             "eps_rms_over_max": rms / float(np.linalg.norm(ex, axis=1).max())})
+    last = rows[-1]
+    line = {"metric": "velocity at all nodes of Hill's vortex, all-ray method (the paper's Table 1 workload)",
+            "value": last["N"] * last["tets"] / (last["ms"] * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": max(3, args.steps), "warmup": 1, "ms_per_step": last["ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Hill's spherical vortex on jittered Kuhn-grid unit balls, N = 1000 .. 15625 nodes",
+                       "far_ratio": "inf", "precision": "fp32"},
+            "rows": rows, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fourier64", choices=["fourier64", "batch", "rings", "allray"],
+    ap.add_argument("--workload", default="fourier64", choices=["fourier64", "batch", "rings", "allray", "hill"],
                     help="fourier64: the headline workload; batch: 256 uneven meshes, batched vs separate "
                          "launches; rings: Heun steps of two colliding rings; allray: the ray rule for every "
-                         "pair on the 32^3 ring mesh")
+                         "pair on the 32^3 ring mesh; hill: the paper's Table 1 experiment (Hill's vortex, all-ray)")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
     ap.add_argument("--rings-mode", default="hybrid", choices=["hybrid", "allray-stretch"],
                     help="rings workload: the far/near rule with frozen vorticity, or the all-ray method with vortex "
@@ -454,6 +502,8 @@ def main():
         return rings_workload(args)
     if args.workload == "allray":
         return allray_workload(args)
+    if args.workload == "hill":
+        return hill_workload(args)
 
     import torch
 

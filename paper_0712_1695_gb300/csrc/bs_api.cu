@@ -394,6 +394,7 @@ int bs_status(bs_handle h, void *stream)
     BS_CUDA(cudaMemset(h->flag, 0, sizeof(int)));
     if (flag & kFlagTimeout) return fail(BS_ERR_TIMEOUT, "a bounded device wait gave up");
     if (flag & kFlagWalk) return fail(BS_ERR_TIMEOUT, "a mesh walk did not leave the mesh within its step limit");
+    if (flag & kFlagWalkStuck) return fail(BS_ERR_MESH, "a mesh walk reached a tet with no face ahead of the line");
     if (flag & kFlagNoWalk)
         return fail(BS_ERR_MESH, "the derivative along directions needs a conforming mesh with a convex domain "
                                  "(the mesh walk); the velocity was computed, the derivative was not");
@@ -493,8 +494,9 @@ int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *d
     BS_CUDA(ensure_lines(h, p->n_phi, p->n_theta, st));
     if (h->walk_version != h->version) {  // the mesh changed: walk records, and is the domain still convex?
         BS_CUDA(launch_walk_records(h->near32, h->walk_nbr, h->n_tets, h->walk_rec, st));
-        BS_CUDA(launch_convex_check(h->nodes, h->tets, h->walk_bface, h->walk_n_bface, h->walk_bnode,
-                                    h->walk_n_bnode, h->walk_conforming ? 1 : 0, h->walk_mode, h->walk_rec, st));
+        BS_CUDA(launch_convex_check(h->nodes, h->tets, h->walk_nbr, h->n_tets, h->walk_bface, h->walk_n_bface,
+                                    h->walk_bnode, h->walk_n_bnode, h->walk_conforming ? 1 : 0, h->walk_mode,
+                                    h->walk_rec, st));
         if (h->walk_conforming) {
             BS_CUDA(launch_walk_grid(h->nodes, h->tets, h->walk_bface, h->walk_n_bface, h->walk_bnode,
                                      h->walk_n_bnode, h->walk_grid, st));
@@ -503,7 +505,9 @@ int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *d
         }
         h->walk_version = h->version;
         if (h->prof)
-            h->prof_all += 2 + (h->walk_conforming && h->walk_n_bface > 0 ? (h->walk_n_bface + 65534) / 65535 : 0);
+            h->prof_all += 2 + (h->walk_conforming && h->n_tets > 0 ? 1 : 0) +
+                           (h->walk_conforming && h->walk_n_bface > 0 && h->walk_n_bnode > 0
+                                ? (h->walk_n_bface + 65534) / 65535 : 0);
     }
     WalkArgs w;
     w.nodes = h->nodes;

@@ -91,6 +91,7 @@ constexpr int kFlagMeshVolume = 2;
 constexpr int kFlagTimeout = 4;
 constexpr int kFlagWalk = 8;     // a mesh walk hit its step limit or a tet with no face ahead
 constexpr int kFlagNoWalk = 16;  // a derivative along directions was asked of a mesh the walk cannot serve
+constexpr int kFlagWalkStuck = 32;  // a mesh walk reached a tet with no face ahead of the line
 
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined in the .cu files).
@@ -239,11 +240,12 @@ cudaError_t launch_walk_grid(const double *nodes, const int32_t *tets, const int
                              const int32_t *bnode, int64_t n_bnode, const WalkGridArrays &g, cudaStream_t st);
 // after the convexity check and the grid: a non-convex mesh whose face grid overflowed gets mode 0
 cudaError_t launch_walk_finalize(const WalkGrid *g, int *mode, cudaStream_t st);
-// mode := 1 if conforming (else 0), then 2 if a boundary node lies outside a boundary face's plane
-// (a non-convex domain: the walk then looks for re-entries through the grid)
-cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const int32_t *bface, int64_t n_bface,
-                                const int32_t *bnode, int64_t n_bnode, int conforming, int *mode, float4 *wrec,
-                                cudaStream_t st);
+// mode := 1 if conforming (else 0); 0 if two tets that share a face lie on the same side of it (a folded
+// mesh); then 2 if a boundary node lies outside a boundary face's plane (a non-convex domain: the walk
+// then looks for re-entries through the grid)
+cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const int32_t *nbr, int64_t n_tets,
+                                const int32_t *bface, int64_t n_bface, const int32_t *bnode, int64_t n_bnode,
+                                int conforming, int *mode, float4 *wrec, cudaStream_t st);
 cudaError_t launch_walk(int precision, const WalkArgs &a, cudaStream_t st, cudaEvent_t ev_start = nullptr,
                         cudaEvent_t ev_stop = nullptr);
 // Heun step position updates (n_values = 3 * nodes)

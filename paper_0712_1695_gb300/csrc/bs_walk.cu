@@ -203,6 +203,7 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, co
     float tcur = 0.f;  // the farthest point reached: re-entries are looked for beyond it only, so that a line
                        // grazing a fold, where the tet tests and the face search round differently, cannot cycle
     const V3<float> xf = mk((float)xd.x, (float)xd.y, (float)xd.z);
+    int prevT = -1;  // the tet the line came from (-1 at the start and after coming back in from outside)
     if (T < 0 || best < -kStartTolF) {  // the half-line leaves the mesh at x
         if constexpr (!RE) return I;
         float th;  // a non-convex mesh: the line may come back
@@ -220,6 +221,9 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, co
         }
         const float4 *r = a.wrec + (int64_t)T * kWalkRecVec4;
         const float4 q0 = __ldg(r), q1 = __ldg(r + 1), q2 = __ldg(r + 2), q3 = __ldg(r + 3);
+        const int4 nb = __ldg(reinterpret_cast<const int4 *>(r + 7));  // the face neighbours
+        // the face the line came in through (from the previous tet, or from outside): never left through again
+        const int inface = prevT >= 0 ? (nb.x == prevT ? 0 : nb.y == prevT ? 1 : nb.z == prevT ? 2 : 3) : entf;
         V3<float> g[4];
         g[1] = mk(q0.x, q0.y, q0.z);
         g[2] = mk(q1.x, q1.y, q1.z);
@@ -243,7 +247,10 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, co
         b[2] = dot3(g[2], d);
         b[3] = dot3(g[3], d);
         b[0] = -(b[1] + b[2] + b[3]);
-        float lo = -INFINITY, hi = INFINITY;
+        // chord [lo, hi] exactly as the ray rule takes it (its contribution); the way on: the nearest face ahead
+        // other than the one the line came in through (hx, exitf), so that two tets that round a nearly
+        // parallel shared face differently cannot hand the line back and forth
+        float lo = -INFINITY, hi = INFINITY, hx = INFINITY;
         int exitf = -1;
         bool empty = false;
 #pragma unroll
@@ -254,19 +261,21 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, co
                 const float ti = -av[i] / b[i];
                 if (b[i] > 0.f) {
                     lo = fmaxf(lo, ti);
-                } else if (ti < hi) {
-                    hi = ti;
-                    exitf = i;
+                } else {
+                    hi = fminf(hi, ti);
+                    if (i != inface && ti < hx) {
+                        hx = ti;
+                        exitf = i;
+                    }
                 }
             }
         }
         if (exitf < 0) {  // no face ahead: not a bounded tet along this line
-            atomicOr(a.flag, kFlagWalk);
+            atomicOr(a.flag, kFlagWalkStuck);
             break;
         }
-        // omega at the vertices (w0 w1 w2 w3, 12 floats) and the face neighbours (4 ints)
+        // omega at the vertices (w0 w1 w2 w3, 12 floats)
         const float4 q4 = __ldg(r + 4), q5 = __ldg(r + 5), q6 = __ldg(r + 6);
-        const int4 nb = __ldg(reinterpret_cast<const int4 *>(r + 7));
         float ge[4];  // g_i . e
         if constexpr (GRAD) {
             ge[1] = dot3(g[1], e);
@@ -297,7 +306,7 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, co
             for (int side = 0; side < 2; ++side) {
                 const int f = side == 0 ? entf : (next < 0 ? exitf : -1);
                 if (f < 0) continue;
-                const float tt = side == 0 ? lo : hi;
+                const float tt = side == 0 ? lo : hx;
                 const float c0 = av[0] + b[0] * tt, c1 = av[1] + b[1] * tt;
                 const float c2 = av[2] + b[2] * tt, c3 = av[3] + b[3] * tt;
                 const float gef = f == 0 ? ge[0] : f == 1 ? ge[1] : f == 2 ? ge[2] : ge[3];
@@ -310,14 +319,16 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, co
         }
         exact = false;
         entf = -1;
+        prevT = T;
         if constexpr (RE) {
-            tcur = fmaxf(tcur, hi);
+            tcur = fmaxf(tcur, hx);
             if (next == -2) {  // left through a face some boundary node lies beyond: does the line come back?
                 float th;
                 const int f = walk_reenter<float>(a, xf, d, tcur, th);
                 if (f >= 0) {  // a grazing entry may give the tet an empty chord: never find it twice
                     T = a.bface[f] >> 2;
                     entf = a.bface[f] & 3;
+                    prevT = -1;
                     tcur = fmaxf(tcur, th);
                     continue;
                 }
@@ -355,6 +366,7 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
     bool exact = true;  // x is vertex kk of T
     int entf = -1;      // face of T through which the line came in from outside the mesh
     double tcur = 0.0;  // the farthest point reached (re-entries only beyond it)
+    int prevT = -1;     // the tet the line came from
     if (T < 0 || best < -kStartTolD) {
         if constexpr (!RE) return I;
         double th;
@@ -371,6 +383,8 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
             break;
         }
         const double *r = a.near64 + (int64_t)T * kNearF64;
+        const int32_t *nbT = a.nbr + 4 * (int64_t)T;
+        const int inface = prevT >= 0 ? (nbT[0] == prevT ? 0 : nbT[1] == prevT ? 1 : nbT[2] == prevT ? 2 : 3) : entf;
         V3<double> g[4];
         for (int i = 1; i < 4; ++i) g[i] = mk(r[nf64::G + 3 * i - 3], r[nf64::G + 3 * i - 2], r[nf64::G + 3 * i - 1]);
         g[0] = mk(-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z));
@@ -389,7 +403,7 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
         b[2] = dot3(g[2], d);
         b[3] = dot3(g[3], d);
         b[0] = -(b[1] + b[2] + b[3]);
-        double lo = -INFINITY, hi = INFINITY;
+        double lo = -INFINITY, hi = INFINITY, hx = INFINITY;  // chord as the rule takes it; the way on (hx, exitf)
         int exitf = -1;
         bool empty = false;
         for (int i = 0; i < 4; ++i) {
@@ -399,14 +413,17 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
                 const double ti = -av[i] / b[i];
                 if (b[i] > 0.0) {
                     lo = fmax(lo, ti);
-                } else if (ti < hi) {
-                    hi = ti;
-                    exitf = i;
+                } else {
+                    hi = fmin(hi, ti);
+                    if (i != inface && ti < hx) {
+                        hx = ti;
+                        exitf = i;
+                    }
                 }
             }
         }
         if (exitf < 0) {
-            atomicOr(a.flag, kFlagWalk);
+            atomicOr(a.flag, kFlagWalkStuck);
             break;
         }
         double ge[4];  // g_i . e
@@ -437,7 +454,7 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
             for (int side = 0; side < 2; ++side) {  // omega jumps where the line enters or leaves the mesh
                 const int f = side == 0 ? entf : (next < 0 ? exitf : -1);
                 if (f < 0) continue;
-                const double tt = side == 0 ? lo : hi;
+                const double tt = side == 0 ? lo : hx;
                 const double gef = f == 0 ? ge[0] : f == 1 ? ge[1] : f == 2 ? ge[2] : ge[3];
                 const double bf = f == 0 ? b[0] : f == 1 ? b[1] : f == 2 ? b[2] : b[3];
                 const double dT = (side == 0 ? gef : -gef) / bf;
@@ -451,14 +468,16 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
         }
         exact = false;
         entf = -1;
+        prevT = T;
         if constexpr (RE) {
-            tcur = fmax(tcur, hi);
+            tcur = fmax(tcur, hx);
             if (next < 0) {
                 double th;
                 const int f = walk_reenter<double>(a, x, d, tcur, th);
                 if (f >= 0) {
                     T = a.bface[f] >> 2;
                     entf = a.bface[f] & 3;
+                    prevT = -1;
                     tcur = fmax(tcur, th);
                     continue;
                 }
@@ -723,6 +742,36 @@ __global__ void walk_records_kernel(const float4 *__restrict__ near32, const int
 // its plane is marked in the float32 walk record (neighbour -2 instead of -1), since a line can re-enter the
 // mesh only after leaving it through such a face; a line that leaves through a face whose plane has the whole
 // mesh on its inner side never comes back.
+// A mesh of positive tets is folded when two tets that share a face lie on the same side of it (the
+// tets overlap).  A line then need not leave a tet through the face it would in a valid mesh, and the
+// walk is switched off (mode 0: the ray kernel serves the nodes).  One thread per interior face slot.
+__global__ void fold_kernel(const double *__restrict__ nodes, const int32_t *__restrict__ tets,
+                            const int32_t *__restrict__ nbr, int64_t n_tets, int *mode)
+{
+    const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (slot >= 4 * n_tets) return;
+    const int64_t t = slot >> 2, u = nbr[slot];
+    if (u <= t) return;  // boundary face, or the pair is checked from the other side
+    const int opp = (int)(slot & 3);
+    int id[3], j = 0;
+    for (int i = 0; i < 4; ++i)
+        if (i != opp) id[j++] = tets[4 * t + i];
+    int ou = -1;
+    for (int i = 0; i < 4; ++i) {
+        const int v = tets[4 * u + i];
+        if (v != id[0] && v != id[1] && v != id[2]) ou = v;
+    }
+    if (ou < 0) return;
+    const int ot = tets[4 * t + opp];
+    const double *p0 = nodes + 3 * id[0], *p1 = nodes + 3 * id[1], *p2 = nodes + 3 * id[2];
+    const double e1x = p1[0] - p0[0], e1y = p1[1] - p0[1], e1z = p1[2] - p0[2];
+    const double e2x = p2[0] - p0[0], e2y = p2[1] - p0[1], e2z = p2[2] - p0[2];
+    const double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    const double st = nx * (nodes[3 * ot] - p0[0]) + ny * (nodes[3 * ot + 1] - p0[1]) + nz * (nodes[3 * ot + 2] - p0[2]);
+    const double su = nx * (nodes[3 * ou] - p0[0]) + ny * (nodes[3 * ou + 1] - p0[1]) + nz * (nodes[3 * ou + 2] - p0[2]);
+    if ((st > 0.0 && su > 0.0) || (st < 0.0 && su < 0.0)) *mode = 0;
+}
+
 __global__ void convex_kernel(const double *__restrict__ nodes, const int32_t *__restrict__ tets,
                               const int32_t *__restrict__ bface, int64_t n_bface, const int32_t *__restrict__ bnode,
                               int64_t n_bnode, int *mode, float4 *wrec)
@@ -822,13 +871,18 @@ bool build_walk_mesh(const int32_t *tets_host, int64_t n_nodes, int64_t n_tets, 
     return true;
 }
 
-cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const int32_t *bface, int64_t n_bface,
-                                const int32_t *bnode, int64_t n_bnode, int conforming, int *mode, float4 *wrec,
-                                cudaStream_t st)
+cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const int32_t *nbr, int64_t n_tets,
+                                const int32_t *bface, int64_t n_bface, const int32_t *bnode, int64_t n_bnode,
+                                int conforming, int *mode, float4 *wrec, cudaStream_t st)
 {
     set_int_kernel<<<1, 1, 0, st>>>(mode, conforming ? 1 : 0);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !conforming || n_bface == 0 || n_bnode == 0) return e;
+    if (e != cudaSuccess || !conforming) return e;
+    if (n_tets > 0) {
+        fold_kernel<<<(unsigned)((4 * n_tets + 255) / 256), 256, 0, st>>>(nodes, tets, nbr, n_tets, mode);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (n_bface == 0 || n_bnode == 0) return e;
     const int64_t gx = std::min<int64_t>((n_bnode + 255) / 256, 8);
     for (int64_t f0 = 0; f0 < n_bface; f0 += 65535) {
         const dim3 grid((unsigned)gx, (unsigned)std::min<int64_t>(65535, n_bface - f0));

@@ -23,7 +23,7 @@ from __future__ import annotations
 import numpy as np
 from brute_force import tet_integral
 
-from workloads import ball_mesh, hill_vorticity
+from workloads import ball_mesh, hill_velocity, hill_vorticity
 from workloads.configs import jittered_grid
 
 
@@ -109,29 +109,6 @@ def ball_outside(orc, n=9, params=None):
     R = np.linalg.norm(X, axis=1)
     exact = np.cross(BALL_OMEGA, X) / (3.0 * R[:, None] ** 3)
     return float(np.abs(v - exact).max() / np.abs(exact).max())
-
-
-def hill_velocity(X, A=1.0, a=1.0):
-    """Velocity of Hill's spherical vortex in the frame where the fluid is at rest far away.
-
-    From the Stokes stream function psi = (A/10) r^2 (a^2 - r^2 - z^2) inside
-    (translation speed U = 2 A a^2 / 15): u_r = A r z / 5,
-    u_z = (A/5)(5a^2/3 - 2 r^2 - z^2) inside, a point dipole
-    (U a^3 / 2 R^3)(3 (z.R^) R^ - z^) outside.  omega = A (-y, x, 0) inside.
-    """
-    X = np.asarray(X, dtype=np.float64)
-    x, y, z = X.T
-    r = np.hypot(x, y)
-    R = np.linalg.norm(X, axis=1)
-    U = 2.0 * A * a * a / 15.0
-    ur = A * r * z / 5.0
-    uz = A / 5.0 * (5.0 * a * a / 3.0 - 2.0 * r * r - z * z)
-    safe = np.where(r > 0, r, 1.0)
-    vin = np.stack([ur * x / safe, ur * y / safe, uz], axis=1)
-    Rs = np.where(R > 0, R, 1.0)
-    rh = X / Rs[:, None]
-    vout = U * a**3 / (2.0 * Rs[:, None] ** 3) * (3.0 * rh[:, 2:3] * rh - np.array([0.0, 0.0, 1.0]))
-    return np.where((R < a)[:, None], vin, vout)
 
 
 def hill(orc, ns=(5, 9, 17), params=None, count=12):

@@ -114,6 +114,35 @@ def test_mesh_the_walk_cannot_serve_reports_no_derivative():
     assert ei.value.code == BS_ERR_MESH
 
 
+def _folded_ball(n=8):
+    """Jittered Kuhn grid mapped onto the ball with no guard against the map's kink at the origin: a few
+    tets turn inside out and are re-oriented, so neighbours overlap (a folded mesh)."""
+    from workloads.mesh import cube_to_ball, jitter_interior, tet_volumes6
+
+    base, tets = kuhn_grid(n, -1.0, 1.0)
+    tets = orient_positive(base, tets)
+    nodes = cube_to_ball(jitter_interior(base, n, 0.1, np.random.default_rng(77)))
+    assert (tet_volumes6(nodes, tets) < 0).sum() > 0
+    tets = orient_positive(nodes, tets)
+    omega = np.array([0.0, 0.0, 1.0]) + 0.2 * np.random.default_rng(14).standard_normal((len(nodes), 3))
+    return nodes, tets, omega
+
+
+def test_folded_mesh_is_served_by_the_ray_kernel(orc):
+    """A folded mesh: the walk is switched off, the node velocities come from the all-ray kernel and still
+    match the oracle (which sums every tet as given), and the derivative is refused."""
+    nodes, tets, omega = _folded_ball()
+    h = bs.Mesh(nodes, tets, omega)
+    v = h.bs_velocity_nodes(precision=bs.BS_FP64, **ALLRAY).cpu().numpy()
+    h.bs_status()
+    vo = orc.velocity(nodes, tets, omega, nodes, tet_order=4, far_ratio=np.inf, n_theta=8, n_phi=16)
+    assert rel_l2(v, vo) <= TOL_FP64_REL_L2
+    h.bs_velocity_nodes_dderiv(precision=bs.BS_FP64, **ALLRAY)
+    with pytest.raises(BSError) as ei:
+        h.bs_status()
+    assert ei.value.code == BS_ERR_MESH
+
+
 def test_ring_mesh_full_size(orc):
     """The 32^3 ring mesh: float32 against float64 at all 32768 nodes, 24 seeded nodes against the oracle."""
     m = config2_ring()

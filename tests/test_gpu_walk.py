@@ -203,3 +203,22 @@ def test_box_deformed_by_lagrangian_steps(orc):
     assert np.array_equal(c, cr)
     vo = orc.velocity(nodes, m.tets, omega, nodes, **_op(ALLRAY))
     assert rel_l2(v, vo) <= TOL_FP64_REL_L2
+
+
+@pytest.mark.parametrize("n", [8, 11])
+def test_ball_mesh(orc, n):
+    """A jittered Kuhn grid mapped onto the unit ball (Hill's vortex, Section 3.1): flattened tets near the
+    mapped cube's edges and a faceted boundary; the walk matches the all-ray kernel and the oracle."""
+    from workloads import ball_mesh, hill_vorticity
+
+    b = ball_mesh(n, hill_vorticity, jitter=0.1)
+    h = bs.Mesh(b.nodes, b.tets, b.omega)
+    p = dict(ALLRAY, n_theta=16, n_phi=16)
+    v, c = nodes_velocity(h, len(b.nodes), bs.BS_FP64, **p)
+    vr, cr = nodes_velocity(h, len(b.nodes), bs.BS_FP64, walk=False, **p)
+    assert rel_l2(v, vr) <= 1e-13
+    assert np.array_equal(c, cr)
+    vo = orc.velocity(b.nodes, b.tets, b.omega, b.nodes, **_op(p))
+    assert rel_l2(v, vo) <= TOL_FP64_REL_L2
+    v32, _ = nodes_velocity(h, len(b.nodes), bs.BS_FP32, **p)
+    assert rms_over_max(v32, vo) <= TOL_FP32_RMS_MAX

@@ -96,13 +96,23 @@ def config5_rings(n: int = 80) -> Mesh:
 
 
 def ball_mesh(n: int, omega_fn=None, seed: int = 77, jitter: float = 0.0) -> Mesh:
-    """Kuhn grid of [-1,1]^3 (n nodes/side) mapped onto the unit ball by y = x |x|_inf / |x|_2."""
+    """Kuhn grid of [-1,1]^3 (n nodes/side) mapped onto the unit ball by y = x |x|_inf / |x|_2.
+
+    Interior nodes are jittered by U(+-jitter h) per coordinate in the cube.  The ball map is not smooth at
+    the origin and would turn some jittered tets inside out (a folded mesh) or into slivers; the jitter of the
+    nodes of a tet is halved until it keeps at least a quarter of its volume in the unjittered ball mesh.
+    """
     rng = np.random.default_rng(seed)
-    nodes, tets = kuhn_grid(n, -1.0, 1.0)
-    if jitter > 0:
-        nodes = jitter_interior(nodes, n, jitter, rng)
-    nodes = cube_to_ball(nodes)
-    tets = orient_positive(nodes, tets)
+    base, tets = kuhn_grid(n, -1.0, 1.0)
+    tets = orient_positive(base, tets)
+    disp = jitter_interior(base, n, jitter, rng) - base if jitter > 0 else np.zeros_like(base)
+    vol_min = 0.25 * tet_volumes6(cube_to_ball(base), tets)
+    for _ in range(40):
+        nodes = cube_to_ball(base + disp)
+        bad = tet_volumes6(nodes, tets) < vol_min
+        if not bad.any():
+            break
+        disp[np.unique(tets[bad])] *= 0.5
     vol6 = tet_volumes6(nodes, tets)
     assert np.all(vol6 > 0), "ball map produced a degenerate tet"
     omega = omega_fn(nodes) if omega_fn is not None else np.zeros_like(nodes)

@@ -67,3 +67,26 @@ def gaussian_blob(nodes: np.ndarray, center, sigma: float, axis) -> np.ndarray:
 def hill_vorticity(nodes: np.ndarray, A=1.0) -> np.ndarray:
     """Hill's spherical vortex: omega = A (-y, x, 0), i.e. omega_theta = A r (linear)."""
     return A * np.stack([-nodes[:, 1], nodes[:, 0], np.zeros(len(nodes))], axis=1)
+
+
+def hill_velocity(X, A=1.0, a=1.0):
+    """Velocity of Hill's spherical vortex in the frame where the fluid is at rest far away.
+
+    From the Stokes stream function psi = (A/10) r^2 (a^2 - r^2 - z^2) inside
+    (translation speed U = 2 A a^2 / 15): u_r = A r z / 5,
+    u_z = (A/5)(5a^2/3 - 2 r^2 - z^2) inside, a point dipole
+    (U a^3 / 2 R^3)(3 (z.R^) R^ - z^) outside.  omega = A (-y, x, 0) inside.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    x, y, z = X.T
+    r = np.hypot(x, y)
+    R = np.linalg.norm(X, axis=1)
+    U = 2.0 * A * a * a / 15.0
+    ur = A * r * z / 5.0
+    uz = A / 5.0 * (5.0 * a * a / 3.0 - 2.0 * r * r - z * z)
+    safe = np.where(r > 0, r, 1.0)
+    vin = np.stack([ur * x / safe, ur * y / safe, uz], axis=1)
+    Rs = np.where(R > 0, R, 1.0)
+    rh = X / Rs[:, None]
+    vout = U * a**3 / (2.0 * Rs[:, None] ** 3) * (3.0 * rh[:, 2:3] * rh - np.array([0.0, 0.0, 1.0]))
+    return np.where((R < a)[:, None], vin, vout)
