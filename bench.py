@@ -141,10 +141,20 @@ def run_oracle_sample(mesh, count: int, seed_offset: int = 0):
     rng = np.random.default_rng(77 + seed_offset)
     sel = np.sort(rng.choice(idx, size=count, replace=False))
     t = time.perf_counter()
-    oracle.velocity(mesh.nodes, mesh.tets, mesh.omega, mesh.nodes[sel], far_ratio=PARAMS["far_ratio"],
-                    tet_order=PARAMS["tet_gauss_order"], n_theta=PARAMS["n_theta"], n_phi=PARAMS["n_phi"])
+    v = oracle.velocity(mesh.nodes, mesh.tets, mesh.omega, mesh.nodes[sel], far_ratio=PARAMS["far_ratio"],
+                        tet_order=PARAMS["tet_gauss_order"], n_theta=PARAMS["n_theta"], n_phi=PARAMS["n_phi"])
     dt = time.perf_counter() - t
+    run_oracle_sample.last = (sel, v)
     return count * mesh.n_tets / dt, dt, oracle.num_threads()
+
+
+def rms_over_max(v, ref):
+    """RMS error over the largest reference speed."""
+    return float(np.sqrt(np.mean(np.sum((v - ref) ** 2, axis=1))) / np.linalg.norm(ref, axis=1).max())
+
+
+def rel_l2(v, ref):
+    return float(np.linalg.norm(v - ref) / np.linalg.norm(ref))
 
 
 def reference_arm(args, rank, world):
@@ -485,6 +495,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=96, help="oracle sample nodes per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 path on the 4096 sample nodes")
     ap.add_argument("--points", type=int, default=0,
                     help="evaluate only this many seeded nodes (small case for profiler captures)")
     args = ap.parse_args()
@@ -620,6 +631,29 @@ def main():
     if clocks.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (n_sm * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e-6)
 
+    # the FP64 path on the 4096 seeded sample nodes: its rate and the FP32 path's error against it
+    fp64 = None
+    v32 = out.cpu().numpy()
+    if not args.no_fp64 and not args.points:
+        idx = config3_samples(mesh.n_nodes, 4096)
+        pts64 = torch.from_numpy(np.ascontiguousarray(mesh.nodes[idx])).cuda()
+        out64 = torch.empty((len(idx), 3), dtype=torch.float64, device="cuda")
+        P64 = dict(PARAMS, precision=bs.BS_FP64)
+        h.bs_velocity(pts64, out_dev=out64, **P64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.bs_velocity(pts64, out_dev=out64, **P64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        h.bs_status()
+        v64 = out64.cpu().numpy()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": len(idx) * mesh.n_tets / (ms64 * 1e-3), "unit": UNIT, "ms": ms64,
+                "sample": f"the 4096 seeded sample nodes x all {mesh.n_tets} tets",
+                "fp32_vs_fp64_rms_over_max": rms_over_max(v32[idx], v64),
+                "fp32_vs_fp64_rel_l2": rel_l2(v32[idx], v64)}
+
     cpu = None
     if not args.no_cpu_baseline and world == 1 and not args.points:
         import oracle
@@ -629,6 +663,13 @@ def main():
         v, dt, cores = run_oracle_sample(mesh, args.cpu_sample)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_sample} of the 4096 seeded sample nodes x all {mesh.n_tets} tets ({dt:.1f} s)"}
+        sel, vo = run_oracle_sample.last
+        cpu["fp32_vs_oracle_rms_over_max"] = rms_over_max(v32[sel], vo)
+        cpu["fp32_vs_oracle_rel_l2"] = rel_l2(v32[sel], vo)
+        if fp64 is not None:
+            pos = np.searchsorted(idx, sel)
+            if np.array_equal(idx[pos], sel):
+                cpu["fp64_vs_oracle_rel_l2"] = rel_l2(v64[pos], vo)
 
     config = workload_config()
     if args.points:
@@ -636,7 +677,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
-            "roofline": roofline, "cpu_baseline": cpu,
+            "roofline": roofline, "cpu_baseline": cpu, "fp64_path": fp64,
             "e2e": e2e,
             "gpu_launches": int(all_launches), "clocks": clocks,
             "counts": {"near_pairs": n_near, "far_pairs": n_far, "ray_hits": n_hit}}
