@@ -67,7 +67,8 @@ class OracleLib:
                                      ctypes.c_double, _D, _D, _D]
         lib.orc_velocity.argtypes = [_D, ctypes.c_int64, _I32, ctypes.c_int64, _D, _D, ctypes.c_int64,
                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                     ctypes.c_double, ctypes.c_double, _D, _I32]
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, _D, _I32]
+        lib.orc_tet_analytic.argtypes = [_D, _D, _D, _D]
         lib.orc_velocity_dderiv.argtypes = [_D, ctypes.c_int64, _I32, ctypes.c_int64, _D, _D, _D, ctypes.c_int64,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
         lib.orc_num_threads.argtypes = []
@@ -113,6 +114,17 @@ class OracleLib:
                                            ctypes.byref(t), ctypes.byref(u), ctypes.byref(v))
         return bool(hit), t.value, u.value, v.value
 
+    def tet_analytic(self, x, verts, om):
+        """Exact Eq. 1 over one tet with linear vorticity (the analytic near-field evaluation)."""
+        x = _f64(x, (3,))
+        v = _f64(verts, (4, 3))
+        w = _f64(om, (4, 3))
+        out = np.zeros(3)
+        rc = self.lib.orc_tet_analytic(_dp(x), _dp(v), _dp(w), _dp(out))
+        if rc != 0:
+            raise ValueError("degenerate tet")
+        return out
+
     def tet_geometry(self, verts):
         v = _f64(verts, (4, 3))
         c = np.zeros(3)
@@ -131,8 +143,10 @@ class OracleLib:
         return bool(hit), R0.value, R1.value, J
 
     def velocity(self, nodes, tets, omega, pts, far_ratio=2.0, tet_order=4, n_theta=8, n_phi=16,
-                 use_precheck=True, eps_b=1e-12, tau=1e-9, counts=False):
-        """Velocity [n_pts, 3] (and optionally counts [n_pts, 3] = near, far, ray hits)."""
+                 use_precheck=True, eps_b=1e-12, tau=1e-9, counts=False, near_rule=0):
+        """Velocity [n_pts, 3] (and optionally counts [n_pts, 3] = near, far, ray hits).
+
+        near_rule 0: near tets by the ray rule; 1: by the exact integral (``tet_analytic``)."""
         nodes = _f64(nodes).reshape(-1, 3)
         omega = _f64(omega).reshape(-1, 3)
         pts = _f64(pts).reshape(-1, 3)
@@ -141,7 +155,7 @@ class OracleLib:
         cnt = np.zeros((len(pts), 3), dtype=np.int32)
         rc = self.lib.orc_velocity(_dp(nodes), len(nodes), tets.ctypes.data_as(_I32), len(tets), _dp(omega),
                                    _dp(pts), len(pts), float(far_ratio), int(tet_order), int(n_theta),
-                                   int(n_phi), int(use_precheck), float(eps_b), float(tau), _dp(vel),
+                                   int(n_phi), int(use_precheck), float(eps_b), float(tau), int(near_rule), _dp(vel),
                                    cnt.ctypes.data_as(_I32))
         if rc != 0:
             raise ValueError(f"oracle rejected arguments (code {rc})")
@@ -228,6 +242,10 @@ def moller_trumbore(*args, **kw):
 
 def tet_geometry(verts):
     return _load().tet_geometry(verts)
+
+
+def tet_analytic(*args, **kw):
+    return _load().tet_analytic(*args, **kw)
 
 
 def line_tet(*args, **kw):

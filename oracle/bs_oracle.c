@@ -21,7 +21,10 @@
  *       area coordinates, and the chord integral of Eq. 5 with the sign of R
  *       kept (a segment with R0 < 0 < R1 is split at R = 0):
  *       v += k_nm * s_nm x integral_{R0}^{R1} sign(R) omega dR,
- *       k_nm = (pi/16) sin(phi_n) w_n w_m.
+ *       k_nm = (pi/16) sin(phi_n) w_n w_m,
+ *       or (near_rule 1) the exact integral of Eq. 1 over the tet
+ *       (orc_tet_analytic), the analytic near-field evaluation that
+ *       Section 1 sets the ray rule against.
  *
  * Readings of the paper taken here (the printed formulas are at odds with
  * Eq. 1 in two places):
@@ -404,17 +407,141 @@ int orc_line_tet(const double *x, const double *s, const double *v /*[4][3]*/, c
 }
 
 /* ------------------------------------------------------------------------ */
+/* Exact Eq. 1 over one tet with linear vorticity: the analytic near-field   */
+/* evaluation of Section 1 (the Stokes-theorem reduction of the volume       */
+/* integral to face integrals and then to closed-form edge integrals, the    */
+/* approach the paper compares its ray rule against).  Written out from the  */
+/* calculus, with R = x - y, rho = |R|:                                      */
+/*   R x omega / rho^3 = grad_y(1/rho) x omega                               */
+/*                     = curl_y(omega / rho) - (curl omega) / rho,           */
+/* and by the divergence theorem (n outward, curl omega constant on T)      */
+/*   v = -(1/4pi) [ sum_f n_f x int_f omega/rho dS                           */
+/*                  - (curl omega) int_T 1/rho dV ],                        */
+/*   int_T 1/rho dV = (1/2) sum_f h_f int_f 1/rho dS,  h_f = n_f.(y - x)    */
+/* (div_y((y - x)/rho) = 2/rho).  With omega(y) = omega(x) + G (y - x),     */
+/* G = grad omega, and p = x + h n the foot of x on the face plane:         */
+/*   int_f omega/rho = omega(x) I0 + G (Ip + h n I0),                       */
+/*   I0 = int_f 1/rho dS,  Ip = int_f (y - p)/rho dS.                       */
+/* In the plane, Ip = int grad_s(rho) = sum_edges m_e int_e rho dl and      */
+/* 1/rho = div_s((y - p)(rho - |h|)/|y - p|^2), so per edge (unit tangent t, */
+/* in-plane outward normal m, l = (y - x).t along it, P0 = (y - x).m,       */
+/* R0^2 = P0^2 + h^2, R at the ends, f = int dl / rho):                     */
+/*   Ip += m (R0^2 f + l+ R+ - l- R-) / 2,                                  */
+/*   I0 += P0 f - |h| [atan(P0 l/(R0^2 + |h| R))]_{l-}^{l+}.                 */
+/* That is one logarithm and two arc tangents per face edge: 12 and 24 per   */
+/* tet, the count the paper quotes for the analytic formulae.  f is taken in */
+/* the form free of cancellation for the signs of l-, l+.  When x is on an   */
+/* edge's line (R0 = 0) that edge's terms vanish (P0 f, R0^2 f -> 0); when   */
+/* P0 = 0 the arc tangent term vanishes.                                     */
+/*   v, om [4][3]; vel [3] overwritten.                                       */
+/* ------------------------------------------------------------------------ */
+static void orc_face_integrals(const double *x, const double *ya, const double *yb, const double *yc,
+                               const double *n, double *h_out, double *I0_out, double *Ip)
+{
+    double d[3];
+    sub3(ya, x, d);
+    const double h = dot3(n, d), ah = fabs(h);
+    const double *ends[3][2] = {{ya, yb}, {yb, yc}, {yc, ya}};
+    double I0 = 0.0;
+    Ip[0] = Ip[1] = Ip[2] = 0.0;
+    for (int e = 0; e < 3; e++) {
+        const double *u = ends[e][0], *w = ends[e][1];
+        double t[3], m[3], um[3], wm[3];
+        sub3(w, u, t);
+        const double L = sqrt(dot3(t, t));
+        for (int j = 0; j < 3; j++) t[j] /= L;
+        cross3(t, n, m);
+        sub3(u, x, um);
+        sub3(w, x, wm);
+        const double lm = dot3(um, t), lp = dot3(wm, t);
+        const double P0 = dot3(um, m);
+        const double Rm = sqrt(dot3(um, um)), Rp = sqrt(dot3(wm, wm));
+        const double R02 = P0 * P0 + h * h;
+        double f = 0.0;
+        if (R02 > 1e-26 * L * L) {
+            if (lm >= 0.0)
+                f = log((Rp + lp) / (Rm + lm));
+            else if (lp <= 0.0)
+                f = log((Rm - lm) / (Rp - lp));
+            else
+                f = log((Rp + lp) * (Rm - lm) / R02);
+        }
+        double beta = 0.0;
+        if (fabs(P0) > 1e-13 * L) beta = atan(P0 * lp / (R02 + ah * Rp)) - atan(P0 * lm / (R02 + ah * Rm));
+        I0 += P0 * f - ah * beta;
+        const double c = 0.5 * (R02 * f + lp * Rp - lm * Rm);
+        for (int j = 0; j < 3; j++) Ip[j] += c * m[j];
+    }
+    *h_out = h;
+    *I0_out = I0;
+}
+
+int orc_tet_analytic(const double *x, const double *v /*[4][3]*/, const double *om /*[4][3]*/, double *vel)
+{
+    /* barycentric gradients g_i (lambda_i(y) = g_i . (y - v_0) for i = 1..3) */
+    double e1[3], e2[3], e3[3], n1[3], n2[3], n3[3];
+    sub3(v + 3, v, e1);
+    sub3(v + 6, v, e2);
+    sub3(v + 9, v, e3);
+    cross3(e2, e3, n1);
+    cross3(e3, e1, n2);
+    cross3(e1, e2, n3);
+    const double V6 = dot3(e1, n1);
+    if (V6 == 0.0) return ORC_ERR_ARG;
+    const double *nn[3] = {n1, n2, n3};
+    /* G[a][b] = d omega_a / d y_b = sum_i (omega_i - omega_0)_a g_i,b */
+    double G[3][3] = {{0}};
+    for (int i = 1; i <= 3; i++)
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++) G[a][b] += (om[3 * i + a] - om[a]) * nn[i - 1][b] / V6;
+    const double curl[3] = {G[2][1] - G[1][2], G[0][2] - G[2][0], G[1][0] - G[0][1]};
+    double xm[3], wx[3];
+    sub3(x, v, xm);
+    for (int a = 0; a < 3; a++) wx[a] = om[a] + G[a][0] * xm[0] + G[a][1] * xm[1] + G[a][2] * xm[2];
+    double S[3] = {0.0, 0.0, 0.0}, volint = 0.0;
+    for (int f = 0; f < 4; f++) {
+        const double *ya = v + 3 * FACE_VERTS[f][0], *yb = v + 3 * FACE_VERTS[f][1], *yc = v + 3 * FACE_VERTS[f][2];
+        double ab[3], ac[3], n[3], od[3];
+        sub3(yb, ya, ab);
+        sub3(yc, ya, ac);
+        cross3(ab, ac, n);
+        const double nl = sqrt(dot3(n, n));
+        for (int j = 0; j < 3; j++) n[j] /= nl;
+        sub3(v + 3 * f, ya, od); /* vertex f is the one off face f */
+        const double *p0 = ya, *p1 = yb, *p2 = yc;
+        if (dot3(n, od) > 0.0) { /* point n outward and keep (p0, p1, p2) counter-clockwise about it */
+            for (int j = 0; j < 3; j++) n[j] = -n[j];
+            p1 = yc;
+            p2 = yb;
+        }
+        double h, I0, Ip[3];
+        orc_face_integrals(x, p0, p1, p2, n, &h, &I0, Ip);
+        double q[3], Iw[3], nxI[3];
+        for (int j = 0; j < 3; j++) q[j] = Ip[j] + h * n[j] * I0;
+        for (int a = 0; a < 3; a++) Iw[a] = wx[a] * I0 + G[a][0] * q[0] + G[a][1] * q[1] + G[a][2] * q[2];
+        cross3(n, Iw, nxI);
+        for (int j = 0; j < 3; j++) S[j] += nxI[j];
+        volint += 0.5 * h * I0;
+    }
+    const double c = -1.0 / (4.0 * M_PI);
+    for (int j = 0; j < 3; j++) vel[j] = c * (S[j] - curl[j] * volint);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Velocity at points (the whole method).                                   */
 /*   nodes [n_nodes][3], tets [n_tets][4] (int32), omega [n_nodes][3],       */
-/*   pts [n_pts][3]; far_ratio >= 0 (INFINITY = rays for every tet);        */
-/*   tet_order in {1, 4, 8, 27, 64}; n_theta, n_phi >= 1.                   */
-/*   vel [n_pts][3] overwritten.  counts [n_pts][3] (near, far, ray hits) or */
-/*   NULL.                                                                   */
+/*   pts [n_pts][3]; far_ratio >= 0 (INFINITY = every tet near);            */
+/*   tet_order in {1, 4, 8, 27, 64}; n_theta, n_phi >= 1; near_rule 0: the  */
+/*   ray rule of Section 2 for near tets, 1: the exact integral              */
+/*   (orc_tet_analytic).  vel [n_pts][3] overwritten.  counts [n_pts][3]     */
+/*   (near, far, ray hits; no hits under near_rule 1) or NULL.               */
 /* ------------------------------------------------------------------------ */
 int orc_velocity(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets, const double *omega,
                  const double *pts, int64_t n_pts, double far_ratio, int tet_order, int n_theta, int n_phi,
-                 int use_precheck, double eps_b, double tau, double *vel, int32_t *counts)
+                 int use_precheck, double eps_b, double tau, int near_rule, double *vel, int32_t *counts)
 {
+    if (near_rule != 0 && near_rule != 1) return ORC_ERR_ARG;
     if (!nodes || !tets || !omega || !pts || !vel || n_pts < 0 || n_tets < 0 || n_nodes < 0) return ORC_ERR_ARG;
     if (n_theta < 1 || n_phi < 1 || n_theta > 512 || n_phi > 512) return ORC_ERR_ARG;
     double bary[64 * 4], wq[64];
@@ -473,6 +600,11 @@ int orc_velocity(const double *nodes, int64_t n_nodes, const int32_t *tets, int6
                     double f = -inv4pi * wq[q] * vol[e] / (R * R * R);
                     for (int j = 0; j < 3; j++) acc[j] += f * rxw[j];
                 }
+            } else if (near_rule == 1) {
+                n_near++;
+                double va[3];
+                orc_tet_analytic(x, v, om, va);
+                for (int j = 0; j < 3; j++) acc[j] += va[j];
             } else {
                 n_near++;
                 for (int l = 0; l < L; l++) {
@@ -545,7 +677,7 @@ int orc_velocity_dderiv(const double *nodes, int64_t n_nodes, const int32_t *tet
         return ORC_ERR_ARG;
     if (n_theta < 1 || n_phi < 1 || n_theta > 512 || n_phi > 512) return ORC_ERR_ARG;
     int rc = orc_velocity(nodes, n_nodes, tets, n_tets, omega, pts, n_pts, INFINITY, 1, n_theta, n_phi, 0, eps_b,
-                          tau, vel, NULL);
+                          tau, 0, vel, NULL);
     if (rc) return rc;
     const int L = n_theta * n_phi;
     double *S = (double *)malloc(sizeof(double) * 3 * L);

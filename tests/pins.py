@@ -17,6 +17,13 @@ mistake) and returns the numbers the tests compare with their bounds.
                stretching term): central differences of the oracle's own
                velocity at interior points and nodes, and the uniform ball's
                exact derivative omega x e / 3.
+  analytic     the exact single-tet integral (the analytic near-field
+               evaluation of Section 1): the Duffy-cone integral at points
+               inside, outside, on a vertex, an edge, a face and an edge's
+               line; additivity when a tet is cut into sub-tets (the faces
+               inside cancel); zero divergence by central differences; the ray
+               rule converging onto it as the angular order grows; and the
+               uniform ball, where only the polyhedral error O(h^2) is left.
 """
 from __future__ import annotations
 
@@ -168,4 +175,63 @@ def dderiv(orc, n=5, count=20, ball_n=7):
     _, dv = orc.velocity_dderiv(m.nodes, m.tets, np.tile(w0, (len(m.nodes), 1)), pts, e, n_theta=16, n_phi=32)
     ex = np.cross(w0, e) / 3.0
     out["ball"] = float(np.abs(dv - ex).max() / np.abs(ex).max())
+    return out
+
+
+def analytic(orc, quick=False):
+    """Measurements of orc.tet_analytic / near_rule 1 against results that do not come from it."""
+    V, om = single_tet_fixture()
+    out = {}
+    pts = {"inside": V.mean(axis=0) + 0.05, "outside": np.array([1.2, 0.9, 0.8]), "vertex": V[2].copy(),
+           "edge": 0.5 * (V[0] + V[1]), "face": (V[1] + V[2] + V[3]) / 3, "edge line": V[0] + 1.7 * (V[1] - V[0]),
+           "far": np.array([3.0, 2.0, 1.0])}
+    if quick:
+        pts = {k: pts[k] for k in ("inside", "outside", "vertex")}
+    out["single"] = {k: _rel(orc.tet_analytic(x, V, om), tet_integral(x, V, om, 96)) for k, x in pts.items()}
+    # cut the tet at a point q of edge 0-1 and at an interior point c: omega interpolates linearly
+    lam = np.array([0.3, 0.7, 0.0, 0.0])
+    q, wq = lam @ V, lam @ om
+    c, wc = np.array([0.1, 0.2, 0.3, 0.4]) @ V, np.array([0.1, 0.2, 0.3, 0.4]) @ om
+    parts = [(np.array([V[0], q, V[2], V[3]]), np.array([om[0], wq, om[2], om[3]])),
+             (np.array([q, V[1], V[2], V[3]]), np.array([wq, om[1], om[2], om[3]]))]
+    cones = []
+    for f in ((1, 2, 3), (0, 2, 3), (0, 1, 3), (0, 1, 2)):
+        cones.append((np.array([c, *V[list(f)]]), np.array([wc, *om[list(f)]])))
+    split = 0.0
+    for x in (V[0], V.mean(axis=0) + 0.03, np.array([0.9, -0.4, 0.6]), q):
+        full = orc.tet_analytic(x, V, om)
+        for pieces in (parts, cones):
+            split = max(split, _rel(sum(orc.tet_analytic(x, a, b) for a, b in pieces), full))
+    out["split"] = split
+    # divergence of the exact integral vanishes (central differences, step 1e-4)
+    rng = np.random.default_rng(41)
+    worst = 0.0
+    d = 1e-4
+    for x in (V.mean(axis=0) + 0.02, np.array([1.1, 0.8, 0.6]), 0.5 * (V[1] + V[2]) + 0.01):
+        grad = np.zeros((3, 3))
+        for j in range(3):
+            e = np.zeros(3)
+            e[j] = d
+            grad[j] = (orc.tet_analytic(x + e, V, om) - orc.tet_analytic(x - e, V, om)) / (2 * d)
+        worst = max(worst, abs(np.trace(grad)) / np.abs(grad).max())
+    out["div"] = worst
+    # the ray rule converges onto the exact integral as the angular order grows
+    tets = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    x = V.mean(axis=0) + 0.05
+    ex = orc.tet_analytic(x, V, om)
+    Ns = (16, 64) if quick else (16, 32, 64, 128)
+    out["ray"] = [_rel(orc.velocity(V, tets, om, x[None], far_ratio=np.inf, n_theta=N, n_phi=N)[0], ex)
+                  for N in Ns]
+    if not quick:
+        # uniform ball, every tet exact: the error left is the polyhedral one, O(h^2)
+        errs, hs = [], []
+        for n in (5, 9, 17):
+            b = ball_mesh(n, lambda X: np.tile(BALL_OMEGA, (len(X), 1)))
+            X = _ball_points(b, 8, 0.55)
+            v = orc.velocity(b.nodes, b.tets, b.omega, X, far_ratio=np.inf, near_rule=1)
+            exact = np.cross(BALL_OMEGA, X) / 3.0
+            errs.append(float(np.sqrt(np.mean(np.sum((v - exact) ** 2, axis=1))) / np.abs(BALL_OMEGA).max()))
+            hs.append(2.0 / (n - 1))
+        out["ball"] = errs
+        out["ball_slope"] = float(np.polyfit(np.log(hs), np.log(errs), 1)[0])
     return out

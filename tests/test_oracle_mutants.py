@@ -48,6 +48,11 @@ MUTANTS = {
                                              "const double dR = dot3(n, ed) / dot3(n, s);"),
     "derivative: signed chord length": ("dJ[j] = (fabs(R1) - fabs(R0)) * gw[j];", "dJ[j] = (R1 - R0) * gw[j];"),
     "derivative: vorticity gradient index": ("gw[j] += om[3 * i + j] * ge;", "gw[j] += om[3 * ((i + 1) % 4) + j] * ge;"),
+    "analytic: curl term dropped": ("vel[j] = c * (S[j] - curl[j] * volint);", "vel[j] = c * S[j];"),
+    "analytic: arc tangent term sign": ("I0 += P0 * f - ah * beta;", "I0 += P0 * f + ah * beta;"),
+    "analytic: normal part of the face moment": ("q[j] = Ip[j] + h * n[j] * I0;", "q[j] = Ip[j];"),
+    "analytic: edge logarithm reversed": ("f = log((Rm - lm) / (Rp - lp));", "f = log((Rp - lp) / (Rm - lm));"),
+    "analytic: volume integral factor": ("volint += 0.5 * h * I0;", "volint += h * I0;"),
 }
 
 
@@ -107,6 +112,10 @@ def battery(orc):
     d = pins.dderiv(orc, count=10)
     if d["points"] > 1e-4 or d["nodes"] > 2e-3 or d["ball"] > 2.5e-2:
         failed.append("derivative")
+    # exact single-tet integral against the Duffy-cone integral, additivity, divergence
+    a = pins.analytic(orc, quick=True)
+    if max(a["single"].values()) > 5e-12 or a["split"] > 1e-12 or a["div"] > 5e-6:
+        failed.append("analytic")
     return failed
 
 
