@@ -470,16 +470,72 @@ def hill_workload(args):
     return 0
 
 
+def exact_workload(args):
+    """The exact near-field rule (the analytic evaluation Section 1 sets the ray rule against) on the 64^3
+    Fourier mesh: the hybrid method with ray-rule near pairs (the default) and with exact near pairs, both
+    FP32 at all nodes; the extra time per near pair, and the ray rule's error against the exact field on the
+    4096 seeded sample nodes (FP64)."""
+    import torch
+
+    import paper_0712_1695_gb300 as bs
+
+    bs.load()
+    mesh = config3_fourier()
+    h = bs.Mesh(mesh.nodes, mesh.tets, mesh.omega)
+    pts = torch.from_numpy(mesh.nodes).cuda()
+    out = torch.empty_like(pts)
+    cnt = torch.zeros((mesh.n_nodes, 3), dtype=torch.int32, device="cuda")
+    res = {}
+    with ClockSampler(0) as clk:
+        for name, rule in (("ray", bs.BS_NEAR_RAY), ("exact", bs.BS_NEAR_EXACT)):
+            P = dict(PARAMS, precision=bs.BS_FP32, near_rule=rule)
+            h.bs_velocity(pts, out_dev=out, counts_dev=cnt, **P)
+            h.bs_status()
+            n_near = int(cnt[:, 0].to(torch.int64).sum())
+            for _ in range(max(1, args.warmup - 1)):
+                h.bs_velocity(pts, out_dev=out, **P)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                h.bs_velocity(pts, out_dev=out, **P)
+            e1.record()
+            torch.cuda.synchronize()
+            h.bs_status()
+            res[name] = {"ms": e0.elapsed_time(e1) / args.steps, "near_pairs": n_near}
+    idx = config3_samples(mesh.n_nodes, 4096)
+    ps = torch.from_numpy(np.ascontiguousarray(mesh.nodes[idx])).cuda()
+    v = {}
+    for name, rule in (("ray", bs.BS_NEAR_RAY), ("exact", bs.BS_NEAR_EXACT)):
+        v[name] = h.bs_velocity(ps, precision=bs.BS_FP64, **dict(PARAMS, near_rule=rule)).cpu().numpy()
+    h.bs_status()
+    pairs = mesh.n_nodes * mesh.n_tets
+    extra = res["exact"]["ms"] - res["ray"]["ms"]
+    line = {"metric": "velocity at all nodes with exact near pairs (the analytic near field), FP32 far field",
+            "value": pairs / (res["exact"]["ms"] * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["exact"]["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": dict(workload_config(), near_rule="exact"),
+            "ray_near_rule": res["ray"], "exact_near_rule": res["exact"],
+            "exact_extra_ns_per_near_pair": extra * 1e6 / max(res["exact"]["near_pairs"], 1),
+            "ray_vs_exact_fp64": {"rel_l2": rel_l2(v["ray"], v["exact"]),
+                                  "rms_over_max": rms_over_max(v["ray"], v["exact"])},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="fourier64", choices=["fourier64", "batch", "rings", "allray", "hill"],
+    ap.add_argument("--workload", default="fourier64",
+                    choices=["fourier64", "batch", "rings", "allray", "hill", "exact"],
                     help="fourier64: the headline workload; batch: 256 uneven meshes, batched vs separate "
                          "launches; rings: Heun steps of two colliding rings; allray: the ray rule for every "
-                         "pair on the 32^3 ring mesh; hill: the paper's Table 1 experiment (Hill's vortex, all-ray)")
+                         "pair on the 32^3 ring mesh; hill: the paper's Table 1 experiment (Hill's vortex, all-ray); "
+                         "exact: the exact near-field rule against the ray rule on the 64^3 mesh")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
     ap.add_argument("--rings-mode", default="hybrid", choices=["hybrid", "allray-stretch"],
                     help="rings workload: the far/near rule with frozen vorticity, or the all-ray method with vortex "
@@ -515,6 +571,8 @@ def main():
         return allray_workload(args)
     if args.workload == "hill":
         return hill_workload(args)
+    if args.workload == "exact":
+        return exact_workload(args)
 
     import torch
 

@@ -54,6 +54,13 @@ extern "C" {
                   /* pairs whose point sits on a vertex, edge or face of the tet run  */
                   /* in float64; the final per-point sum is float64                   */
 
+#define BS_NEAR_RAY 0   /* near tets by the ray rule of Section 2 (the paper's method)      */
+#define BS_NEAR_EXACT 1 /* near tets by the exact integral of Eq. 1 over the tet (the       */
+                        /* analytic near-field evaluation Section 1 compares against:       */
+                        /* face and edge integrals in closed form, 6 logarithms and 12      */
+                        /* atan2 per tet), in float64 under both precisions; no ray hits    */
+                        /* are counted                                                      */
+
 typedef struct bs_ctx *bs_handle;
 typedef struct bs_batch_ctx *bs_batch;
 
@@ -69,6 +76,7 @@ typedef struct {
     int32_t *counts;     /* optional device [k][3] int32 output: near tets, far tets,
                             ray hits (line-tet pairs with chord > 1e-9 * longest edge);
                             NULL to skip                                             */
+    int near_rule;       /* BS_NEAR_RAY (0) or BS_NEAR_EXACT (1)                      */
 } bs_params;
 
 /* Upload a mesh and precompute its per-tet tables (Section 2.2 steps 2-3 and

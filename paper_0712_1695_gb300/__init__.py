@@ -6,6 +6,8 @@ include/bs.h); ``binding`` is the Python view of that ABI.
 from .binding import (  # noqa: F401
     BS_FP32,
     BS_FP64,
+    BS_NEAR_EXACT,
+    BS_NEAR_RAY,
     INF,
     Batch,
     BSError,

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libbs.so")
 
 BS_OK, BS_ERR_ARG, BS_ERR_MESH, BS_ERR_ORDER, BS_ERR_CUDA, BS_ERR_TIMEOUT = range(6)
 BS_FP64, BS_FP32 = 0, 1
+BS_NEAR_RAY, BS_NEAR_EXACT = 0, 1
 EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_status", "bs_destroy",
             "bs_mesh_size", "bs_last_error", "bs_direction_table", "bs_tet_rule", "bs_batch_create",
             "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read",
@@ -34,7 +35,8 @@ class BSError(RuntimeError):
 
 class bs_params(ctypes.Structure):
     _fields_ = [("far_ratio", ctypes.c_double), ("tet_gauss_order", ctypes.c_int), ("n_theta", ctypes.c_int),
-                ("n_phi", ctypes.c_int), ("precision", ctypes.c_int), ("counts", ctypes.c_void_p)]
+                ("n_phi", ctypes.c_int), ("precision", ctypes.c_int), ("counts", ctypes.c_void_p),
+                ("near_rule", ctypes.c_int)]
 
 
 _lib = None
@@ -98,8 +100,10 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def make_params(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16, precision=BS_FP64, counts=None):
+def make_params(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16, precision=BS_FP64, counts=None,
+                near_rule=0):
     p = bs_params()
+    p.near_rule = int(near_rule)
     p.far_ratio = float(far_ratio)
     p.tet_gauss_order = int(tet_gauss_order)
     p.n_theta = int(n_theta)

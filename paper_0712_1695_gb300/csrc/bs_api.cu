@@ -51,6 +51,8 @@ int check_params(const bs_params *p)
         return fail(BS_ERR_ARG, "n_theta and n_phi must be in 1..256");
     if (p->precision != BS_FP32 && p->precision != BS_FP64) return fail(BS_ERR_ARG, "precision must be BS_FP64 or BS_FP32");
     if (!valid_order(p->tet_gauss_order)) return fail(BS_ERR_ORDER, "tet_gauss_order must be 1, 4, 8, 27 or 64");
+    if (p->near_rule != BS_NEAR_RAY && p->near_rule != BS_NEAR_EXACT)
+        return fail(BS_ERR_ARG, "near_rule must be BS_NEAR_RAY or BS_NEAR_EXACT");
     return BS_OK;
 }
 
@@ -99,6 +101,7 @@ struct bs_ctx {
     double *rk = nullptr;
     double *rk_w = nullptr;
     int occ[2][65][kMaxVariants] = {};  // cached CTAs per SM by [precision][Q][variant]
+    int occ_exact[2][65] = {};          // the same for the exact near rule (variant 0)
     int ray_occ[2] = {};                // cached CTAs per SM of the all-ray kernel by [precision]
     int ray_occ_L[2] = {};              // ... for this many directions
     int variant[2][65] = {};  // chosen kernel variant by [precision][Q] (bs_autotune, or BS_VARIANT)
@@ -484,7 +487,8 @@ int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *d
     if (!out_dev) return fail(BS_ERR_ARG, "NULL output");
     const int L = p->n_phi * p->n_theta;
     const char *env = getenv("BS_WALK");
-    const bool walk = isinf(p->far_ratio) && L <= kRayLinesSmemMax && h->n_tets > 0 && !(env && atoi(env) == 0);
+    const bool walk = isinf(p->far_ratio) && L <= kRayLinesSmemMax && h->n_tets > 0 && !(env && atoi(env) == 0) &&
+                      p->near_rule == BS_NEAR_RAY;
     if (dout && !walk)
         return fail(BS_ERR_ARG, "the derivative along directions is the all-ray method's (far_ratio = +inf, at most "
                                 "4096 directions) computed by the mesh walk");
@@ -628,12 +632,13 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     // direction windows, the direction table in shared memory: up to kRayLinesSmemMax lines);
     // BS_ALLRAY_GENERIC=1 keeps such calls on the velocity kernel
     const char *generic_env = getenv("BS_ALLRAY_GENERIC");
-    const bool ray = isinf(p->far_ratio) && L <= kRayLinesSmemMax && !(generic_env && atoi(generic_env) != 0);
+    const bool ray = isinf(p->far_ratio) && L <= kRayLinesSmemMax && !(generic_env && atoi(generic_env) != 0) &&
+                     p->near_rule == BS_NEAR_RAY;
     if (!ray) BS_CUDA(ensure_far(h, Q, st));
 
     int variant = h->variant[p->precision][Q];
     if (const char *env = getenv("BS_VARIANT")) variant = atoi(env);
-    if (variant < 0 || variant >= num_variants(p->precision, Q)) variant = 0;
+    if (variant < 0 || variant >= num_variants(p->precision, Q) || p->near_rule == BS_NEAR_EXACT) variant = 0;
     const LaunchShape shape = ray ? ray_shape() : shape_for(p->precision, Q, variant);
     int occ_ray = 0;
     if (ray) {
@@ -643,8 +648,9 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
         }
         occ_ray = h->ray_occ[p->precision];
     }
-    int &occ = ray ? occ_ray : h->occ[p->precision][Q][variant];
-    if (occ == 0) occ = std::max(1, velocity_ctas_per_sm(p->precision, Q, variant));
+    int &occ = ray ? occ_ray
+                   : (p->near_rule == BS_NEAR_EXACT ? h->occ_exact[p->precision][Q] : h->occ[p->precision][Q][variant]);
+    if (occ == 0) occ = std::max(1, velocity_ctas_per_sm(p->precision, Q, variant, p->near_rule));
     const int64_t BP = (int64_t)shape.threads * shape.points_per_thread;
     const int64_t n_blocks = (k + BP - 1) / BP;
     const int64_t n_tiles = (h->n_tets + shape.tile - 1) / shape.tile;
@@ -684,6 +690,7 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     a.m.partial = h->partial;
     a.variant = variant;
     a.skip = skip;
+    a.near_rule = p->near_rule;
     a.n_items = n_blocks * n_chunks;
     int grid = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -894,10 +901,10 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     // decomposition: items of roughly equal work over all meshes
     int variant = b->meshes[0]->variant[prec][Q];
     if (const char *env = getenv("BS_VARIANT")) variant = atoi(env);
-    if (variant < 0 || variant >= num_variants(prec, Q)) variant = 0;
+    if (variant < 0 || variant >= num_variants(prec, Q) || p->near_rule == BS_NEAR_EXACT) variant = 0;
     const LaunchShape shape = shape_for(prec, Q, variant);
-    int &occ = b->meshes[0]->occ[prec][Q][variant];
-    if (occ == 0) occ = std::max(1, velocity_ctas_per_sm(prec, Q, variant));
+    int &occ = p->near_rule == BS_NEAR_EXACT ? b->meshes[0]->occ_exact[prec][Q] : b->meshes[0]->occ[prec][Q][variant];
+    if (occ == 0) occ = std::max(1, velocity_ctas_per_sm(prec, Q, variant, p->near_rule));
     const int64_t BP = (int64_t)shape.threads * shape.points_per_thread;
     double total_pairs = 0.0;
     for (int i = 0; i < n; ++i) total_pairs += (double)b->meshes[i]->n_nodes * b->meshes[i]->n_tets;
@@ -965,6 +972,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     a.flag = b->flag;
     a.work_counter = b->work_counter;
     a.variant = variant;
+    a.near_rule = p->near_rule;
     if (items == 0) {  // every mesh is empty: the reduction alone writes the zeros
         BS_CUDA(launch_reduce(a, st));
         return BS_OK;

@@ -147,6 +147,7 @@ struct VelocityArgs {
     int *work_counter = nullptr;  // device int, zeroed by launch_velocity
     int variant = 0;  // kernel variant (points per thread / registers) for this precision and rule
     const int *skip = nullptr;  // device flag: when set, the all-ray and reduce kernels return at once
+    int near_rule = 0;          // BS_NEAR_RAY or BS_NEAR_EXACT
 };
 
 constexpr int64_t kMinTilesPerItem = 2;  // work items shorter than this are dominated by their set-up
@@ -163,7 +164,7 @@ struct LaunchShape {
 constexpr int kMaxVariants = 16;  // num_variants() never exceeds this
 int num_variants(int precision, int Q);
 LaunchShape shape_for(int precision, int Q, int variant = 0);
-int velocity_ctas_per_sm(int precision, int Q, int variant = 0);
+int velocity_ctas_per_sm(int precision, int Q, int variant = 0, int near_rule = 0);
 // ev_start/ev_stop (optional) are recorded around the velocity kernel alone
 cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
                             cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);

@@ -97,6 +97,8 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
         return fail(BS_ERR_ARG, "bs_velocity_noalloc: n_theta * n_phi above 4096 (fixed scratch limit)");
     if (p->precision != BS_FP32 && p->precision != BS_FP64)
         return fail(BS_ERR_ARG, "bs_velocity_noalloc: precision must be BS_FP64 or BS_FP32");
+    if (p->near_rule != BS_NEAR_RAY && p->near_rule != BS_NEAR_EXACT)
+        return fail(BS_ERR_ARG, "bs_velocity_noalloc: near_rule must be BS_NEAR_RAY or BS_NEAR_EXACT");
     if (p->tet_gauss_order != 1 && p->tet_gauss_order != 4)
         return fail(BS_ERR_ORDER, "bs_velocity_noalloc: tet_gauss_order must be 1 or 4 (fixed scratch limit)");
     if (k == 0) return BS_OK;
@@ -174,7 +176,7 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
         return cuda_fail(e, "direction table");
 
     // decomposition, as in bs_velocity but with at most kMaxChunks chunks
-    const int occ = std::max(1, velocity_ctas_per_sm(p->precision, Q, 0));
+    const int occ = std::max(1, velocity_ctas_per_sm(p->precision, Q, 0, p->near_rule));
     const int64_t BP = (int64_t)shape.threads * shape.points_per_thread;
     const int64_t n_blocks = (k + BP - 1) / BP;
     const int64_t n_tiles = (n_tets + shape.tile - 1) / shape.tile;
@@ -216,6 +218,7 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
     a.m.tiles_per_chunk = (int)per;
     a.m.partial = reinterpret_cast<double *>(base + kPartial);
     a.variant = 0;
+    a.near_rule = p->near_rule;
     a.n_items = n_blocks * n_chunks;
     int grid = 0;
     if ((e = launch_velocity(p->precision, a, n_sm, st, &grid)) != cudaSuccess) return cuda_fail(e, "velocity");

@@ -32,6 +32,7 @@
 #include <type_traits>
 
 #include "bs_internal.cuh"
+#include "bs_exact.cuh"
 #include "bs_near.cuh"
 
 namespace bs {
@@ -323,7 +324,40 @@ struct Pipe {
 // slots w*32*P + p*32 + l.  A warp therefore covers a compact patch of
 // points, and a tile whose tets are all far from that patch skips the
 // per-pair near/far test (culled=true below).
-template <typename T, int Q, int P, int NT, int TILE, int S, int MINB, bool INL>
+// The near pairs of a warp's queue, 32 at a time over the lanes: round r gives lane i the (32 r + i)-th
+// pair in queue order (entry e, the k-th set lane of its mask).  (e0, k0) is the round's first pair.
+struct PairCursor {
+    int e0 = 0, k0 = 0;
+};
+// This lane's pair of the round: its entry and the point lane it belongs to (false past the last pair).
+__device__ __forceinline__ bool cursor_pair(const PairCursor &c, const uint32_t *wm, int qn, int lane, int &e,
+                                            int &owner)
+{
+    e = c.e0;
+    int k = c.k0 + lane;
+    while (e < qn && k >= __popc(wm[e])) {
+        k -= __popc(wm[e]);
+        ++e;
+    }
+    if (e >= qn) return false;
+    unsigned m = wm[e];
+    for (int i = 0; i < k; ++i) m &= m - 1u;
+    owner = __ffs(m) - 1;
+    return true;
+}
+__device__ __forceinline__ void cursor_advance(PairCursor &c, const uint32_t *wm, int qn)
+{
+    int k = c.k0 + 32;
+    while (c.e0 < qn && k >= __popc(wm[c.e0])) {
+        k -= __popc(wm[c.e0]);
+        ++c.e0;
+    }
+    c.k0 = k;
+}
+
+// EXACT: near pairs take the exact integral (tet_exact_f64, float64) instead of the ray rule, the
+// warp's pairs spread over all 32 lanes and each result handed to the lane that owns its point.
+template <typename T, int Q, int P, int NT, int TILE, int S, int MINB, bool INL, bool EXACT>
 __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a)
 {
     constexpr int RS = far_stride<T>(Q);
@@ -624,7 +658,37 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                 }
                 // near pairs of the tile: the warp takes them one at a time; each tet's near record is
                 // staged once (one coalesced load into this warp's shared slot, read by broadcast)
-                if (qn > 0) {
+                if (EXACT && qn > 0) {
+                    __syncwarp();
+                    PairCursor cur;
+#pragma unroll 1
+                    while (cur.e0 < qn) {
+                        int e = 0, owner = 0, tag = 0;
+                        float ox = 0.f, oy = 0.f, oz = 0.f;
+                        if (cursor_pair(cur, wm, qn, lane, e, owner)) {
+                            const int code = wc[e];
+                            const int pp = code >> 8, j = code & 255;
+                            const float *sp = spts + 9 * (warp * 32 * P + pp * 32 + owner);
+                            const V3<double> xd = mk(join3(sp[0], sp[1], sp[2]), join3(sp[3], sp[4], sp[5]),
+                                                     join3(sp[6], sp[7], sp[8]));
+                            const Vel64 o = tet_exact_f64(xd, md.near64 + (t * TILE + j) * kNearF64);
+                            ox = (float)o.x;
+                            oy = (float)o.y;
+                            oz = (float)o.z;
+                            tag = 1 | (pp << 1) | (owner << 8);
+                        }
+                        cursor_advance(cur, wm, qn);
+#pragma unroll 1
+                        for (int src = 0; src < 32; ++src) {
+                            const int tg = __shfl_sync(0xffffffffu, tag, src);
+                            const float sx = __shfl_sync(0xffffffffu, ox, src);
+                            const float sy = __shfl_sync(0xffffffffu, oy, src);
+                            const float sz = __shfl_sync(0xffffffffu, oz, src);
+                            if ((tg & 1) && (tg >> 8) == lane) kahan(warp * 32 * P + ((tg >> 1) & 127) * 32 + lane, sx, sy, sz);
+                        }
+                    }
+                    __syncwarp();
+                } else if (qn > 0) {
                     __syncwarp();
                     int held = -1;
 #pragma unroll 1
@@ -711,7 +775,43 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                     }
                 }
                 release();
-                if (qn > 0) {
+                if (EXACT && qn > 0) {
+                    __syncwarp();
+                    PairCursor cur;
+#pragma unroll 1
+                    while (cur.e0 < qn) {
+                        int e = 0, owner = 0, tag = 0;
+                        Vel64 o = {0.0, 0.0, 0.0};
+                        if (cursor_pair(cur, wm, qn, lane, e, owner)) {
+                            const int code = wc[e];
+                            const int pp = code >> 8, j = code & 255;
+                            const float *sp = spts + 9 * (warp * 32 * P + pp * 32 + owner);
+                            const V3<double> xd = mk(join3(sp[0], sp[1], sp[2]), join3(sp[3], sp[4], sp[5]),
+                                                     join3(sp[6], sp[7], sp[8]));
+                            o = tet_exact_f64(xd, md.near64 + (t * TILE + j) * kNearF64);
+                            tag = 1 | (pp << 1) | (owner << 8);
+                        }
+                        cursor_advance(cur, wm, qn);
+#pragma unroll 1
+                        for (int src = 0; src < 32; ++src) {
+                            const int tg = __shfl_sync(0xffffffffu, tag, src);
+                            const double sx = __shfl_sync(0xffffffffu, o.x, src);
+                            const double sy = __shfl_sync(0xffffffffu, o.y, src);
+                            const double sz = __shfl_sync(0xffffffffu, o.z, src);
+                            if ((tg & 1) && (tg >> 8) == lane) {
+                                const int pp = (tg >> 1) & 127;
+#pragma unroll
+                                for (int p = 0; p < P; ++p)
+                                    if (p == pp) {
+                                        tacc[p][0] += sx;
+                                        tacc[p][1] += sy;
+                                        tacc[p][2] += sz;
+                                    }
+                            }
+                        }
+                    }
+                    __syncwarp();
+                } else if (qn > 0) {
                     __syncwarp();
 #pragma unroll 1
                     for (int e = 0; e < qn; ++e) {
@@ -834,10 +934,10 @@ size_t smem_bytes(int lines_in_smem)
            round16(sizeof(float4) * NW);
 }
 
-template <typename T, int Q, int P, int NT, int TILE, int S, int MINB, bool INL>
+template <typename T, int Q, int P, int NT, int TILE, int S, int MINB, bool INL, bool EXACT = false>
 cudaError_t launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out, bool query_only, int *occ_out)
 {
-    auto kern = velocity_kernel<T, Q, P, NT, TILE, S, MINB, INL>;
+    auto kern = velocity_kernel<T, Q, P, NT, TILE, S, MINB, INL, EXACT>;
     const size_t sm = smem_bytes<T, Q, P, NT, TILE, S>(a.smem_lines ? a.L : 0);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -875,6 +975,17 @@ template <typename T>
 cudaError_t dispatch(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out, bool qo, int *occ)
 {
 #define BS_L(Q_, V_) launch_t<T, Q_, V_.P, 128, V_.TILE, V_.S, V_.MINB, V_.INL>(a, n_sm, st, grid_out, qo, occ)
+#define BS_LX(Q_, V_) launch_t<T, Q_, V_.P, 128, V_.TILE, V_.S, V_.MINB, V_.INL, true>(a, n_sm, st, grid_out, qo, occ)
+    if (a.near_rule == BS_NEAR_EXACT) {  // the exact near-field rule: variant 0 of each tet rule
+        switch (a.Q) {
+        case 1: return BS_LX(1, kQ1[0]);
+        case 4: return BS_LX(4, kQ4[0]);
+        case 8: return BS_LX(8, kQ8[0]);
+        case 27: return BS_LX(27, kQ27[0]);
+        case 64: return BS_LX(64, kQ64[0]);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (a.Q) {
     case 1: return BS_L(1, kQ1[0]);
     case 4:
@@ -902,6 +1013,7 @@ cudaError_t dispatch(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
     default: return cudaErrorInvalidValue;
     }
 #undef BS_L
+#undef BS_LX
 }
 
 }  // namespace
@@ -927,11 +1039,12 @@ LaunchShape shape_for(int precision, int Q, int variant)
     return s;
 }
 
-int velocity_ctas_per_sm(int precision, int Q, int variant)
+int velocity_ctas_per_sm(int precision, int Q, int variant, int near_rule)
 {
     VelocityArgs q;
     q.Q = Q;
     q.variant = variant;
+    q.near_rule = near_rule;
     int occ = 0;
     if (precision == BS_FP32)
         dispatch<float>(q, 1, 0, nullptr, true, &occ);

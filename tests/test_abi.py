@@ -41,9 +41,10 @@ def test_every_declared_symbol_is_exported(lib):
 def test_params_struct_layout():
     from paper_0712_1695_gb300.binding import bs_params
 
-    # double far_ratio; int order, n_theta, n_phi, precision; int32_t *counts
-    assert ctypes.sizeof(bs_params) == 32
+    # double far_ratio; int order, n_theta, n_phi, precision; int32_t *counts; int near_rule
+    assert ctypes.sizeof(bs_params) == 40
     assert bs_params.counts.offset == 24
+    assert bs_params.near_rule.offset == 32
 
 
 def test_argument_errors_without_gpu(lib):

@@ -64,6 +64,18 @@ def test_noalloc_matches_bs_velocity_on_two_calls(case, precision):
         assert torch.equal(counts, ref_counts), f"call {call}"
 
 
+def test_noalloc_with_the_exact_near_rule(case):
+    m, d = case
+    h = bs.Mesh(m.nodes, m.tets, m.omega)
+    P = dict(PARAMS, near_rule=bs.BS_NEAR_EXACT)
+    ref = h.bs_velocity(d["pts"], precision=bs.BS_FP64, **P).cpu().numpy()
+    h.bs_status()
+    out = torch.full(tuple(d["pts"].shape), float("nan"), dtype=torch.float64, device="cuda")
+    bs_velocity_noalloc(d["nodes"], d["tets"], d["omega"], d["pts"], out, precision=bs.BS_FP64, **P)
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), ref) <= TOL_FP64_REL_L2
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(case):
     m, d = case
     out = torch.empty_like(d["pts"])
