@@ -12,6 +12,9 @@
  *       x + R s through T and the exact integral of the linear omega along
  *       it (Eq. 5, with the factor sign(R) that Eq. 2 needs when theta
  *       covers [0, pi] only), weighted by k_nm = (pi/16) sin(phi_n) w_n w_m.
+ *       With near_rule = BS_NEAR_EXACT the near tets take instead the exact
+ *       integral of Eq. 1 over the tet (the analytic near-field evaluation
+ *       Section 1 compares the ray rule against).
  *
  * Conventions for every call:
  *   - Arrays are row-major and tightly packed: points/nodes/omega/velocity
@@ -114,9 +117,11 @@ BS_API int bs_velocity_host(bs_handle h, const double *eval_pts_host, int64_t k,
  * neighbours (the tracing through the mesh that the paper's conclusion, §4,
  * proposes): from the node, each half-line crosses the tets it meets one after
  * the other until it leaves the mesh, each tet adding its chord of Eq. 5.
- * The walk is used when the mesh is conforming (a face belongs to at most two
- * tets, every node to some tet); otherwise the call evaluates the nodes as
- * bs_velocity does.  On a convex domain every line leaves the mesh once; on a
+ * The walk is used with the ray near rule (p->near_rule = BS_NEAR_RAY) when
+ * the mesh is conforming (a face belongs to at most two tets, every node to
+ * some tet) and not folded (no two tets sharing a face on the same side of
+ * it, checked on the device after each change of the node positions);
+ * otherwise the call evaluates the nodes as bs_velocity does.  On a convex domain every line leaves the mesh once; on a
  * non-convex one (checked on the device after each change of the node
  * positions: some boundary node outside some boundary face's plane) a line
  * that leaves is followed through a uniform grid of the boundary faces to
@@ -141,9 +146,10 @@ BS_API int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, v
  * leaves the mesh (omega there times the shift of the exit point), computed
  * during the mesh walk.  At a node on the mesh boundary the rule is not
  * differentiable (omega jumps at the node itself); the value returned there
- * leaves out the jump at the node.  Other parameters return BS_ERR_ARG; a mesh
- * the walk cannot serve (not conforming) gets the velocity but no derivative,
- * reported as BS_ERR_MESH by the next bs_status.
+ * leaves out the jump at the node.  Other parameters (including
+ * near_rule = BS_NEAR_EXACT) return BS_ERR_ARG; a mesh the walk cannot serve
+ * (not conforming, or folded) gets the velocity but no derivative, reported as
+ * BS_ERR_MESH by the next bs_status.
  * Asynchronous on `stream` after the first call (see bs_velocity_nodes). */
 BS_API int bs_velocity_nodes_dderiv(bs_handle h, const bs_params *p, const double *dirs_dev, double *out_dev,
                                     double *dout_dev, void *stream);
