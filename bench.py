@@ -524,6 +524,27 @@ def exact_workload(args):
     return 0
 
 
+def peaks_workload(args):
+    """Measured arithmetic rates of this GPU (bs_fma_rate): float64 fma (the float64 path and the exact near
+    rule), float32 fma and packed float32x2 fma (the far sweep), beside the nominal float32 peak the headline's
+    roofline divides by."""
+    import torch
+
+    import paper_0712_1695_gb300 as bs
+
+    bs.load()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    with ClockSampler(0) as clk:
+        rates = {name: max(bs.bs_fma_rate(kind) for _ in range(2))
+                 for name, kind in (("fp64_fma", 0), ("fp32_fma", 1), ("fp32x2_fma", 2))}
+    nominal = n_sm * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
+    line = {"metric": "measured fma-chain rates", "unit": "TFLOP/s", "rates": rates,
+            "fp32_nominal_peak": nominal, "fp32x2_over_nominal": rates["fp32x2_fma"] / nominal,
+            "fp64_over_fp32": rates["fp64_fma"] / rates["fp32_fma"], "n_sm": n_sm, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -531,11 +552,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fourier64",
-                    choices=["fourier64", "batch", "rings", "allray", "hill", "exact"],
+                    choices=["fourier64", "batch", "rings", "allray", "hill", "exact", "peaks"],
                     help="fourier64: the headline workload; batch: 256 uneven meshes, batched vs separate "
                          "launches; rings: Heun steps of two colliding rings; allray: the ray rule for every "
                          "pair on the 32^3 ring mesh; hill: the paper's Table 1 experiment (Hill's vortex, all-ray); "
-                         "exact: the exact near-field rule against the ray rule on the 64^3 mesh")
+                         "exact: the exact near-field rule against the ray rule on the 64^3 mesh; peaks: measured fma rates")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
     ap.add_argument("--rings-mode", default="hybrid", choices=["hybrid", "allray-stretch"],
                     help="rings workload: the far/near rule with frozen vorticity, or the all-ray method with vortex "
@@ -573,6 +594,8 @@ def main():
         return hill_workload(args)
     if args.workload == "exact":
         return exact_workload(args)
+    if args.workload == "peaks":
+        return peaks_workload(args)
 
     import torch
 

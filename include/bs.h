@@ -237,6 +237,15 @@ BS_API const char *bs_last_error(void);
  * line index l = n*n_theta + m;  tet rule barycentric points [order][4] and
  * weights [order] (fractions of |V|). */
 BS_API int bs_direction_table(int n_phi, int n_theta, double *s_host, double *k_host);
+
+/* Measured rate of the arithmetic pipe a precision runs on, in TFLOP/s (two
+ * flops per lane fused multiply-add): independent chains of fma over 8 CTAs of
+ * 256 threads per SM of the current device, timed with CUDA events (the
+ * second of two launches of about 5-20 ms).  kind 0: float64 fma (the float64
+ * path and the exact near rule), 1: float32 fma, 2: packed float32x2 fma (the
+ * far sweep).  Synchronous; allocates and frees a scratch buffer of 2 KB per
+ * CTA.  Errors: BS_ERR_ARG, BS_ERR_CUDA. */
+BS_API int bs_fma_rate(int kind, double *tflops, void *stream);
 BS_API int bs_tet_rule(int order, double *bary_host, double *w_host);
 
 /* Many meshes in one persistent launch (evaluation points = each mesh's own

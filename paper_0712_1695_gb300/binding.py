@@ -24,7 +24,7 @@ EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_sta
             "bs_mesh_size", "bs_last_error", "bs_direction_table", "bs_tet_rule", "bs_batch_create",
             "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read",
             "bs_velocity_noalloc", "bs_tuned_variant", "bs_rk2_step", "bs_nodes", "bs_velocity_nodes",
-            "bs_velocity_nodes_dderiv", "bs_rk2_step_stretch", "bs_omega")
+            "bs_velocity_nodes_dderiv", "bs_rk2_step_stretch", "bs_omega", "bs_fma_rate")
 
 
 class BSError(RuntimeError):
@@ -66,6 +66,7 @@ def load(path: str = LIB_PATH):
         lib.bs_last_error.restype = ctypes.c_char_p
         lib.bs_direction_table.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
         lib.bs_tet_rule.argtypes = [ctypes.c_int, _D, _D]
+        lib.bs_fma_rate.argtypes = [ctypes.c_int, _D, _P]
         lib.bs_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]
         lib.bs_batch_velocity.argtypes = [_P, ctypes.POINTER(bs_params), ctypes.POINTER(_P), _P]
         lib.bs_batch_destroy.argtypes = [_P]
@@ -275,6 +276,13 @@ def _require_dev(t, shape):
 
 def bs_create(nodes, tets, omega) -> Mesh:
     return Mesh(nodes, tets, omega)
+
+
+def bs_fma_rate(kind: int, stream=None) -> float:
+    """Measured TFLOP/s of fma chains: kind 0 float64, 1 float32, 2 packed float32x2."""
+    r = ctypes.c_double()
+    _check(load().bs_fma_rate(int(kind), ctypes.byref(r), _stream_ptr(stream)))
+    return r.value
 
 
 def bs_direction_table(n_phi: int, n_theta: int):

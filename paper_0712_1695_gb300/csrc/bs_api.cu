@@ -752,6 +752,17 @@ int bs_destroy(bs_handle h)
     return BS_OK;
 }
 
+int bs_fma_rate(int kind, double *tflops, void *stream)
+{
+    if (kind < 0 || kind > 2) return fail(BS_ERR_ARG, "kind must be 0 (float64), 1 (float32) or 2 (float32x2)");
+    if (!tflops) return fail(BS_ERR_ARG, "NULL output");
+    int dev = 0, n_sm = 0;
+    BS_CUDA(cudaGetDevice(&dev));
+    BS_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    BS_CUDA(measure_fma_rate(kind, n_sm, (cudaStream_t)stream, tflops));
+    return BS_OK;
+}
+
 int bs_direction_table(int n_phi, int n_theta, double *s_host, double *k_host)
 {
     if (n_phi < 1 || n_phi > 256 || n_theta < 1 || n_theta > 256) return fail(BS_ERR_ARG, "n_phi/n_theta out of 1..256");

@@ -169,6 +169,8 @@ int velocity_ctas_per_sm(int precision, int Q, int variant = 0, int near_rule = 
 cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
                             cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);
 cudaError_t launch_reduce(const VelocityArgs &a, cudaStream_t st);
+// chains of fused multiply-adds (kind 0 float64, 1 float32, 2 float32x2) over 8 CTAs per SM: TFLOP/s
+cudaError_t measure_fma_rate(int kind, int n_sm, cudaStream_t st, double *tflops);
 // all-ray kernel (bs_ray.cu): one point per thread, near records streamed in tiles of ray_shape().tile;
 // single-mesh launches (a.meshes == nullptr); the partial sums and the reduction are those of the
 // velocity kernel.  The float32 direction table is staged in shared memory: the host uses this kernel
