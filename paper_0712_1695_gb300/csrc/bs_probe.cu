@@ -1,5 +1,7 @@
 // Throughput of the arithmetic pipes the velocity kernels run on: chains of dependent fused multiply-adds,
-// several independent chains per thread, a grid of 8 CTAs of 256 threads per SM.  The float32 rate bounds
+// several independent chains per thread, a grid of 8 CTAs of 256 threads per SM.  The iteration loop is
+// unrolled by 4 so that its counter and branch take few issue slots (a plain float32 fma issues one
+// instruction per lane operation, so every other instruction shows in the rate).  The float32 rate bounds
 // the far sweep (FMA pipe), the float64 rate the float64 path and the exact near rule.
 #include <cuda_runtime.h>
 
@@ -16,7 +18,7 @@ __global__ void __launch_bounds__(kProbeThreads) fma_f64_kernel(double *out, int
     double a[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) a[j] = 1e-3 * (threadIdx.x + j);
-#pragma unroll 1
+#pragma unroll 4
     for (int i = 0; i < iters; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) a[j] = fma(a[j], 0.9999999, 1e-9);
@@ -31,7 +33,7 @@ __global__ void __launch_bounds__(kProbeThreads) fma_f32_kernel(double *out, int
     float a[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) a[j] = 1e-3f * (threadIdx.x + j);
-#pragma unroll 1
+#pragma unroll 4
     for (int i = 0; i < iters; ++i)
 #pragma unroll
         for (int j = 0; j < 16; ++j) a[j] = fmaf(a[j], 0.9999999f, 1e-9f);
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(kProbeThreads) fma_f32x2_kernel(double *out, i
     const float m0 = 0.9999999f, c0 = 1e-9f;
     asm("mov.b64 %0, {%1, %1};" : "=l"(m) : "f"(m0));
     asm("mov.b64 %0, {%1, %1};" : "=l"(c) : "f"(c0));
-#pragma unroll 1
+#pragma unroll 4
     for (int i = 0; i < iters; ++i)
 #pragma unroll
         for (int j = 0; j < 8; ++j) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(a[j]) : "l"(m), "l"(c));
