@@ -29,7 +29,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import ball_mesh, config2_ring, config3_fourier, config3_samples, config4_batch, config5_rings  # noqa: E402
+from workloads import (  # noqa: E402
+    ball_mesh, config1_plain, config2_ring, config3_fourier, config3_samples, config4_batch, config5_rings)
 
 PARAMS = dict(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16)
 METRIC = "node-tet interactions/s (velocity at all nodes, FP32 path)"
@@ -524,6 +525,52 @@ def exact_workload(args):
     return 0
 
 
+def steps_workload(args):
+    """The stage driver on small meshes, where launches dominate: time per Heun step (FP32, far/near rule) of
+    bs_rk2_step called per step against bs_rk2_steps (one captured CUDA graph replayed), on the 9^3 plain cube
+    and a 16^3 two-ring grid; and the all-ray step with stretching on the plain cube."""
+    import torch
+
+    import paper_0712_1695_gb300 as bs
+
+    bs.load()
+    n = max(args.steps, 20)
+    rows = []
+    cases = [("plain cube 9^3 (729 nodes, 3072 tets), far/near", config1_plain(), dict(PARAMS), False),
+             ("two rings 16^3 (4096 nodes, 20250 tets), far/near", config5_rings(n=16), dict(PARAMS), False),
+             ("plain cube 9^3, all-ray with stretching (4x8 directions)", config1_plain(),
+              dict(far_ratio=float("inf"), tet_gauss_order=4, n_theta=4, n_phi=8), True)]
+    with ClockSampler(0) as clk:
+        for name, m, P, stretch in cases:
+            P = dict(P, precision=bs.BS_FP32)
+            res = {}
+            for mode in ("eager", "graph"):
+                h = bs.Mesh(m.nodes, m.tets, m.omega)
+                step = h.bs_rk2_step_stretch if stretch else h.bs_rk2_step
+                for _ in range(3):  # warm-up: connectivity, tables, work arrays
+                    step(0.001, **P)
+                h.bs_status()
+                t0 = time.perf_counter()
+                if mode == "eager":
+                    for _ in range(n):
+                        step(0.001, **P)
+                else:
+                    h.bs_rk2_steps(0.001, n, stretch=stretch, **P)
+                torch.cuda.synchronize()
+                res[mode] = 1e3 * (time.perf_counter() - t0) / n
+                h.bs_status()
+                if mode == "graph":
+                    res["graph_steps"] = h.bs_graph_steps()
+            rows.append({"case": name, "steps": n, "eager_ms_per_step": res["eager"],
+                         "graph_ms_per_step": res["graph"], "speedup": res["eager"] / res["graph"],
+                         "graph_replays": res["graph_steps"]})
+    line = {"metric": "Heun step time on small meshes, per-step calls vs one replayed CUDA graph", "unit": "ms",
+            "higher_is_better": False, "rows": rows, "clocks": clk.summary(),
+            "note": "wall clock over the steps after the device work is done (the host enqueue cost included)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def peaks_workload(args):
     """Measured arithmetic rates of this GPU (bs_fma_rate): float64 fma (the float64 path and the exact near
     rule), float32 fma and packed float32x2 fma (the far sweep), beside the nominal float32 peak the headline's
@@ -552,11 +599,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fourier64",
-                    choices=["fourier64", "batch", "rings", "allray", "hill", "exact", "peaks"],
+                    choices=["fourier64", "batch", "rings", "allray", "hill", "exact", "peaks", "steps"],
                     help="fourier64: the headline workload; batch: 256 uneven meshes, batched vs separate "
                          "launches; rings: Heun steps of two colliding rings; allray: the ray rule for every "
                          "pair on the 32^3 ring mesh; hill: the paper's Table 1 experiment (Hill's vortex, all-ray); "
-                         "exact: the exact near-field rule against the ray rule on the 64^3 mesh; peaks: measured fma rates")
+                         "exact: the exact near-field rule against the ray rule on the 64^3 mesh; peaks: measured fma rates; "
+                         "steps: Heun steps on small meshes, per-step calls vs a replayed CUDA graph")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
     ap.add_argument("--rings-mode", default="hybrid", choices=["hybrid", "allray-stretch"],
                     help="rings workload: the far/near rule with frozen vorticity, or the all-ray method with vortex "
@@ -596,6 +644,8 @@ def main():
         return exact_workload(args)
     if args.workload == "peaks":
         return peaks_workload(args)
+    if args.workload == "steps":
+        return steps_workload(args)
 
     import torch
 

@@ -177,6 +177,20 @@ BS_API int bs_rk2_step_stretch(bs_handle h, double dt, const bs_params *p, void 
  * call allocates three [n_nodes][3] work arrays owned by the handle. */
 BS_API int bs_rk2_step(bs_handle h, double dt, const bs_params *p, void *stream);
 
+/* n_steps Heun steps: bs_rk2_step (stretch = 0) or bs_rk2_step_stretch
+ * (stretch = 1) repeated, with the same results bit for bit.  The first step
+ * runs as a plain call; the second is captured as a CUDA graph on a stream of
+ * the handle (joined to `stream` by events) and the graph is launched for the
+ * remaining steps, which removes the host cost of the step's ~25 launches.
+ * The steps run one by one instead when n_steps <= 1, while bs_profile is on,
+ * or when the capture does not succeed.  Asynchronous on `stream`; the first
+ * call creates the handle's stream and two events.  Errors: as bs_rk2_step,
+ * and BS_ERR_ARG for n_steps < 0 or stretch not 0/1. */
+BS_API int bs_rk2_steps(bs_handle h, double dt, int64_t n_steps, int stretch, const bs_params *p, void *stream);
+
+/* Number of steps bs_rk2_steps has run by graph launch on this handle. */
+BS_API int bs_graph_steps(bs_handle h, int64_t *steps);
+
 /* Copy the handle's current node positions to device array nodes_dev [n_nodes][3]. */
 BS_API int bs_nodes(bs_handle h, double *nodes_dev, void *stream);
 

@@ -24,7 +24,8 @@ EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_sta
             "bs_mesh_size", "bs_last_error", "bs_direction_table", "bs_tet_rule", "bs_batch_create",
             "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read",
             "bs_velocity_noalloc", "bs_tuned_variant", "bs_rk2_step", "bs_nodes", "bs_velocity_nodes",
-            "bs_velocity_nodes_dderiv", "bs_rk2_step_stretch", "bs_omega", "bs_fma_rate")
+            "bs_velocity_nodes_dderiv", "bs_rk2_step_stretch", "bs_omega", "bs_fma_rate", "bs_rk2_steps",
+            "bs_graph_steps")
 
 
 class BSError(RuntimeError):
@@ -67,6 +68,8 @@ def load(path: str = LIB_PATH):
         lib.bs_direction_table.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
         lib.bs_tet_rule.argtypes = [ctypes.c_int, _D, _D]
         lib.bs_fma_rate.argtypes = [ctypes.c_int, _D, _P]
+        lib.bs_rk2_steps.argtypes = [_P, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(bs_params), _P]
+        lib.bs_graph_steps.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
         lib.bs_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]
         lib.bs_batch_velocity.argtypes = [_P, ctypes.POINTER(bs_params), ctypes.POINTER(_P), _P]
         lib.bs_batch_destroy.argtypes = [_P]
@@ -234,6 +237,18 @@ class Mesh:
         """One Heun step: the mesh nodes move with the velocity (vorticity carried unchanged)."""
         p = make_params(**params)
         _check(load().bs_rk2_step(self.handle, float(dt), ctypes.byref(p), _stream_ptr(stream)))
+
+    def bs_rk2_steps(self, dt: float, n_steps: int, stretch: bool = False, stream=None, **params):
+        """n_steps Heun steps (with vortex stretching if ``stretch``), replayed as a CUDA graph after the first."""
+        p = make_params(**params)
+        _check(load().bs_rk2_steps(self.handle, float(dt), int(n_steps), int(bool(stretch)), ctypes.byref(p),
+                                   _stream_ptr(stream)))
+
+    def bs_graph_steps(self) -> int:
+        """Steps bs_rk2_steps has run by graph launch on this mesh."""
+        n = ctypes.c_int64()
+        _check(load().bs_graph_steps(self.handle, ctypes.byref(n)))
+        return n.value
 
     def bs_nodes(self, out_dev=None, stream=None):
         """Current node positions as a float64 [n_nodes, 3] CUDA tensor."""

@@ -115,6 +115,11 @@ struct bs_ctx {
     float4 *walk_rec = nullptr;    // float32 walk records [n_tets][kWalkRecVec4]
     WalkGridArrays walk_grid;      // boundary faces on a uniform grid (re-entries into a non-convex mesh)
     uint64_t walk_version = 0;     // mesh version when walk_mode was computed
+    // bs_rk2_steps: a stream of the handle on which steps are captured and replayed as a CUDA graph, and
+    // the events that join it to the caller's stream
+    cudaStream_t step_stream = nullptr;
+    cudaEvent_t step_in = nullptr, step_out = nullptr;
+    int64_t graph_steps = 0;  // steps run by graph replay since the handle was created
     // kernel timing (bs_profile)
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
@@ -132,6 +137,9 @@ void drop_events(bs_ctx *h)
 void free_ctx(bs_ctx *h)
 {
     drop_events(h);
+    if (h->step_in) cudaEventDestroy(h->step_in);
+    if (h->step_out) cudaEventDestroy(h->step_out);
+    if (h->step_stream) cudaStreamDestroy(h->step_stream);
     for (auto &p : h->ev_free) {
         cudaEventDestroy(p.first);
         cudaEventDestroy(p.second);
@@ -605,6 +613,62 @@ int bs_rk2_step_stretch(bs_handle h, double dt, const bs_params *p, void *stream
     BS_CUDA(launch_heun(w0, s0, s1, dt, nv, h->omega, st));
     if ((rc = bs_update(h, nullptr, nullptr, stream))) return rc;
     if (h->prof) h->prof_all += 4;
+    return BS_OK;
+}
+
+int bs_rk2_steps(bs_handle h, double dt, int64_t n_steps, int stretch, const bs_params *p, void *stream)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    if (n_steps < 0) return fail(BS_ERR_ARG, "bs_rk2_steps: n_steps < 0");
+    if (stretch != 0 && stretch != 1) return fail(BS_ERR_ARG, "bs_rk2_steps: stretch must be 0 or 1");
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (n_steps == 0) return BS_OK;
+    auto step = [&](void *s) { return stretch ? bs_rk2_step_stretch(h, dt, p, s) : bs_rk2_step(h, dt, p, s); };
+    // the first step runs as it is: it allocates the work arrays and builds what the later steps reuse
+    if ((rc = step(stream))) return rc;
+    int64_t done = 1;
+    if (n_steps > 1 && !h->prof) {  // under bs_profile every launch is counted, so the steps run one by one
+        cudaStream_t caller = (cudaStream_t)stream;
+        if (!h->step_stream) {
+            BS_CUDA(cudaStreamCreateWithFlags(&h->step_stream, cudaStreamNonBlocking));
+            BS_CUDA(cudaEventCreateWithFlags(&h->step_in, cudaEventDisableTiming));
+            BS_CUDA(cudaEventCreateWithFlags(&h->step_out, cudaEventDisableTiming));
+        }
+        cudaStream_t ss = h->step_stream;
+        BS_CUDA(cudaEventRecord(h->step_in, caller));
+        BS_CUDA(cudaStreamWaitEvent(ss, h->step_in, 0));
+        // capture one step.  It launches the same kernels with the same arguments as the eager step: the
+        // handle's buffers are all allocated by now, and since every step ends with bs_update the captured
+        // step includes the rebuild of the tables that depend on the node positions
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        if (cudaStreamBeginCapture(ss, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const int rc2 = step(ss);
+            const cudaError_t e2 = cudaStreamEndCapture(ss, &g);
+            if (rc2 != BS_OK || e2 != cudaSuccess || !g || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) x = nullptr;
+        }
+        if (g) cudaGraphDestroy(g);
+        (void)cudaGetLastError();  // a capture that failed leaves no launch behind; the steps then run eagerly
+        cudaError_t e = cudaSuccess;
+        if (x) {
+            for (; done < n_steps && e == cudaSuccess; ++done) e = cudaGraphLaunch(x, ss);
+            h->graph_steps += done - 1;
+            cudaGraphExecDestroy(x);
+        }
+        BS_CUDA(cudaEventRecord(h->step_out, ss));
+        BS_CUDA(cudaStreamWaitEvent(caller, h->step_out, 0));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    }
+    for (; done < n_steps; ++done)
+        if ((rc = step(stream))) return rc;
+    return BS_OK;
+}
+
+int bs_graph_steps(bs_handle h, int64_t *steps)
+{
+    if (!h || !steps) return fail(BS_ERR_ARG, "NULL argument");
+    *steps = h->graph_steps;
     return BS_OK;
 }
 

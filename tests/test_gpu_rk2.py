@@ -54,3 +54,45 @@ def test_rings_trajectory_fp32_vs_fp64():
     drift = np.linalg.norm(traj[bs.BS_FP32] - traj[bs.BS_FP64], axis=1)
     assert drift.max() <= 1e-5 * np.abs(d64).max() * 100  # <= 1e-3 of the largest displacement
     assert np.sqrt(np.mean(drift**2)) <= 1e-5 * np.abs(d64).max()
+
+
+@pytest.mark.parametrize("side_stream", [False, True])
+def test_graph_steps_equal_eager_steps(side_stream):
+    """bs_rk2_steps (first step eager, the rest replayed from a captured CUDA graph) moves the nodes exactly as
+    the same number of bs_rk2_step calls, on the default stream and on a side stream."""
+    m = config1_plain()
+    params = dict(P, precision=bs.BS_FP32)
+    eager = bs.Mesh(m.nodes, m.tets, m.omega)
+    for _ in range(6):
+        eager.bs_rk2_step(0.02, **params)
+    eager.bs_status()
+    g = bs.Mesh(m.nodes, m.tets, m.omega)
+    stream = torch.cuda.Stream() if side_stream else None
+    g.bs_rk2_steps(0.02, 6, stream=stream, **params)
+    if stream is not None:
+        stream.synchronize()
+    g.bs_status()
+    assert g.bs_graph_steps() == 5
+    assert np.array_equal(g.bs_nodes().cpu().numpy(), eager.bs_nodes().cpu().numpy())
+    # zero steps change nothing; a negative count is an argument error
+    before = g.bs_nodes().cpu().numpy()
+    g.bs_rk2_steps(0.02, 0, **params)
+    assert np.array_equal(g.bs_nodes().cpu().numpy(), before)
+    with pytest.raises(bs.BSError):
+        g.bs_rk2_steps(0.02, -1, **params)
+
+
+def test_graph_steps_with_stretching_equal_eager_steps():
+    """The same for the all-ray Heun step with vortex stretching (the mesh walk, nodes and vorticity)."""
+    m = config1_plain()
+    params = dict(far_ratio=np.inf, tet_gauss_order=4, n_theta=4, n_phi=8, precision=bs.BS_FP32)
+    eager = bs.Mesh(m.nodes, m.tets, m.omega)
+    for _ in range(4):
+        eager.bs_rk2_step_stretch(0.01, **params)
+    eager.bs_status()
+    g = bs.Mesh(m.nodes, m.tets, m.omega)
+    g.bs_rk2_steps(0.01, 4, stretch=True, **params)
+    g.bs_status()
+    assert g.bs_graph_steps() == 3
+    assert np.array_equal(g.bs_nodes().cpu().numpy(), eager.bs_nodes().cpu().numpy())
+    assert np.array_equal(g.bs_omega().cpu().numpy(), eager.bs_omega().cpu().numpy())
