@@ -105,6 +105,7 @@ struct bs_ctx {
     int ray_occ[2] = {};                // cached CTAs per SM of the all-ray kernel by [precision]
     int ray_occ_L[2] = {};              // ... for this many directions
     int variant[2][65] = {};  // chosen kernel variant by [precision][Q] (bs_autotune, or BS_VARIANT)
+    bool tuned[2][65] = {};   // variant[][] was set by bs_autotune
     // mesh walk of the all-ray velocity at the nodes (built on first use)
     bool walk_built = false;
     bool walk_conforming = false;
@@ -701,8 +702,24 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     if (!ray) BS_CUDA(ensure_far(h, Q, st));
 
     int variant = h->variant[p->precision][Q];
-    if (const char *env = getenv("BS_VARIANT")) variant = atoi(env);
+    const char *variant_env = getenv("BS_VARIANT");
+    if (variant_env) variant = atoi(variant_env);
     if (variant < 0 || variant >= num_variants(p->precision, Q) || p->near_rule == BS_NEAR_EXACT) variant = 0;
+    if (!ray && !variant_env && !h->tuned[p->precision][Q] && p->near_rule == BS_NEAR_RAY) {
+        // a mesh whose default work items would not fill the GPU several times over: 128-point blocks give
+        // its near pairs (each warp drains its own one at a time) three times as many warps
+        const int sv = small_mesh_variant(p->precision, Q);
+        if (sv >= 0 && sv != variant) {
+            const LaunchShape s0 = shape_for(p->precision, Q, variant);
+            int &o0 = h->occ[p->precision][Q][variant];
+            if (o0 == 0) o0 = std::max(1, velocity_ctas_per_sm(p->precision, Q, variant));
+            const int64_t b0 = (k + (int64_t)s0.threads * s0.points_per_thread - 1) /
+                               ((int64_t)s0.threads * s0.points_per_thread);
+            const int64_t t0 = (h->n_tets + s0.tile - 1) / s0.tile;
+            if (b0 * ((t0 + kMinTilesPerItem - 1) / kMinTilesPerItem) < (int64_t)kSmallMeshWaves * h->n_sm * o0)
+                variant = sv;
+        }
+    }
     const LaunchShape shape = ray ? ray_shape() : shape_for(p->precision, Q, variant);
     int occ_ray = 0;
     if (ray) {
@@ -720,9 +737,11 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     const int64_t n_tiles = (h->n_tets + shape.tile - 1) / shape.tile;
     const int64_t target = 16LL * h->n_sm * occ;
     int64_t n_chunks = std::min<int64_t>(std::max<int64_t>((target + n_blocks - 1) / n_blocks, 1), n_tiles);
-    // at least kMinTilesPerItem tiles per item: shorter items are dominated by their set-up
-    const int64_t per = std::min<int64_t>(std::max<int64_t>((n_tiles + n_chunks - 1) / n_chunks, kMinTilesPerItem),
-                                          n_tiles);
+    // at least kMinTilesPerItem tiles per item (shorter items are dominated by their set-up), unless that
+    // leaves the GPU with fewer items than it has CTA slots
+    const int64_t min_per =
+        n_blocks * ((n_tiles + kMinTilesPerItem - 1) / kMinTilesPerItem) < (int64_t)h->n_sm * occ ? 1 : kMinTilesPerItem;
+    const int64_t per = std::min<int64_t>(std::max<int64_t>((n_tiles + n_chunks - 1) / n_chunks, min_per), n_tiles);
     n_chunks = (n_tiles + per - 1) / per;
 
     const int bits = order_grid_bits(k);
@@ -1119,6 +1138,8 @@ int bs_autotune(bs_handle h, const bs_params *p, void *stream)
     float best = INFINITY;
     int best_v = 0;
     const int saved = h->variant[prec][Q];
+    const bool saved_tuned = h->tuned[prec][Q];
+    h->tuned[prec][Q] = true;  // each timed call runs exactly variant v
     for (int v = 0; v < nv; ++v) {
         h->variant[prec][Q] = v;
         rc = bs_velocity(h, h->nodes, h->n_nodes, &q, out, stream);  // warm-up (also builds tables)
@@ -1139,9 +1160,11 @@ int bs_autotune(bs_handle h, const bs_params *p, void *stream)
     cudaFreeAsync(out, st);
     if (rc) {
         h->variant[prec][Q] = saved;
+        h->tuned[prec][Q] = saved_tuned;
         return rc;
     }
     h->variant[prec][Q] = best_v;
+    h->tuned[prec][Q] = true;
     BS_CUDA(cudaStreamSynchronize(st));
     return BS_OK;
 }

@@ -163,6 +163,10 @@ struct LaunchShape {
 // all variants of a rule share the tile size (the far records depend on it)
 constexpr int kMaxVariants = 16;  // num_variants() never exceeds this
 int num_variants(int precision, int Q);
+// the variant with one point per thread (128-point blocks), or -1: for meshes too small to fill the GPU with
+// the default blocks, where each warp's near pairs (drained one at a time) set the time
+int small_mesh_variant(int precision, int Q);
+constexpr int kSmallMeshWaves = 8;  // fewer default work items than this many GPU-fulls: a small mesh
 LaunchShape shape_for(int precision, int Q, int variant = 0);
 int velocity_ctas_per_sm(int precision, int Q, int variant = 0, int near_rule = 0);
 // ev_start/ev_stop (optional) are recorded around the velocity kernel alone

@@ -157,7 +157,10 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
     lines.f64 = reinterpret_cast<dbl4 *>(base + kLines64);
 
     const int Q = p->tet_gauss_order;
-    const LaunchShape shape = shape_for(p->precision, Q, 0);
+    // meshes within the fixed limits are small: the one-point-per-thread variant where there is one
+    const int sv = p->near_rule == BS_NEAR_RAY ? small_mesh_variant(p->precision, Q) : -1;
+    const int variant = sv >= 0 ? sv : 0;
+    const LaunchShape shape = shape_for(p->precision, Q, variant);
     if (shape.tile > kMaxTile) return fail(BS_ERR_ARG, "bs_velocity_noalloc: tile larger than the scratch layout");
 
     // the per-call state that must start from zero / "none"
@@ -176,7 +179,7 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
         return cuda_fail(e, "direction table");
 
     // decomposition, as in bs_velocity but with at most kMaxChunks chunks
-    const int occ = std::max(1, velocity_ctas_per_sm(p->precision, Q, 0, p->near_rule));
+    const int occ = std::max(1, velocity_ctas_per_sm(p->precision, Q, variant, p->near_rule));
     const int64_t BP = (int64_t)shape.threads * shape.points_per_thread;
     const int64_t n_blocks = (k + BP - 1) / BP;
     const int64_t n_tiles = (n_tets + shape.tile - 1) / shape.tile;
@@ -217,7 +220,7 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
     a.m.n_chunks = (int)n_chunks;
     a.m.tiles_per_chunk = (int)per;
     a.m.partial = reinterpret_cast<double *>(base + kPartial);
-    a.variant = 0;
+    a.variant = variant;
     a.near_rule = p->near_rule;
     a.n_items = n_blocks * n_chunks;
     int grid = 0;

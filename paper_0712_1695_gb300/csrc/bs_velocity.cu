@@ -1019,6 +1019,14 @@ cudaError_t dispatch(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
 }  // namespace
 
 int num_variants(int precision, int Q) { return (precision == BS_FP32 && Q == 4) ? kNumQ4 : 1; }
+
+int small_mesh_variant(int precision, int Q)
+{
+    if (precision != BS_FP32 || Q != 4) return -1;
+    for (int v = 0; v < kNumQ4; ++v)
+        if (kQ4[v].P == 1) return v;
+    return -1;
+}
 static_assert(kNumQ4 <= kMaxVariants, "variant table larger than the per-handle caches");
 
 LaunchShape shape_for(int precision, int Q, int variant)
