@@ -994,8 +994,15 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
 
     // decomposition: items of roughly equal work over all meshes
     int variant = b->meshes[0]->variant[prec][Q];
-    if (const char *env = getenv("BS_VARIANT")) variant = atoi(env);
+    const char *variant_env = getenv("BS_VARIANT");
+    if (variant_env) variant = atoi(variant_env);
     if (variant < 0 || variant >= num_variants(prec, Q) || p->near_rule == BS_NEAR_EXACT) variant = 0;
+    if (!variant_env && !b->meshes[0]->tuned[prec][Q] && p->near_rule == BS_NEAR_RAY) {
+        int64_t largest = 0;
+        for (int i = 0; i < n; ++i) largest = std::max(largest, b->meshes[i]->n_tets);
+        const int sv = small_mesh_variant(prec, Q);
+        if (sv >= 0 && largest <= kSmallBatchMeshTets) variant = sv;
+    }
     const LaunchShape shape = shape_for(prec, Q, variant);
     int &occ = p->near_rule == BS_NEAR_EXACT ? b->meshes[0]->occ_exact[prec][Q] : b->meshes[0]->occ[prec][Q][variant];
     if (occ == 0) occ = std::max(1, velocity_ctas_per_sm(prec, Q, variant, p->near_rule));

@@ -167,6 +167,9 @@ int num_variants(int precision, int Q);
 // the default blocks, where each warp's near pairs (drained one at a time) set the time
 int small_mesh_variant(int precision, int Q);
 constexpr int kSmallMeshWaves = 8;  // fewer default work items than this many GPU-fulls: a small mesh
+// a batch of meshes of at most this many tets each takes the small-mesh variant (measured on 256 meshes of
+// 8^3..24^3 nodes: 551 ms against 607 ms for the default variant)
+constexpr int64_t kSmallBatchMeshTets = 80000;
 LaunchShape shape_for(int precision, int Q, int variant = 0);
 int velocity_ctas_per_sm(int precision, int Q, int variant = 0, int near_rule = 0);
 // ev_start/ev_stop (optional) are recorded around the velocity kernel alone
