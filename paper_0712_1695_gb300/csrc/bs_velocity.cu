@@ -752,7 +752,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             if (nearp[p]) continue;
                             const double dx = xp[p].x - qq[0], dy = xp[p].y - qq[1], dz = xp[p].z - qq[2];
                             const double r2 = dx * dx + dy * dy + dz * dz;
-                            const double ir = 1.0 / sqrt(r2);
+                            const double ir = rsqrt(r2);  // one library call instead of a sqrt and a divide
                             const double ir3 = ir * ir * ir;
                             tacc[p][0] += ir3 * (dy * qq[5] - dz * qq[4]);
                             tacc[p][1] += ir3 * (dz * qq[3] - dx * qq[5]);
@@ -967,6 +967,7 @@ constexpr VariantShape kQ4[] = {{3, 32, 2, 4, true},  {2, 32, 4, 3, false}, {4, 
                                 {2, 32, 4, 3, true},  {3, 32, 3, 4, true},  {2, 32, 4, 5, true},
                                 {2, 32, 3, 4, true},  {4, 32, 3, 3, true},  {3, 32, 3, 4, false}};
 constexpr int kNumQ4 = sizeof(kQ4) / sizeof(kQ4[0]);
+constexpr VariantShape kQ4D[] = {{1, 32, 2, 4, true}};  // float64, four-point rule (FP64-pipe bound)
 constexpr VariantShape kQ8[] = {{2, 16, 4, 4, true}};
 constexpr VariantShape kQ27[] = {{1, 16, 4, 4, false}};
 constexpr VariantShape kQ64[] = {{1, 8, 4, 4, false}};
@@ -979,7 +980,11 @@ cudaError_t dispatch(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
     if (a.near_rule == BS_NEAR_EXACT) {  // the exact near-field rule: variant 0 of each tet rule
         switch (a.Q) {
         case 1: return BS_LX(1, kQ1[0]);
-        case 4: return BS_LX(4, kQ4[0]);
+        case 4:
+            if constexpr (sizeof(T) == 4)
+                return BS_LX(4, kQ4[0]);
+            else
+                return BS_LX(4, kQ4D[0]);
         case 8: return BS_LX(8, kQ8[0]);
         case 27: return BS_LX(27, kQ27[0]);
         case 64: return BS_LX(64, kQ64[0]);
@@ -1005,7 +1010,7 @@ cudaError_t dispatch(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
             default: return BS_L(4, kQ4[0]);
             }
         } else {
-            return BS_L(4, kQ4[0]);
+            return BS_L(4, kQ4D[0]);
         }
     case 8: return BS_L(8, kQ8[0]);
     case 27: return BS_L(27, kQ27[0]);
@@ -1034,7 +1039,9 @@ LaunchShape shape_for(int precision, int Q, int variant)
     VariantShape v = kQ4[0];
     switch (Q) {
     case 1: v = kQ1[0]; break;
-    case 4: v = (precision == BS_FP32 && variant >= 0 && variant < kNumQ4) ? kQ4[variant] : kQ4[0]; break;
+    case 4:
+        v = precision == BS_FP32 ? ((variant >= 0 && variant < kNumQ4) ? kQ4[variant] : kQ4[0]) : kQ4D[0];
+        break;
     case 8: v = kQ8[0]; break;
     case 27: v = kQ27[0]; break;
     case 64: v = kQ64[0]; break;
