@@ -795,6 +795,13 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_sample} of the 4096 seeded sample nodes x all {mesh.n_tets} tets ({dt:.1f} s)"}
         sel, vo = run_oracle_sample.last
+        # one core, on a smaller sample of the same nodes
+        all_threads = oracle.num_threads()
+        oracle.set_num_threads(1)
+        v1, dt1, _ = run_oracle_sample(mesh, 48, seed_offset=7)
+        oracle.set_num_threads(all_threads)
+        cpu["one_core"] = {"value": v1, "unit": UNIT, "cores": 1,
+                           "sample": f"48 of the 4096 seeded sample nodes x all {mesh.n_tets} tets ({dt1:.1f} s)"}
         cpu["fp32_vs_oracle_rms_over_max"] = rms_over_max(v32[sel], vo)
         cpu["fp32_vs_oracle_rel_l2"] = rel_l2(v32[sel], vo)
         if fp64 is not None:

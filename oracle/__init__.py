@@ -72,11 +72,15 @@ class OracleLib:
         lib.orc_velocity_dderiv.argtypes = [_D, ctypes.c_int64, _I32, ctypes.c_int64, _D, _D, _D, ctypes.c_int64,
                                             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]
         lib.orc_num_threads.argtypes = []
+        lib.orc_set_num_threads.argtypes = [ctypes.c_int]
         self.lib = lib
         self.path = path
 
     def num_threads(self) -> int:
         return int(self.lib.orc_num_threads())
+
+    def set_num_threads(self, n: int) -> None:
+        self.lib.orc_set_num_threads(int(n))
 
     def gauss_legendre(self, n: int):
         t = np.zeros(n)
@@ -218,6 +222,10 @@ def _load() -> OracleLib:
 
 def num_threads() -> int:
     return _load().num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    _load().set_num_threads(n)
 
 
 def gauss_legendre(n):

@@ -793,6 +793,17 @@ int orc_velocity_dderiv(const double *nodes, int64_t n_nodes, const int32_t *tet
     return ORC_OK;
 }
 
+/* Threads of the later OpenMP loops (n >= 1); no effect without OpenMP.  Results do not depend on it. */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int orc_num_threads(void)
 {
 #ifdef _OPENMP
