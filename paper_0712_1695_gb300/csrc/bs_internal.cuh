@@ -42,7 +42,7 @@ constexpr double kPi = 3.14159265358979323846;
 template <typename T>
 __host__ __device__ constexpr int far_stride(int Q)
 {
-    return sizeof(T) == 4 ? (4 + 20 * ((Q + 1) / 2)) : (4 + 6 * Q);
+    return sizeof(T) == 4 ? (4 + 20 * ((Q + 1) / 2)) : (4 + 10 * Q);
 }
 constexpr int kNearF32Vec4 = 15;  // float4 per near record
 namespace nf32 {

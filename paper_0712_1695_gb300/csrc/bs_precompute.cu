@@ -200,10 +200,11 @@ __global__ void far_records_kernel(const double *__restrict__ near64, const doub
             wv = {wv.x + b * w[i].x, wv.y + b * w[i].y, wv.z + b * w[i].z};
         }
         wv = scale(wv, s * wq[q]);
-        const double vals[6] = {xq.x, xq.y, xq.z, wv.x, wv.y, wv.z};
-        for (int j = 0; j < 6; ++j) d[4 + 6 * q + j] = vals[j];
         const D3 xl = sub(xq, o);
         const D3 B = cross(xl, wv);
+        // float64: the same tile-frame values, one point after the other
+        const double vals[10] = {-2.0 * xl.x, -2.0 * xl.y, -2.0 * xl.z, dot(xl, xl), wv.x, wv.y, wv.z, B.x, B.y, B.z};
+        for (int j = 0; j < 10; ++j) d[4 + 10 * q + j] = vals[j];
         // pair q/2, slot q%2: value k of the point goes to float 2k + slot of the pair's 20
         float *g = f + 4 + 20 * (q / 2) + (q % 2);
         const double vals32[10] = {-2.0 * xl.x, -2.0 * xl.y, -2.0 * xl.z, dot(xl, xl), wv.x, wv.y, wv.z,

@@ -728,11 +728,18 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                 // float64: direct form in global coordinates
                 double tacc[P][3];
                 V3<double> xp[P];
+                // tile frame x' = x - o (exact: the origin is a float), as in the float32 sweep
+                V3<double> xl[P];
+                double xx[P], A[P][3], B[P][3];
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
                     tacc[p][0] = tacc[p][1] = tacc[p][2] = 0.0;
                     const float *sp = spts + 9 * (slot0 + 32 * p);
                     xp[p] = mk(join3(sp[0], sp[1], sp[2]), join3(sp[3], sp[4], sp[5]), join3(sp[6], sp[7], sp[8]));
+                    xl[p] = mk(xp[p].x - (double)hd.x, xp[p].y - (double)hd.y, xp[p].z - (double)hd.z);
+                    xx[p] = xl[p].x * xl[p].x + xl[p].y * xl[p].y + xl[p].z * xl[p].z;
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) A[p][jj] = B[p][jj] = 0.0;
                 }
 #pragma unroll 1
                 for (int j = 0; j < cnt; ++j) {
@@ -744,19 +751,22 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         const double dx = xp[p].x - rec[0], dy = xp[p].y - rec[1], dz = xp[p].z - rec[2];
                         nearp[p] = !culled && !(dx * dx + dy * dy + dz * dz > thr2);
                     }
+                    // per point q: (-2 x_q', |x_q'|^2, w', B = x_q' x w'); sum (x' - x_q') x w' / r^3 = x' x A - B
 #pragma unroll
                     for (int q = 0; q < Q; ++q) {
-                        const double *qq = rec + 4 + 6 * q;
+                        const double *qq = rec + 4 + 10 * q;
 #pragma unroll
                         for (int p = 0; p < P; ++p) {
                             if (nearp[p]) continue;
-                            const double dx = xp[p].x - qq[0], dy = xp[p].y - qq[1], dz = xp[p].z - qq[2];
-                            const double r2 = dx * dx + dy * dy + dz * dz;
+                            const double r2 = fma(xl[p].x, qq[0], fma(xl[p].y, qq[1], fma(xl[p].z, qq[2], xx[p] + qq[3])));
                             const double ir = rsqrt(r2);  // one library call instead of a sqrt and a divide
                             const double ir3 = ir * ir * ir;
-                            tacc[p][0] += ir3 * (dy * qq[5] - dz * qq[4]);
-                            tacc[p][1] += ir3 * (dz * qq[3] - dx * qq[5]);
-                            tacc[p][2] += ir3 * (dx * qq[4] - dy * qq[3]);
+                            A[p][0] = fma(ir3, qq[4], A[p][0]);
+                            A[p][1] = fma(ir3, qq[5], A[p][1]);
+                            A[p][2] = fma(ir3, qq[6], A[p][2]);
+                            B[p][0] = fma(ir3, qq[7], B[p][0]);
+                            B[p][1] = fma(ir3, qq[8], B[p][1]);
+                            B[p][2] = fma(ir3, qq[9], B[p][2]);
                         }
                     }
                     if (!culled) {
@@ -773,6 +783,12 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             }
                         }
                     }
+                }
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    tacc[p][0] += xl[p].y * A[p][2] - xl[p].z * A[p][1] - B[p][0];
+                    tacc[p][1] += xl[p].z * A[p][0] - xl[p].x * A[p][2] - B[p][1];
+                    tacc[p][2] += xl[p].x * A[p][1] - xl[p].y * A[p][0] - B[p][2];
                 }
                 release();
                 if (EXACT && qn > 0) {
