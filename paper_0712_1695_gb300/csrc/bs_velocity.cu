@@ -725,7 +725,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                     __syncwarp();
                 }
             } else {
-                // float64: direct form in global coordinates
+                // float64: near/far test in global coordinates, far rule in the tile frame
                 double tacc[P][3];
                 V3<double> xp[P];
                 // tile frame x' = x - o (exact: the origin is a float), as in the float32 sweep
