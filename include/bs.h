@@ -274,7 +274,13 @@ BS_API int bs_batch_destroy(bs_batch b);
 
 /* Time the kernel variants (points per thread, tet tile) for this mesh and
  * parameters on `stream` and keep the fastest for later calls with the same
- * precision/order/direction count.  Synchronises the stream. */
+ * precision/order/direction count.  Synchronises the stream.
+ * Without it, a handle uses the default variant, except for meshes too small
+ * to fill the GPU with the default work items (fewer than 8 GPU-fulls): those
+ * take the variant with one point per thread, and their work items one tet
+ * tile each when two would leave CTA slots empty.  A batch whose meshes have
+ * at most 80000 tets each also takes that variant (unless its first mesh was
+ * tuned).  The environment variable BS_VARIANT overrides every choice. */
 BS_API int bs_autotune(bs_handle h, const bs_params *p, void *stream);
 /* The kernel variant bs_autotune chose for this precision and rule (0 = default). */
 BS_API int bs_tuned_variant(bs_handle h, int precision, int tet_gauss_order, int *variant);
