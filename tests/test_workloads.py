@@ -46,3 +46,27 @@ def test_ball_and_batch():
     assert np.linalg.norm(b.nodes, axis=1).max() <= 1.0 + 1e-15
     batch = config4_batch(count=4)
     assert len(batch) == 4 and all(8 <= m.n_side <= 24 for m in batch)
+
+
+def test_jittered_ball_is_not_folded():
+    """The jittered ball keeps every tet at >= 1/4 of its unjittered volume and positive, and no two tets that share
+    a face lie on the same side of it (the ball map alone would fold tets near the origin)."""
+    for n in (8, 11, 16):
+        b = ball_mesh(n, jitter=0.1)
+        b0 = ball_mesh(n)
+        v, v0 = tet_volumes6(b.nodes, b.tets), tet_volumes6(b0.nodes, b0.tets)
+        assert np.all(v > 0) and np.all(v >= 0.25 * v0 - 1e-15)
+        assert np.abs(b.nodes - b0.nodes).max() > 0  # the jitter moved the interior
+        # every interior face: the two opposite vertices on opposite sides of its plane
+        faces = {}
+        for t, tet in enumerate(b.tets):
+            for k in range(4):
+                key = tuple(sorted(np.delete(tet, k)))
+                faces.setdefault(key, []).append((t, tet[k]))
+        for key, owners in faces.items():
+            if len(owners) != 2:
+                continue
+            p0, p1, p2 = b.nodes[list(key)]
+            nrm = np.cross(p1 - p0, p2 - p0)
+            s = [np.dot(nrm, b.nodes[o] - p0) for _, o in owners]
+            assert s[0] * s[1] < 0
