@@ -222,3 +222,20 @@ def test_ball_mesh(orc, n):
     assert rel_l2(v, vo) <= TOL_FP64_REL_L2
     v32, _ = nodes_velocity(h, len(b.nodes), bs.BS_FP32, **p)
     assert rms_over_max(v32, vo) <= TOL_FP32_RMS_MAX
+
+
+def test_hill_vortex_error_falls_with_the_mesh():
+    """Hill's spherical vortex (Section 3.1, the Table 1 case) by the all-ray walk at 16 x 16 directions on
+    jittered balls of 10^3 and 16^3 grid nodes: the r.m.s. error against the closed-form velocity falls, and is
+    below 1.5e-3 (largest speed 1/3) on the finer mesh."""
+    from workloads import ball_mesh, hill_velocity, hill_vorticity
+
+    p = dict(ALLRAY, n_theta=16, n_phi=16)
+    eps = []
+    for n in (10, 16):
+        b = ball_mesh(n, hill_vorticity, jitter=0.1)
+        h = bs.Mesh(b.nodes, b.tets, b.omega)
+        v, _ = nodes_velocity(h, len(b.nodes), bs.BS_FP32, **p)
+        eps.append(float(np.sqrt(np.mean(np.sum((v - hill_velocity(b.nodes)) ** 2, axis=1)))))
+    assert eps[1] < 0.7 * eps[0]
+    assert eps[1] < 1.5e-3
