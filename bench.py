@@ -509,6 +509,20 @@ def exact_workload(args):
     for name, rule in (("ray", bs.BS_NEAR_RAY), ("exact", bs.BS_NEAR_EXACT)):
         v[name] = h.bs_velocity(ps, precision=bs.BS_FP64, **dict(PARAMS, near_rule=rule)).cpu().numpy()
     h.bs_status()
+    # the ray rule's cost and error (against the exact rule, FP64 on the samples) as the angular order grows
+    sweep = []
+    for nt, nphi in ((8, 16), (16, 16), (32, 32), (64, 64)):
+        P = dict(PARAMS, n_theta=nt, n_phi=nphi, precision=bs.BS_FP32)
+        h.bs_velocity(pts, out_dev=out, **P)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h.bs_velocity(pts, out_dev=out, **P)
+        e1.record()
+        torch.cuda.synchronize()
+        vr = h.bs_velocity(ps, **dict(P, precision=bs.BS_FP64)).cpu().numpy()
+        h.bs_status()
+        sweep.append({"directions": f"{nphi}x{nt}", "fp32_ms_all_nodes": e0.elapsed_time(e1),
+                      "rel_l2_vs_exact": rel_l2(vr, v["exact"])})
     pairs = mesh.n_nodes * mesh.n_tets
     extra = res["exact"]["ms"] - res["ray"]["ms"]
     line = {"metric": "velocity at all nodes with exact near pairs (the analytic near field), FP32 far field",
@@ -520,6 +534,7 @@ def exact_workload(args):
             "exact_extra_ns_per_near_pair": extra * 1e6 / max(res["exact"]["near_pairs"], 1),
             "ray_vs_exact_fp64": {"rel_l2": rel_l2(v["ray"], v["exact"]),
                                   "rms_over_max": rms_over_max(v["ray"], v["exact"])},
+            "ray_rule_by_directions": sweep,
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     return 0
