@@ -61,7 +61,8 @@ extern "C" {
 #define BS_NEAR_EXACT 1 /* near tets by the exact integral of Eq. 1 over the tet (the       */
                         /* analytic near-field evaluation Section 1 compares against:       */
                         /* face and edge integrals in closed form, 6 logarithms and 12      */
-                        /* atan2 per tet), in float64 under both precisions; no ray hits    */
+                        /* atan2 per tet) with float64 geometry; the logarithms and arc     */
+                        /* tangents in float64 (BS_FP64) or float32 (BS_FP32); no ray hits   */
                         /* are counted                                                      */
 
 typedef struct bs_ctx *bs_handle;

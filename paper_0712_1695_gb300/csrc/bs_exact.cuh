@@ -1,4 +1,4 @@
-// Exact integral of Eq. 1 over one tetrahedron with linear vorticity (float64): the analytic near-field
+// Exact integral of Eq. 1 over one tetrahedron with linear vorticity (float64 geometry): the analytic near-field
 // evaluation that Section 1 sets the ray rule against (the reduction of the volume integral to face
 // integrals and then to closed-form edge integrals).
 //
@@ -33,8 +33,11 @@ struct Vel64 {
     double x, y, z;
 };
 
-// v: contribution of the tet of near record r to the velocity at x.
-__device__ __noinline__ Vel64 tet_exact_f64(const V3<double> x, const double *__restrict__ r)
+// v: contribution of the tet of near record r to the velocity at x.  LOWT: the logarithms and arc tangents
+// in float32 (the geometry stays float64; about 1e-7 relative error per pair, for the float32 path); else
+// every step in float64.
+template <bool LOWT>
+__device__ __noinline__ Vel64 tet_exact(const V3<double> x, const double *__restrict__ r)
 {
     // vertices relative to x and their distances
     double dx[4], dy[4], dz[4], R[4];
@@ -74,24 +77,26 @@ __device__ __noinline__ Vel64 tet_exact_f64(const V3<double> x, const double *__
 
     // edge terms: f = int dl / rho and E = R0^2 f + l_b R_b - l_a R_a
     constexpr int EA[6] = {0, 0, 0, 1, 1, 2}, EB[6] = {1, 2, 3, 2, 3, 3};
-    double f[6], E[6], R02[6];
+    double f[6], E[6], R02[6], IL[6];
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
         const int a = EA[e], b = EB[e];
         const double ex = dx[b] - dx[a], ey = dy[b] - dy[a], ez = dz[b] - dz[a];
         const double L2 = ex * ex + ey * ey + ez * ez, iL = rsqrt(L2);
+        IL[e] = iL;
         const double tx = ex * iL, ty = ey * iL, tz = ez * iL;
         const double la = dx[a] * tx + dy[a] * ty + dz[a] * tz, lb = dx[b] * tx + dy[b] * ty + dz[b] * tz;
         const double cx = dy[a] * tz - dz[a] * ty, cy = dz[a] * tx - dx[a] * tz, cz = dx[a] * ty - dy[a] * tx;
         const double r02 = cx * cx + cy * cy + cz * cz;  // squared distance from x to the edge's line
         double fe = 0.0;
         if (r02 > 1e-26 * L2) {
-            if (la >= 0.0)
-                fe = log((R[b] + lb) / (R[a] + la));
-            else if (lb <= 0.0)
-                fe = log((R[a] - la) / (R[b] - lb));
+            // the ratio is at most about 1e26 (r02 > 1e-26 L^2): within float range
+            const double q = la >= 0.0 ? (R[b] + lb) / (R[a] + la)
+                                       : (lb <= 0.0 ? (R[a] - la) / (R[b] - lb) : (R[b] + lb) * (R[a] - la) / r02);
+            if constexpr (LOWT)
+                fe = (double)logf((float)q);
             else
-                fe = log((R[b] + lb) * (R[a] - la) / r02);
+                fe = log(q);
         }
         f[e] = fe;
         R02[e] = r02;
@@ -113,9 +118,8 @@ __device__ __noinline__ Vel64 tet_exact_f64(const V3<double> x, const double *__
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int e = FE[k][j], a = EA[e], b = EB[e], o = FO[k][j];
-            const double ex = dx[b] - dx[a], ey = dy[b] - dy[a], ez = dz[b] - dz[a];
-            const double iL = rsqrt(ex * ex + ey * ey + ez * ez);
-            const double tx = ex * iL, ty = ey * iL, tz = ez * iL;
+            const double iL = IL[e];
+            const double tx = (dx[b] - dx[a]) * iL, ty = (dy[b] - dy[a]) * iL, tz = (dz[b] - dz[a]) * iL;
             // in-plane normal of the edge, pointing away from the face's third vertex
             double mx = ty * nz - tz * ny, my = tz * nx - tx * nz, mz = tx * ny - ty * nx;
             if (mx * (dx[o] - dx[a]) + my * (dy[o] - dy[a]) + mz * (dz[o] - dz[a]) > 0.0) {
@@ -129,7 +133,14 @@ __device__ __noinline__ Vel64 tet_exact_f64(const V3<double> x, const double *__
                 // u - w and 1 + u w over the common positive factor Da Db (atan2 ignores it): no division
                 const double la = dx[a] * tx + dy[a] * ty + dz[a] * tz, lb = dx[b] * tx + dy[b] * ty + dz[b] * tz;
                 const double Da = R02[e] + ah * R[a], Db = R02[e] + ah * R[b];
-                beta = atan2(P0 * (lb * Da - la * Db), Da * Db + P0 * P0 * la * lb);
+                const double yy = P0 * (lb * Da - la * Db), xx = Da * Db + P0 * P0 * la * lb;
+                if constexpr (LOWT) {
+                    // atan2 ignores a common positive scale: bring both into float range first
+                    const double m = fmax(fabs(yy), fabs(xx));
+                    beta = m > 0.0 ? (double)atan2f((float)(yy / m), (float)(xx / m)) : 0.0;
+                } else {
+                    beta = atan2(yy, xx);
+                }
             }
             I0 += P0 * f[e] - ah * beta;
             const double c = 0.5 * E[e];

@@ -355,7 +355,7 @@ __device__ __forceinline__ void cursor_advance(PairCursor &c, const uint32_t *wm
     c.k0 = k;
 }
 
-// EXACT: near pairs take the exact integral (tet_exact_f64, float64) instead of the ray rule, the
+// EXACT: near pairs take the exact integral (tet_exact) instead of the ray rule, the
 // warp's pairs spread over all 32 lanes and each result handed to the lane that owns its point.
 template <typename T, int Q, int P, int NT, int TILE, int S, int MINB, bool INL, bool EXACT>
 __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a)
@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             const float *sp = spts + 9 * (warp * 32 * P + pp * 32 + owner);
                             const V3<double> xd = mk(join3(sp[0], sp[1], sp[2]), join3(sp[3], sp[4], sp[5]),
                                                      join3(sp[6], sp[7], sp[8]));
-                            const Vel64 o = tet_exact_f64(xd, md.near64 + (t * TILE + j) * kNearF64);
+                            const Vel64 o = tet_exact<true>(xd, md.near64 + (t * TILE + j) * kNearF64);
                             ox = (float)o.x;
                             oy = (float)o.y;
                             oz = (float)o.z;
@@ -804,7 +804,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             const float *sp = spts + 9 * (warp * 32 * P + pp * 32 + owner);
                             const V3<double> xd = mk(join3(sp[0], sp[1], sp[2]), join3(sp[3], sp[4], sp[5]),
                                                      join3(sp[6], sp[7], sp[8]));
-                            o = tet_exact_f64(xd, md.near64 + (t * TILE + j) * kNearF64);
+                            o = tet_exact<false>(xd, md.near64 + (t * TILE + j) * kNearF64);
                             tag = 1 | (pp << 1) | (owner << 8);
                         }
                         cursor_advance(cur, wm, qn);
