@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from workloads import (  # noqa: E402
-    ball_mesh, config1_plain, config2_ring, config3_fourier, config3_samples, config4_batch, config5_rings)
+    config1_plain, config2_ring, config3_fourier, config3_samples, config4_batch, config5_rings)
 
 PARAMS = dict(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16)
 METRIC = "node-tet interactions/s (velocity at all nodes, FP32 path)"
@@ -423,54 +423,6 @@ def allray_workload(args):
     return 0
 
 
-def hill_workload(args):
-    """The paper's Table 1 experiment on this hardware: Hill's spherical vortex (Section 3.1) on a tetrahedralised
-    unit ball of N nodes, velocity at all nodes by the all-ray method (the mesh walk) with 4x4 and 16x16
-    directions, FP32; r.m.s. error against the closed-form velocity (the paper's epsilon, here over the largest
-    speed too) and the time per evaluation.  The paper's meshes are TETGEN meshes of N random points (not
-    published); jittered Kuhn grids mapped onto the ball stand in for them."""
-    import torch
-
-    import paper_0712_1695_gb300 as bs
-    from workloads import hill_velocity, hill_vorticity
-
-    bs.load()
-    rows = []
-    with ClockSampler(0) as clk:
-        for n in (10, 13, 16, 20, 25):  # 1000 .. 15625 nodes, the paper's N = 1000 .. 16000
-            b = ball_mesh(n, hill_vorticity, jitter=0.1)
-            h = bs.Mesh(b.nodes, b.tets, b.omega)
-            ex = hill_velocity(b.nodes)
-            for N in (4, 16):
-                P = dict(far_ratio=float("inf"), tet_gauss_order=4, n_theta=N, n_phi=N, precision=bs.BS_FP32)
-                out = h.bs_velocity_nodes(**P)  # connectivity, tables
-                h.bs_status()
-                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                reps = max(3, args.steps)
-                ev0.record()
-                for _ in range(reps):
-                    h.bs_velocity_nodes(out_dev=out, **P)
-                ev1.record()
-                torch.cuda.synchronize()
-                h.bs_status()
-                v = out.cpu().numpy()
-                err = v - ex
-                rms = float(np.sqrt(np.mean(np.sum(err ** 2, axis=1))))
-                rows.append({"N": len(b.nodes), "tets": len(b.tets), "directions": f"{N}x{N}",
-                             "ms": ev0.elapsed_time(ev1) / reps, "eps_rms": rms,
-                             "eps_rms_over_max": rms / float(np.linalg.norm(ex, axis=1).max())})
-    last = rows[-1]
-    line = {"metric": "velocity at all nodes of Hill's vortex, all-ray method (the paper's Table 1 workload)",
-            "value": last["N"] * last["tets"] / (last["ms"] * 1e-3), "unit": UNIT, "n_gpus": 1,
-            "steps": max(3, args.steps), "warmup": 1, "ms_per_step": last["ms"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "Hill's spherical vortex on jittered Kuhn-grid unit balls, N = 1000 .. 15625 nodes",
-                       "far_ratio": "inf", "precision": "fp32"},
-            "rows": rows, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
 def exact_workload(args):
     """The exact near-field rule (the analytic evaluation Section 1 sets the ray rule against) on the 64^3
     Fourier mesh: the hybrid method with ray-rule near pairs (the default) and with exact near pairs, both
@@ -586,18 +538,39 @@ def steps_workload(args):
     return 0
 
 
+def fma_probe():
+    """The bench-only fma-chain probe (bench_fma_probe.cu), compiled on demand with the library's nvcc flags."""
+    import ctypes
+
+    from paper_0712_1695_gb300.build import ARCH, nvcc
+
+    src = os.path.join(ROOT, "bench_fma_probe.cu")
+    lib = os.path.join(ROOT, "_build", "libfma_probe.so")
+    if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+        os.makedirs(os.path.dirname(lib), exist_ok=True)
+        subprocess.run([nvcc(), *ARCH, "-O3", "-Xcompiler", "-fPIC", "-shared", src, "-o", lib], check=True)
+    so = ctypes.CDLL(lib)
+    so.fma_probe_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+
+    def rate(kind):
+        r = ctypes.c_double()
+        if so.fma_probe_rate(kind, ctypes.byref(r)) != 0:
+            raise RuntimeError(f"fma probe kind {kind} failed")
+        return r.value
+
+    return rate
+
+
 def peaks_workload(args):
-    """Measured arithmetic rates of this GPU (bs_fma_rate): float64 fma (the float64 path and the exact near
-    rule), float32 fma and packed float32x2 fma (the far sweep), beside the nominal float32 peak the headline's
-    roofline divides by."""
+    """Measured arithmetic rates of this GPU (bench_fma_probe.cu): float64 fma (the float64 path and the exact
+    near rule), float32 fma and packed float32x2 fma (the far sweep), beside the nominal float32 peak the
+    headline's roofline divides by."""
     import torch
 
-    import paper_0712_1695_gb300 as bs
-
-    bs.load()
+    rate = fma_probe()
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
     with ClockSampler(0) as clk:
-        rates = {name: max(bs.bs_fma_rate(kind) for _ in range(2))
+        rates = {name: max(rate(kind) for _ in range(2))
                  for name, kind in (("fp64_fma", 0), ("fp32_fma", 1), ("fp32x2_fma", 2))}
     nominal = n_sm * FP32_LANES_PER_SM * 2 * MAX_SM_MHZ * 1e6 / 1e12
     line = {"metric": "measured fma-chain rates", "unit": "TFLOP/s", "rates": rates,
@@ -614,10 +587,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fourier64",
-                    choices=["fourier64", "batch", "rings", "allray", "hill", "exact", "peaks", "steps"],
+                    choices=["fourier64", "batch", "rings", "allray", "exact", "peaks", "steps"],
                     help="fourier64: the headline workload; batch: 256 uneven meshes, batched vs separate "
                          "launches; rings: Heun steps of two colliding rings; allray: the ray rule for every "
-                         "pair on the 32^3 ring mesh; hill: the paper's Table 1 experiment (Hill's vortex, all-ray); "
+                         "pair on the 32^3 ring mesh; "
                          "exact: the exact near-field rule against the ray rule on the 64^3 mesh; peaks: measured fma rates; "
                          "steps: Heun steps on small meshes, per-step calls vs a replayed CUDA graph")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
@@ -653,8 +626,6 @@ def main():
         return rings_workload(args)
     if args.workload == "allray":
         return allray_workload(args)
-    if args.workload == "hill":
-        return hill_workload(args)
     if args.workload == "exact":
         return exact_workload(args)
     if args.workload == "peaks":

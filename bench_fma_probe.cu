@@ -1,17 +1,17 @@
-// Throughput of the arithmetic pipes the velocity kernels run on: chains of dependent fused multiply-adds,
-// several independent chains per thread, a grid of 8 CTAs of 256 threads per SM.  The iteration loop is
-// unrolled by 4 so that its counter and branch take few issue slots (a plain float32 fma issues one
-// instruction per lane operation, so every other instruction shows in the rate).  The float32 rate bounds
-// the far sweep (FMA pipe), the float64 rate the float64 path and the exact near rule.
+// bench_fma_probe.cu -- a benchmark helper, not part of libbs: the throughput of the arithmetic pipes the
+// velocity kernels run on, measured as chains of dependent fused multiply-adds, several independent chains
+// per thread, a grid of 8 CTAs of 256 threads per SM.  The iteration loop is unrolled by 4 so that its
+// counter and branch take few issue slots (a plain float32 fma issues one instruction per lane operation, so
+// every other instruction shows in the rate).  The float32 rate bounds the far sweep (FMA pipe), the float64
+// rate the float64 path and the exact near rule.  bench.py (--workload peaks) compiles it on demand.
 #include <cuda_runtime.h>
+#include <stdint.h>
 
-#include "bs_internal.cuh"
-
-namespace bs {
 namespace {
 
 constexpr int kProbeThreads = 256;
 constexpr int kProbeCtasPerSm = 8;
+
 
 __global__ void __launch_bounds__(kProbeThreads) fma_f64_kernel(double *out, int iters)
 {
@@ -71,10 +71,16 @@ __global__ void __launch_bounds__(kProbeThreads) fma_f32x2_kernel(double *out, i
 
 }  // namespace
 
-// kind 0: float64 fma, 1: float32 fma, 2: packed float32x2 fma.  Returns TFLOP/s (2 flop per lane fma) of
-// the second of two timed launches in *tflops.
-cudaError_t measure_fma_rate(int kind, int n_sm, cudaStream_t st, double *tflops)
+// kind 0: float64 fma, 1: float32 fma, 2: packed float32x2 fma.  Writes the TFLOP/s (2 flop per lane fma)
+// of the second of two timed launches on the current device to *tflops.  Returns 0, 1 (bad kind) or
+// 2 (a CUDA call failed).
+extern "C" __attribute__((visibility("default"))) int fma_probe_rate(int kind, double *tflops)
 {
+    if (kind < 0 || kind > 2 || !tflops) return 1;
+    int dev = 0, n_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 2;
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 2;
+    cudaStream_t st = nullptr;
     const int blocks = n_sm * kProbeCtasPerSm;
     const int64_t n = (int64_t)blocks * kProbeThreads;
     double *buf = nullptr;
@@ -103,7 +109,6 @@ cudaError_t measure_fma_rate(int kind, int n_sm, cudaStream_t st, double *tflops
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (buf) cudaFree(buf);
-    return e;
+    return e == cudaSuccess ? 0 : 2;
 }
 
-}  // namespace bs

@@ -203,6 +203,27 @@ BS_API int bs_omega(bs_handle h, double *omega_dev, void *stream);
  * this handle raised its device error flag since the last call (clears it). */
 BS_API int bs_status(bs_handle h, void *stream);
 
+/* Limits of the handle's bounded device waits, and a test of their give-up
+ * path (the paper has no counterpart).  Every device wait of the library is
+ * bounded: a mesh walk stops after a number of tets per half-line, and the
+ * velocity and all-ray kernels stop waiting for a bulk copy of a tet tile
+ * after a number of polls; either then raises the handle's error flag, the
+ * kernel returns, and the next bs_status reports BS_ERR_TIMEOUT.
+ *   walk_max_steps  > 0: tets a half-line may cross (0: the default,
+ *                   max(4096, 64 n_tets^(1/3)) capped at n_tets);
+ *   copy_wait_polls > 0: polls of a bulk-copy wait (0: the default, 2^26,
+ *                   about a second);
+ *   withhold_copies = 1: the velocity and all-ray kernels arm their copy
+ *                   barriers but issue no copy, so every wait runs out (a
+ *                   test of the give-up path: no copy is ever in flight, so
+ *                   nothing can land after the kernel returned).  Results are
+ *                   then meaningless; 0 restores normal operation.
+ * On a valid mesh with the defaults no limit is ever reached.  A kernel that
+ * gives up first waits (with the same bound) for its own copies still in
+ * flight.  The settings apply to the calls on this handle that follow.
+ * Errors: BS_ERR_ARG (NULL handle, negative limit, withhold_copies not 0/1). */
+BS_API int bs_set_wait_limits(bs_handle h, int64_t walk_max_steps, int64_t copy_wait_polls, int withhold_copies);
+
 /* Free every device buffer of the handle (synchronises the device). */
 BS_API int bs_destroy(bs_handle h);
 
@@ -228,8 +249,12 @@ BS_API int bs_mesh_size(bs_handle h, int64_t *n_nodes, int64_t *n_tets);
  * capture.  All calls share the one array, which keeps the last call's
  * contents: two calls whose work overlaps on the GPU (different streams, or
  * different host threads, without ordering between them) race and give
- * wrong results; order them on one stream.  The mesh is not validated
- * (use bs_create for that): invalid node indices give zero contributions. */
+ * wrong results; order them on one stream.  The mesh is not validated on
+ * the host (that would need a synchronisation): a node index out of range,
+ * a degenerate tet (|volume| <= 1e-14 h^3) or a bulk-copy wait that gave up
+ * is found on the device, and the call's last kernel then overwrites every
+ * velocity with NaN and every count with -1 (use bs_create to validate a
+ * mesh beforehand). */
 BS_API int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, const int32_t *tets_dev, int64_t n_tets,
                                const double *omega_dev, const double *eval_pts_dev, int64_t k, const bs_params *p,
                                double *out_dev, void *stream);
@@ -253,14 +278,6 @@ BS_API const char *bs_last_error(void);
  * weights [order] (fractions of |V|). */
 BS_API int bs_direction_table(int n_phi, int n_theta, double *s_host, double *k_host);
 
-/* Measured rate of the arithmetic pipe a precision runs on, in TFLOP/s (two
- * flops per lane fused multiply-add): independent chains of fma over 8 CTAs of
- * 256 threads per SM of the current device, timed with CUDA events (the
- * second of two launches of about 5-20 ms).  kind 0: float64 fma (the float64
- * path and the exact near rule), 1: float32 fma, 2: packed float32x2 fma (the
- * far sweep).  Synchronous; allocates and frees a scratch buffer of 2 KB per
- * CTA.  Errors: BS_ERR_ARG, BS_ERR_CUDA. */
-BS_API int bs_fma_rate(int kind, double *tflops, void *stream);
 BS_API int bs_tet_rule(int order, double *bary_host, double *w_host);
 
 /* Many meshes in one persistent launch (evaluation points = each mesh's own

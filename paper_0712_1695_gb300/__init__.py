@@ -14,7 +14,6 @@ from .binding import (  # noqa: F401
     Mesh,
     bs_create,
     bs_direction_table,
-    bs_fma_rate,
     bs_tet_rule,
     load,
 )

@@ -24,8 +24,8 @@ EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_sta
             "bs_mesh_size", "bs_last_error", "bs_direction_table", "bs_tet_rule", "bs_batch_create",
             "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read",
             "bs_velocity_noalloc", "bs_tuned_variant", "bs_rk2_step", "bs_nodes", "bs_velocity_nodes",
-            "bs_velocity_nodes_dderiv", "bs_rk2_step_stretch", "bs_omega", "bs_fma_rate", "bs_rk2_steps",
-            "bs_graph_steps")
+            "bs_velocity_nodes_dderiv", "bs_rk2_step_stretch", "bs_omega", "bs_rk2_steps",
+            "bs_graph_steps", "bs_set_wait_limits")
 
 
 class BSError(RuntimeError):
@@ -67,7 +67,7 @@ def load(path: str = LIB_PATH):
         lib.bs_last_error.restype = ctypes.c_char_p
         lib.bs_direction_table.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
         lib.bs_tet_rule.argtypes = [ctypes.c_int, _D, _D]
-        lib.bs_fma_rate.argtypes = [ctypes.c_int, _D, _P]
+        lib.bs_set_wait_limits.argtypes = [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
         lib.bs_rk2_steps.argtypes = [_P, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(bs_params), _P]
         lib.bs_graph_steps.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
         lib.bs_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]
@@ -158,6 +158,11 @@ class Mesh:
     def bs_status(self, stream=None):
         _check(load().bs_status(self.handle, _stream_ptr(stream)))
 
+    def bs_set_wait_limits(self, walk_max_steps=0, copy_wait_polls=0, withhold_copies=False):
+        """Limits of the bounded device waits (0 = the defaults); withhold_copies tests their give-up path."""
+        _check(load().bs_set_wait_limits(self.handle, int(walk_max_steps), int(copy_wait_polls),
+                                         int(bool(withhold_copies))))
+
     def bs_velocity(self, pts_dev, out_dev=None, counts_dev=None, stream=None, **params):
         """Velocity at device points (torch float64 [k, 3]); returns the output tensor."""
         import torch
@@ -168,8 +173,9 @@ class Mesh:
             out_dev = torch.empty((k, 3), dtype=torch.float64, device=pts_dev.device)
         _require_dev(out_dev, (k, 3))
         if counts_dev is not None:
-            if counts_dev.dtype != torch.int32 or tuple(counts_dev.shape) != (k, 3) or not counts_dev.is_contiguous():
-                raise ValueError("counts must be a contiguous int32 [k, 3] CUDA tensor")
+            if not (counts_dev.is_cuda and counts_dev.device == pts_dev.device and counts_dev.dtype == torch.int32
+                    and tuple(counts_dev.shape) == (k, 3) and counts_dev.is_contiguous()):
+                raise ValueError("counts must be a contiguous int32 [k, 3] CUDA tensor on the points' device")
         p = make_params(counts=counts_dev, **params)
         _check(load().bs_velocity(self.handle, pts_dev.data_ptr(), k, ctypes.byref(p), out_dev.data_ptr(),
                                   _stream_ptr(stream)))
@@ -184,7 +190,8 @@ class Mesh:
             out_dev = torch.empty((n, 3), dtype=torch.float64, device="cuda")
         _require_dev(out_dev, (n, 3))
         if counts_dev is not None:
-            if counts_dev.dtype != torch.int32 or tuple(counts_dev.shape) != (n, 3) or not counts_dev.is_contiguous():
+            if not (counts_dev.is_cuda and counts_dev.dtype == torch.int32 and tuple(counts_dev.shape) == (n, 3)
+                    and counts_dev.is_contiguous()):
                 raise ValueError("counts must be a contiguous int32 [n_nodes, 3] CUDA tensor")
         p = make_params(counts=counts_dev, **params)
         _check(load().bs_velocity_nodes(self.handle, ctypes.byref(p), out_dev.data_ptr(), _stream_ptr(stream)))
@@ -293,13 +300,6 @@ def bs_create(nodes, tets, omega) -> Mesh:
     return Mesh(nodes, tets, omega)
 
 
-def bs_fma_rate(kind: int, stream=None) -> float:
-    """Measured TFLOP/s of fma chains: kind 0 float64, 1 float32, 2 packed float32x2."""
-    r = ctypes.c_double()
-    _check(load().bs_fma_rate(int(kind), ctypes.byref(r), _stream_ptr(stream)))
-    return r.value
-
-
 def bs_direction_table(n_phi: int, n_theta: int):
     L = n_phi * n_theta
     s = np.zeros((L, 3))
@@ -321,7 +321,8 @@ def bs_velocity_noalloc(nodes_dev, tets_dev, omega_dev, pts_dev, out_dev, counts
     For callers that may not let the library allocate GPU memory; the
     library's fixed scratch caps the sizes (8192 tets, 4096 points, 4096
     directions, tet rules 1 and 4).  Calls share that scratch: keep them
-    ordered on one stream.
+    ordered on one stream.  A mesh error found on the device (node index out
+    of range, degenerate tet) makes every output NaN and every count -1.
     """
     import torch
 
@@ -334,6 +335,13 @@ def bs_velocity_noalloc(nodes_dev, tets_dev, omega_dev, pts_dev, out_dev, counts
     if not (tets_dev.is_cuda and tets_dev.dtype == torch.int32 and tets_dev.is_contiguous() and tets_dev.dim() == 2
             and tets_dev.shape[1] == 4):
         raise ValueError("tets must be a contiguous int32 [n_tets, 4] CUDA tensor")
+    for t in (nodes_dev, omega_dev, tets_dev, out_dev):
+        if t.device != pts_dev.device:
+            raise ValueError("all arrays must be on the same CUDA device")
+    if counts_dev is not None:
+        if not (counts_dev.is_cuda and counts_dev.device == pts_dev.device and counts_dev.dtype == torch.int32
+                and counts_dev.is_contiguous() and tuple(counts_dev.shape) == (k, 3)):
+            raise ValueError("counts must be a contiguous int32 [k, 3] CUDA tensor on the points' device")
     p = make_params(counts=counts_dev, **params)
     _check(load().bs_velocity_noalloc(nodes_dev.data_ptr(), n_nodes, tets_dev.data_ptr(), int(tets_dev.shape[0]),
                                       omega_dev.data_ptr(), pts_dev.data_ptr(), k, ctypes.byref(p),

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libbs.so")
-SOURCES = ["bs_tables.cu", "bs_precompute.cu", "bs_order.cu", "bs_velocity.cu", "bs_ray.cu", "bs_walk.cu", "bs_api.cu", "bs_noalloc.cu", "bs_step.cu", "bs_probe.cu"]
+SOURCES = ["bs_tables.cu", "bs_precompute.cu", "bs_order.cu", "bs_velocity.cu", "bs_ray.cu", "bs_walk.cu", "bs_api.cu", "bs_noalloc.cu", "bs_step.cu"]
 HEADERS = ["bs_internal.cuh", "bs_near.cuh", "bs_exact.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -73,7 +73,7 @@ struct bs_ctx {
     double *rho2 = nullptr;
     int *flag = nullptr;
     unsigned long long *first_bad = nullptr;
-    int *work_counter = nullptr;
+    unsigned long long *work_counter = nullptr;
     uint64_t version = 1;  // bumped whenever the near records change
     // far records of the last tet rule
     TetRule rule;
@@ -125,6 +125,10 @@ struct bs_ctx {
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used, ev_free;
     int64_t prof_kernel = 0, prof_all = 0;
+    // bounded-wait settings (bs_set_wait_limits): 0 = the defaults
+    int64_t walk_max_steps = 0;
+    int64_t copy_wait_polls = 0;
+    int withhold_copies = 0;
 };
 
 namespace {
@@ -174,7 +178,7 @@ struct bs_batch_ctx {
     std::vector<MeshDesc> h_meshes;  // last descriptor table copied to the device
     double *partial = nullptr;
     size_t partial_cap = 0;
-    int *work_counter = nullptr;
+    unsigned long long *work_counter = nullptr;
     int *flag = nullptr;
     LineTables lines;
     cudaGraphExec_t graph = nullptr;
@@ -414,6 +418,17 @@ int bs_status(bs_handle h, void *stream)
     return BS_OK;
 }
 
+int bs_set_wait_limits(bs_handle h, int64_t walk_max_steps, int64_t copy_wait_polls, int withhold_copies)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    if (walk_max_steps < 0 || copy_wait_polls < 0 || (withhold_copies != 0 && withhold_copies != 1))
+        return fail(BS_ERR_ARG, "bs_set_wait_limits: limits must be >= 0 and withhold_copies 0 or 1");
+    h->walk_max_steps = walk_max_steps;
+    h->copy_wait_polls = copy_wait_polls;
+    h->withhold_copies = withhold_copies;
+    return BS_OK;
+}
+
 int bs_mesh_size(bs_handle h, int64_t *n_nodes, int64_t *n_tets)
 {
     if (!h || !n_nodes || !n_tets) return fail(BS_ERR_ARG, "NULL argument");
@@ -550,6 +565,7 @@ int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *d
     w.flag = h->flag;
     // no valid mesh needs more steps than tets; a small cap keeps a broken walk short
     w.max_steps = (int)std::min<int64_t>(h->n_tets, std::max<int64_t>(4096, 64 * (int64_t)std::cbrt((double)h->n_tets)));
+    if (h->walk_max_steps > 0) w.max_steps = (int)std::min<int64_t>(h->walk_max_steps, INT32_MAX);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->prof) {
         if (h->ev_free.empty()) {
@@ -775,6 +791,8 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     a.skip = skip;
     a.near_rule = p->near_rule;
     a.n_items = n_blocks * n_chunks;
+    a.wait_polls = h->copy_wait_polls;
+    a.withhold_copies = h->withhold_copies;
     int grid = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->prof) {
@@ -832,17 +850,6 @@ int bs_destroy(bs_handle h)
     if (!h) return fail(BS_ERR_ARG, "handle is NULL");
     cudaDeviceSynchronize();
     free_ctx(h);
-    return BS_OK;
-}
-
-int bs_fma_rate(int kind, double *tflops, void *stream)
-{
-    if (kind < 0 || kind > 2) return fail(BS_ERR_ARG, "kind must be 0 (float64), 1 (float32) or 2 (float32x2)");
-    if (!tflops) return fail(BS_ERR_ARG, "NULL output");
-    int dev = 0, n_sm = 0;
-    BS_CUDA(cudaGetDevice(&dev));
-    BS_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-    BS_CUDA(measure_fma_rate(kind, n_sm, (cudaStream_t)stream, tflops));
     return BS_OK;
 }
 

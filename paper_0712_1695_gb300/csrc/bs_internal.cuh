@@ -144,10 +144,15 @@ struct VelocityArgs {
     // outputs
     int32_t *counts = nullptr;  // [k][3] or null (single mesh only; zeroed before)
     int *flag = nullptr;
-    int *work_counter = nullptr;  // device int, zeroed by launch_velocity
+    unsigned long long *work_counter = nullptr;  // device item counter, zeroed by launch_velocity
     int variant = 0;  // kernel variant (points per thread / registers) for this precision and rule
     const int *skip = nullptr;  // device flag: when set, the all-ray and reduce kernels return at once
     int near_rule = 0;          // BS_NEAR_RAY or BS_NEAR_EXACT
+    // bounded waits: polls of a bulk-copy wait before the kernel gives up (raises kFlagTimeout and
+    // returns); withhold_copies = 1 arms the copy barriers without issuing the copies (a test of the
+    // give-up path: nothing can land after the kernel returned)
+    long long wait_polls = 0;
+    int withhold_copies = 0;
 };
 
 constexpr int64_t kMinTilesPerItem = 2;  // work items shorter than this are dominated by their set-up
@@ -176,8 +181,6 @@ int velocity_ctas_per_sm(int precision, int Q, int variant = 0, int near_rule = 
 cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
                             cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);
 cudaError_t launch_reduce(const VelocityArgs &a, cudaStream_t st);
-// chains of fused multiply-adds (kind 0 float64, 1 float32, 2 float32x2) over 8 CTAs per SM: TFLOP/s
-cudaError_t measure_fma_rate(int kind, int n_sm, cudaStream_t st, double *tflops);
 // all-ray kernel (bs_ray.cu): one point per thread, near records streamed in tiles of ray_shape().tile;
 // single-mesh launches (a.meshes == nullptr); the partial sums and the reduction are those of the
 // velocity kernel.  The float32 direction table is staged in shared memory: the host uses this kernel

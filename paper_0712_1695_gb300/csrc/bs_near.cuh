@@ -20,7 +20,7 @@ constexpr float kDegenA = 1e-5f;     // float32: |a_i| below this with x inside/
 constexpr double kParD = 1e-12;
 constexpr float kParF = 1e-6f;
 constexpr float kVertexFallback = 1e-5f;
-constexpr long long kWaitCap = 1LL << 26;
+constexpr long long kWaitCap = 1LL << 26;  // default poll limit of a bulk-copy wait (about a second)
 
 // ---------------------------------------------------------------------------
 // mbarrier / bulk-copy helpers (inline PTX, sm_90+ forms valid on sm_103a)
@@ -58,12 +58,21 @@ __device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// bounded wait: false when the cap is reached
-__device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity)
+// bounded wait: false when `cap` polls did not see the phase complete
+__device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity, long long cap)
 {
-    for (long long i = 0; i < kWaitCap; ++i)
+    for (long long i = 0; i < cap; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
+}
+// After a wait gave up: wait (bounded again) for the next completion of every stage, so that no bulk
+// copy of this CTA can still be landing in its shared memory when the CTA exits.  A stage whose copy
+// was never issued gives up after `cap` polls.
+template <int S>
+__device__ inline void mbar_drain(uint64_t *full, uint32_t phase, long long cap)
+{
+#pragma unroll 1
+    for (int st = 0; st < S; ++st) mbar_wait(&full[st], (phase >> st) & 1u, cap);
 }
 
 // ---------------------------------------------------------------------------

@@ -16,6 +16,12 @@
 // Limits (anything larger is rejected with BS_ERR_ARG): kMaxTets tets,
 // kMaxPoints evaluation points, kMaxLines = n_theta * n_phi directions, tet
 // rules with 1 or 4 points.
+//
+// Errors found on the device: the mesh is not validated on the host (that
+// would need a synchronisation).  A node index out of range, a degenerate tet
+// (|volume| <= 1e-14 h^3) or a bulk-copy wait that gave up raises a flag in
+// the scratch array, and the call's last kernel then overwrites every
+// velocity with NaN and every count with -1.
 #include <math.h>
 
 #include <algorithm>
@@ -57,7 +63,7 @@ constexpr size_t kPartial = kBox + align256(8 * sizeof(int));
 constexpr size_t kFlag = kPartial + align256((size_t)kMaxChunks * kMaxPoints * 3 * sizeof(double));
 constexpr size_t kFirstBad = kFlag + align256(sizeof(int));
 constexpr size_t kCounter = kFirstBad + align256(sizeof(unsigned long long));
-constexpr size_t kScratchBytes = kCounter + align256(sizeof(int));
+constexpr size_t kScratchBytes = kCounter + align256(sizeof(unsigned long long));
 
 // The library's fixed scratch memory (about 11 MB).  Host code must not take
 // its address directly: the name is a host-side stand-in, so the device
@@ -66,6 +72,18 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;
 unsigned char *g_addr[64] = {};  // device address of g_scratch, per device ordinal
+
+// Runs after the reduction: if any kernel of this call raised the error flag (a node index out of range,
+// a degenerate tet, a bulk-copy wait that gave up), the whole output becomes NaN and the counts -1.  The
+// caller learns of the error from its own results without a synchronisation or a status call.
+__global__ void poison_kernel(const int *flag, double *out, int32_t *counts, int64_t k)
+{
+    if (*flag == 0) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * k; i += (int64_t)gridDim.x * blockDim.x) {
+        out[i] = __longlong_as_double(0x7ff8000000000000LL);  // quiet NaN
+        if (counts) counts[i] = -1;
+    }
+}
 
 }  // namespace
 
@@ -216,7 +234,7 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
     a.counts = p->counts;
     a.m.out = out_dev;
     a.flag = flag;
-    a.work_counter = reinterpret_cast<int *>(base + kCounter);
+    a.work_counter = reinterpret_cast<unsigned long long *>(base + kCounter);
     a.m.n_chunks = (int)n_chunks;
     a.m.tiles_per_chunk = (int)per;
     a.m.partial = reinterpret_cast<double *>(base + kPartial);
@@ -226,5 +244,7 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
     int grid = 0;
     if ((e = launch_velocity(p->precision, a, n_sm, st, &grid)) != cudaSuccess) return cuda_fail(e, "velocity");
     if ((e = launch_reduce(a, st)) != cudaSuccess) return cuda_fail(e, "reduce");
+    poison_kernel<<<(unsigned)std::min<int64_t>((3 * k + 255) / 256, 1024), 256, 0, st>>>(flag, out_dev, p->counts, k);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poison");
     return BS_OK;
 }

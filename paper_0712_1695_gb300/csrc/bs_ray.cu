@@ -316,12 +316,14 @@ __global__ void __launch_bounds__(kRayThreads) ray_kernel(const VelocityArgs a)
                               : (const void *)(md.near64 + first * kNearF64);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&pipe->full[st], bytes);
+        if (a.withhold_copies) return;
         bulk_g2s(stages + st * STAGE, src, bytes, &pipe->full[st]);
     };
+    const long long wait_cap = a.wait_polls > 0 ? a.wait_polls : kWaitCap;
 
     for (;;) {
         if (tid == 0) {
-            int64_t item = atomicAdd(reinterpret_cast<unsigned long long *>(a.work_counter), 1ull);
+            int64_t item = atomicAdd(a.work_counter, 1ull);
             if (item < a.n_items) {
                 *s_md = a.m;
             } else {
@@ -379,7 +381,8 @@ __global__ void __launch_bounds__(kRayThreads) ray_kernel(const VelocityArgs a)
         for (int i = 0; i < n_local; ++i) {
             const int st = i % kRayStages;
             const int64_t t = t0 + i;
-            if (!mbar_wait(&pipe->full[st], (phase >> st) & 1u)) {
+            // the warp gives up as one (a lane that saw the copy land leaves with the others)
+            if (!__all_sync(0xffffffffu, mbar_wait(&pipe->full[st], (phase >> st) & 1u, wait_cap))) {
                 aborted = true;
                 break;
             }
@@ -430,6 +433,7 @@ __global__ void __launch_bounds__(kRayThreads) ray_kernel(const VelocityArgs a)
         }
         if (aborted) {
             if (tid == 0) atomicOr(a.flag, kFlagTimeout);
+            mbar_drain<kRayStages>(pipe->full, phase, wait_cap);
             return;
         }
         if (valid) {
@@ -452,11 +456,11 @@ __global__ void __launch_bounds__(kRayThreads) ray_kernel(const VelocityArgs a)
     }
 }
 
-__global__ void ray_zero_kernel(int32_t *counts, int64_t n, int *work_counter, const int *skip)
+__global__ void ray_zero_kernel(int32_t *counts, int64_t n, unsigned long long *work_counter, const int *skip)
 {
     if (skip && *skip) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i == 0) *reinterpret_cast<unsigned long long *>(work_counter) = 0ull;
+    if (i == 0) *work_counter = 0ull;
     if (counts && i < n) counts[i] = 0;
 }
 

@@ -419,13 +419,15 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
         unsigned char *dst = stages + st * STAGE_BYTES;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&pipe->full[st], bytes + HDR_BYTES);
+        if (a.withhold_copies) return;
         bulk_g2s(dst, md.tile_hdr + 2 * t, HDR_BYTES, &pipe->full[st]);
         bulk_g2s(dst + HDR_BYTES, reinterpret_cast<const T *>(md.far) + first * RS, bytes, &pipe->full[st]);
     };
+    const long long wait_cap = a.wait_polls > 0 ? a.wait_polls : kWaitCap;
 
     for (;;) {
         if (tid == 0) {
-            int64_t item = atomicAdd(reinterpret_cast<unsigned long long *>(a.work_counter), 1ull);
+            int64_t item = atomicAdd(a.work_counter, 1ull);
             if (item < a.n_items) {
                 if (a.meshes) {
                     // the mesh whose item range holds this item (binary search on item_begin)
@@ -511,7 +513,8 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
         for (int i = 0; i < n_local; ++i) {
             const int st = i % S;
             const int64_t t = t0 + i;
-            if (!mbar_wait(&pipe->full[st], (phase >> st) & 1u)) {
+            // the warp gives up as one (a lane that saw the copy land leaves with the others)
+            if (!__all_sync(0xffffffffu, mbar_wait(&pipe->full[st], (phase >> st) & 1u, wait_cap))) {
                 aborted = true;
                 break;
             }
@@ -866,6 +869,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
         }
         if (aborted) {
             if (tid == 0) atomicOr(a.flag, kFlagTimeout);
+            mbar_drain<S>(pipe->full, phase, wait_cap);
             return;
         }
 
@@ -929,11 +933,11 @@ __global__ void reduce_kernel(const VelocityArgs a)
     m->out[3 * o + 2] = s2;
 }
 
-__global__ void zero_kernel(int32_t *counts, int64_t n, int *work_counter, const int *skip)
+__global__ void zero_kernel(int32_t *counts, int64_t n, unsigned long long *work_counter, const int *skip)
 {
     if (skip && *skip) return;  // the mesh walk evaluated these points
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i == 0) *reinterpret_cast<unsigned long long *>(work_counter) = 0ull;
+    if (i == 0) *work_counter = 0ull;
     if (counts && i < n) counts[i] = 0;
 }
 

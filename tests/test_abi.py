@@ -57,3 +57,4 @@ def test_argument_errors_without_gpu(lib):
     assert lib.bs_destroy(None) == binding.BS_ERR_ARG
     assert lib.bs_tet_rule(5, None, None) == binding.BS_ERR_ORDER
     assert lib.bs_direction_table(0, 4, None, None) == binding.BS_ERR_ARG
+    assert lib.bs_set_wait_limits(None, 0, 0, 0) == binding.BS_ERR_ARG
