@@ -44,7 +44,8 @@ FLOPS_PER_HIT = 80
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ = 2070.0
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "velocity_fp32_fourier64_traffic.json")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_0712_1695_gb300", "csrc", f) for f in ("bs_velocity.cu", "bs_near.cuh", "bs_internal.cuh")]
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_0712_1695_gb300", "csrc", f)
+                  for f in ("bs_velocity_kernel.cuh", "bs_vel_f32_q4.cu", "bs_near.cuh", "bs_internal.cuh")]
 
 
 def workload_config():
@@ -538,6 +539,50 @@ def steps_workload(args):
     return 0
 
 
+def variants_workload(args):
+    """Every variant of the float32 four-point ray rule on the headline workload (the 64^3 Fourier mesh at
+    all nodes, or --points nodes nearest the centre), each pinned in turn: ms per evaluation (mean of
+    --steps after --warmup), registers-bound CTAs per SM as launched, and the shape."""
+    import torch
+
+    import paper_0712_1695_gb300 as bs
+
+    bs.load()
+    mesh = config3_fourier()
+    h = bs.Mesh(mesh.nodes, mesh.tets, mesh.omega)
+    nodes = mesh.nodes
+    if args.points:
+        sel = np.sort(np.argsort(np.linalg.norm(mesh.nodes, axis=1), kind="stable")[:args.points])
+        nodes = np.ascontiguousarray(mesh.nodes[sel])
+    pts = torch.from_numpy(nodes).cuda()
+    out = torch.empty_like(pts)
+    P = dict(PARAMS, precision=bs.BS_FP32)
+    n = bs.bs_num_variants(bs.BS_FP32, 4)
+    only = [int(v) for v in args.variants.split(",")] if args.variants else range(n)
+    rows = []
+    with ClockSampler(0) as clk:
+        for v in only:
+            h.bs_set_variant(bs.BS_FP32, 4, bs.BS_NEAR_RAY, v)
+            for _ in range(args.warmup):
+                h.bs_velocity(pts, out_dev=out, **P)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                h.bs_velocity(pts, out_dev=out, **P)
+            e1.record()
+            torch.cuda.synchronize()
+            h.bs_status()
+            ms = e0.elapsed_time(e1) / args.steps
+            rows.append(dict(bs.bs_variant_shape(bs.BS_FP32, 4, bs.BS_NEAR_RAY, v), variant=v, ms=ms,
+                             interactions_per_s=len(nodes) * mesh.n_tets / (ms * 1e-3)))
+    rows.sort(key=lambda r: r["ms"])
+    print(json.dumps({"metric": "ms per evaluation by kernel variant (FP32, 4-point rule, 8x16 directions)",
+                      "points": len(nodes), "tets": mesh.n_tets, "steps": args.steps, "warmup": args.warmup,
+                      "rows": rows, "clocks": clk.summary()}), flush=True)
+    return 0
+
+
 def fma_probe():
     """The bench-only fma-chain probe (bench_fma_probe.cu), compiled on demand with the library's nvcc flags."""
     import ctypes
@@ -587,12 +632,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fourier64",
-                    choices=["fourier64", "batch", "rings", "allray", "exact", "peaks", "steps"],
+                    choices=["fourier64", "batch", "rings", "allray", "exact", "peaks", "steps", "variants"],
                     help="fourier64: the headline workload; batch: 256 uneven meshes, batched vs separate "
                          "launches; rings: Heun steps of two colliding rings; allray: the ray rule for every "
                          "pair on the 32^3 ring mesh; "
                          "exact: the exact near-field rule against the ray rule on the 64^3 mesh; peaks: measured fma rates; "
-                         "steps: Heun steps on small meshes, per-step calls vs a replayed CUDA graph")
+                         "steps: Heun steps on small meshes, per-step calls vs a replayed CUDA graph; variants: "
+                         "every float32 kernel variant timed on the headline workload")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
     ap.add_argument("--rings-mode", default="hybrid", choices=["hybrid", "allray-stretch"],
                     help="rings workload: the far/near rule with frozen vorticity, or the all-ray method with vortex "
@@ -609,6 +655,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 path on the 4096 sample nodes")
+    ap.add_argument("--variants", default="", help="variants workload: comma-separated variant indices (default all)")
     ap.add_argument("--points", type=int, default=0,
                     help="evaluate only this many seeded nodes (small case for profiler captures)")
     args = ap.parse_args()
@@ -632,6 +679,8 @@ def main():
         return peaks_workload(args)
     if args.workload == "steps":
         return steps_workload(args)
+    if args.workload == "variants":
+        return variants_workload(args)
 
     import torch
 
@@ -664,6 +713,15 @@ def main():
     out = torch.empty((k, 3), dtype=torch.float64, device="cuda")
     P = dict(PARAMS, precision=bs.BS_FP32)
 
+    # the kernel variant: the autotuner's choice for this GPU and workload (a hit in the shipped tuning
+    # cache on a GB300; timed once otherwise)
+    h.bs_autotune(**P)
+    variant = h.bs_tuned_variant(bs.BS_FP32, PARAMS["tet_gauss_order"])
+    chosen_by = "bs_autotune"
+    if os.environ.get("BS_VARIANT"):
+        variant, chosen_by = int(os.environ["BS_VARIANT"]), "BS_VARIANT"
+    variant_shape = bs.bs_variant_shape(bs.BS_FP32, PARAMS["tet_gauss_order"], bs.BS_NEAR_RAY, variant)
+
     # counts of one untimed evaluation give the algorithmic flops of a launch
     cnt = torch.zeros((k, 3), dtype=torch.int32, device="cuda")
     h.bs_velocity(pts, out_dev=out, counts_dev=cnt, **P)
@@ -678,8 +736,8 @@ def main():
         h.bs_velocity(pts, out_dev=out, **P)
     barrier()
 
+    # the timed region: the production path (no profiling events), inputs resident in HBM
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    h.bs_profile(True)
     with ClockSampler(local_rank) as clk:
         barrier()
         ev0.record(stream)
@@ -687,41 +745,50 @@ def main():
             h.bs_velocity(pts, out_dev=out, **P)
         ev1.record(stream)
         barrier()
-    kernel_ms, kernel_launches, all_launches = h.bs_profile_read()
-    h.bs_profile(False)
     h.bs_status()
     ms = ev0.elapsed_time(ev1) / args.steps
     ms_max = max_over_ranks(ms, dist, "cuda")
     value = whole_job_rate(pairs, world, ms_max)
 
-    # end to end through the public API: pinned host inputs of a Lagrangian step (node
-    # positions and vorticity) -> device, bs_update, bs_velocity at all nodes, velocities -> host
+    # a separate profiled pass (untimed for `value`): the velocity kernel's own event time on its launch
+    # stream, and the number of the library's kernel launches per step
+    prof_steps = max(1, min(args.steps, 3))
+    h.bs_profile(True)
+    for _ in range(prof_steps):
+        h.bs_velocity(pts, out_dev=out, **P)
+    kernel_ms, kernel_launches, all_launches = h.bs_profile_read()
+    h.bs_profile(False)
+    h.bs_status()
+    launches_per_step = all_launches / prof_steps
+
+    # end to end through the public C ABI with host buffers, every step: the step's node positions and
+    # vorticity copied from pinned host memory to the device and bs_update (a Lagrangian step's new
+    # mesh), then bs_velocity_host (points host -> device, evaluation, velocities device -> host)
     nodes_h = torch.from_numpy(mesh.nodes).pin_memory()
     omega_h = torch.from_numpy(mesh.omega).pin_memory()
+    pts_h = torch.from_numpy(eval_nodes).pin_memory()
     vel_h = torch.empty((k, 3), dtype=torch.float64).pin_memory()
-    nodes_d = torch.empty_like(pts)
-    omega_d = torch.empty_like(pts)
+    nodes_d = torch.empty((mesh.n_nodes, 3), dtype=torch.float64, device="cuda")
+    omega_d = torch.empty_like(nodes_d)
 
     def e2e_step():
         nodes_d.copy_(nodes_h, non_blocking=True)
         omega_d.copy_(omega_h, non_blocking=True)
         h.bs_update(nodes_d, omega_d)
-        h.bs_velocity(nodes_d, out_dev=out, **P)
-        vel_h.copy_(out, non_blocking=True)
-        stream.synchronize()
+        h.bs_velocity_host(pts_h.numpy(), out=vel_h.numpy(), **P)
 
     e2e = None
     if not args.no_e2e and not args.points:
         e2e_step()
         barrier()
         t0 = time.perf_counter()
-        e2e_steps = max(1, min(args.steps, 3))
-        for _ in range(e2e_steps):
+        for _ in range(args.steps):
             e2e_step()
         barrier()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_s = (time.perf_counter() - t0) / args.steps
         e2e = {"value": whole_job_rate(pairs, world, 1e3 * max_over_ranks(e2e_s, dist, "cuda")), "unit": UNIT,
-               "h2d_bytes_per_step": 2 * k * 24, "d2h_bytes_per_step": k * 24}
+               "h2d_bytes_per_step": 2 * mesh.n_nodes * 24 + k * 24, "d2h_bytes_per_step": k * 24,
+               "ms_per_step": 1e3 * e2e_s}
 
     if rank != 0:
         if dist is not None:
@@ -803,7 +870,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
             "roofline": roofline, "cpu_baseline": cpu, "fp64_path": fp64,
             "e2e": e2e,
-            "gpu_launches": int(all_launches), "clocks": clocks,
+            "gpu_launches": int(round(launches_per_step * args.steps)), "clocks": clocks,
+            "variant": dict(variant_shape, index=variant, chosen_by=chosen_by),
             "counts": {"near_pairs": n_near, "far_pairs": n_far, "ray_hits": n_hit}}
     print(json.dumps(line), flush=True)
     if dist is not None:

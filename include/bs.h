@@ -290,17 +290,57 @@ BS_API int bs_batch_create(const bs_handle *meshes, int n, bs_batch *out);
 BS_API int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void *stream);
 BS_API int bs_batch_destroy(bs_batch b);
 
-/* Time the kernel variants (points per thread, tet tile) for this mesh and
- * parameters on `stream` and keep the fastest for later calls with the same
- * precision/order/direction count.  Synchronises the stream.
- * Without it, a handle uses the default variant, except for meshes too small
- * to fill the GPU with the default work items (fewer than 8 GPU-fulls): those
- * take the variant with one point per thread, and their work items one tet
- * tile each when two would leave CTA slots empty.  A batch whose meshes have
- * at most 80000 tets each also takes that variant (unless its first mesh was
- * tuned).  The environment variable BS_VARIANT overrides every choice. */
+/* Kernel variants and the autotuner (the paper has no counterpart: launch
+ * shapes of this GPU implementation).
+ *
+ * The velocity kernel is compiled in several variants per (precision, tet
+ * rule, near rule), each a launch shape: evaluation points per thread, tets
+ * per shared-memory tile, pipeline stages, CTAs per SM its registers are
+ * budgeted for, near-pair routine inlined or called, ray bundle (lines each
+ * lane takes per iteration of the ray rule), and how the far sweep pairs
+ * values in its packed float32x2 registers (two quadrature points, or two
+ * evaluation points).  Every variant computes the same rule; results differ
+ * only by rounding.
+ *
+ * Which variant a bs_velocity call uses: the environment variable BS_VARIANT
+ * if set (every call), else the variant pinned by bs_set_variant, else the
+ * autotuner's cache entry for this GPU (name and SM count), precision, tet
+ * rule, near rule, direction count and size class (ceil(log2) of the point
+ * and tet counts), else variant 0 -- except that, for the ray rule, a mesh
+ * too small to fill the GPU with variant 0's work items (fewer than 8
+ * GPU-fulls) takes the variant with one point per thread.  A batch uses
+ * BS_VARIANT, else its first mesh's pinned variant, else the one-point
+ * variant when every mesh has at most 80000 tets, else variant 0.
+ *
+ * The cache is a JSON file: entries are read from tune_cache.json beside the
+ * package directory (shipped, written by bs_autotune on this GPU model) and
+ * from the file named by the environment variable BS_TUNE_CACHE, whose
+ * entries take precedence. */
+
+/* Number of variants for a precision, tet rule and near rule. */
+BS_API int bs_num_variants(int precision, int tet_gauss_order, int near_rule, int *n);
+/* Launch shape of a variant: shape[0..6] = points per thread, tets per tile,
+ * pipeline stages, CTAs per SM of the register budget, near routine inlined
+ * (1) or called (0), ray bundle (lines per lane per iteration), far sweep
+ * pairing two evaluation points (1) or two quadrature points (0). */
+BS_API int bs_variant_shape(int precision, int tet_gauss_order, int near_rule, int variant, int32_t *shape);
+/* Pin a variant for this handle's calls with this precision, tet rule and
+ * near rule (-1 restores the automatic choice).  Errors: BS_ERR_ARG (variant
+ * out of range), BS_ERR_ORDER. */
+BS_API int bs_set_variant(bs_handle h, int precision, int tet_gauss_order, int near_rule, int variant);
+
+/* Choose the variant for this mesh's own nodes and the parameters p: if the
+ * cache holds an entry for this GPU and problem (see above), take it without
+ * timing; else time every variant on `stream` (each after a warm-up call),
+ * take the fastest, and store it in the cache (in BS_TUNE_CACHE if set, else
+ * the shipped file, when the file is writable; for this process in any case).
+ * The environment variable BS_TUNE_FORCE=1 times even on a cache hit.  Calls
+ * that run the all-ray kernel (far_ratio = +inf, at most 4096 directions, the
+ * ray rule) have a single launch shape and need no tuning.  Synchronises the
+ * stream; allocates and frees one [n_nodes][3] output. */
 BS_API int bs_autotune(bs_handle h, const bs_params *p, void *stream);
-/* The kernel variant bs_autotune chose for this precision and rule (0 = default). */
+/* The variant the last bs_autotune for this precision and tet rule (ray
+ * near rule) chose or found in the cache (0 if none). */
 BS_API int bs_tuned_variant(bs_handle h, int precision, int tet_gauss_order, int *variant);
 
 #ifdef __cplusplus

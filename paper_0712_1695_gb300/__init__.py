@@ -14,6 +14,8 @@ from .binding import (  # noqa: F401
     Mesh,
     bs_create,
     bs_direction_table,
+    bs_num_variants,
+    bs_variant_shape,
     bs_tet_rule,
     load,
 )

@@ -25,7 +25,7 @@ EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_sta
             "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read",
             "bs_velocity_noalloc", "bs_tuned_variant", "bs_rk2_step", "bs_nodes", "bs_velocity_nodes",
             "bs_velocity_nodes_dderiv", "bs_rk2_step_stretch", "bs_omega", "bs_rk2_steps",
-            "bs_graph_steps", "bs_set_wait_limits")
+            "bs_graph_steps", "bs_set_wait_limits", "bs_num_variants", "bs_variant_shape", "bs_set_variant")
 
 
 class BSError(RuntimeError):
@@ -68,6 +68,10 @@ def load(path: str = LIB_PATH):
         lib.bs_direction_table.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
         lib.bs_tet_rule.argtypes = [ctypes.c_int, _D, _D]
         lib.bs_set_wait_limits.argtypes = [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
+        lib.bs_num_variants.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        lib.bs_variant_shape.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int32)]
+        lib.bs_set_variant.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.bs_rk2_steps.argtypes = [_P, ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(bs_params), _P]
         lib.bs_graph_steps.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
         lib.bs_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]
@@ -288,6 +292,10 @@ class Mesh:
         _check(load().bs_tuned_variant(self.handle, int(precision), int(tet_gauss_order), ctypes.byref(v)))
         return v.value
 
+    def bs_set_variant(self, precision, tet_gauss_order, near_rule, variant):
+        """Pin a kernel variant for this mesh's calls with these settings (-1: automatic choice)."""
+        _check(load().bs_set_variant(self.handle, int(precision), int(tet_gauss_order), int(near_rule), int(variant)))
+
 
 def _require_dev(t, shape):
     import torch
@@ -298,6 +306,21 @@ def _require_dev(t, shape):
 
 def bs_create(nodes, tets, omega) -> Mesh:
     return Mesh(nodes, tets, omega)
+
+
+VARIANT_FIELDS = ("points_per_thread", "tile", "stages", "ctas_per_sm", "inlined", "ray_bundle", "point_pairs")
+
+
+def bs_num_variants(precision: int, tet_gauss_order: int, near_rule: int = BS_NEAR_RAY) -> int:
+    n = ctypes.c_int()
+    _check(load().bs_num_variants(int(precision), int(tet_gauss_order), int(near_rule), ctypes.byref(n)))
+    return n.value
+
+
+def bs_variant_shape(precision: int, tet_gauss_order: int, near_rule: int, variant: int) -> dict:
+    s = (ctypes.c_int32 * 7)()
+    _check(load().bs_variant_shape(int(precision), int(tet_gauss_order), int(near_rule), int(variant), s))
+    return dict(zip(VARIANT_FIELDS, list(s)))
 
 
 def bs_direction_table(n_phi: int, n_theta: int):

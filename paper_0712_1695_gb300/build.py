@@ -17,8 +17,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libbs.so")
-SOURCES = ["bs_tables.cu", "bs_precompute.cu", "bs_order.cu", "bs_velocity.cu", "bs_ray.cu", "bs_walk.cu", "bs_api.cu", "bs_noalloc.cu", "bs_step.cu"]
-HEADERS = ["bs_internal.cuh", "bs_near.cuh", "bs_exact.cuh"]
+SOURCES = ["bs_tables.cu", "bs_precompute.cu", "bs_order.cu", "bs_velocity.cu", "bs_vel_f32_q4.cu", "bs_vel_f32_rules.cu",
+           "bs_vel_f64.cu", "bs_vel_exact.cu", "bs_ray.cu", "bs_walk.cu", "bs_api.cu", "bs_noalloc.cu", "bs_step.cu",
+           "bs_tune.cu"]
+HEADERS = ["bs_internal.cuh", "bs_near.cuh", "bs_exact.cuh", "bs_velocity_kernel.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -59,7 +61,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
     if jobs or force or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+        r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"], capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("nvcc link of libbs.so failed")

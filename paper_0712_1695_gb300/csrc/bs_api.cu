@@ -10,6 +10,7 @@
 #include <cstring>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -82,6 +83,8 @@ struct bs_ctx {
     double *far64 = nullptr;
     float4 *tile_hdr = nullptr;
     int far_tile = 0;
+    int far_layout = 0;            // float32 layout of far32 (kFarQuadPairs / kFarPointPairs)
+    size_t far32_cap = 0, far64_cap = 0, hdr_cap = 0;  // allocated elements
     // spatial order of the evaluation points
     int *perm = nullptr;
     unsigned *keys = nullptr;
@@ -100,12 +103,13 @@ struct bs_ctx {
     // work arrays of bs_rk2_step: x0, v0, v1 (each [n_nodes][3]); of bs_rk2_step_stretch also w0, s0, s1
     double *rk = nullptr;
     double *rk_w = nullptr;
-    int occ[2][65][kMaxVariants] = {};  // cached CTAs per SM by [precision][Q][variant]
-    int occ_exact[2][65] = {};          // the same for the exact near rule (variant 0)
-    int ray_occ[2] = {};                // cached CTAs per SM of the all-ray kernel by [precision]
-    int ray_occ_L[2] = {};              // ... for this many directions
-    int variant[2][65] = {};  // chosen kernel variant by [precision][Q] (bs_autotune, or BS_VARIANT)
-    bool tuned[2][65] = {};   // variant[][] was set by bs_autotune
+    int occ[2][2][65][kMaxVariants] = {};  // cached CTAs per SM by [near rule][precision][Q][variant]
+    int ray_occ[2] = {};                   // cached CTAs per SM of the all-ray kernel by [precision]
+    int ray_occ_L[2] = {};                 // ... for this many directions
+    int pinned[2][2][65];                  // bs_set_variant by [near rule][precision][Q], -1: automatic
+    int tuned[2][2][65] = {};              // the variant bs_autotune last chose (or found in the cache)
+    std::map<std::string, int> tune_memo;  // tuning key -> cached variant (-1: no entry)
+    char gpu_name[256] = {};
     // mesh walk of the all-ray velocity at the nodes (built on first use)
     bool walk_built = false;
     bool walk_conforming = false;
@@ -218,39 +222,84 @@ cudaError_t ensure_lines(bs_ctx *h, int n_phi, int n_theta, cudaStream_t st)
     return cudaSuccess;
 }
 
-cudaError_t ensure_far(bs_ctx *h, int Q, cudaStream_t st)
+// The far records of tet rule Q in the float32 layout and tile size of the variant a call uses (the tile
+// headers and the float32 tile frame depend on the tile), rebuilt when the mesh changed.
+cudaError_t ensure_far(bs_ctx *h, int Q, int tile, int layout, cudaStream_t st)
 {
-    if (h->far32 && h->rule.order == Q && h->far_version == h->version) return cudaSuccess;
+    if (h->far32 && h->rule.order == Q && h->far_tile == tile && h->far_layout == layout &&
+        h->far_version == h->version)
+        return cudaSuccess;
     cudaError_t e;
-    const int tile = shape_for(BS_FP32, Q).tile;
     if (h->rule.order != Q) {
-        void *old[] = {h->rule.bary, h->rule.w, h->far32, h->far64, h->tile_hdr};
-        for (void *b : old)
-            if (b) cudaFreeAsync(b, st);
+        if (h->rule.bary) cudaFreeAsync(h->rule.bary, st);
+        if (h->rule.w) cudaFreeAsync(h->rule.w, st);
         h->rule = TetRule();
-        h->far32 = nullptr;
-        h->far64 = nullptr;
-        h->tile_hdr = nullptr;
         if ((e = cudaMallocAsync((void **)&h->rule.bary, sizeof(double) * 4 * Q, st)) != cudaSuccess) return e;
         if ((e = cudaMallocAsync((void **)&h->rule.w, sizeof(double) * Q, st)) != cudaSuccess) return e;
         if ((e = build_tet_rule(Q, h->rule.bary, h->rule.w, st)) != cudaSuccess) return e;
         if (h->prof) h->prof_all += 1;
-        const size_t n = (size_t)std::max<int64_t>(h->n_tets, 1);
-        const size_t nt = (n + tile - 1) / tile;
-        if ((e = cudaMallocAsync((void **)&h->far32, n * far_stride<float>(Q) * sizeof(float), st)) != cudaSuccess)
-            return e;
-        if ((e = cudaMallocAsync((void **)&h->far64, n * far_stride<double>(Q) * sizeof(double), st)) != cudaSuccess)
-            return e;
-        if ((e = cudaMallocAsync((void **)&h->tile_hdr, 2 * nt * sizeof(float4), st)) != cudaSuccess) return e;
         h->rule.order = Q;
-        h->far_tile = tile;
     }
-    if ((e = build_far_records(h->near64, h->rho2, h->n_tets, h->rule, tile, h->tile_hdr, h->far32, h->far64,
+    const size_t n = (size_t)std::max<int64_t>(h->n_tets, 1);
+    auto grow = [&](void **buf, size_t &cap, size_t need, size_t elem) -> cudaError_t {
+        if (need <= cap && *buf) return cudaSuccess;
+        if (*buf) cudaFreeAsync(*buf, st);
+        *buf = nullptr;
+        cap = 0;
+        cudaError_t r = cudaMallocAsync(buf, need * elem, st);
+        if (r == cudaSuccess) cap = need;
+        return r;
+    };
+    if ((e = grow((void **)&h->far32, h->far32_cap, n * far_stride<float>(Q, layout), sizeof(float))) != cudaSuccess)
+        return e;
+    if ((e = grow((void **)&h->far64, h->far64_cap, n * far_stride<double>(Q), sizeof(double))) != cudaSuccess)
+        return e;
+    if ((e = grow((void **)&h->tile_hdr, h->hdr_cap, 2 * ((n + tile - 1) / tile), sizeof(float4))) != cudaSuccess)
+        return e;
+    if ((e = build_far_records(h->near64, h->rho2, h->n_tets, h->rule, tile, layout, h->tile_hdr, h->far32, h->far64,
                                st)) != cudaSuccess)
         return e;
     if (h->prof) h->prof_all += 2;
+    h->far_tile = tile;
+    h->far_layout = layout;
     h->far_version = h->version;
     return cudaSuccess;
+}
+
+// The kernel variant of the velocity kernel a call on k points uses: the environment variable
+// BS_VARIANT, else the variant bs_set_variant pinned, else the autotuner's cache entry for this GPU and
+// problem, else (the ray rule) the small-mesh rule, else variant 0.
+int choose_variant(bs_ctx *h, const bs_params *p, int64_t k)
+{
+    const int prec = p->precision, Q = p->tet_gauss_order, nr = p->near_rule;
+    const int nv = num_variants(prec, Q, nr);
+    const char *env = getenv("BS_VARIANT");
+    if (env) {
+        const int v = atoi(env);
+        return (v >= 0 && v < nv) ? v : 0;
+    }
+    const int pin = h->pinned[nr][prec][Q];
+    if (pin >= 0 && pin < nv) return pin;
+    const std::string key = tune_key(h->gpu_name, h->n_sm, prec, Q, nr, p->n_phi * p->n_theta, k, h->n_tets);
+    auto it = h->tune_memo.find(key);
+    const int tv = it != h->tune_memo.end() ? it->second : (h->tune_memo[key] = tune_lookup(key, prec, Q, nr));
+    if (tv >= 0 && tv < nv) return tv;
+    if (nr == BS_NEAR_RAY) {
+        // a mesh whose default work items would not fill the GPU several times over: 128-point blocks give
+        // its near pairs (each warp drains its own one at a time) three times as many warps
+        const int sv = small_mesh_variant(prec, Q);
+        if (sv > 0) {
+            const LaunchShape s0 = shape_for(prec, Q, 0, nr);
+            int &o0 = h->occ[nr][prec][Q][0];
+            if (o0 == 0) o0 = std::max(1, velocity_ctas_per_sm(prec, Q, 0, nr));
+            const int64_t b0 = (k + (int64_t)s0.threads * s0.points_per_thread - 1) /
+                               ((int64_t)s0.threads * s0.points_per_thread);
+            const int64_t t0 = (h->n_tets + s0.tile - 1) / s0.tile;
+            if (b0 * ((t0 + kMinTilesPerItem - 1) / kMinTilesPerItem) < (int64_t)kSmallMeshWaves * h->n_sm * o0)
+                return sv;
+        }
+    }
+    return 0;
 }
 
 cudaError_t ensure_order(bs_ctx *h, int64_t k, int bits, cudaStream_t st)
@@ -305,8 +354,14 @@ int bs_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t
     bs_ctx *h = new bs_ctx();
     h->n_nodes = n_nodes;
     h->n_tets = n_tets;
+    for (auto &a : h->pinned)
+        for (auto &b : a)
+            for (int &c : b) c = -1;
     cudaError_t e = cudaGetDevice(&h->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->n_sm, cudaDevAttrMultiProcessorCount, h->device);
+    cudaDeviceProp prop;
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&prop, h->device);
+    if (e == cudaSuccess) snprintf(h->gpu_name, sizeof h->gpu_name, "%s", prop.name);
     const size_t nt = (size_t)std::max<int64_t>(n_tets, 1);
     if (e == cudaSuccess) e = cudaMalloc(&h->nodes, sizeof(double) * 3 * n_nodes);
     if (e == cudaSuccess) e = cudaMalloc(&h->omega, sizeof(double) * 3 * n_nodes);
@@ -715,28 +770,9 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     const char *generic_env = getenv("BS_ALLRAY_GENERIC");
     const bool ray = isinf(p->far_ratio) && L <= kRayLinesSmemMax && !(generic_env && atoi(generic_env) != 0) &&
                      p->near_rule == BS_NEAR_RAY;
-    if (!ray) BS_CUDA(ensure_far(h, Q, st));
-
-    int variant = h->variant[p->precision][Q];
-    const char *variant_env = getenv("BS_VARIANT");
-    if (variant_env) variant = atoi(variant_env);
-    if (variant < 0 || variant >= num_variants(p->precision, Q) || p->near_rule == BS_NEAR_EXACT) variant = 0;
-    if (!ray && !variant_env && !h->tuned[p->precision][Q] && p->near_rule == BS_NEAR_RAY) {
-        // a mesh whose default work items would not fill the GPU several times over: 128-point blocks give
-        // its near pairs (each warp drains its own one at a time) three times as many warps
-        const int sv = small_mesh_variant(p->precision, Q);
-        if (sv >= 0 && sv != variant) {
-            const LaunchShape s0 = shape_for(p->precision, Q, variant);
-            int &o0 = h->occ[p->precision][Q][variant];
-            if (o0 == 0) o0 = std::max(1, velocity_ctas_per_sm(p->precision, Q, variant));
-            const int64_t b0 = (k + (int64_t)s0.threads * s0.points_per_thread - 1) /
-                               ((int64_t)s0.threads * s0.points_per_thread);
-            const int64_t t0 = (h->n_tets + s0.tile - 1) / s0.tile;
-            if (b0 * ((t0 + kMinTilesPerItem - 1) / kMinTilesPerItem) < (int64_t)kSmallMeshWaves * h->n_sm * o0)
-                variant = sv;
-        }
-    }
-    const LaunchShape shape = ray ? ray_shape() : shape_for(p->precision, Q, variant);
+    const int variant = ray ? 0 : choose_variant(h, p, k);
+    const LaunchShape shape = ray ? ray_shape() : shape_for(p->precision, Q, variant, p->near_rule);
+    if (!ray) BS_CUDA(ensure_far(h, Q, shape.tile, shape.layout, st));
     int occ_ray = 0;
     if (ray) {
         if (h->ray_occ[p->precision] == 0 || h->ray_occ_L[p->precision] != L) {
@@ -745,8 +781,7 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
         }
         occ_ray = h->ray_occ[p->precision];
     }
-    int &occ = ray ? occ_ray
-                   : (p->near_rule == BS_NEAR_EXACT ? h->occ_exact[p->precision][Q] : h->occ[p->precision][Q][variant]);
+    int &occ = ray ? occ_ray : h->occ[p->near_rule][p->precision][Q][variant];
     if (occ == 0) occ = std::max(1, velocity_ctas_per_sm(p->precision, Q, variant, p->near_rule));
     const int64_t BP = (int64_t)shape.threads * shape.points_per_thread;
     const int64_t n_blocks = (k + BP - 1) / BP;
@@ -972,13 +1007,32 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     const int prec = p->precision;
     bool changed = false;
 
+    // the variant: BS_VARIANT, else the first mesh's pinned variant (bs_set_variant), else (ray rule) the
+    // one-point-per-thread variant for batches of small meshes, else variant 0
+    const int nr = p->near_rule;
+    const int nv = num_variants(prec, Q, nr);
+    int variant = b->meshes[0]->pinned[nr][prec][Q];
+    const char *variant_env = getenv("BS_VARIANT");
+    if (variant_env) variant = atoi(variant_env);
+    if (variant < 0 || variant >= nv) {
+        variant = 0;
+        if (!variant_env && nr == BS_NEAR_RAY) {
+            int64_t largest = 0;
+            for (int i = 0; i < n; ++i) largest = std::max(largest, b->meshes[i]->n_tets);
+            const int sv = small_mesh_variant(prec, Q);
+            if (sv >= 0 && largest <= kSmallBatchMeshTets) variant = sv;
+        }
+    }
+    const LaunchShape shape = shape_for(prec, Q, variant, nr);
+
     // per-mesh tables (rebuilt only when stale) and per-mesh point orders (nodes = evaluation points)
     for (int i = 0; i < n; ++i) {
         bs_ctx *h = b->meshes[i];
         const uint64_t before = h->far_version;
-        const int before_q = h->rule.order;
-        BS_CUDA(ensure_far(h, Q, st));
-        changed = changed || before != h->far_version || before_q != h->rule.order;
+        const int before_q = h->rule.order, before_tile = h->far_tile, before_layout = h->far_layout;
+        BS_CUDA(ensure_far(h, Q, shape.tile, shape.layout, st));
+        changed = changed || before != h->far_version || before_q != h->rule.order || before_tile != h->far_tile ||
+                  before_layout != h->far_layout;
         if (b->order_version[i] != h->version) {
             const int bits = order_grid_bits(h->n_nodes);
             BS_CUDA(spatial_order(h->nodes, h->n_nodes, bits, b->box, b->keys, b->cell_count,
@@ -1000,18 +1054,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     }
 
     // decomposition: items of roughly equal work over all meshes
-    int variant = b->meshes[0]->variant[prec][Q];
-    const char *variant_env = getenv("BS_VARIANT");
-    if (variant_env) variant = atoi(variant_env);
-    if (variant < 0 || variant >= num_variants(prec, Q) || p->near_rule == BS_NEAR_EXACT) variant = 0;
-    if (!variant_env && !b->meshes[0]->tuned[prec][Q] && p->near_rule == BS_NEAR_RAY) {
-        int64_t largest = 0;
-        for (int i = 0; i < n; ++i) largest = std::max(largest, b->meshes[i]->n_tets);
-        const int sv = small_mesh_variant(prec, Q);
-        if (sv >= 0 && largest <= kSmallBatchMeshTets) variant = sv;
-    }
-    const LaunchShape shape = shape_for(prec, Q, variant);
-    int &occ = p->near_rule == BS_NEAR_EXACT ? b->meshes[0]->occ_exact[prec][Q] : b->meshes[0]->occ[prec][Q][variant];
+    int &occ = b->meshes[0]->occ[nr][prec][Q][variant];
     if (occ == 0) occ = std::max(1, velocity_ctas_per_sm(prec, Q, variant, p->near_rule));
     const int64_t BP = (int64_t)shape.threads * shape.points_per_thread;
     double total_pairs = 0.0;
@@ -1095,7 +1138,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         if (b->graph) cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
         // attributes and occupancy are set outside the capture
-        BS_CUDA(velocity_ctas_per_sm(prec, Q, variant) > 0 ? cudaSuccess : cudaErrorUnknown);
+        BS_CUDA(velocity_ctas_per_sm(prec, Q, variant, nr) > 0 ? cudaSuccess : cudaErrorUnknown);
         cudaGraph_t g = nullptr;
         BS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         int grid = 0;
@@ -1135,51 +1178,72 @@ int bs_autotune(bs_handle h, const bs_params *p, void *stream)
     int rc = check_params(p);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    const int prec = p->precision, Q = p->tet_gauss_order;
-    const int nv = num_variants(prec, Q);
-    if (nv <= 1 || h->n_tets == 0) {
-        h->variant[prec][Q] = 0;
-        return BS_OK;
+    const int prec = p->precision, Q = p->tet_gauss_order, nr = p->near_rule;
+    const int L = p->n_phi * p->n_theta;
+    const int nv = num_variants(prec, Q, nr);
+    h->tuned[nr][prec][Q] = 0;
+    // nothing to choose: no tets, or the call would run the all-ray kernel (one launch shape)
+    const char *generic_env = getenv("BS_ALLRAY_GENERIC");
+    const bool ray = isinf(p->far_ratio) && L <= kRayLinesSmemMax && !(generic_env && atoi(generic_env) != 0) &&
+                     nr == BS_NEAR_RAY;
+    if (h->n_tets == 0 || ray || nv <= 0) return BS_OK;
+    const int64_t k = h->n_nodes;  // tuned on the mesh's own nodes, the common use
+    const std::string key = tune_key(h->gpu_name, h->n_sm, prec, Q, nr, L, k, h->n_tets);
+    const char *force = getenv("BS_TUNE_FORCE");
+    if (!(force && atoi(force) != 0)) {
+        const int v = tune_lookup(key, prec, Q, nr);
+        if (v >= 0 && v < nv) {  // a cache hit: no timing
+            h->tune_memo[key] = v;
+            h->tuned[nr][prec][Q] = v;
+            return BS_OK;
+        }
     }
-    // time every variant on the mesh's own nodes (the common use), keep the fastest
+    // time every variant (each pinned in turn), keep the fastest
     double *out = nullptr;
     BS_CUDA(cudaMallocAsync((void **)&out, sizeof(double) * 3 * h->n_nodes, st));
     bs_params q = *p;
     q.counts = nullptr;
-    cudaEvent_t e0, e1;
-    BS_CUDA(cudaEventCreate(&e0));
-    BS_CUDA(cudaEventCreate(&e1));
-    float best = INFINITY;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    double best = INFINITY;
     int best_v = 0;
-    const int saved = h->variant[prec][Q];
-    const bool saved_tuned = h->tuned[prec][Q];
-    h->tuned[prec][Q] = true;  // each timed call runs exactly variant v
-    for (int v = 0; v < nv; ++v) {
-        h->variant[prec][Q] = v;
-        rc = bs_velocity(h, h->nodes, h->n_nodes, &q, out, stream);  // warm-up (also builds tables)
-        if (rc) break;
-        BS_CUDA(cudaEventRecord(e0, st));
-        for (int r = 0; r < 3 && rc == 0; ++r) rc = bs_velocity(h, h->nodes, h->n_nodes, &q, out, stream);
-        BS_CUDA(cudaEventRecord(e1, st));
-        BS_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        BS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
+    const int saved = h->pinned[nr][prec][Q];
+    for (int v = 0; v < nv && e == cudaSuccess && rc == BS_OK; ++v) {
+        h->pinned[nr][prec][Q] = v;
+        rc = bs_velocity(h, h->nodes, k, &q, out, stream);  // warm-up (also builds this variant's tables)
+        double total = 0.0;
+        int reps = 0;
+        // at least one timed call, more while they take under 20 ms in all (at most 10)
+        while (rc == BS_OK && e == cudaSuccess && reps < 10 && (reps == 0 || total < 20.0)) {
+            if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+            rc = bs_velocity(h, h->nodes, k, &q, out, stream);
+            if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.f;
+            if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+            total += ms;
+            ++reps;
+        }
+        if (reps > 0 && total / reps < best) {
+            best = total / reps;
             best_v = v;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    h->pinned[nr][prec][Q] = saved;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     cudaFreeAsync(out, st);
-    if (rc) {
-        h->variant[prec][Q] = saved;
-        h->tuned[prec][Q] = saved_tuned;
-        return rc;
-    }
-    h->variant[prec][Q] = best_v;
-    h->tuned[prec][Q] = true;
+    if (e != cudaSuccess) return cuda_fail(e, "bs_autotune");
+    if (rc) return rc;
     BS_CUDA(cudaStreamSynchronize(st));
+    int status = BS_OK;
+    if (int fs = bs_status(h, stream)) status = fs;  // a timed call that raised the flag: keep nothing
+    if (status) return status;
+    h->tune_memo[key] = best_v;
+    h->tuned[nr][prec][Q] = best_v;
+    // persisted where the cache file is writable; kept for this process in any case
+    tune_store(key, prec, Q, nr, best_v, best, nv);
     return BS_OK;
 }
 
@@ -1187,7 +1251,39 @@ int bs_tuned_variant(bs_handle h, int precision, int tet_gauss_order, int *varia
 {
     if (!h || !variant || (precision != BS_FP32 && precision != BS_FP64) || !valid_order(tet_gauss_order))
         return fail(BS_ERR_ARG, "bad argument");
-    *variant = h->variant[precision][tet_gauss_order];
+    *variant = h->tuned[BS_NEAR_RAY][precision][tet_gauss_order];
+    return BS_OK;
+}
+
+int bs_num_variants(int precision, int tet_gauss_order, int near_rule, int *n)
+{
+    if (!n || (precision != BS_FP32 && precision != BS_FP64) || (near_rule != BS_NEAR_RAY && near_rule != BS_NEAR_EXACT))
+        return fail(BS_ERR_ARG, "bad argument");
+    if (!valid_order(tet_gauss_order)) return fail(BS_ERR_ORDER, "tet_gauss_order must be 1, 4, 8, 27 or 64");
+    *n = num_variants(precision, tet_gauss_order, near_rule);
+    return BS_OK;
+}
+
+int bs_variant_shape(int precision, int tet_gauss_order, int near_rule, int variant, int32_t *shape)
+{
+    int n = 0;
+    int rc = bs_num_variants(precision, tet_gauss_order, near_rule, &n);
+    if (rc) return rc;
+    if (!shape || variant < 0 || variant >= n) return fail(BS_ERR_ARG, "variant out of range");
+    const VariantShape &s = velocity_variants(precision, tet_gauss_order, near_rule).v[variant].s;
+    const int32_t v[7] = {s.P, s.TILE, s.S, s.MINB, s.INL ? 1 : 0, s.U, s.PK ? 1 : 0};
+    for (int i = 0; i < 7; ++i) shape[i] = v[i];
+    return BS_OK;
+}
+
+int bs_set_variant(bs_handle h, int precision, int tet_gauss_order, int near_rule, int variant)
+{
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    int n = 0;
+    int rc = bs_num_variants(precision, tet_gauss_order, near_rule, &n);
+    if (rc) return rc;
+    if (variant < -1 || variant >= n) return fail(BS_ERR_ARG, "variant out of range (-1 for automatic)");
+    h->pinned[near_rule][precision][tet_gauss_order] = variant;
     return BS_OK;
 }
 

@@ -21,12 +21,15 @@ constexpr double kPi = 3.14159265358979323846;
 // far rule and the near/far test need, streamed through shared memory, with
 // w'_q = -(w_q |V| / 4pi) omega(x_q) (sign and 1/4pi of Eq. 1 folded in).
 //   double: [c (3), rho^2] then per quadrature point [x_q (3), w'_q (3)]  (4 + 6Q)
-//   float : tile frame (coordinates relative to the tile origin o):
-//           [c - o (3), rho^2] then the quadrature points in pairs (a, b), five float4 per pair,
-//           every value stored as the pair (value_a, value_b) so that one packed f32x2
-//           instruction serves both points:
+//   float : tile frame (coordinates relative to the tile origin o), in one of two layouts:
+//           quadrature-pair layout: [c - o (3), rho^2] then the quadrature points in pairs (a, b),
+//           five float4 per pair, every value stored as the pair (value_a, value_b) so that one
+//           packed f32x2 instruction serves both points:
 //           [-2x'.x, -2x'.y] [-2x'.z, |x'|^2] [w'.x, w'.y] [w'.z, B.x] [B.y, B.z]
-//           (B = x_q' x w'_q; an odd Q is padded with a point of zero weight)  (4 + 20 ceil(Q/2))
+//           (B = x_q' x w'_q; an odd Q is padded with a point of zero weight)  (4 + 20 ceil(Q/2));
+//           point-pair layout: the same five float4 per quadrature point with every value
+//           stored twice, (value, value), so that one packed instruction serves two evaluation
+//           points  (4 + 20 Q)
 // Tile header (per TILE consecutive tets): float4 [o (3), rc], float4 [rho_max, 0, 0, 0].
 //
 // Near record (one per tet, independent of the parameters): what the ray rule
@@ -39,10 +42,12 @@ constexpr double kPi = 3.14159265358979323846;
 //   double : 40 doubles  v0..v3 (12) g1 g2 g3 (9) w0..w3 (12) c (3) h Rb^2 (2) pad (2)
 //   h = longest edge, c = centroid, Rb = largest vertex distance from c.
 // ---------------------------------------------------------------------------
+constexpr int kFarQuadPairs = 0;   // float32 far-record layouts (see above)
+constexpr int kFarPointPairs = 1;
 template <typename T>
-__host__ __device__ constexpr int far_stride(int Q)
+__host__ __device__ constexpr int far_stride(int Q, int layout = kFarQuadPairs)
 {
-    return sizeof(T) == 4 ? (4 + 20 * ((Q + 1) / 2)) : (4 + 10 * Q);
+    return sizeof(T) == 4 ? (layout == kFarPointPairs ? 4 + 20 * Q : 4 + 20 * ((Q + 1) / 2)) : (4 + 10 * Q);
 }
 constexpr int kNearF32Vec4 = 15;  // float4 per near record
 namespace nf32 {
@@ -103,9 +108,9 @@ cudaError_t build_tet_rule(int order, double *bary, double *w, cudaStream_t st);
 cudaError_t build_near_records(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
                                const double *omega, float4 *near32, double *near64, double *rho2,
                                int *flag, unsigned long long *first_bad, cudaStream_t st);
-// tile headers and far records for a tet rule and tile size (needs near64 and rho2)
+// tile headers and far records for a tet rule, tile size and float32 layout (needs near64 and rho2)
 cudaError_t build_far_records(const double *near64, const double *rho2, int64_t n_tets, const TetRule &rule,
-                              int tile, float4 *hdr, float *far32, double *far64, cudaStream_t st);
+                              int tile, int layout32, float4 *hdr, float *far32, double *far64, cudaStream_t st);
 // spatial order of the evaluation points (Morton counting sort on a 2^bits grid)
 int order_grid_bits(int64_t k);
 cudaError_t spatial_order(const double *pts, int64_t k, int bits, int *box, unsigned *keys, int *count, int *perm,
@@ -161,26 +166,64 @@ constexpr int kSmemLinesMax = 256;       // direction tables up to this many lin
 struct LaunchShape {
     int points_per_thread = 2;  // P
     int threads = 128;
-    int tile = 64;  // tets per shared-memory tile
+    int tile = 64;    // tets per shared-memory tile
+    int layout = 0;   // float32 far-record layout (kFarQuadPairs / kFarPointPairs)
 };
 
-// kernel variants (points per thread, register budget) for a precision and tet rule;
-// all variants of a rule share the tile size (the far records depend on it)
-constexpr int kMaxVariants = 16;  // num_variants() never exceeds this
-int num_variants(int precision, int Q);
+// Kernel variants of the velocity kernel, per (precision, tet rule, near rule): the launch shape is
+// a template parameter of the kernel, so each variant is its own instance.
+struct VariantShape {
+    int P;      // evaluation points per thread (block of 128 P points)
+    int TILE;   // tets per pipeline stage (and per tile header)
+    int S;      // pipeline stages
+    int MINB;   // CTAs per SM the register budget is set for (__launch_bounds__)
+    bool INL;   // near-pair routine inlined in the tile loop (else called)
+    int U;      // ray bundle: lines per lane per iteration of the ray rule
+    bool PK;    // float32: packed registers pair two evaluation points (point-pair layout)
+};
+using VariantLaunch = cudaError_t (*)(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
+                                      bool query_only, int *occ_out);
+struct VariantEntry {
+    VariantShape s;
+    VariantLaunch launch;
+};
+struct VariantList {
+    const VariantEntry *v = nullptr;
+    int n = 0;
+};
+// the instances, one translation unit per family (bs_vel_*.cu); n = 0 for an unsupported rule
+VariantList variants_f32_q4();
+VariantList variants_f32_rules(int Q);  // Q = 1, 8, 27, 64
+VariantList variants_f64(int Q);
+VariantList variants_exact(int precision, int Q);
+VariantList velocity_variants(int precision, int Q, int near_rule);
+
+constexpr int kMaxVariants = 32;  // num_variants() never exceeds this
+int num_variants(int precision, int Q, int near_rule = BS_NEAR_RAY);
 // the variant with one point per thread (128-point blocks), or -1: for meshes too small to fill the GPU with
 // the default blocks, where each warp's near pairs (drained one at a time) set the time
 int small_mesh_variant(int precision, int Q);
+// a variant the fixed scratch of the no-alloc entry point can hold (quadrature-pair layout, tiles of 8..32
+// tets), preferring one point per thread for the ray rule
+int noalloc_variant(int precision, int Q, int near_rule);
 constexpr int kSmallMeshWaves = 8;  // fewer default work items than this many GPU-fulls: a small mesh
 // a batch of meshes of at most this many tets each takes the small-mesh variant (measured on 256 meshes of
 // 8^3..24^3 nodes: 551 ms against 607 ms for the default variant)
 constexpr int64_t kSmallBatchMeshTets = 80000;
-LaunchShape shape_for(int precision, int Q, int variant = 0);
+LaunchShape shape_for(int precision, int Q, int variant = 0, int near_rule = 0);
 int velocity_ctas_per_sm(int precision, int Q, int variant = 0, int near_rule = 0);
 // ev_start/ev_stop (optional) are recorded around the velocity kernel alone
 cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
                             cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);
 cudaError_t launch_reduce(const VelocityArgs &a, cudaStream_t st);
+// autotuner cache (bs_tune.cu): key of a (GPU, precision, rule, near rule, directions, size class), the
+// variant stored for it (-1 if none, or if its launch shape does not match this build), and a store that
+// also writes the cache file
+std::string variant_shape_string(int precision, int Q, int near_rule, int variant);
+std::string tune_key(const char *gpu_name, int n_sm, int precision, int Q, int near_rule, int L, int64_t k,
+                     int64_t n_tets);
+int tune_lookup(const std::string &key, int precision, int Q, int near_rule);
+bool tune_store(const std::string &key, int precision, int Q, int near_rule, int variant, double ms, int candidates);
 // all-ray kernel (bs_ray.cu): one point per thread, near records streamed in tiles of ray_shape().tile;
 // single-mesh launches (a.meshes == nullptr); the partial sums and the reduction are those of the
 // velocity kernel.  The float32 direction table is staged in shared memory: the host uses this kernel

@@ -175,11 +175,12 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
     lines.f64 = reinterpret_cast<dbl4 *>(base + kLines64);
 
     const int Q = p->tet_gauss_order;
-    // meshes within the fixed limits are small: the one-point-per-thread variant where there is one
-    const int sv = p->near_rule == BS_NEAR_RAY ? small_mesh_variant(p->precision, Q) : -1;
-    const int variant = sv >= 0 ? sv : 0;
-    const LaunchShape shape = shape_for(p->precision, Q, variant);
-    if (shape.tile > kMaxTile) return fail(BS_ERR_ARG, "bs_velocity_noalloc: tile larger than the scratch layout");
+    // meshes within the fixed limits are small: the one-point-per-thread variant where there is one, and a
+    // variant whose far records and tile headers fit the scratch layout
+    const int variant = noalloc_variant(p->precision, Q, p->near_rule);
+    const LaunchShape shape = shape_for(p->precision, Q, variant, p->near_rule);
+    if (variant < 0 || shape.tile > kMaxTile || shape.tile < 8 || shape.layout != kFarQuadPairs)
+        return fail(BS_ERR_ARG, "bs_velocity_noalloc: no kernel variant fits the scratch layout");
 
     // the per-call state that must start from zero / "none"
     if ((e = cudaMemsetAsync(flag, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
@@ -191,7 +192,8 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
                                 first_bad, st)) != cudaSuccess)
         return cuda_fail(e, "near records");
     if ((e = build_tet_rule(Q, rule.bary, rule.w, st)) != cudaSuccess) return cuda_fail(e, "tet rule");
-    if ((e = build_far_records(near64, rho2, n_tets, rule, shape.tile, hdr, far32, far64, st)) != cudaSuccess)
+    if ((e = build_far_records(near64, rho2, n_tets, rule, shape.tile, kFarQuadPairs, hdr, far32, far64, st)) !=
+        cudaSuccess)
         return cuda_fail(e, "far records");
     if ((e = build_lines(p->n_phi, p->n_theta, lines.f32, lines.f64, st)) != cudaSuccess)
         return cuda_fail(e, "direction table");

@@ -155,15 +155,15 @@ __global__ void tile_headers_kernel(const double *__restrict__ near64, const dou
     hdr[2 * t + 1] = make_float4((float)(sqrt(rmax) * (1.0 + 1e-6)), 0.f, 0.f, 0.f);
 }
 
-// float32 far record (tile frame, x' = x - o of the tet's tile):
-//   [c' (3), rho^2] then per quadrature point three float4:
-//   [-2 x_q' (3), |x_q'|^2] [w'_q (3), B_q.x] [B_q.y, B_q.z, 0, 0]
-//   with B_q = x_q' x w'_q, so that sum_q (x' - x_q') x w'_q / |x' - x_q'|^3
-//   = x' x A - B with A = sum_q w'_q / r_q^3, B = sum_q B_q / r_q^3 and
-//   r_q^2 = |x'|^2 - 2 x'.x_q' + |x_q'|^2 (small terms in the tile frame).
-// float64 far record (global frame): [c (3), rho^2] then per q [x_q (3), w'_q (3)].
+// float32 far record (tile frame, x' = x - o of the tet's tile): [c' (3), rho^2] then per
+// quadrature point the ten values [-2 x_q' (3), |x_q'|^2, w'_q (3), B_q (3)], with B_q = x_q' x w'_q,
+// so that sum_q (x' - x_q') x w'_q / |x' - x_q'|^3 = x' x A - B with A = sum_q w'_q / r_q^3,
+// B = sum_q B_q / r_q^3 and r_q^2 = |x'|^2 - 2 x'.x_q' + |x_q'|^2 (small terms in the tile frame).
+// Quadrature-pair layout: value k of point q at float 4 + 20 (q / 2) + 2k + (q % 2); point-pair layout:
+// at floats 4 + 20 q + 2k and 4 + 20 q + 2k + 1 (twice).
+// float64 far record: [c (3), rho^2] then per q the same ten values.
 __global__ void far_records_kernel(const double *__restrict__ near64, const double *__restrict__ rho2,
-                                   int64_t n_tets, int Q, int tile, const double *__restrict__ bary,
+                                   int64_t n_tets, int Q, int tile, int layout, const double *__restrict__ bary,
                                    const double *__restrict__ wq, const float4 *__restrict__ hdr,
                                    float *__restrict__ far32, double *__restrict__ far64)
 {
@@ -176,7 +176,7 @@ __global__ void far_records_kernel(const double *__restrict__ near64, const doub
         w[i] = load3(r + nf64::W + 3 * i);
     }
     const double vol = fabs(dot(sub(v[1], v[0]), cross(sub(v[2], v[0]), sub(v[3], v[0])))) / 6.0;
-    const int s32 = far_stride<float>(Q), s64 = far_stride<double>(Q);
+    const int s32 = far_stride<float>(Q, layout), s64 = far_stride<double>(Q);
     float *f = far32 + e * s32;
     double *d = far64 + e * s64;
     const float4 h = hdr[2 * (e / tile)];
@@ -205,13 +205,16 @@ __global__ void far_records_kernel(const double *__restrict__ near64, const doub
         // float64: the same tile-frame values, one point after the other
         const double vals[10] = {-2.0 * xl.x, -2.0 * xl.y, -2.0 * xl.z, dot(xl, xl), wv.x, wv.y, wv.z, B.x, B.y, B.z};
         for (int j = 0; j < 10; ++j) d[4 + 10 * q + j] = vals[j];
-        // pair q/2, slot q%2: value k of the point goes to float 2k + slot of the pair's 20
-        float *g = f + 4 + 20 * (q / 2) + (q % 2);
-        const double vals32[10] = {-2.0 * xl.x, -2.0 * xl.y, -2.0 * xl.z, dot(xl, xl), wv.x, wv.y, wv.z,
-                                   B.x, B.y, B.z};
-        for (int k = 0; k < 10; ++k) g[2 * k] = (float)vals32[k];
+        if (layout == kFarPointPairs) {
+            float *g = f + 4 + 20 * q;
+            for (int k = 0; k < 10; ++k) g[2 * k] = g[2 * k + 1] = (float)vals[k];
+        } else {
+            // pair q/2, slot q%2: value k of the point goes to float 2k + slot of the pair's 20
+            float *g = f + 4 + 20 * (q / 2) + (q % 2);
+            for (int k = 0; k < 10; ++k) g[2 * k] = (float)vals[k];
+        }
     }
-    if (Q % 2) {
+    if (layout == kFarQuadPairs && Q % 2) {
         // pad the last pair with a point of zero weight (|x - x_q| = sqrt(|x'|^2 + 1) > 0)
         float *g = f + 4 + 20 * (Q / 2) + 1;
         for (int k = 0; k < 10; ++k) g[2 * k] = (k == 3) ? 1.0f : 0.0f;
@@ -232,14 +235,15 @@ cudaError_t build_near_records(const double *nodes, int64_t n_nodes, const int32
 }
 
 cudaError_t build_far_records(const double *near64, const double *rho2, int64_t n_tets, const TetRule &rule,
-                              int tile, float4 *hdr, float *far32, double *far64, cudaStream_t st)
+                              int tile, int layout32, float4 *hdr, float *far32, double *far64, cudaStream_t st)
 {
     if (n_tets == 0) return cudaSuccess;
     const int tb = 128;
     const int64_t n_tiles = (n_tets + tile - 1) / tile;
     tile_headers_kernel<<<(unsigned)((n_tiles + tb - 1) / tb), tb, 0, st>>>(near64, rho2, n_tets, tile, hdr);
     far_records_kernel<<<(unsigned)((n_tets + tb - 1) / tb), tb, 0, st>>>(near64, rho2, n_tets, rule.order, tile,
-                                                                         rule.bary, rule.w, hdr, far32, far64);
+                                                                         layout32, rule.bary, rule.w, hdr, far32,
+                                                                         far64);
     return cudaGetLastError();
 }
 
