@@ -753,6 +753,7 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     int rc = check_params(p);
     if (rc) return rc;
     if (k < 0) return fail(BS_ERR_ARG, "k < 0");
+    if (k > INT32_MAX) return fail(BS_ERR_ARG, "k exceeds the int32 index range");
     if (k == 0) return BS_OK;
     if (!eval_pts_dev || !out_dev) return fail(BS_ERR_ARG, "NULL points or output");
     cudaStream_t st = (cudaStream_t)stream;
@@ -810,8 +811,7 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     a.m.perm = h->perm;
     a.m.k = k;
     a.Q = Q;
-    a.far_ratio2 = isinf(p->far_ratio) ? INFINITY : p->far_ratio * p->far_ratio;
-    a.all_ray = isinf(p->far_ratio) ? 1 : 0;
+    set_far_ratio(a, p->far_ratio);
     a.lines = h->lines;
     a.L = L;
     a.smem_lines = a.L <= (ray ? kRayLinesSmemMax : kSmemLinesMax) ? 1 : 0;
@@ -826,6 +826,7 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     a.skip = skip;
     a.near_rule = p->near_rule;
     a.n_items = n_blocks * n_chunks;
+    if (a.n_items > INT32_MAX) return fail(BS_ERR_ARG, "too many work items for one launch (points x tet chunks)");
     a.wait_polls = h->copy_wait_polls;
     a.withhold_copies = h->withhold_copies;
     int grid = 0;
@@ -1113,10 +1114,10 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     a.meshes = b->d_meshes;
     a.n_meshes = n;
     a.n_items = items;
+    if (items > INT32_MAX) return fail(BS_ERR_ARG, "too many work items for one batch launch");
     a.n_points = b->n_points;
     a.Q = Q;
-    a.far_ratio2 = isinf(p->far_ratio) ? INFINITY : p->far_ratio * p->far_ratio;
-    a.all_ray = isinf(p->far_ratio) ? 1 : 0;
+    set_far_ratio(a, p->far_ratio);
     a.lines = b->lines;
     a.L = p->n_phi * p->n_theta;
     a.smem_lines = a.L <= kSmemLinesMax ? 1 : 0;

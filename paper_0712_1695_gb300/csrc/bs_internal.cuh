@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <string>
@@ -142,6 +143,7 @@ struct VelocityArgs {
     // rule
     int Q = 4;
     double far_ratio2 = 4.0;  // +inf for all-ray
+    float far_ratio2_f = 4.0f, far_ratio_f = 2.0f;  // the same in float, and the far ratio (+inf for all-ray)
     int all_ray = 0;
     LineTables lines;
     int L = 0;
@@ -159,6 +161,16 @@ struct VelocityArgs {
     long long wait_polls = 0;
     int withhold_copies = 0;
 };
+
+// far ratio of a launch: its square (+inf for the all-ray rule) in double and float, the ratio in float
+inline void set_far_ratio(VelocityArgs &a, double far_ratio)
+{
+    const bool inf = far_ratio > 1e300;
+    a.far_ratio2 = inf ? (double)INFINITY : far_ratio * far_ratio;
+    a.far_ratio2_f = (float)a.far_ratio2;
+    a.far_ratio_f = inf ? INFINITY : (float)sqrt(a.far_ratio2);
+    a.all_ray = inf ? 1 : 0;
+}
 
 constexpr int64_t kMinTilesPerItem = 2;  // work items shorter than this are dominated by their set-up
 constexpr int kSmemLinesMax = 256;       // direction tables up to this many lines live in shared memory

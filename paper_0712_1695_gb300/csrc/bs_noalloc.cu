@@ -228,8 +228,7 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
     a.m.perm = perm;
     a.m.k = k;
     a.Q = Q;
-    a.far_ratio2 = isinf(fr) ? INFINITY : fr * fr;
-    a.all_ray = isinf(fr) ? 1 : 0;
+    set_far_ratio(a, fr);
     a.lines = lines;
     a.L = p->n_phi * p->n_theta;
     a.smem_lines = a.L <= kSmemLinesMax ? 1 : 0;

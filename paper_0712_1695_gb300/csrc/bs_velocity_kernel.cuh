@@ -406,22 +406,23 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
     Pipe<S> *pipe = reinterpret_cast<Pipe<S> *>(carve.take(sizeof(Pipe<S>)));
     MeshDesc *s_md = reinterpret_cast<MeshDesc *>(carve.take(sizeof(MeshDesc)));
     int64_t *s_item = reinterpret_cast<int64_t *>(carve.take(16));
-    float4 *sdir = reinterpret_cast<float4 *>(carve.take(a.smem_lines ? sizeof(float4) * a.L : 0));
     // per-point state, touched once per tile: compensated sums [NACC][BP] and counts [2][BP]
     // (near pairs, chord hits); the warp's bounding sphere [NW]
     T *sacc = reinterpret_cast<T *>(carve.take(sizeof(T) * NACC * BP));
     int *scnt = reinterpret_cast<int *>(carve.take(sizeof(int) * 2 * BP));
     float4 *swarp = reinterpret_cast<float4 *>(carve.take(sizeof(float4) * NW));
-    // direction table: a shared copy when it fits in the launch's dynamic shared memory
-    const float4 *slines = a.lines.f32;
-    if (F32 && a.smem_lines) {
+    // direction table last: its size depends on the launch, every region above has a fixed offset
+    float4 *sdir = reinterpret_cast<float4 *>(carve.take(a.smem_lines ? sizeof(float4) * a.L : 0));
+    if (F32 && a.smem_lines)
         for (int l = threadIdx.x; l < a.L; l += NT) sdir[l] = a.lines.f32[l];
-        slines = sdir;
-    }
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const T fr2 = (T)a.far_ratio2;
-    const float fr = a.all_ray ? INFINITY : (float)sqrt(a.far_ratio2);
+    // far ratio squared in T, and the far ratio in float (+inf for the all-ray rule): kernel parameters
+    // read where they are used, not held in registers across the loops
+    auto fr2 = [&]() -> T {
+        if constexpr (F32) return a.far_ratio2_f;
+        else return a.far_ratio2;
+    };
     const MeshDesc &md = *s_md;  // mesh of the current item (shared memory)
 
     if (tid == 0) {
@@ -434,8 +435,8 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
     __syncthreads();
     uint32_t phase = 0u;  // bit st: parity of the next completion of full[st]
 
-    auto issue = [&](int64_t t, int st) {
-        const int64_t first = t * TILE;
+    auto issue = [&](int t, int st) {
+        const int64_t first = (int64_t)t * TILE;
         const int cnt = (int)min((int64_t)TILE, md.n_tets - first);
         const uint32_t bytes = (uint32_t)cnt * RS * sizeof(T);
         unsigned char *dst = stages + st * STAGE_BYTES;
@@ -445,7 +446,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
         bulk_g2s(dst, md.tile_hdr + 2 * t, HDR_BYTES, &pipe->full[st]);
         bulk_g2s(dst + HDR_BYTES, reinterpret_cast<const T *>(md.far) + first * RS, bytes, &pipe->full[st]);
     };
-    const long long wait_cap = a.wait_polls > 0 ? a.wait_polls : kWaitCap;
+    auto wait_cap = [&]() -> long long { return a.wait_polls > 0 ? a.wait_polls : kWaitCap; };
 
     for (;;) {
         if (tid == 0) {
@@ -470,22 +471,23 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
             *s_item = item;
         }
         __syncthreads();
-        const int64_t item = *s_item;
+        // 32-bit item arithmetic: points, tiles and work items of a launch are below 2^31 (the host checks)
+        const int item = (int)*s_item;
         if (item < 0) break;
-        const int64_t k = md.k;
-        const int64_t n_blocks = (k + BP - 1) / BP;
-        const int64_t n_tiles = (md.n_tets + TILE - 1) / TILE;
-        const int64_t pb = item % n_blocks, ck = item / n_blocks;
-        const int64_t t0 = ck * md.tiles_per_chunk;
-        const int64_t t1 = min(t0 + (int64_t)md.tiles_per_chunk, n_tiles);
-        const int n_local = (int)(t1 - t0);
+        const int k = (int)md.k;
+        const int n_blocks = (k + BP - 1) / BP;
+        const int n_tiles = (int)((md.n_tets + TILE - 1) / TILE);
+        const int pb = item % n_blocks, ck = item / n_blocks;
+        const int t0 = ck * md.tiles_per_chunk;
+        const int t1 = min(t0 + md.tiles_per_chunk, n_tiles);
+        const int n_local = t1 - t0;
 
         // prologue: fill every stage while the points are loaded
         if (tid == 0)
             for (int i = 0; i < S && i < n_local; ++i) issue(t0 + i, i);
 
         for (int i = tid; i < BP; i += NT) {
-            int64_t gi = pb * BP + i;
+            int gi = pb * BP + i;
             if (gi >= k) gi = k - 1;  // pad with a real point; its result is not written
             const int64_t src = md.perm[gi];
 #pragma unroll
@@ -534,9 +536,9 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
 #pragma unroll 1
         for (int i = 0; i < n_local; ++i) {
             const int st = i % S;
-            const int64_t t = t0 + i;
+            const int t = t0 + i;
             // the warp gives up as one (a lane that saw the copy land leaves with the others)
-            if (!__all_sync(0xffffffffu, mbar_wait(&pipe->full[st], (phase >> st) & 1u, wait_cap))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(&pipe->full[st], (phase >> st) & 1u, wait_cap()))) {
                 aborted = true;
                 break;
             }
@@ -551,9 +553,9 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                 const float dx = cw.x - hd.x, dy = cw.y - hd.y, dz = cw.z - hd.z;
                 const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
                 const float scale = fabsf(hd.x) + fabsf(hd.y) + fabsf(hd.z) + dist;
-                culled = dist - cw.w - hd.w > fr * sh[1].x * 1.001f + 1e-5f * scale;
+                culled = dist - cw.w - hd.w > a.far_ratio_f * sh[1].x * 1.001f + 1e-5f * scale;
             }
-            const int cnt = (int)min((int64_t)TILE, md.n_tets - t * TILE);
+            const int cnt = (int)min((int64_t)TILE, md.n_tets - (int64_t)t * TILE);
             int qn = 0;  // warp-uniform
             // this warp is done with stage st (the near pairs read global memory only);
             // the last warp to finish refills it
@@ -613,7 +615,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         bool nearp[P];
                         if constexpr (MIXED) {
                             const float4 h0 = rec[0];
-                            const float thr2 = fr2 * h0.w;
+                            const float thr2 = fr2() * h0.w;
 #pragma unroll
                             for (int p = 0; p < P; ++p) {
                                 const float dx = xl(p, 0) - h0.x, dy = xl(p, 1) - h0.y, dz = xl(p, 2) - h0.z;
@@ -717,7 +719,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             const float *sp = spts + 9 * (warp * 32 * P + pp * 32 + owner);
                             const V3<double> xd = mk(join3(sp[0], sp[1], sp[2]), join3(sp[3], sp[4], sp[5]),
                                                      join3(sp[6], sp[7], sp[8]));
-                            const Vel64 o = tet_exact<true>(xd, md.near64 + (t * TILE + j) * kNearF64);
+                            const Vel64 o = tet_exact<true>(xd, md.near64 + ((int64_t)t * TILE + j) * kNearF64);
                             ox = (float)o.x;
                             oy = (float)o.y;
                             oz = (float)o.z;
@@ -742,7 +744,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         unsigned m = wm[e];
                         const int code = wc[e];
                         const int pp = code >> 8, j = code & 255;
-                        const int64_t tet = t * TILE + j;
+                        const int64_t tet = (int64_t)t * TILE + j;
                         if (j != held) {
                             __syncwarp();
                             if (lane < kNearF32Vec4)
@@ -758,10 +760,12 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             NearOut32 o;
                             if constexpr (INL)
                                 o = near_pair_f32_body<U>(spts + 9 * bi, srec + warp * kNearF32Vec4,
-                                                          md.near64 + tet * kNearF64, slines, a.lines.f64, a.L, lane);
+                                                          md.near64 + tet * kNearF64, a.smem_lines ? sdir : a.lines.f32,
+                                                          a.lines.f64, a.L, lane);
                             else
                                 o = near_pair_f32<U>(spts + 9 * bi, srec + warp * kNearF32Vec4,
-                                                     md.near64 + tet * kNearF64, slines, a.lines.f64, a.L, lane);
+                                                     md.near64 + tet * kNearF64, a.smem_lines ? sdir : a.lines.f32,
+                                                     a.lines.f64, a.L, lane);
                             if (lane == owner) {
                                 kahan(bi, o.vx, o.vy, o.vz);
                                 scnt[BP + bi] += o.hits;
@@ -791,7 +795,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                 for (int j = 0; j < cnt; ++j) {
                     const double *rec = tb + j * RS;
                     bool nearp[P];
-                    const double thr2 = fr2 * rec[3];
+                    const double thr2 = fr2() * rec[3];
 #pragma unroll
                     for (int p = 0; p < P; ++p) {
                         const double dx = xp[p].x - rec[0], dy = xp[p].y - rec[1], dz = xp[p].z - rec[2];
@@ -850,7 +854,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             const float *sp = spts + 9 * (warp * 32 * P + pp * 32 + owner);
                             const V3<double> xd = mk(join3(sp[0], sp[1], sp[2]), join3(sp[3], sp[4], sp[5]),
                                                      join3(sp[6], sp[7], sp[8]));
-                            o = tet_exact<false>(xd, md.near64 + (t * TILE + j) * kNearF64);
+                            o = tet_exact<false>(xd, md.near64 + ((int64_t)t * TILE + j) * kNearF64);
                             tag = 1 | (pp << 1) | (owner << 8);
                         }
                         cursor_advance(cur, wm, qn);
@@ -880,7 +884,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         unsigned m = wm[e];
                         const int code = wc[e];
                         const int pp = code >> 8, j = code & 255;
-                        const int64_t tet = t * TILE + j;
+                        const int64_t tet = (int64_t)t * TILE + j;
 #pragma unroll 1
                         while (m) {
                             const int owner = __ffs(m) - 1;
@@ -912,16 +916,16 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
         }
         if (aborted) {
             if (tid == 0) atomicOr(a.flag, kFlagTimeout);
-            mbar_drain<S>(pipe->full, phase, wait_cap);
+            mbar_drain<S>(pipe->full, phase, wait_cap());
             return;
         }
 
-        const int64_t ntets_chunk = min(md.n_tets, t1 * TILE) - t0 * TILE;
+        const int64_t ntets_chunk = min(md.n_tets, (int64_t)t1 * TILE) - (int64_t)t0 * TILE;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const int64_t gi = pb * BP + warp * 32 * P + p * 32 + lane;  // position in the spatial order
+            const int gi = pb * BP + warp * 32 * P + p * 32 + lane;  // position in the spatial order
             if (gi >= k) continue;
-            double *dst = md.partial + (ck * k + gi) * 3;
+            double *dst = md.partial + ((int64_t)ck * k + gi) * 3;
             const int sl = slot0 + 32 * p;
 #pragma unroll
             for (int jj = 0; jj < 3; ++jj) {
