@@ -296,11 +296,12 @@ BS_API int bs_batch_destroy(bs_batch b);
  * The velocity kernel is compiled in several variants per (precision, tet
  * rule, near rule), each a launch shape: evaluation points per thread, tets
  * per shared-memory tile, pipeline stages, CTAs per SM its registers are
- * budgeted for, near-pair routine inlined or called, ray bundle (lines each
- * lane takes per iteration of the ray rule), and how the far sweep pairs
- * values in its packed float32x2 registers (two quadrature points, or two
- * evaluation points).  Every variant computes the same rule; results differ
- * only by rounding.
+ * budgeted for, how the near pairs are drained (routine called, inlined, or
+ * inlined with the pair's state in shared memory), ray bundle (lines each
+ * lane takes per iteration of the ray rule), how the far sweep pairs values
+ * in its packed float32x2 registers (two quadrature points, or two
+ * evaluation points), and the unroll of the far sweep's tet loop.  Every
+ * variant computes the same rule; results differ only by rounding.
  *
  * Which variant a bs_velocity call uses: the environment variable BS_VARIANT
  * if set (every call), else the variant pinned by bs_set_variant, else the
@@ -319,10 +320,12 @@ BS_API int bs_batch_destroy(bs_batch b);
 
 /* Number of variants for a precision, tet rule and near rule. */
 BS_API int bs_num_variants(int precision, int tet_gauss_order, int near_rule, int *n);
-/* Launch shape of a variant: shape[0..6] = points per thread, tets per tile,
- * pipeline stages, CTAs per SM of the register budget, near routine inlined
- * (1) or called (0), ray bundle (lines per lane per iteration), far sweep
- * pairing two evaluation points (1) or two quadrature points (0). */
+/* Launch shape of a variant: shape[0..7] = points per thread, tets per tile,
+ * pipeline stages, CTAs per SM of the register budget, near-pair drain
+ * (0 routine called, 1 inlined, 2 inlined with the pair's state in shared
+ * memory), ray bundle (lines per lane per iteration), far sweep pairing two
+ * evaluation points (1) or two quadrature points (0), unroll of the far
+ * sweep's tet loop. */
 BS_API int bs_variant_shape(int precision, int tet_gauss_order, int near_rule, int variant, int32_t *shape);
 /* Pin a variant for this handle's calls with this precision, tet rule and
  * near rule (-1 restores the automatic choice).  Errors: BS_ERR_ARG (variant

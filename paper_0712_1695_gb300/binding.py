@@ -308,7 +308,8 @@ def bs_create(nodes, tets, omega) -> Mesh:
     return Mesh(nodes, tets, omega)
 
 
-VARIANT_FIELDS = ("points_per_thread", "tile", "stages", "ctas_per_sm", "inlined", "ray_bundle", "point_pairs")
+VARIANT_FIELDS = ("points_per_thread", "tile", "stages", "ctas_per_sm", "near_drain", "ray_bundle", "point_pairs",
+                  "tet_unroll")
 
 
 def bs_num_variants(precision: int, tet_gauss_order: int, near_rule: int = BS_NEAR_RAY) -> int:
@@ -318,7 +319,7 @@ def bs_num_variants(precision: int, tet_gauss_order: int, near_rule: int = BS_NE
 
 
 def bs_variant_shape(precision: int, tet_gauss_order: int, near_rule: int, variant: int) -> dict:
-    s = (ctypes.c_int32 * 7)()
+    s = (ctypes.c_int32 * 8)()
     _check(load().bs_variant_shape(int(precision), int(tet_gauss_order), int(near_rule), int(variant), s))
     return dict(zip(VARIANT_FIELDS, list(s)))
 

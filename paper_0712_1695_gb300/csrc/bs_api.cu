@@ -1272,8 +1272,8 @@ int bs_variant_shape(int precision, int tet_gauss_order, int near_rule, int vari
     if (rc) return rc;
     if (!shape || variant < 0 || variant >= n) return fail(BS_ERR_ARG, "variant out of range");
     const VariantShape &s = velocity_variants(precision, tet_gauss_order, near_rule).v[variant].s;
-    const int32_t v[7] = {s.P, s.TILE, s.S, s.MINB, s.INL ? 1 : 0, s.U, s.PK ? 1 : 0};
-    for (int i = 0; i < 7; ++i) shape[i] = v[i];
+    const int32_t v[8] = {s.P, s.TILE, s.S, s.MINB, s.DR, s.U, s.PK ? 1 : 0, s.UJ};
+    for (int i = 0; i < 8; ++i) shape[i] = v[i];
     return BS_OK;
 }
 

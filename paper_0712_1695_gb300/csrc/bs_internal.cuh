@@ -189,9 +189,10 @@ struct VariantShape {
     int TILE;   // tets per pipeline stage (and per tile header)
     int S;      // pipeline stages
     int MINB;   // CTAs per SM the register budget is set for (__launch_bounds__)
-    bool INL;   // near-pair routine inlined in the tile loop (else called)
+    int DR;     // near-pair drain: routine called (0), inlined (1), inlined with the pair's state in shared memory (2)
     int U;      // ray bundle: lines per lane per iteration of the ray rule
     bool PK;    // float32: packed registers pair two evaluation points (point-pair layout)
+    int UJ;     // float32 far sweep: tet loop unrolled by UJ
 };
 using VariantLaunch = cudaError_t (*)(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
                                       bool query_only, int *occ_out);

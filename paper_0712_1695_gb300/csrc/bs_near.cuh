@@ -241,5 +241,65 @@ __device__ __noinline__ bool line_f64_lean(V3<double> x, const double *__restric
     return true;
 }
 
+// The same, inlined (the lean drain of the velocity kernel runs it where little else is live).
+__device__ __forceinline__ bool line_f64_lean_inl(V3<double> x, const double *__restrict__ r, int vk, const dbl4 ln,
+                                           V3<double> &acc)
+{
+    const V3<double> s = mk(ln.x, ln.y, ln.z);
+    {
+        const V3<double> rc = mk(r[nf64::C] - x.x, r[nf64::C + 1] - x.y, r[nf64::C + 2] - x.z);
+        const double rs = dot3(rc, s);
+        if (dot3(rc, rc) - rs * rs > r[nf64::RB2] * (1.0 + kBoundPadD)) return false;
+    }
+    double a[4], b[4];
+    {
+        const V3<double> d0 = mk(x.x - r[nf64::V], x.y - r[nf64::V + 1], x.z - r[nf64::V + 2]);
+        double sa = 0.0, sb = 0.0;
+        for (int i = 1; i < 4; ++i) {
+            const V3<double> g = mk(r[nf64::G + 3 * i - 3], r[nf64::G + 3 * i - 2], r[nf64::G + 3 * i - 1]);
+            a[i] = dot3(g, d0);
+            b[i] = dot3(g, s);
+            sa += a[i];
+            sb += b[i];
+        }
+        a[0] = 1.0 - sa;
+        b[0] = -sb;
+        if (vk >= 0)
+            for (int i = 0; i < 4; ++i) a[i] = (i == vk) ? 1.0 : 0.0;
+    }
+    double lo = -INFINITY, hi = INFINITY;
+    bool empty = false;
+    for (int i = 0; i < 4; ++i) {
+        V3<double> g;
+        if (i == 0) {
+            g = mk(0.0, 0.0, 0.0);
+            for (int j = 1; j < 4; ++j) {
+                g.x -= r[nf64::G + 3 * j - 3];
+                g.y -= r[nf64::G + 3 * j - 2];
+                g.z -= r[nf64::G + 3 * j - 1];
+            }
+        } else {
+            g = mk(r[nf64::G + 3 * i - 3], r[nf64::G + 3 * i - 2], r[nf64::G + 3 * i - 1]);
+        }
+        if (b[i] * b[i] <= kParD * kParD * dot3(g, g)) empty = empty || (a[i] < -kParD);
+        else if (b[i] > 0.0) lo = fmax(lo, -a[i] / b[i]);
+        else hi = fmin(hi, -a[i] / b[i]);
+    }
+    if (empty || !(hi - lo > kTau * r[nf64::H])) return false;
+    const double f1 = fabs(hi) - fabs(lo);
+    const double f2 = 0.5 * (hi * fabs(hi) - lo * fabs(lo));
+    V3<double> J = mk(0.0, 0.0, 0.0);
+    for (int i = 0; i < 4; ++i) {
+        const double c = f1 * a[i] + f2 * b[i];
+        J.x += c * r[nf64::W + 3 * i];
+        J.y += c * r[nf64::W + 3 * i + 1];
+        J.z += c * r[nf64::W + 3 * i + 2];
+    }
+    acc.x += ln.w * (s.y * J.z - s.z * J.y);
+    acc.y += ln.w * (s.z * J.x - s.x * J.z);
+    acc.z += ln.w * (s.x * J.y - s.y * J.x);
+    return true;
+}
+
 }  // namespace
 }  // namespace bs

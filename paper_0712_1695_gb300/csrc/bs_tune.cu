@@ -144,8 +144,8 @@ std::string variant_shape_string(int precision, int Q, int near_rule, int varian
     if (variant < 0 || variant >= vl.n) return std::string();
     const VariantShape &s = vl.v[variant].s;
     char b[96];
-    snprintf(b, sizeof b, "P%d T%d S%d B%d %s U%d %s", s.P, s.TILE, s.S, s.MINB, s.INL ? "inl" : "call", s.U,
-             s.PK ? "pp" : "qp");
+    snprintf(b, sizeof b, "P%d T%d S%d B%d D%d U%d %s J%d", s.P, s.TILE, s.S, s.MINB, s.DR, s.U, s.PK ? "pp" : "qp",
+             s.UJ);
     return b;
 }
 

@@ -6,7 +6,7 @@ namespace bs {
 namespace {
 
 #define BS_V(T, Q, P, TILE, S, MINB, INL) \
-    { {P, TILE, S, MINB, INL, 1, false}, &launch_t<T, Q, P, 128, TILE, S, MINB, INL, true, 1, false> }
+    { {P, TILE, S, MINB, INL, 1, false, 1}, &launch_t<T, Q, P, 128, TILE, S, MINB, INL, true, 1, false, 1> }
 
 const VariantEntry kF32Q1[] = {BS_V(float, 1, 2, 32, 4, 4, true)};
 const VariantEntry kF32Q4[] = {BS_V(float, 4, 3, 32, 2, 4, true), BS_V(float, 4, 1, 32, 4, 5, false)};

@@ -6,7 +6,7 @@ namespace bs {
 namespace {
 
 #define BS_V(Q, P, TILE, S, MINB, INL, U, PK) \
-    { {P, TILE, S, MINB, INL, U, PK}, &launch_t<float, Q, P, 128, TILE, S, MINB, INL, false, U, PK> }
+    { {P, TILE, S, MINB, INL, U, PK, 1}, &launch_t<float, Q, P, 128, TILE, S, MINB, INL, false, U, PK, 1> }
 
 const VariantEntry kF32Q1[] = {BS_V(1, 2, 32, 4, 4, true, 1, false), BS_V(1, 1, 32, 4, 5, false, 1, false),
                                BS_V(1, 4, 32, 2, 4, true, 1, true), BS_V(1, 2, 32, 4, 4, true, 1, true)};

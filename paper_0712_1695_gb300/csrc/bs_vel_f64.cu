@@ -5,7 +5,7 @@ namespace bs {
 namespace {
 
 #define BS_V(Q, P, TILE, S, MINB) \
-    { {P, TILE, S, MINB, true, 1, false}, &launch_t<double, Q, P, 128, TILE, S, MINB, true, false, 1, false> }
+    { {P, TILE, S, MINB, 1, 1, false, 1}, &launch_t<double, Q, P, 128, TILE, S, MINB, 1, false, 1, false, 1> }
 
 const VariantEntry kF64Q1[] = {BS_V(1, 2, 32, 4, 4), BS_V(1, 1, 32, 4, 4)};
 const VariantEntry kF64Q4[] = {BS_V(4, 1, 32, 2, 4), BS_V(4, 2, 32, 2, 3), BS_V(4, 1, 64, 2, 4), BS_V(4, 1, 16, 3, 4)};

@@ -273,6 +273,169 @@ __device__ __forceinline__ NearOut32 near_pair_f32_body(const float *__restrict_
     return o;
 }
 
+// Shared-memory load the compiler may not hoist or merge (the lean drain reads its per-pair values
+// per line on purpose, so that they do not occupy registers across the line loop).
+__device__ __forceinline__ float4 lds4(const float4 *p)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(smem_u32(p)));
+    return v;
+}
+
+// The lean form of near_pair_f32_body: the same ray rule, the same float64 fallbacks, but the
+// pair's warp-uniform values (barycentric coordinates a_i of the point, the parallel and
+// vertex-fallback thresholds, W_a, the centroid offset and the bounding test, g_0, the chord
+// threshold) are written once to the warp's shared slot (kPairSlotVec4 float4) and read back per
+// line, with the face gradients and nodal vorticity read from the staged near record.  The drain
+// then holds only a line's temporaries in registers, so the kernel's far sweep keeps its registers.
+constexpr int kPairSlotVec4 = 6;
+// The pairs that need float64 steps (the point on an edge or face of the tet, or lines nearly in a face
+// through the point's vertex) are not finished here: *redo is set (warp-uniform), *vk_out and *whole_out
+// say how, and the caller runs line_fallback_f64_inl for the pair later.
+template <int U>
+__device__ __forceinline__ NearOut32 near_pair_f32_lean(const float *__restrict__ xs, const float4 *__restrict__ r32,
+                                                        const float4 *__restrict__ lines, int L, int lane, float4 *slot,
+                                                        bool *redo_out, int *vk_out, bool *whole_out)
+{
+    const float xh0 = xs[0], xm0 = xs[1], xh1 = xs[3], xm1 = xs[4], xh2 = xs[6], xm2 = xs[7];
+    int vk = -1;
+    {
+        const float *vh = reinterpret_cast<const float *>(r32 + nf32::VH);
+        const float *vm = reinterpret_cast<const float *>(r32 + nf32::VM);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (vk < 0 && vh[3 * i] == xh0 && vm[3 * i] == xm0 && vh[3 * i + 1] == xh1 && vm[3 * i + 1] == xm1 &&
+                vh[3 * i + 2] == xh2 && vm[3 * i + 2] == xm2)
+                vk = i;
+    }
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    int hits = 0;
+    bool any_redo = false;
+    bool whole_f64 = false;
+    __syncwarp();  // every lane is done with the slot's previous pair
+    {
+        const float4 q0 = r32[nf32::G1], q1 = r32[nf32::G2], q2 = r32[nf32::G3];
+        const V3<float> g1 = mk(q0.x, q0.y, q0.z), g2 = mk(q1.x, q1.y, q1.z), g3 = mk(q2.x, q2.y, q2.z);
+        const V3<float> g0 = mk(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
+        float a[4];
+        if (vk >= 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = (i == vk) ? 1.0f : 0.0f;
+        } else {
+            const float *vh = reinterpret_cast<const float *>(r32 + nf32::VH);
+            const float *vm = reinterpret_cast<const float *>(r32 + nf32::VM);
+            const V3<float> d0 = mk((xh0 - vh[0]) + (xm0 - vm[0]), (xh1 - vh[1]) + (xm1 - vm[1]),
+                                    (xh2 - vh[2]) + (xm2 - vm[2]));
+            a[1] = dot3(g1, d0);
+            a[2] = dot3(g2, d0);
+            a[3] = dot3(g3, d0);
+            a[0] = 1.0f - a[1] - a[2] - a[3];
+            const float amin = fminf(fminf(a[0], a[1]), fminf(a[2], a[3]));
+            const float aabs = fminf(fminf(fabsf(a[0]), fabsf(a[1])), fminf(fabsf(a[2]), fabsf(a[3])));
+            whole_f64 = amin > -kDegenA && aabs < kDegenA;
+        }
+        if (!whole_f64 && lane == 0) {
+            float wa[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 t = r32[nf32::W + i];
+                wa[0] += a[i] * t.x;
+                wa[1] += a[i] * t.y;
+                wa[2] += a[i] * t.z;
+            }
+            const float4 ch = r32[nf32::CH], cm = r32[nf32::CM];
+            const V3<float> rc = mk((ch.x - xh0) + (cm.x - xm0), (ch.y - xh1) + (cm.y - xm1), (ch.z - xh2) + (cm.z - xm2));
+            const V3<float> gg[4] = {g0, g1, g2, g3};
+            float par2[4], fb2[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float n2 = dot3(gg[i], gg[i]);
+                par2[i] = kParF * kParF * n2;
+                fb2[i] = (vk >= 0 && i != vk) ? kVertexFallback * kVertexFallback * n2 : -1.0f;
+            }
+            slot[0] = make_float4(a[0], a[1], a[2], a[3]);
+            slot[1] = make_float4(par2[0], par2[1], par2[2], par2[3]);
+            slot[2] = make_float4(fb2[0], fb2[1], fb2[2], fb2[3]);
+            slot[3] = make_float4(wa[0], wa[1], wa[2], dot3(rc, rc));
+            slot[4] = make_float4(rc.x, rc.y, rc.z, q1.w * (1.0f + kBoundPadF));
+            slot[5] = make_float4(g0.x, g0.y, g0.z, (float)kTau * q0.w);
+        }
+    }
+    __syncwarp();
+    if (!whole_f64) {
+        auto line = [&](const float4 ln) {
+            const V3<float> s = mk(ln.x, ln.y, ln.z);
+            const float4 rcb = lds4(slot + 4);
+            const float rs = rcb.x * s.x + rcb.y * s.y + rcb.z * s.z;
+            if (lds4(slot + 3).w - rs * rs > rcb.w) return;
+            const float4 q0 = lds4(r32 + nf32::G1), q1 = lds4(r32 + nf32::G2), q2 = lds4(r32 + nf32::G3);
+            const float4 gz = lds4(slot + 5);
+            float b[4];
+            b[1] = q0.x * s.x + q0.y * s.y + q0.z * s.z;
+            b[2] = q1.x * s.x + q1.y * s.y + q1.z * s.z;
+            b[3] = q2.x * s.x + q2.y * s.y + q2.z * s.z;
+            b[0] = -(b[1] + b[2] + b[3]);
+            const float4 f4 = lds4(slot + 2);
+            const float fb2[4] = {f4.x, f4.y, f4.z, f4.w};
+            bool redo = false;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) redo = redo || (b[i] * b[i] <= fb2[i]);
+            if (redo) {
+                any_redo = true;
+                return;
+            }
+            const float4 p4 = lds4(slot + 1), a4 = lds4(slot);
+            const float par2[4] = {p4.x, p4.y, p4.z, p4.w}, a[4] = {a4.x, a4.y, a4.z, a4.w};
+            float lo = -INFINITY, hi = INFINITY;
+            bool empty = false;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (b[i] * b[i] <= par2[i]) empty = empty || (a[i] < -kParF);
+                else if (b[i] > 0.f) lo = fmaxf(lo, -a[i] / b[i]);
+                else hi = fminf(hi, -a[i] / b[i]);
+            }
+            if (empty || !(hi - lo > gz.w)) return;
+            float Wb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 t = lds4(r32 + nf32::W + i);
+                Wb[0] += b[i] * t.x;
+                Wb[1] += b[i] * t.y;
+                Wb[2] += b[i] * t.z;
+            }
+            const float4 wa = lds4(slot + 3);
+            const float f1 = fabsf(hi) - fabsf(lo);
+            const float f2 = 0.5f * (hi * fabsf(hi) - lo * fabsf(lo));
+            const V3<float> J = mk(f1 * wa.x + f2 * Wb[0], f1 * wa.y + f2 * Wb[1], f1 * wa.z + f2 * Wb[2]);
+            ax += ln.w * (s.y * J.z - s.z * J.y);
+            ay += ln.w * (s.z * J.x - s.x * J.z);
+            az += ln.w * (s.x * J.y - s.y * J.x);
+            ++hits;
+        };
+#pragma unroll 1
+        for (int l0 = lane; l0 < L; l0 += 32 * U) {
+            float4 ln[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                ln[u] = (l0 + 32 * u < L) ? lines[l0 + 32 * u] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (l0 + 32 * u < L) line(ln[u]);
+        }
+    }
+    *redo_out = whole_f64 || __any_sync(0xffffffffu, any_redo);
+    *vk_out = vk;
+    *whole_out = whole_f64;
+    NearOut32 o;
+    o.vx = warp_sum(ax);
+    o.vy = warp_sum(ay);
+    o.vz = warp_sum(az);
+    o.hits = warp_sum(hits);
+    return o;
+}
+
 template <int U>
 __device__ __noinline__ NearOut32 near_pair_f32(const float *__restrict__ xs, const float4 *__restrict__ r32,
                                                 const double *__restrict__ r64, const float4 *__restrict__ lines,
@@ -311,6 +474,40 @@ __device__ __noinline__ void line_fallback_f64(V3<double> x, const float *__rest
             const bool redo = (vk != 0 && b0 * b0 <= f * dot3(g0, g0)) || (vk != 1 && b1 * b1 <= f * dot3(g1, g1)) ||
                               (vk != 2 && b2 * b2 <= f * dot3(g2, g2)) || (vk != 3 && b3 * b3 <= f * dot3(g3, g3));
             if (redo && line_f64_lean(x, r64, vk, lines64[l], acc)) ++hits;
+        }
+    }
+}
+
+// The same float64 steps, inlined (with the float64 line routine inlined too): the lean drain runs them
+// after a queue entry's pairs, where little else is live, instead of calling out from the pair routine.
+__device__ __forceinline__ void line_fallback_f64_inl(V3<double> x, const float *__restrict__ xs,
+                                               const float4 *__restrict__ r32, const double *__restrict__ r64,
+                                               const float4 *__restrict__ lines, const dbl4 *__restrict__ lines64,
+                                               int L, int lane, int vk, bool whole_f64, V3<double> &acc, int &hits)
+{
+    const float xh0 = xs[0], xm0 = xs[1], xh1 = xs[3], xm1 = xs[4], xh2 = xs[6], xm2 = xs[7];
+    if (whole_f64) {
+#pragma unroll 1
+        for (int l = lane; l < L; l += 32) hits += line_f64_lean_inl(x, r64, -1, lines64[l], acc) ? 1 : 0;
+    } else {
+        // second pass: find this lane's flagged lines again (same float32 test) and redo them in float64
+        const float4 q0 = r32[nf32::G1], q1 = r32[nf32::G2], q2 = r32[nf32::G3];
+        const V3<float> g1 = mk(q0.x, q0.y, q0.z), g2 = mk(q1.x, q1.y, q1.z), g3 = mk(q2.x, q2.y, q2.z);
+        const V3<float> g0 = mk(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
+        const float4 ch = r32[nf32::CH], cm = r32[nf32::CM];
+        const V3<float> rc = mk((ch.x - xh0) + (cm.x - xm0), (ch.y - xh1) + (cm.y - xm1), (ch.z - xh2) + (cm.z - xm2));
+        const float rc2 = dot3(rc, rc), bound = q1.w * (1.0f + kBoundPadF);
+        const float f = kVertexFallback * kVertexFallback;
+#pragma unroll 1
+        for (int l = lane; l < L; l += 32) {
+            const float4 ln = lines[l];
+            const V3<float> s = mk(ln.x, ln.y, ln.z);
+            const float rs = dot3(rc, s);
+            if (rc2 - rs * rs > bound) continue;
+            const float b1 = dot3(g1, s), b2 = dot3(g2, s), b3 = dot3(g3, s), b0 = -(b1 + b2 + b3);
+            const bool redo = (vk != 0 && b0 * b0 <= f * dot3(g0, g0)) || (vk != 1 && b1 * b1 <= f * dot3(g1, g1)) ||
+                              (vk != 2 && b2 * b2 <= f * dot3(g2, g2)) || (vk != 3 && b3 * b3 <= f * dot3(g3, g3));
+            if (redo && line_f64_lean_inl(x, r64, vk, lines64[l], acc)) ++hits;
         }
     }
 }
@@ -375,10 +572,12 @@ __device__ __forceinline__ void cursor_advance(PairCursor &c, const uint32_t *wm
 
 // EXACT: near pairs take the exact integral (tet_exact) instead of the ray rule, the
 // warp's pairs spread over all 32 lanes and each result handed to the lane that owns its point.
-// U: lines per lane per iteration of the ray rule (the ray bundle).
+// DR: the near-pair drain's routine is called (0), inlined (1), or inlined in its lean form with the
+// pair's state in the warp's shared slot (2).  U: lines per lane per iteration of the ray rule (the ray bundle).
+// UJ: the float32 far sweep's tet loop unrolled by UJ (two tets' chains interleave).
 // PK (float32): the far sweep's packed f32x2 registers pair two evaluation points of the thread
 // (the far record holds every value twice: the point-pair layout) instead of two quadrature points.
-template <typename T, int Q, int P, int NT, int TILE, int S, int MINB, bool INL, bool EXACT, int U, bool PK>
+template <typename T, int Q, int P, int NT, int TILE, int S, int MINB, int DR, bool EXACT, int U, bool PK, int UJ>
 __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a)
 {
     static_assert(!PK || (sizeof(T) == 4 && P % 2 == 0), "the point-pair sweep is float32 with an even P");
@@ -411,6 +610,8 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
     T *sacc = reinterpret_cast<T *>(carve.take(sizeof(T) * NACC * BP));
     int *scnt = reinterpret_cast<int *>(carve.take(sizeof(int) * 2 * BP));
     float4 *swarp = reinterpret_cast<float4 *>(carve.take(sizeof(float4) * NW));
+    float4 *sslot = reinterpret_cast<float4 *>(carve.take(sizeof(float4) * NW * kPairSlotVec4));  // lean drain
+    uint32_t *sredo = reinterpret_cast<uint32_t *>(carve.take(sizeof(uint32_t) * NW * 32));      // its float64 redo list
     // direction table last: its size depends on the launch, every region above has a fixed offset
     float4 *sdir = reinterpret_cast<float4 *>(carve.take(a.smem_lines ? sizeof(float4) * a.L : 0));
     if (F32 && a.smem_lines)
@@ -608,7 +809,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                 // far sweep over the tile; MIXED: per-pair near/far test, near pairs masked and queued
                 auto sweep = [&](auto mixed_tag) {
                     constexpr bool MIXED = decltype(mixed_tag)::value;
-#pragma unroll 1
+#pragma unroll UJ
                     for (int j = 0; j < cnt; ++j) {
                         const float4 *rec = tb4 + j * (RS / 4);
                         const ulonglong2 *rec2 = reinterpret_cast<const ulonglong2 *>(rec);
@@ -752,13 +953,26 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             __syncwarp();
                             held = j;
                         }
+                        int n_redo = 0;  // lean drain: pairs of this entry queued for their float64 steps
 #pragma unroll 1
                         while (m) {
                             const int owner = __ffs(m) - 1;
                             m &= m - 1u;
                             const int bi = warp * 32 * P + pp * 32 + owner;
                             NearOut32 o;
-                            if constexpr (INL)
+                            if constexpr (DR == 2) {
+                                bool redo = false, whole = false;
+                                int vk = -1;
+                                o = near_pair_f32_lean<U>(spts + 9 * bi, srec + warp * kNearF32Vec4,
+                                                          a.smem_lines ? sdir : a.lines.f32, a.L, lane,
+                                                          sslot + warp * kPairSlotVec4, &redo, &vk, &whole);
+                                if (redo) {  // warp-uniform
+                                    if (lane == 0)
+                                        sredo[warp * 32 + n_redo] = (uint32_t)bi | ((uint32_t)(vk + 1) << 16) |
+                                                                    (whole ? 1u << 20 : 0u);
+                                    ++n_redo;
+                                }
+                            } else if constexpr (DR == 1)
                                 o = near_pair_f32_body<U>(spts + 9 * bi, srec + warp * kNearF32Vec4,
                                                           md.near64 + tet * kNearF64, a.smem_lines ? sdir : a.lines.f32,
                                                           a.lines.f64, a.L, lane);
@@ -769,6 +983,30 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             if (lane == owner) {
                                 kahan(bi, o.vx, o.vy, o.vz);
                                 scnt[BP + bi] += o.hits;
+                            }
+                        }
+                        if constexpr (DR == 2) {
+                            // the float64 steps of the entry's flagged pairs (at most one per lane of the mask)
+                            __syncwarp();
+#pragma unroll 1
+                            for (int f = 0; f < n_redo; ++f) {
+                                const uint32_t c = sredo[warp * 32 + f];
+                                const int bi = (int)(c & 0xffffu), vk = (int)((c >> 16) & 15u) - 1;
+                                const bool whole = (c >> 20) & 1u;
+                                const float *xs = spts + 9 * bi;
+                                const V3<double> x = mk(join3(xs[0], xs[1], xs[2]), join3(xs[3], xs[4], xs[5]),
+                                                        join3(xs[6], xs[7], xs[8]));
+                                V3<double> acc = mk(0.0, 0.0, 0.0);
+                                int hits = 0;
+                                line_fallback_f64_inl(x, xs, srec + warp * kNearF32Vec4, md.near64 + tet * kNearF64,
+                                                      a.smem_lines ? sdir : a.lines.f32, a.lines.f64, a.L, lane, vk,
+                                                      whole, acc, hits);
+                                const double vx = warp_sum(acc.x), vy = warp_sum(acc.y), vz = warp_sum(acc.z);
+                                hits = warp_sum(hits);
+                                if (lane == (bi & 31)) {
+                                    kahan(bi, (float)vx, (float)vy, (float)vz);
+                                    scnt[BP + bi] += hits;
+                                }
                             }
                         }
                     }
@@ -956,13 +1194,14 @@ size_t smem_bytes(int lines_in_smem)
            round16(sizeof(float4) * NW * kNearF32Vec4) + round16(sizeof(Pipe<S>)) +
            round16(sizeof(MeshDesc)) + 16 + round16(sizeof(float4) * lines_in_smem) +
            round16(sizeof(T) * (sizeof(T) == 4 ? 6 : 3) * NT * P) + round16(sizeof(int) * 2 * NT * P) +
-           round16(sizeof(float4) * NW);
+           round16(sizeof(float4) * NW) + round16(sizeof(float4) * NW * kPairSlotVec4) +
+           round16(sizeof(uint32_t) * NW * 32);
 }
 
-template <typename T, int Q, int P, int NT, int TILE, int S, int MINB, bool INL, bool EXACT, int U, bool PK>
+template <typename T, int Q, int P, int NT, int TILE, int S, int MINB, int DR, bool EXACT, int U, bool PK, int UJ>
 cudaError_t launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out, bool query_only, int *occ_out)
 {
-    auto kern = velocity_kernel<T, Q, P, NT, TILE, S, MINB, INL, EXACT, U, PK>;
+    auto kern = velocity_kernel<T, Q, P, NT, TILE, S, MINB, DR, EXACT, U, PK, UJ>;
     const size_t sm = smem_bytes<T, Q, P, NT, TILE, S, PK>(a.smem_lines ? a.L : 0);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;

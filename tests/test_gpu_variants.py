@@ -39,7 +39,8 @@ def _id(c):
     prec, q, nr, v = c
     s = bs.bs_variant_shape(prec, q, nr, v)
     return (f"{'fp32' if prec == bs.BS_FP32 else 'fp64'}-q{q}-{'exact' if nr else 'ray'}-v{v}-P{s['points_per_thread']}"
-            f"T{s['tile']}S{s['stages']}B{s['ctas_per_sm']}U{s['ray_bundle']}{'pp' if s['point_pairs'] else 'qp'}")
+            f"T{s['tile']}S{s['stages']}B{s['ctas_per_sm']}D{s['near_drain']}U{s['ray_bundle']}"
+            f"{'pp' if s['point_pairs'] else 'qp'}J{s['tet_unroll']}")
 
 
 @pytest.fixture(scope="module")
