@@ -94,9 +94,11 @@ struct bs_ctx {
     int *box = nullptr;
     // direction table of the last (n_phi, n_theta)
     LineTables lines;
-    // scratch for per-chunk partial sums
+    // scratch for per-chunk partial sums, and the near pass's totals ([k][3], variants that take it)
     double *partial = nullptr;
     size_t partial_cap = 0;
+    double *near_out = nullptr;
+    size_t near_cap = 0;
     // staging for bs_velocity_host
     double *stage = nullptr;
     size_t stage_cap = 0;
@@ -159,7 +161,7 @@ void free_ctx(bs_ctx *h)
                     h->cell_count, h->box, h->walk_nbr, h->walk_inc_off, h->walk_inc, h->walk_bface,
                     h->walk_bnode, h->walk_mode, h->walk_rec, h->rk_w, h->walk_grid.grid,
                     h->walk_grid.cell_off, h->walk_grid.cell_cnt, h->walk_grid.cell_face, h->walk_grid.geo,
-                    h->walk_grid.geo32};
+                    h->walk_grid.geo32, h->near_out};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete h;
@@ -182,6 +184,7 @@ struct bs_batch_ctx {
     std::vector<MeshDesc> h_meshes;  // last descriptor table copied to the device
     double *partial = nullptr;
     size_t partial_cap = 0;
+    double *near_out = nullptr;  // the near pass's totals over all meshes' points
     unsigned long long *work_counter = nullptr;
     int *flag = nullptr;
     LineTables lines;
@@ -197,7 +200,7 @@ void free_batch(bs_batch_ctx *b)
 {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     void *bufs[] = {b->perm, b->keys, b->cell_count, b->box, b->d_meshes, b->partial, b->work_counter, b->flag,
-                    b->lines.f32, b->lines.f64};
+                    b->lines.f32, b->lines.f64, b->near_out};
     for (void *p : bufs)
         if (p) cudaFree(p);
     delete b;
@@ -829,6 +832,20 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     if (a.n_items > INT32_MAX) return fail(BS_ERR_ARG, "too many work items for one launch (points x tet chunks)");
     a.wait_polls = h->copy_wait_polls;
     a.withhold_copies = h->withhold_copies;
+    if (!ray && shape.drain == 3) {  // the near pass evaluates the near pairs the far sweep leaves out
+        const size_t need = 3 * (size_t)k;
+        if (need > h->near_cap) {
+            if (h->near_out) cudaFreeAsync(h->near_out, st);
+            h->near_out = nullptr;
+            h->near_cap = 0;
+            BS_CUDA(cudaMallocAsync((void **)&h->near_out, sizeof(double) * need, st));
+            h->near_cap = need;
+        }
+        a.near_out = h->near_out;
+        a.tile = shape.tile;
+        a.far_stride = p->precision == BS_FP32 ? far_stride<float>(Q, shape.layout) : far_stride<double>(Q);
+        a.n_near_warps = (k + 31) / 32;
+    }
     int grid = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->prof) {
@@ -1062,10 +1079,12 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     for (int i = 0; i < n; ++i) total_pairs += (double)b->meshes[i]->n_nodes * b->meshes[i]->n_tets;
     const double per_item = std::max(1.0, total_pairs / (16.0 * b->n_sm * occ));
     std::vector<MeshDesc> md(n);
-    int64_t items = 0, partial_elems = 0;
+    int64_t items = 0, partial_elems = 0, near_warps = 0;
     for (int i = 0; i < n; ++i) {
         bs_ctx *h = b->meshes[i];
         MeshDesc &m = md[i];
+        m.near_warp_begin = near_warps;
+        near_warps += (h->n_nodes + 31) / 32;
         const int64_t k = h->n_nodes;
         const int64_t n_tiles = std::max<int64_t>(1, (h->n_tets + shape.tile - 1) / shape.tile);
         const double block_pairs = (double)std::min<int64_t>(BP, k) * shape.tile;
@@ -1099,6 +1118,10 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         changed = true;
     }
     for (int i = 0; i < n; ++i) md[i].partial = b->partial + reinterpret_cast<intptr_t>(md[i].partial);
+    if (shape.drain == 3 && !b->near_out) {  // the near pass's totals, all meshes' points
+        BS_CUDA(cudaMallocAsync((void **)&b->near_out, sizeof(double) * 3 * std::max<int64_t>(b->n_points, 1), st));
+        changed = true;
+    }
 
     const bool same_desc = b->h_meshes.size() == md.size() &&
                            memcmp(b->h_meshes.data(), md.data(), sizeof(MeshDesc) * md.size()) == 0;
@@ -1125,6 +1148,12 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     a.work_counter = b->work_counter;
     a.variant = variant;
     a.near_rule = p->near_rule;
+    if (shape.drain == 3) {
+        a.near_out = b->near_out;
+        a.tile = shape.tile;
+        a.far_stride = prec == BS_FP32 ? far_stride<float>(Q, shape.layout) : far_stride<double>(Q);
+        a.n_near_warps = near_warps;
+    }
     if (items == 0) {  // every mesh is empty: the reduction alone writes the zeros
         BS_CUDA(launch_reduce(a, st));
         return BS_OK;

@@ -132,6 +132,7 @@ struct MeshDesc {
     int n_chunks = 1, tiles_per_chunk = 1;
     int64_t item_begin = 0;   // batch: first work item of this mesh
     int64_t point_begin = 0;  // batch: first point of this mesh in the batched reduction
+    int64_t near_warp_begin = 0;  // batch: first warp of this mesh in the near pass
 };
 
 struct VelocityArgs {
@@ -160,6 +161,11 @@ struct VelocityArgs {
     // give-up path: nothing can land after the kernel returned)
     long long wait_polls = 0;
     int withhold_copies = 0;
+    // the near pass (variants that leave the near pairs to it): float64 near totals by spatial position
+    // ([n_points][3]; batch: over all meshes), the far records' tile and stride, and its number of warps
+    double *near_out = nullptr;
+    int tile = 0, far_stride = 0;
+    int64_t n_near_warps = 0;
 };
 
 // far ratio of a launch: its square (+inf for the all-ray rule) in double and float, the ratio in float
@@ -180,6 +186,7 @@ struct LaunchShape {
     int threads = 128;
     int tile = 64;    // tets per shared-memory tile
     int layout = 0;   // float32 far-record layout (kFarQuadPairs / kFarPointPairs)
+    int drain = 1;    // VariantShape::DR (3: the near pass evaluates the near pairs)
 };
 
 // Kernel variants of the velocity kernel, per (precision, tet rule, near rule): the launch shape is
@@ -189,7 +196,8 @@ struct VariantShape {
     int TILE;   // tets per pipeline stage (and per tile header)
     int S;      // pipeline stages
     int MINB;   // CTAs per SM the register budget is set for (__launch_bounds__)
-    int DR;     // near-pair drain: routine called (0), inlined (1), inlined with the pair's state in shared memory (2)
+    int DR;     // near-pair drain: routine called (0), inlined (1), inlined with the pair's state in shared memory (2),
+                // or none (3): the near pairs are counted and left to the near pass
     int U;      // ray bundle: lines per lane per iteration of the ray rule
     bool PK;    // float32: packed registers pair two evaluation points (point-pair layout)
     int UJ;     // float32 far sweep: tet loop unrolled by UJ

@@ -58,6 +58,17 @@ __device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
+// Shared-memory load the compiler may not hoist or merge: the line loops read warp-uniform per-pair or
+// per-tet values per line on purpose, so that they do not occupy registers across the loop.
+__device__ __forceinline__ float4 lds4(const float4 *p)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(smem_u32(p)));
+    return v;
+}
+
 // bounded wait: false when `cap` polls did not see the phase complete
 __device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity, long long cap)
 {

@@ -137,10 +137,13 @@ __device__ __forceinline__ void ray_tet_f32(const float *__restrict__ xs, const 
     const int lA = a0 * M, lB = b0 * M - nA;
 
     bool ready = false;  // warp-uniform
+    bool any_redo = false;
     int vk = -1;
     bool whole_f64 = false;
+    // per lane: the point's barycentric coordinates, the parallel and vertex-fallback thresholds, W_a;
+    // the tet's face gradients and vorticity stay in the staged record and are read per line
     float a[4], par2[4], fb2[4], tau_h = 0.f;
-    V3<float> g[4], w[4], Wa = mk(0.f, 0.f, 0.f);
+    V3<float> Wa = mk(0.f, 0.f, 0.f);
 #pragma unroll 1
     for (int w0 = 0; w0 < nW; w0 += 32) {
         const int nw = min(32, nW - w0);
@@ -163,6 +166,7 @@ __device__ __forceinline__ void ray_tet_f32(const float *__restrict__ xs, const 
                     vh[3 * i + 2] == xh2 && vm[3 * i + 2] == xm2)
                     vk = i;
             const float4 q0 = r32[nf32::G1], q1 = r32[nf32::G2], q2 = r32[nf32::G3];
+            V3<float> g[4];
             g[1] = mk(q0.x, q0.y, q0.z);
             g[2] = mk(q1.x, q1.y, q1.z);
             g[3] = mk(q2.x, q2.y, q2.z);
@@ -181,17 +185,18 @@ __device__ __forceinline__ void ray_tet_f32(const float *__restrict__ xs, const 
                 const float aabs = fminf(fminf(fabsf(a[0]), fabsf(a[1])), fminf(fabsf(a[2]), fabsf(a[3])));
                 whole_f64 = amin > -kDegenA && aabs < kDegenA;
             }
+            float wa[3] = {0.f, 0.f, 0.f};
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float4 t = r32[nf32::W + i];
-                w[i] = mk(t.x, t.y, t.z);
+                wa[0] += a[i] * t.x;
+                wa[1] += a[i] * t.y;
+                wa[2] += a[i] * t.z;
                 const float gg = dot3(g[i], g[i]);
                 par2[i] = kParF * kParF * gg;
                 fb2[i] = (vk >= 0 && i != vk) ? kVertexFallback * kVertexFallback * gg : -1.0f;
             }
-            Wa = mk(a[0] * w[0].x + a[1] * w[1].x + a[2] * w[2].x + a[3] * w[3].x,
-                    a[0] * w[0].y + a[1] * w[1].y + a[2] * w[2].y + a[3] * w[3].y,
-                    a[0] * w[0].z + a[1] * w[1].z + a[2] * w[2].z + a[3] * w[3].z);
+            Wa = mk(wa[0], wa[1], wa[2]);
             tau_h = (float)kTau * q0.w;
         }
 #pragma unroll 1
@@ -202,23 +207,17 @@ __device__ __forceinline__ void ray_tet_f32(const float *__restrict__ xs, const 
             const int l = wi < nA ? lA + wi : lB + wi;
             const float4 ln = lines[l];
             const V3<float> s = mk(ln.x, ln.y, ln.z);
+            const float4 q0 = lds4(r32 + nf32::G1), q1 = lds4(r32 + nf32::G2), q2 = lds4(r32 + nf32::G3);
             float b[4];
-            b[1] = dot3(g[1], s);
-            b[2] = dot3(g[2], s);
-            b[3] = dot3(g[3], s);
+            b[1] = q0.x * s.x + q0.y * s.y + q0.z * s.z;
+            b[2] = q1.x * s.x + q1.y * s.y + q1.z * s.z;
+            b[3] = q2.x * s.x + q2.y * s.y + q2.z * s.z;
             b[0] = -(b[1] + b[2] + b[3]);
             bool redo = whole_f64;
 #pragma unroll
             for (int k = 0; k < 4; ++k) redo = redo || (b[k] * b[k] <= fb2[k]);
-            if (redo) {
-                // rare: this line in float64 (the point's exact coordinates from its splits)
-                const V3<double> xd =
-                    mk(join3(xs[0], xs[1], xs[2]), join3(xs[3], xs[4], xs[5]), join3(xs[6], xs[7], xs[8]));
-                V3<double> acc = mk(0.0, 0.0, 0.0);
-                if (line_f64_lean(xd, r64, whole_f64 ? -1 : vk, lines64[l], acc)) ++hits;
-                ax += (float)acc.x;
-                ay += (float)acc.y;
-                az += (float)acc.z;
+            if (redo) {  // rare: this line in float64, in the second pass below
+                any_redo = true;
                 continue;
             }
             float lo = -INFINITY, hi = INFINITY;
@@ -230,17 +229,49 @@ __device__ __forceinline__ void ray_tet_f32(const float *__restrict__ xs, const 
                 else hi = fminf(hi, -a[k] / b[k]);
             }
             if (empty || !(hi - lo > tau_h)) continue;
-            const V3<float> Wb = mk(b[0] * w[0].x + b[1] * w[1].x + b[2] * w[2].x + b[3] * w[3].x,
-                                    b[0] * w[0].y + b[1] * w[1].y + b[2] * w[2].y + b[3] * w[3].y,
-                                    b[0] * w[0].z + b[1] * w[1].z + b[2] * w[2].z + b[3] * w[3].z);
+            float Wb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 t = lds4(r32 + nf32::W + k);
+                Wb[0] += b[k] * t.x;
+                Wb[1] += b[k] * t.y;
+                Wb[2] += b[k] * t.z;
+            }
             const float f1 = fabsf(hi) - fabsf(lo);
             const float f2 = 0.5f * (hi * fabsf(hi) - lo * fabsf(lo));
-            const V3<float> J = mk(f1 * Wa.x + f2 * Wb.x, f1 * Wa.y + f2 * Wb.y, f1 * Wa.z + f2 * Wb.z);
+            const V3<float> J = mk(f1 * Wa.x + f2 * Wb[0], f1 * Wa.y + f2 * Wb[1], f1 * Wa.z + f2 * Wb[2]);
             ax += ln.w * (s.y * J.z - s.z * J.y);
             ay += ln.w * (s.z * J.x - s.x * J.z);
             az += ln.w * (s.x * J.y - s.y * J.x);
             ++hits;
         }
+    }
+    // the float64 steps, as a second pass over this lane's window lines (the same float32 tests pick the
+    // lines again): out of the line loop, so that their registers do not count against it
+    if (__any_sync(0xffffffffu, any_redo) && any_redo) {
+        const V3<double> xd = mk(join3(xs[0], xs[1], xs[2]), join3(xs[3], xs[4], xs[5]), join3(xs[6], xs[7], xs[8]));
+        V3<double> acc = mk(0.0, 0.0, 0.0);
+#pragma unroll 1
+        for (int wi = 0; wi < nW; ++wi) {
+            const int l = wi < nA ? lA + wi : lB + wi;
+            const float4 ln = lines[l];
+            const float rs = rc.x * ln.x + rc.y * ln.y + rc.z * ln.z;
+            if (rc2 - rs * rs > bound) continue;
+            const V3<float> s = mk(ln.x, ln.y, ln.z);
+            const float4 q0 = lds4(r32 + nf32::G1), q1 = lds4(r32 + nf32::G2), q2 = lds4(r32 + nf32::G3);
+            float b[4];
+            b[1] = q0.x * s.x + q0.y * s.y + q0.z * s.z;
+            b[2] = q1.x * s.x + q1.y * s.y + q1.z * s.z;
+            b[3] = q2.x * s.x + q2.y * s.y + q2.z * s.z;
+            b[0] = -(b[1] + b[2] + b[3]);
+            bool redo = whole_f64;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) redo = redo || (b[k] * b[k] <= fb2[k]);
+            if (redo && line_f64_lean_inl(xd, r64, whole_f64 ? -1 : vk, lines64[l], acc)) ++hits;
+        }
+        ax += (float)acc.x;
+        ay += (float)acc.y;
+        az += (float)acc.z;
     }
 }
 
@@ -273,7 +304,7 @@ __device__ __forceinline__ void ray_tet_f64(V3<double> x, const double *__restri
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kRayThreads) ray_kernel(const VelocityArgs a)
+__global__ void __launch_bounds__(kRayThreads, 4) ray_kernel(const VelocityArgs a)
 {
     constexpr bool F32 = sizeof(T) == 4;
     constexpr int RB = ray_rec_bytes<T>();

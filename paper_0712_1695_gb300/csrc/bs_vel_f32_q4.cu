@@ -1,7 +1,8 @@
 // bs_vel_f32_q4.cu -- float32 instances of the velocity kernel for the four-point far rule (the
 // workhorse, and the widest choice for the autotuner): points per thread, tile, stages, register
-// budget, near-pair drain (called, inlined, or inlined with its state in shared memory), ray bundle,
-// the far sweep's register pairing, and the unroll of its tet loop.
+// budget, near pairs (drained in the kernel: routine called, inlined, or inlined with its state in shared
+// memory; or left to the near pass), ray bundle, the far sweep's register pairing, and the unroll of its
+// tet loop.
 #include "bs_velocity_kernel.cuh"
 
 namespace bs {
@@ -12,22 +13,21 @@ namespace {
 
 // variant 0 is the default; the first variant with one point per thread and tiles of 32 serves small meshes
 const VariantEntry kF32Q4[] = {
-    // drain state in shared memory: the far sweep keeps its registers (no spills at 4 CTAs per SM)
-    BS_V(3, 32, 3, 4, 2, 1, false, 2), BS_V(3, 32, 2, 4, 2, 1, false, 2), BS_V(3, 32, 2, 4, 2, 1, false, 1),
-    BS_V(3, 64, 2, 4, 2, 1, false, 2),
+    // near pairs left to the near pass: the far sweep has no drain (no spills at 4 CTAs per SM)
+    BS_V(3, 32, 3, 4, 3, 1, false, 2), BS_V(3, 32, 2, 4, 3, 1, false, 1), BS_V(3, 64, 2, 4, 3, 1, false, 1),
+    BS_V(4, 32, 2, 4, 3, 1, false, 1),
     // one point per thread (small meshes)
     BS_V(1, 32, 4, 5, 0, 1, false, 1),
-    BS_V(4, 32, 2, 4, 2, 1, false, 1), BS_V(4, 32, 2, 4, 2, 1, true, 1), BS_V(2, 32, 2, 4, 2, 1, false, 2),
-    BS_V(1, 32, 4, 5, 2, 1, false, 1),
+    BS_V(2, 32, 2, 4, 3, 1, false, 2), BS_V(4, 32, 2, 4, 3, 1, true, 1), BS_V(3, 32, 2, 4, 3, 1, false, 2),
+    // near pairs drained in the far kernel: the pair's state in shared memory
+    BS_V(3, 32, 2, 4, 2, 1, false, 1), BS_V(4, 32, 2, 4, 2, 1, false, 1),
     // ray bundles of 2 and 4 lines per lane
     BS_V(1, 32, 4, 5, 0, 2, false, 1), BS_V(1, 32, 4, 5, 0, 4, false, 1),
     // near routine in registers, inlined or called
     BS_V(3, 32, 2, 4, 1, 1, false, 1), BS_V(3, 64, 2, 4, 1, 1, false, 1), BS_V(2, 64, 2, 4, 1, 1, false, 1),
     BS_V(3, 32, 3, 4, 1, 1, false, 1), BS_V(3, 16, 3, 4, 1, 1, false, 1), BS_V(2, 32, 4, 3, 1, 1, false, 1),
     BS_V(2, 32, 3, 4, 0, 1, false, 1), BS_V(2, 32, 4, 5, 1, 1, false, 1), BS_V(3, 32, 2, 4, 1, 4, false, 1),
-    BS_V(4, 32, 2, 3, 1, 1, true, 1),
-    // more
-    BS_V(3, 32, 3, 4, 2, 4, false, 2), BS_V(6, 32, 2, 3, 2, 1, false, 1), BS_V(4, 64, 2, 4, 2, 1, false, 1),
+    BS_V(4, 32, 2, 3, 1, 1, true, 1), BS_V(1, 32, 4, 5, 2, 1, false, 1),
 };
 #undef BS_V
 

@@ -5,7 +5,7 @@
 
 #include <algorithm>
 
-#include "bs_internal.cuh"
+#include "bs_velocity_kernel.cuh"
 
 namespace bs {
 namespace {
@@ -34,6 +34,12 @@ __global__ void reduce_kernel(const VelocityArgs a)
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (int c = 0; c < m->n_chunks; ++c) {
         const double *q = m->partial + (c * k + i) * 3;
+        s0 += q[0];
+        s1 += q[1];
+        s2 += q[2];
+    }
+    if (a.near_out && m->n_tets > 0) {  // the near pass's totals
+        const double *q = a.near_out + 3 * ((a.meshes ? m->point_begin : 0) + i);
         s0 += q[0];
         s1 += q[1];
         s2 += q[2];
@@ -78,7 +84,7 @@ int noalloc_variant(int precision, int Q, int near_rule)
     int best = -1;
     for (int v = 0; v < vl.n; ++v) {
         const VariantShape &s = vl.v[v].s;
-        if (s.PK || s.TILE > 32 || s.TILE < 8) continue;
+        if (s.PK || s.TILE > 32 || s.TILE < 8 || s.DR == 3) continue;
         if (best < 0 || (near_rule == BS_NEAR_RAY && s.P == 1 && vl.v[best].s.P != 1)) best = v;
     }
     return best;
@@ -94,6 +100,7 @@ LaunchShape shape_for(int precision, int Q, int variant, int near_rule)
     s.points_per_thread = v.P;
     s.tile = v.TILE;
     s.layout = v.PK ? kFarPointPairs : kFarQuadPairs;
+    s.drain = v.DR;
     return s;
 }
 
@@ -123,6 +130,23 @@ cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cuda
     if (ev_start && (e = cudaEventRecord(ev_start, st)) != cudaSuccess) return e;
     e = vl.v[a.variant].launch(a, n_sm, st, grid_out, false, nullptr);
     if (e != cudaSuccess) return e;
+    if (vl.v[a.variant].s.DR == 3 && a.n_near_warps > 0) {  // the near pass
+        if (!a.near_out || a.tile <= 0 || a.far_stride <= 0) return cudaErrorInvalidValue;
+        const size_t sm = a.smem_lines ? sizeof(float4) * a.L : 0;
+        const unsigned blocks = (unsigned)((a.n_near_warps + 3) / 4);
+        if (precision == BS_FP32) {
+            if ((e = cudaFuncSetAttribute(near_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm)) != cudaSuccess)
+                return e;
+            near_pass_kernel<float><<<blocks, 128, sm, st>>>(a);
+        } else {
+            if ((e = cudaFuncSetAttribute(near_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm)) != cudaSuccess)
+                return e;
+            near_pass_kernel<double><<<blocks, 128, sm, st>>>(a);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if (ev_stop) e = cudaEventRecord(ev_stop, st);
     return e;
 }

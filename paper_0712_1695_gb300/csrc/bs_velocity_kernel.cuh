@@ -273,16 +273,6 @@ __device__ __forceinline__ NearOut32 near_pair_f32_body(const float *__restrict_
     return o;
 }
 
-// Shared-memory load the compiler may not hoist or merge (the lean drain reads its per-pair values
-// per line on purpose, so that they do not occupy registers across the line loop).
-__device__ __forceinline__ float4 lds4(const float4 *p)
-{
-    float4 v;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(smem_u32(p)));
-    return v;
-}
 
 // The lean form of near_pair_f32_body: the same ray rule, the same float64 fallbacks, but the
 // pair's warp-uniform values (barycentric coordinates a_i of the point, the parallel and
@@ -570,10 +560,42 @@ __device__ __forceinline__ void cursor_advance(PairCursor &c, const uint32_t *wm
     c.k0 = k;
 }
 
+// The near/far decision of a (point, tet) pair (Section 1: the tet is far when the point lies beyond
+// far_ratio circumradii of its centroid), with explicit round-to-nearest operations (no contraction), so
+// that every kernel that takes it -- the far sweep, which leaves the near pairs out of its sums, and the
+// near pass, which evaluates them -- decides every pair the same way, bit for bit.  float32: the point
+// x' and the centroid c' in the tile frame (x' = x_hi - o, as the far sweep forms it), c_rho2 = the far
+// record's first float4 (c', rho^2); float64: global coordinates, c_rho2 = the record's first four.
+__device__ __forceinline__ bool pair_is_near_f32(float xp, float yp, float zp, float4 c_rho2, float fr2)
+{
+    const float dx = __fsub_rn(xp, c_rho2.x), dy = __fsub_rn(yp, c_rho2.y), dz = __fsub_rn(zp, c_rho2.z);
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    return !(d2 > __fmul_rn(fr2, c_rho2.w));
+}
+__device__ __forceinline__ bool pair_is_near_f64(double x, double y, double z, const double *c_rho2, double fr2)
+{
+    const double dx = __dsub_rn(x, c_rho2[0]), dy = __dsub_rn(y, c_rho2[1]), dz = __dsub_rn(z, c_rho2[2]);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return !(d2 > __dmul_rn(fr2, c_rho2[3]));
+}
+// Can a point of the ball (centre, radius) = sphere be near a tet of the tile (header: origin o and the
+// radius rc of its centroids about o; rho_max its largest circumradius)?  No, when the ball is farther
+// than far_ratio rho_max from every centroid, with a margin (0.1% and 1e-5 of the coordinates' scale)
+// that covers the float32 rounding of this test and of the per-pair test: a culled tile holds no pair
+// the per-pair test would call near.
+__device__ __forceinline__ bool tile_culled(float4 sphere, float4 hdr, float rho_max, float far_ratio)
+{
+    const float dx = sphere.x - hdr.x, dy = sphere.y - hdr.y, dz = sphere.z - hdr.z;
+    const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float scale = fabsf(hdr.x) + fabsf(hdr.y) + fabsf(hdr.z) + dist;
+    return dist - sphere.w - hdr.w > far_ratio * rho_max * 1.001f + 1e-5f * scale;
+}
+
 // EXACT: near pairs take the exact integral (tet_exact) instead of the ray rule, the
 // warp's pairs spread over all 32 lanes and each result handed to the lane that owns its point.
 // DR: the near-pair drain's routine is called (0), inlined (1), or inlined in its lean form with the
-// pair's state in the warp's shared slot (2).  U: lines per lane per iteration of the ray rule (the ray bundle).
+// pair's state in the warp's shared slot (2); or (3) there is no drain: the near pairs are left out of
+// the sums and counted, and the near pass (near_pass_kernel) evaluates them.  U: lines per lane per iteration of the ray rule (the ray bundle).
 // UJ: the float32 far sweep's tet loop unrolled by UJ (two tets' chains interleave).
 // PK (float32): the far sweep's packed f32x2 registers pair two evaluation points of the thread
 // (the far record holds every value twice: the point-pair layout) instead of two quadrature points.
@@ -748,14 +770,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
             const float4 hd = sh[0];
             const T *tb = reinterpret_cast<const T *>(stages + st * STAGE_BYTES + HDR_BYTES);
             // can any point of this warp be near a tet of this tile?
-            bool culled = false;
-            if (!a.all_ray) {
-                const float4 cw = swarp[warp];
-                const float dx = cw.x - hd.x, dy = cw.y - hd.y, dz = cw.z - hd.z;
-                const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-                const float scale = fabsf(hd.x) + fabsf(hd.y) + fabsf(hd.z) + dist;
-                culled = dist - cw.w - hd.w > a.far_ratio_f * sh[1].x * 1.001f + 1e-5f * scale;
-            }
+            const bool culled = !a.all_ray && tile_culled(swarp[warp], hd, sh[1].x, a.far_ratio_f);
             const int cnt = (int)min((int64_t)TILE, md.n_tets - (int64_t)t * TILE);
             int qn = 0;  // warp-uniform
             // this warp is done with stage st (the near pairs read global memory only);
@@ -816,12 +831,8 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         bool nearp[P];
                         if constexpr (MIXED) {
                             const float4 h0 = rec[0];
-                            const float thr2 = fr2() * h0.w;
 #pragma unroll
-                            for (int p = 0; p < P; ++p) {
-                                const float dx = xl(p, 0) - h0.x, dy = xl(p, 1) - h0.y, dz = xl(p, 2) - h0.z;
-                                nearp[p] = !(dx * dx + dy * dy + dz * dz > thr2);
-                            }
+                            for (int p = 0; p < P; ++p) nearp[p] = pair_is_near_f32(xl(p, 0), xl(p, 1), xl(p, 2), h0, fr2());
                         }
 #pragma unroll
                         for (int g = 0; g < NQ; ++g) {
@@ -851,7 +862,11 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                                 B2[r][2] = fma2(ir3, v4.y, B2[r][2]);
                             }
                         }
-                        if constexpr (MIXED) {
+                        if constexpr (MIXED && DR == 3) {  // counted here, evaluated by the near pass
+#pragma unroll
+                            for (int p = 0; p < P; ++p)
+                                if (nearp[p]) ++scnt[slot0 + 32 * p];
+                        } else if constexpr (MIXED) {
 #pragma unroll
                             for (int p = 0; p < P; ++p) {
                                 const unsigned m = __ballot_sync(0xffffffffu, nearp[p]);
@@ -937,7 +952,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         }
                     }
                     __syncwarp();
-                } else if (qn > 0) {
+                } else if (DR != 3 && qn > 0) {
                     __syncwarp();
                     int held = -1;
 #pragma unroll 1
@@ -1033,12 +1048,8 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                 for (int j = 0; j < cnt; ++j) {
                     const double *rec = tb + j * RS;
                     bool nearp[P];
-                    const double thr2 = fr2() * rec[3];
 #pragma unroll
-                    for (int p = 0; p < P; ++p) {
-                        const double dx = xp[p].x - rec[0], dy = xp[p].y - rec[1], dz = xp[p].z - rec[2];
-                        nearp[p] = !culled && !(dx * dx + dy * dy + dz * dz > thr2);
-                    }
+                    for (int p = 0; p < P; ++p) nearp[p] = !culled && pair_is_near_f64(xp[p].x, xp[p].y, xp[p].z, rec, fr2());
                     // per point q: (-2 x_q', |x_q'|^2, w', B = x_q' x w'); sum (x' - x_q') x w' / r^3 = x' x A - B
 #pragma unroll
                     for (int q = 0; q < Q; ++q) {
@@ -1057,7 +1068,11 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                             B[p][2] = fma(ir3, qq[9], B[p][2]);
                         }
                     }
-                    if (!culled) {
+                    if (!culled && DR == 3) {
+#pragma unroll
+                        for (int p = 0; p < P; ++p)
+                            if (nearp[p]) ++scnt[slot0 + 32 * p];
+                    } else if (!culled) {
 #pragma unroll
                         for (int p = 0; p < P; ++p) {
                             const unsigned m = __ballot_sync(0xffffffffu, nearp[p]);
@@ -1115,7 +1130,7 @@ __global__ void __launch_bounds__(NT, MINB) velocity_kernel(const VelocityArgs a
                         }
                     }
                     __syncwarp();
-                } else if (qn > 0) {
+                } else if (DR != 3 && qn > 0) {
                     __syncwarp();
 #pragma unroll 1
                     for (int e = 0; e < qn; ++e) {
@@ -1215,6 +1230,172 @@ cudaError_t launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
     if (grid_out) *grid_out = (int)grid;
     kern<<<(unsigned)grid, NT, sm, st>>>(a);
     return cudaGetLastError();
+}
+
+
+// The near field as a pass of its own, after the far sweep of a variant with DR == 3 (which leaves the
+// near pairs out of its sums).  One warp per 32 consecutive points of the spatial order, one point per
+// lane; a batch gives every mesh its own warps (MeshDesc::near_warp_begin).  The warp scans the mesh's
+// tile headers 32 at a time with the far sweep's culling test against its own bounding sphere; in each
+// tile that can hold a near pair it classifies every (point, tet) pair with the far sweep's test
+// (pair_is_near_*, the same decision bit for bit, so the near pass evaluates exactly the pairs the far
+// sweep left out), and evaluates each near pair by the ray rule, the 32 lanes splitting its lines as
+// in the fused drain.  The lane of the pair's point adds the result to its own total (compensated in
+// float32), in ascending tet order (deterministic, independent of how points are grouped), and at the
+// end writes it to near_out (float64, by spatial position) and its ray hits to counts.
+template <typename T>
+__global__ void __launch_bounds__(128, 4) near_pass_kernel(const VelocityArgs a)
+{
+    constexpr bool F32 = sizeof(T) == 4;
+    __shared__ float spts[128 * 9];                  // the lanes' points as float splits
+    __shared__ float4 srec[4][kNearF32Vec4];         // the near record of the current tet, per warp
+    extern __shared__ __align__(16) float4 sdir[];   // float32 direction table (a.smem_lines)
+    if (a.skip && *a.skip) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (F32 && a.smem_lines)
+        for (int l = threadIdx.x; l < a.L; l += blockDim.x) sdir[l] = a.lines.f32[l];
+    __syncthreads();
+    const int64_t wg = (int64_t)blockIdx.x * 4 + warp;  // this warp's index over all meshes
+    const MeshDesc *m = &a.m;
+    if (a.meshes) {
+        int lo = 0, hi = a.n_meshes - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.meshes[mid].near_warp_begin <= wg) lo = mid;
+            else hi = mid - 1;
+        }
+        m = &a.meshes[lo];
+    }
+    const int64_t k = m->k;
+    const int64_t w = wg - (a.meshes ? m->near_warp_begin : 0);
+    if (w * 32 >= k || m->n_tets == 0) return;  // warp-uniform
+    const int64_t gi = w * 32 + lane;
+    const int64_t gp = gi < k ? gi : k - 1;  // pad with a real point; its result is not written
+    float *xs = spts + 9 * threadIdx.x;
+    {
+        const int64_t src = m->perm[gp];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) split3(m->pts[3 * src + j], xs[3 * j], xs[3 * j + 1], xs[3 * j + 2]);
+    }
+    // bounding sphere of the warp's points (float, padded), as the far sweep's
+    float4 sphere;
+    {
+        float mnx = xs[0], mxx = mnx, mny = xs[3], mxy = mny, mnz = xs[6], mxz = mnz;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+            mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+            mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+            mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+            mnz = fminf(mnz, __shfl_xor_sync(0xffffffffu, mnz, o));
+            mxz = fmaxf(mxz, __shfl_xor_sync(0xffffffffu, mxz, o));
+        }
+        const float ex = mxx - mnx, ey = mxy - mny, ez = mxz - mnz;
+        sphere = make_float4(0.5f * (mnx + mxx), 0.5f * (mny + mxy), 0.5f * (mnz + mxz),
+                             0.5f * sqrtf(ex * ex + ey * ey + ez * ez) * 1.001f + 1e-6f);
+    }
+    const float4 *lines = (F32 && a.smem_lines) ? sdir : a.lines.f32;
+    const int tile = a.tile, rs = a.far_stride;
+    const int64_t n_tiles = (m->n_tets + tile - 1) / tile;
+    const V3<double> xd = mk(join3(xs[0], xs[1], xs[2]), join3(xs[3], xs[4], xs[5]), join3(xs[6], xs[7], xs[8]));
+    float s32[3] = {0.f, 0.f, 0.f}, c32[3] = {0.f, 0.f, 0.f};  // float32: compensated total
+    double s64[3] = {0.0, 0.0, 0.0};                            // float64: plain total
+    int hits = 0;
+#pragma unroll 1
+    for (int64_t t0 = 0; t0 < n_tiles; t0 += 32) {
+        const int64_t tl = t0 + lane;
+        bool open = false;
+        if (tl < n_tiles) open = a.all_ray || !tile_culled(sphere, m->tile_hdr[2 * tl], m->tile_hdr[2 * tl + 1].x,
+                                                           a.far_ratio_f);
+        unsigned tiles = __ballot_sync(0xffffffffu, open);
+#pragma unroll 1
+        while (tiles) {
+            const int64_t t = t0 + __ffs(tiles) - 1;
+            tiles &= tiles - 1u;
+            const float4 o = m->tile_hdr[2 * t];
+            const int cnt = (int)min((int64_t)tile, m->n_tets - t * tile);
+            const float xp = xs[0] - o.x, yp = xs[3] - o.y, zp = xs[6] - o.z;  // tile frame (float32)
+#pragma unroll 1
+            for (int j0 = 0; j0 < cnt; j0 += 32) {
+                // lane jj holds the decision data of tet j0 + jj of the tile
+                const int64_t tj = t * tile + j0 + lane;
+                float4 c32v = make_float4(0.f, 0.f, 0.f, 0.f);
+                double c64v[4] = {0.0, 0.0, 0.0, 0.0};
+                if (j0 + lane < cnt) {
+                    if constexpr (F32) {
+                        c32v = *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(m->far) + tj * rs);
+                    } else {
+                        const double *r = reinterpret_cast<const double *>(m->far) + tj * rs;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) c64v[q] = r[q];
+                    }
+                }
+                const int nj = min(32, cnt - j0);
+#pragma unroll 1
+                for (int jj = 0; jj < nj; ++jj) {
+                    bool nearp;
+                    if constexpr (F32) {
+                        float4 c;
+                        c.x = __shfl_sync(0xffffffffu, c32v.x, jj);
+                        c.y = __shfl_sync(0xffffffffu, c32v.y, jj);
+                        c.z = __shfl_sync(0xffffffffu, c32v.z, jj);
+                        c.w = __shfl_sync(0xffffffffu, c32v.w, jj);
+                        nearp = pair_is_near_f32(xp, yp, zp, c, a.far_ratio2_f);
+                    } else {
+                        double c[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) c[q] = __shfl_sync(0xffffffffu, c64v[q], jj);
+                        nearp = pair_is_near_f64(xd.x, xd.y, xd.z, c, a.far_ratio2);
+                    }
+                    unsigned owners = __ballot_sync(0xffffffffu, nearp && gi < k);
+                    if (!owners) continue;
+                    const int64_t tet = t * tile + j0 + jj;
+                    if constexpr (F32) {
+                        __syncwarp();
+                        if (lane < kNearF32Vec4) srec[warp][lane] = m->near32[tet * kNearF32Vec4 + lane];
+                        __syncwarp();
+                    }
+#pragma unroll 1
+                    while (owners) {
+                        const int owner = __ffs(owners) - 1;
+                        owners &= owners - 1u;
+                        if constexpr (F32) {
+                            const NearOut32 r = near_pair_f32_body<1>(spts + 9 * (warp * 32 + owner), srec[warp],
+                                                                      m->near64 + tet * kNearF64, lines, a.lines.f64,
+                                                                      a.L, lane);
+                            if (lane == owner) {
+                                const float v[3] = {r.vx, r.vy, r.vz};
+#pragma unroll
+                                for (int q = 0; q < 3; ++q) {
+                                    const float y = v[q] - c32[q];
+                                    const float s2 = s32[q] + y;
+                                    c32[q] = (s2 - s32[q]) - y;
+                                    s32[q] = s2;
+                                }
+                                hits += r.hits;
+                            }
+                        } else {
+                            const V3<double> xo = mk(__shfl_sync(0xffffffffu, xd.x, owner),
+                                                     __shfl_sync(0xffffffffu, xd.y, owner),
+                                                     __shfl_sync(0xffffffffu, xd.z, owner));
+                            const NearOut r = near_pair_f64(xo, m->near64 + tet * kNearF64, a.lines.f64, a.L, lane);
+                            if (lane == owner) {
+                                s64[0] += r.vx;
+                                s64[1] += r.vy;
+                                s64[2] += r.vz;
+                                hits += r.hits;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (gi >= k) return;
+    double *dst = a.near_out + 3 * ((a.meshes ? m->point_begin : 0) + gi);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) dst[q] = F32 ? (double)s32[q] - (double)c32[q] : s64[q];
+    if (a.counts) a.counts[3 * m->perm[gi] + 2] += hits;
 }
 
 }  // namespace
