@@ -122,9 +122,10 @@ __device__ inline void ring_window(const T *z, int N, V3<T> D, T rw, T bound, in
 // passing lines.  xs: the lane's point as float splits [component][hi, mid, lo]; r32: the
 // near record (shared memory); r64: its float64 copy (global, read only by the float64
 // steps); [a0, a1), [b0, b1): the warp's rings.  Adds the pair's k s x J to (ax, ay, az).
-__device__ __forceinline__ void ray_tet_f32(const float *__restrict__ xs, const float4 *__restrict__ r32,
-                                            const double *__restrict__ r64, const float4 *__restrict__ lines,
-                                            const dbl4 *__restrict__ lines64, int M, int a0, int a1, int b0, int b1,
+// Returns true when some of this lane's lines need the float64 steps (x on a vertex with the line nearly in
+// a face through it, or x within 1e-5 of the tet's boundary): ray_tet_redo_f64 does them afterwards.
+__device__ __forceinline__ bool ray_tet_f32(const float *__restrict__ xs, const float4 *__restrict__ r32,
+                                            const float4 *__restrict__ lines, int M, int a0, int a1, int b0, int b1,
                                             float &ax, float &ay, float &az, int &hits)
 {
     const float xh0 = xs[0], xm0 = xs[1], xh1 = xs[3], xm1 = xs[4], xh2 = xs[6], xm2 = xs[7];
@@ -246,33 +247,74 @@ __device__ __forceinline__ void ray_tet_f32(const float *__restrict__ xs, const 
             ++hits;
         }
     }
-    // the float64 steps, as a second pass over this lane's window lines (the same float32 tests pick the
-    // lines again): out of the line loop, so that their registers do not count against it
-    if (__any_sync(0xffffffffu, any_redo) && any_redo) {
-        const V3<double> xd = mk(join3(xs[0], xs[1], xs[2]), join3(xs[3], xs[4], xs[5]), join3(xs[6], xs[7], xs[8]));
-        V3<double> acc = mk(0.0, 0.0, 0.0);
-#pragma unroll 1
-        for (int wi = 0; wi < nW; ++wi) {
-            const int l = wi < nA ? lA + wi : lB + wi;
-            const float4 ln = lines[l];
-            const float rs = rc.x * ln.x + rc.y * ln.y + rc.z * ln.z;
-            if (rc2 - rs * rs > bound) continue;
-            const V3<float> s = mk(ln.x, ln.y, ln.z);
-            const float4 q0 = lds4(r32 + nf32::G1), q1 = lds4(r32 + nf32::G2), q2 = lds4(r32 + nf32::G3);
-            float b[4];
-            b[1] = q0.x * s.x + q0.y * s.y + q0.z * s.z;
-            b[2] = q1.x * s.x + q1.y * s.y + q1.z * s.z;
-            b[3] = q2.x * s.x + q2.y * s.y + q2.z * s.z;
-            b[0] = -(b[1] + b[2] + b[3]);
-            bool redo = whole_f64;
+    return any_redo;
+}
+
+// The float64 steps of ray_tet_f32 for this lane's point and one tet: the same float32 tests pick the
+// lines again (the window's lines that pass the bounding test and need float64), each is redone in
+// float64 and added to (ax, ay, az).  Run after the tile's tets, where few registers are live.
+__device__ __forceinline__ void ray_tet_redo_f64(const float *__restrict__ xs, const float4 *__restrict__ r32,
+                                                 const double *__restrict__ r64, const float4 *__restrict__ lines,
+                                                 const dbl4 *__restrict__ lines64, int M, int a0, int a1, int b0,
+                                                 int b1, float &ax, float &ay, float &az, int &hits)
+{
+    const float xh0 = xs[0], xm0 = xs[1], xh1 = xs[3], xm1 = xs[4], xh2 = xs[6], xm2 = xs[7];
+    const float4 ch = r32[nf32::CH], cm = r32[nf32::CM];
+    const V3<float> rc = mk((ch.x - xh0) + (cm.x - xm0), (ch.y - xh1) + (cm.y - xm1), (ch.z - xh2) + (cm.z - xm2));
+    const float rc2 = dot3(rc, rc);
+    const float bound = r32[nf32::G2].w * (1.0f + kBoundPadF);
+    const int nA = (a1 - a0) * M, nW = nA + (b1 - b0) * M;
+    const int lA = a0 * M, lB = b0 * M - nA;
+    const float *vh = reinterpret_cast<const float *>(r32 + nf32::VH);
+    const float *vm = reinterpret_cast<const float *>(r32 + nf32::VM);
+    int vk = -1;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) redo = redo || (b[k] * b[k] <= fb2[k]);
-            if (redo && line_f64_lean_inl(xd, r64, whole_f64 ? -1 : vk, lines64[l], acc)) ++hits;
-        }
-        ax += (float)acc.x;
-        ay += (float)acc.y;
-        az += (float)acc.z;
+    for (int i = 0; i < 4; ++i)
+        if (vk < 0 && vh[3 * i] == xh0 && vm[3 * i] == xm0 && vh[3 * i + 1] == xh1 && vm[3 * i + 1] == xm1 &&
+            vh[3 * i + 2] == xh2 && vm[3 * i + 2] == xm2)
+            vk = i;
+    const float4 q0 = r32[nf32::G1], q1 = r32[nf32::G2], q2 = r32[nf32::G3];
+    V3<float> g[4];
+    g[1] = mk(q0.x, q0.y, q0.z);
+    g[2] = mk(q1.x, q1.y, q1.z);
+    g[3] = mk(q2.x, q2.y, q2.z);
+    g[0] = mk(-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z));
+    bool whole_f64 = false;
+    if (vk < 0) {
+        const V3<float> d0 = mk((xh0 - vh[0]) + (xm0 - vm[0]), (xh1 - vh[1]) + (xm1 - vm[1]), (xh2 - vh[2]) + (xm2 - vm[2]));
+        float a[4];
+        a[1] = dot3(g[1], d0);
+        a[2] = dot3(g[2], d0);
+        a[3] = dot3(g[3], d0);
+        a[0] = 1.0f - a[1] - a[2] - a[3];
+        const float amin = fminf(fminf(a[0], a[1]), fminf(a[2], a[3]));
+        const float aabs = fminf(fminf(fabsf(a[0]), fabsf(a[1])), fminf(fabsf(a[2]), fabsf(a[3])));
+        whole_f64 = amin > -kDegenA && aabs < kDegenA;
     }
+    float fb2[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        fb2[i] = (vk >= 0 && i != vk) ? kVertexFallback * kVertexFallback * dot3(g[i], g[i]) : -1.0f;
+    const V3<double> xd = mk(join3(xs[0], xs[1], xs[2]), join3(xs[3], xs[4], xs[5]), join3(xs[6], xs[7], xs[8]));
+    V3<double> acc = mk(0.0, 0.0, 0.0);
+#pragma unroll 1
+    for (int wi = 0; wi < nW; ++wi) {
+        const int l = wi < nA ? lA + wi : lB + wi;
+        const float4 ln = lines[l];
+        const float rs = rc.x * ln.x + rc.y * ln.y + rc.z * ln.z;
+        if (rc2 - rs * rs > bound) continue;
+        const V3<float> s = mk(ln.x, ln.y, ln.z);
+        bool redo = whole_f64;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float bk = dot3(g[k], s);
+            redo = redo || (bk * bk <= fb2[k]);
+        }
+        if (redo && line_f64_lean_inl(xd, r64, whole_f64 ? -1 : vk, lines64[l], acc)) ++hits;
+    }
+    ax += (float)acc.x;
+    ay += (float)acc.y;
+    az += (float)acc.z;
 }
 
 // float64 form of ray_tet_f32 (the velocity kernel's line_f64 per line); r: the near record.
@@ -422,6 +464,7 @@ __global__ void __launch_bounds__(kRayThreads, 4) ray_kernel(const VelocityArgs 
             const unsigned char *tb = stages + st * STAGE;
             if constexpr (F32) {
                 float ax = 0.f, ay = 0.f, az = 0.f;
+                uint32_t redo_tets = 0u;  // this lane's tets of the tile that need float64 steps
 #pragma unroll 1
                 for (int j = 0; j < cnt; ++j) {
                     const float4 *r32 = reinterpret_cast<const float4 *>(tb) + j * kNearF32Vec4;
@@ -429,8 +472,20 @@ __global__ void __launch_bounds__(kRayThreads, 4) ray_kernel(const VelocityArgs 
                     int a0, a1, b0, b1;
                     ring_window<float>(sz, N, mk(ch.x - cwx, ch.y - cwy, ch.z - cwz), rw,
                                        r32[nf32::G2].w * (1.0f + kBoundPadF), a0, a1, b0, b1);
-                    ray_tet_f32(xs, r32, md.near64 + (t * kRayTile + j) * kNearF64, sdir, a.lines.f64, M, a0, a1, b0,
-                                b1, ax, ay, az, hits);
+                    if (ray_tet_f32(xs, r32, sdir, M, a0, a1, b0, b1, ax, ay, az, hits)) redo_tets |= 1u << j;
+                }
+                // the float64 steps of the tile (rare), while its records are still staged
+#pragma unroll 1
+                while (redo_tets) {
+                    const int j = __ffs(redo_tets) - 1;
+                    redo_tets &= redo_tets - 1u;
+                    const float4 *r32 = reinterpret_cast<const float4 *>(tb) + j * kNearF32Vec4;
+                    const float4 ch = r32[nf32::CH];
+                    int a0, a1, b0, b1;
+                    ring_window<float>(sz, N, mk(ch.x - cwx, ch.y - cwy, ch.z - cwz), rw,
+                                       r32[nf32::G2].w * (1.0f + kBoundPadF), a0, a1, b0, b1);
+                    ray_tet_redo_f64(xs, r32, md.near64 + (t * kRayTile + j) * kNearF64, sdir, a.lines.f64, M, a0,
+                                     a1, b0, b1, ax, ay, az, hits);
                 }
                 const float v[3] = {ax, ay, az};
 #pragma unroll
