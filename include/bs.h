@@ -131,8 +131,17 @@ BS_API int bs_velocity_host(bs_handle h, const double *eval_pts_host, int64_t k,
  * handle; about 200 bytes per tet and 100 per boundary face of device memory,
  * owned by the handle); later calls are asynchronous on `stream`.  A walk that exceeds max(4096, 64 n_tets^(1/3))
  * tets (impossible on a valid mesh) stops and raises BS_ERR_TIMEOUT at the next
- * bs_status.  Setting the environment variable BS_WALK=0 disables the walk.
- * Errors: BS_ERR_ARG, BS_ERR_ORDER, BS_ERR_CUDA. */
+ * bs_status.  With a finite far_ratio (the hybrid rule) and the ray near
+ * rule, when the kernel variant in use leaves the near pairs to a pass of
+ * their own (see bs_variant_shape), the far rule runs as in bs_velocity and
+ * the near field is taken by the same walk, restricted to the tets the far
+ * rule's test calls near (the same decision, bit for bit): a half-line
+ * stops once it is farther from the node than max over tets of (far_ratio
+ * circumradius + the tet's bounding radius about its centroid), beyond
+ * which every tet is far.  On a mesh the walk cannot serve, the near pass
+ * evaluates the near pairs instead.  Setting the environment variable
+ * BS_WALK=0 disables the walk.  Errors: BS_ERR_ARG, BS_ERR_ORDER,
+ * BS_ERR_CUDA. */
 BS_API int bs_velocity_nodes(bs_handle h, const bs_params *p, double *out_dev, void *stream);
 
 /* Velocity at the nodes (as bs_velocity_nodes) and its derivative along a
@@ -337,14 +346,19 @@ BS_API int bs_set_variant(bs_handle h, int precision, int tet_gauss_order, int n
  * timing; else time every variant on `stream` (each after a warm-up call),
  * take the fastest, and store it in the cache (in BS_TUNE_CACHE if set, else
  * the shipped file, when the file is writable; for this process in any case).
- * The environment variable BS_TUNE_FORCE=1 times even on a cache hit.  Calls
- * that run the all-ray kernel (far_ratio = +inf, at most 4096 directions, the
- * ray rule) have a single launch shape and need no tuning.  Synchronises the
- * stream; allocates and frees one [n_nodes][3] output. */
+ * The environment variable BS_TUNE_FORCE=1 times even on a cache hit.  Two
+ * paths are tuned, each with its own cache entry: bs_velocity at the nodes
+ * (the points path) and, for the hybrid rule with the ray near rule,
+ * bs_velocity_nodes (the nodes path, where the mesh walk can take the near
+ * field).  Calls that run the all-ray kernel (far_ratio = +inf, at most 4096
+ * directions, the ray rule) have a single launch shape and need no tuning.
+ * Synchronises the stream; allocates and frees one [n_nodes][3] output. */
 BS_API int bs_autotune(bs_handle h, const bs_params *p, void *stream);
 /* The variant the last bs_autotune for this precision and tet rule (ray
- * near rule) chose or found in the cache (0 if none). */
-BS_API int bs_tuned_variant(bs_handle h, int precision, int tet_gauss_order, int *variant);
+ * near rule) chose or found in the cache for the points path (at_nodes = 0:
+ * bs_velocity) or the nodes path (at_nodes = 1: bs_velocity_nodes); 0 if
+ * none. */
+BS_API int bs_tuned_variant(bs_handle h, int precision, int tet_gauss_order, int at_nodes, int *variant);
 
 #ifdef __cplusplus
 }

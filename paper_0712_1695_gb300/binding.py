@@ -86,7 +86,7 @@ def load(path: str = LIB_PATH):
         lib.bs_velocity_nodes_dderiv.argtypes = [_P, ctypes.POINTER(bs_params), _P, _P, _P, _P]
         lib.bs_rk2_step_stretch.argtypes = [_P, ctypes.c_double, ctypes.POINTER(bs_params), _P]
         lib.bs_omega.argtypes = [_P, _P, _P]
-        lib.bs_tuned_variant.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        lib.bs_tuned_variant.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         lib.bs_profile.argtypes = [_P, ctypes.c_int]
         lib.bs_profile_read.argtypes = [_P, _D, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         _lib = lib
@@ -282,14 +282,17 @@ class Mesh:
         _check(load().bs_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(kl), ctypes.byref(al)))
         return ms.value, kl.value, al.value
 
-    def bs_autotune(self, stream=None, **params):
+    def bs_autotune(self, stream=None, at_nodes=False, **params):
+        """Tune the kernel variant for these parameters (both paths); returns the variant of the points path
+        (bs_velocity) or, with at_nodes, of the nodes path (bs_velocity_nodes)."""
         p = make_params(**params)
         _check(load().bs_autotune(self.handle, ctypes.byref(p), _stream_ptr(stream)))
-        return self.bs_tuned_variant(params.get("precision", BS_FP64), params.get("tet_gauss_order", 4))
+        return self.bs_tuned_variant(params.get("precision", BS_FP64), params.get("tet_gauss_order", 4), at_nodes)
 
-    def bs_tuned_variant(self, precision, tet_gauss_order):
+    def bs_tuned_variant(self, precision, tet_gauss_order, at_nodes=False):
         v = ctypes.c_int()
-        _check(load().bs_tuned_variant(self.handle, int(precision), int(tet_gauss_order), ctypes.byref(v)))
+        _check(load().bs_tuned_variant(self.handle, int(precision), int(tet_gauss_order), int(bool(at_nodes)),
+                                       ctypes.byref(v)))
         return v.value
 
     def bs_set_variant(self, precision, tet_gauss_order, near_rule, variant):

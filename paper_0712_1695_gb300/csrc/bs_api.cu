@@ -99,6 +99,9 @@ struct bs_ctx {
     size_t partial_cap = 0;
     double *near_out = nullptr;
     size_t near_cap = 0;
+    float *r_stop = nullptr;  // the near walk's stop radius (device), for rstop_version and rstop_fr
+    uint64_t rstop_version = 0;
+    double rstop_fr = 0.0;
     // staging for bs_velocity_host
     double *stage = nullptr;
     size_t stage_cap = 0;
@@ -109,7 +112,8 @@ struct bs_ctx {
     int ray_occ[2] = {};                   // cached CTAs per SM of the all-ray kernel by [precision]
     int ray_occ_L[2] = {};                 // ... for this many directions
     int pinned[2][2][65];                  // bs_set_variant by [near rule][precision][Q], -1: automatic
-    int tuned[2][2][65] = {};              // the variant bs_autotune last chose (or found in the cache)
+    int tuned[2][2][2][65] = {};           // the variant bs_autotune last chose (or found in the cache) by
+                                           // [nodes path][near rule][precision][Q]
     std::map<std::string, int> tune_memo;  // tuning key -> cached variant (-1: no entry)
     char gpu_name[256] = {};
     // mesh walk of the all-ray velocity at the nodes (built on first use)
@@ -161,7 +165,7 @@ void free_ctx(bs_ctx *h)
                     h->cell_count, h->box, h->walk_nbr, h->walk_inc_off, h->walk_inc, h->walk_bface,
                     h->walk_bnode, h->walk_mode, h->walk_rec, h->rk_w, h->walk_grid.grid,
                     h->walk_grid.cell_off, h->walk_grid.cell_cnt, h->walk_grid.cell_face, h->walk_grid.geo,
-                    h->walk_grid.geo32, h->near_out};
+                    h->walk_grid.geo32, h->near_out, h->r_stop};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete h;
@@ -271,8 +275,9 @@ cudaError_t ensure_far(bs_ctx *h, int Q, int tile, int layout, cudaStream_t st)
 
 // The kernel variant of the velocity kernel a call on k points uses: the environment variable
 // BS_VARIANT, else the variant bs_set_variant pinned, else the autotuner's cache entry for this GPU and
-// problem, else (the ray rule) the small-mesh rule, else variant 0.
-int choose_variant(bs_ctx *h, const bs_params *p, int64_t k)
+// problem (at_nodes: the mesh's nodes by bs_velocity_nodes, where the walk can take the near field), else
+// (the ray rule) the small-mesh rule, else variant 0.
+int choose_variant(bs_ctx *h, const bs_params *p, int64_t k, bool at_nodes)
 {
     const int prec = p->precision, Q = p->tet_gauss_order, nr = p->near_rule;
     const int nv = num_variants(prec, Q, nr);
@@ -283,7 +288,8 @@ int choose_variant(bs_ctx *h, const bs_params *p, int64_t k)
     }
     const int pin = h->pinned[nr][prec][Q];
     if (pin >= 0 && pin < nv) return pin;
-    const std::string key = tune_key(h->gpu_name, h->n_sm, prec, Q, nr, p->n_phi * p->n_theta, k, h->n_tets);
+    const std::string key =
+        tune_key(h->gpu_name, h->n_sm, prec, Q, nr, p->n_phi * p->n_theta, k, h->n_tets, at_nodes);
     auto it = h->tune_memo.find(key);
     const int tv = it != h->tune_memo.end() ? it->second : (h->tune_memo[key] = tune_lookup(key, prec, Q, nr));
     if (tv >= 0 && tv < nv) return tv;
@@ -497,7 +503,7 @@ int bs_mesh_size(bs_handle h, int64_t *n_nodes, int64_t *n_tets)
 
 namespace {
 int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_params *p, double *out_dev,
-                  void *stream, const int *skip);
+                  void *stream, const int *skip, const WalkArgs *near_walk = nullptr);
 }
 
 int bs_velocity(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_params *p, double *out_dev,
@@ -569,12 +575,17 @@ int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *d
     if (!out_dev) return fail(BS_ERR_ARG, "NULL output");
     const int L = p->n_phi * p->n_theta;
     const char *env = getenv("BS_WALK");
-    const bool walk = isinf(p->far_ratio) && L <= kRayLinesSmemMax && h->n_tets > 0 && !(env && atoi(env) == 0) &&
-                      p->near_rule == BS_NEAR_RAY;
+    const bool can_walk = L <= kRayLinesSmemMax && h->n_tets > 0 && !(env && atoi(env) == 0) &&
+                          p->near_rule == BS_NEAR_RAY;
+    const bool walk = isinf(p->far_ratio) && can_walk;  // the all-ray rule at every pair
     if (dout && !walk)
         return fail(BS_ERR_ARG, "the derivative along directions is the all-ray method's (far_ratio = +inf, at most "
                                 "4096 directions) computed by the mesh walk");
-    if (!walk) return velocity_impl(h, h->nodes, h->n_nodes, p, out_dev, stream, nullptr);
+    // the hybrid rule: the walk takes the near field when the variant leaves it to a pass of its own
+    const bool near_walk = !isinf(p->far_ratio) && can_walk && !dout &&
+                           shape_for(p->precision, p->tet_gauss_order, choose_variant(h, p, h->n_nodes, true),
+                                     p->near_rule).drain == 3;
+    if (!walk && !near_walk) return velocity_impl(h, h->nodes, h->n_nodes, p, out_dev, stream, nullptr);
     cudaStream_t st = (cudaStream_t)stream;
     BS_CUDA(ensure_walk(h));
     BS_CUDA(ensure_lines(h, p->n_phi, p->n_theta, st));
@@ -624,6 +635,20 @@ int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *d
     // no valid mesh needs more steps than tets; a small cap keeps a broken walk short
     w.max_steps = (int)std::min<int64_t>(h->n_tets, std::max<int64_t>(4096, 64 * (int64_t)std::cbrt((double)h->n_tets)));
     if (h->walk_max_steps > 0) w.max_steps = (int)std::min<int64_t>(h->walk_max_steps, INT32_MAX);
+    if (near_walk) {
+        // the stop radius for this mesh version and far ratio; velocity_impl fills in the rest
+        if (!h->r_stop) BS_CUDA(cudaMallocAsync((void **)&h->r_stop, sizeof(float), st));
+        if (h->rstop_version != h->version || h->rstop_fr != p->far_ratio) {
+            BS_CUDA(launch_near_reach(h->rho2, h->near64, h->n_tets, p->far_ratio, h->r_stop, st));
+            h->rstop_version = h->version;
+            h->rstop_fr = p->far_ratio;
+            if (h->prof) h->prof_all += 1;
+        }
+        w.near_mode = 1;
+        w.r_stop = h->r_stop;
+        w.counts = p->counts;
+        return velocity_impl(h, h->nodes, h->n_nodes, p, out_dev, stream, nullptr, &w);
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->prof) {
         if (h->ev_free.empty()) {
@@ -749,8 +774,10 @@ int bs_graph_steps(bs_handle h, int64_t *steps)
 
 namespace {
 
+// near_walk (evaluation points = the mesh's nodes, hybrid rule): the mesh walk's arguments for the near field;
+// used when the variant leaves the near pairs to a pass of their own.
 int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_params *p, double *out_dev,
-                  void *stream, const int *skip)
+                  void *stream, const int *skip, const WalkArgs *near_walk)
 {
     if (!h) return fail(BS_ERR_ARG, "handle is NULL");
     int rc = check_params(p);
@@ -774,7 +801,7 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     const char *generic_env = getenv("BS_ALLRAY_GENERIC");
     const bool ray = isinf(p->far_ratio) && L <= kRayLinesSmemMax && !(generic_env && atoi(generic_env) != 0) &&
                      p->near_rule == BS_NEAR_RAY;
-    const int variant = ray ? 0 : choose_variant(h, p, k);
+    const int variant = ray ? 0 : choose_variant(h, p, k, near_walk != nullptr);
     const LaunchShape shape = ray ? ray_shape() : shape_for(p->precision, Q, variant, p->near_rule);
     if (!ray) BS_CUDA(ensure_far(h, Q, shape.tile, shape.layout, st));
     int occ_ray = 0;
@@ -859,12 +886,36 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
         }
         h->ev_used.push_back({e0, e1});
     }
-    if (ray) BS_CUDA(launch_ray(p->precision, a, h->n_sm, st, &grid, e0, e1));
-    else BS_CUDA(launch_velocity(p->precision, a, h->n_sm, st, &grid, e0, e1));
+    int extra = 0;  // kernels launched beyond zero, velocity and reduce (for bs_profile)
+    if (ray) {
+        BS_CUDA(launch_ray(p->precision, a, h->n_sm, st, &grid, e0, e1));
+    } else {
+        BS_CUDA(launch_velocity(p->precision, a, h->n_sm, st, &grid, e0, nullptr));
+        if (shape.drain == 3) {  // the near field: by the mesh walk at the nodes when it can, else the near pass
+            if (near_walk) {
+                WalkArgs w = *near_walk;
+                w.perm = h->perm;
+                w.near_out = a.near_out;
+                w.far = a.m.far;
+                w.tile_hdr = h->tile_hdr;
+                w.tile = a.tile;
+                w.far_stride = a.far_stride;
+                w.far_ratio2_f = a.far_ratio2_f;
+                w.far_ratio2 = a.far_ratio2;
+                w.counts = p->counts;
+                BS_CUDA(launch_walk(p->precision, w, st));
+                a.near_skip = near_walk->mode;  // the walk is in charge unless the mesh is not conforming
+                extra += 2;
+            }
+            BS_CUDA(launch_near_pass(p->precision, a, st));
+            extra += 1;
+        }
+        if (e1) BS_CUDA(cudaEventRecord(e1, st));
+    }
     BS_CUDA(launch_reduce(a, st));
     if (h->prof) {
         h->prof_kernel += 1;
-        h->prof_all += 5 /* ordering */ + 3 /* zero, velocity, reduce */;
+        h->prof_all += 5 /* ordering */ + 3 /* zero, velocity, reduce */ + extra;
     }
     return BS_OK;
 }
@@ -1202,33 +1253,30 @@ int bs_batch_destroy(bs_batch b)
     return BS_OK;
 }
 
-int bs_autotune(bs_handle h, const bs_params *p, void *stream)
+}  // extern "C"
+
+namespace {
+
+// bs_autotune for one path: the points path (bs_velocity at the mesh's nodes: arbitrary points) or the nodes
+// path (bs_velocity_nodes, where the mesh walk can take the near field).  A cache hit takes the stored
+// variant; else every variant is pinned in turn and timed.  *chosen: the variant.
+int tune_path(bs_handle h, const bs_params *p, void *stream, bool at_nodes, int *chosen)
 {
-    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
-    int rc = check_params(p);
-    if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int prec = p->precision, Q = p->tet_gauss_order, nr = p->near_rule;
     const int L = p->n_phi * p->n_theta;
     const int nv = num_variants(prec, Q, nr);
-    h->tuned[nr][prec][Q] = 0;
-    // nothing to choose: no tets, or the call would run the all-ray kernel (one launch shape)
-    const char *generic_env = getenv("BS_ALLRAY_GENERIC");
-    const bool ray = isinf(p->far_ratio) && L <= kRayLinesSmemMax && !(generic_env && atoi(generic_env) != 0) &&
-                     nr == BS_NEAR_RAY;
-    if (h->n_tets == 0 || ray || nv <= 0) return BS_OK;
-    const int64_t k = h->n_nodes;  // tuned on the mesh's own nodes, the common use
-    const std::string key = tune_key(h->gpu_name, h->n_sm, prec, Q, nr, L, k, h->n_tets);
+    const int64_t k = h->n_nodes;
+    const std::string key = tune_key(h->gpu_name, h->n_sm, prec, Q, nr, L, k, h->n_tets, at_nodes);
     const char *force = getenv("BS_TUNE_FORCE");
     if (!(force && atoi(force) != 0)) {
         const int v = tune_lookup(key, prec, Q, nr);
         if (v >= 0 && v < nv) {  // a cache hit: no timing
             h->tune_memo[key] = v;
-            h->tuned[nr][prec][Q] = v;
+            *chosen = v;
             return BS_OK;
         }
     }
-    // time every variant (each pinned in turn), keep the fastest
     double *out = nullptr;
     BS_CUDA(cudaMallocAsync((void **)&out, sizeof(double) * 3 * h->n_nodes, st));
     bs_params q = *p;
@@ -1237,17 +1285,20 @@ int bs_autotune(bs_handle h, const bs_params *p, void *stream)
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     double best = INFINITY;
-    int best_v = 0;
+    int best_v = 0, rc = BS_OK;
     const int saved = h->pinned[nr][prec][Q];
+    auto call = [&]() {
+        return at_nodes ? bs_velocity_nodes(h, &q, out, stream) : bs_velocity(h, h->nodes, k, &q, out, stream);
+    };
     for (int v = 0; v < nv && e == cudaSuccess && rc == BS_OK; ++v) {
         h->pinned[nr][prec][Q] = v;
-        rc = bs_velocity(h, h->nodes, k, &q, out, stream);  // warm-up (also builds this variant's tables)
+        rc = call();  // warm-up (also builds this variant's tables)
         double total = 0.0;
         int reps = 0;
         // at least one timed call, more while they take under 20 ms in all (at most 10)
         while (rc == BS_OK && e == cudaSuccess && reps < 10 && (reps == 0 || total < 20.0)) {
             if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
-            rc = bs_velocity(h, h->nodes, k, &q, out, stream);
+            rc = call();
             if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
             if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
             float ms = 0.f;
@@ -1267,21 +1318,49 @@ int bs_autotune(bs_handle h, const bs_params *p, void *stream)
     if (e != cudaSuccess) return cuda_fail(e, "bs_autotune");
     if (rc) return rc;
     BS_CUDA(cudaStreamSynchronize(st));
-    int status = BS_OK;
-    if (int fs = bs_status(h, stream)) status = fs;  // a timed call that raised the flag: keep nothing
-    if (status) return status;
+    if (int fs = bs_status(h, stream)) return fs;  // a timed call raised the flag: keep nothing
     h->tune_memo[key] = best_v;
-    h->tuned[nr][prec][Q] = best_v;
+    *chosen = best_v;
     // persisted where the cache file is writable; kept for this process in any case
     tune_store(key, prec, Q, nr, best_v, best, nv);
     return BS_OK;
 }
 
-int bs_tuned_variant(bs_handle h, int precision, int tet_gauss_order, int *variant)
+}  // namespace
+
+extern "C" {
+
+int bs_autotune(bs_handle h, const bs_params *p, void *stream)
 {
-    if (!h || !variant || (precision != BS_FP32 && precision != BS_FP64) || !valid_order(tet_gauss_order))
+    if (!h) return fail(BS_ERR_ARG, "handle is NULL");
+    int rc = check_params(p);
+    if (rc) return rc;
+    const int prec = p->precision, Q = p->tet_gauss_order, nr = p->near_rule;
+    const int L = p->n_phi * p->n_theta;
+    h->tuned[0][nr][prec][Q] = h->tuned[1][nr][prec][Q] = 0;
+    // nothing to choose: no tets, or the calls would run the all-ray kernel or the all-ray walk (one shape)
+    const char *generic_env = getenv("BS_ALLRAY_GENERIC");
+    const bool ray = isinf(p->far_ratio) && L <= kRayLinesSmemMax && !(generic_env && atoi(generic_env) != 0) &&
+                     nr == BS_NEAR_RAY;
+    if (h->n_tets == 0 || ray || num_variants(prec, Q, nr) <= 0) return BS_OK;
+    int v = 0;
+    if ((rc = tune_path(h, p, stream, false, &v))) return rc;
+    h->tuned[0][nr][prec][Q] = v;
+    // the nodes path differs where the mesh walk can take the near field (the hybrid rule, the ray near rule)
+    const char *env = getenv("BS_WALK");
+    if (!isinf(p->far_ratio) && L <= kRayLinesSmemMax && nr == BS_NEAR_RAY && !(env && atoi(env) == 0)) {
+        if ((rc = tune_path(h, p, stream, true, &v))) return rc;
+    }
+    h->tuned[1][nr][prec][Q] = v;
+    return BS_OK;
+}
+
+int bs_tuned_variant(bs_handle h, int precision, int tet_gauss_order, int at_nodes, int *variant)
+{
+    if (!h || !variant || (precision != BS_FP32 && precision != BS_FP64) || !valid_order(tet_gauss_order) ||
+        (at_nodes != 0 && at_nodes != 1))
         return fail(BS_ERR_ARG, "bad argument");
-    *variant = h->tuned[BS_NEAR_RAY][precision][tet_gauss_order];
+    *variant = h->tuned[at_nodes][BS_NEAR_RAY][precision][tet_gauss_order];
     return BS_OK;
 }
 

@@ -166,6 +166,7 @@ struct VelocityArgs {
     double *near_out = nullptr;
     int tile = 0, far_stride = 0;
     int64_t n_near_warps = 0;
+    const int *near_skip = nullptr;  // device flag: when set, the near pass returns at once
 };
 
 // far ratio of a launch: its square (+inf for the all-ray rule) in double and float, the ratio in float
@@ -237,12 +238,15 @@ int velocity_ctas_per_sm(int precision, int Q, int variant = 0, int near_rule = 
 cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid_out,
                             cudaEvent_t ev_start = nullptr, cudaEvent_t ev_stop = nullptr);
 cudaError_t launch_reduce(const VelocityArgs &a, cudaStream_t st);
+// the near pass after the far sweep of a variant that leaves the near pairs to it (no-op otherwise); it returns
+// at once when *a.near_skip is set (the mesh walk evaluated the near field)
+cudaError_t launch_near_pass(int precision, const VelocityArgs &a, cudaStream_t st);
 // autotuner cache (bs_tune.cu): key of a (GPU, precision, rule, near rule, directions, size class), the
 // variant stored for it (-1 if none, or if its launch shape does not match this build), and a store that
 // also writes the cache file
 std::string variant_shape_string(int precision, int Q, int near_rule, int variant);
 std::string tune_key(const char *gpu_name, int n_sm, int precision, int Q, int near_rule, int L, int64_t k,
-                     int64_t n_tets);
+                     int64_t n_tets, bool at_nodes);
 int tune_lookup(const std::string &key, int precision, int Q, int near_rule);
 bool tune_store(const std::string &key, int precision, int Q, int near_rule, int variant, double ms, int candidates);
 // all-ray kernel (bs_ray.cu): one point per thread, near records streamed in tiles of ray_shape().tile;
@@ -308,6 +312,19 @@ struct WalkArgs {
     const float *bgeo32 = nullptr;
     int *flag = nullptr;
     int max_steps = 0;           // tets per half-line before the walk gives up (error flag)
+    // near mode (the hybrid rule at the nodes): only the tets the far sweep's test calls near contribute
+    // (pair_is_near_*, the same decision as the far sweep, which leaves them out), a half-line stops once it
+    // is farther than *r_stop from the node (every tet beyond is far), warp w takes node perm[w] and writes
+    // its totals to near_out[w] (float64, by spatial position) and its ray hits to counts[node][2]
+    int near_mode = 0;
+    const int *perm = nullptr;
+    double *near_out = nullptr;
+    const void *far = nullptr;        // far records (float32 tile frame, or float64)
+    const float4 *tile_hdr = nullptr;
+    int tile = 0, far_stride = 0;
+    float far_ratio2_f = 0.f;
+    double far_ratio2 = 0.0;
+    const float *r_stop = nullptr;    // device: max over tets of far_ratio * circumradius + bounding radius
 };
 constexpr int kWalkRecVec4 = 8;  // float4 per float32 walk record (one 128-byte line)
 // float32 walk records from the near records and the face neighbours (after every mesh update)
@@ -325,6 +342,10 @@ cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const 
                                 int conforming, int *mode, float4 *wrec, cudaStream_t st);
 cudaError_t launch_walk(int precision, const WalkArgs &a, cudaStream_t st, cudaEvent_t ev_start = nullptr,
                         cudaEvent_t ev_stop = nullptr);
+// *r_stop := (1 + 1e-4) max over tets of (far_ratio * circumradius + bounding radius about the centroid):
+// a half-line point farther than this from a node lies in no tet the node is near to
+cudaError_t launch_near_reach(const double *rho2, const double *near64, int64_t n_tets, double far_ratio,
+                              float *r_stop, cudaStream_t st);
 // Heun step position updates (n_values = 3 * nodes)
 cudaError_t launch_euler(const double *x0, const double *v0, double dt, int64_t n_values, double *x, cudaStream_t st);
 cudaError_t launch_heun(const double *x0, const double *v0, const double *v1, double dt, int64_t n_values, double *x,

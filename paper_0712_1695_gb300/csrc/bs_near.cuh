@@ -106,6 +106,37 @@ __device__ inline T warp_sum(T v)
     return v;
 }
 
+// The near/far decision of a (point, tet) pair (Section 1: the tet is far when the point lies beyond
+// far_ratio circumradii of its centroid), with explicit round-to-nearest operations (no contraction), so
+// that every kernel that takes it -- the far sweep, which leaves the near pairs out of its sums, and the
+// near pass and the mesh walk, which evaluate them -- decides every pair the same way, bit for bit.  float32: the point
+// x' and the centroid c' in the tile frame (x' = x_hi - o, as the far sweep forms it), c_rho2 = the far
+// record's first float4 (c', rho^2); float64: global coordinates, c_rho2 = the record's first four.
+__device__ __forceinline__ bool pair_is_near_f32(float xp, float yp, float zp, float4 c_rho2, float fr2)
+{
+    const float dx = __fsub_rn(xp, c_rho2.x), dy = __fsub_rn(yp, c_rho2.y), dz = __fsub_rn(zp, c_rho2.z);
+    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    return !(d2 > __fmul_rn(fr2, c_rho2.w));
+}
+__device__ __forceinline__ bool pair_is_near_f64(double x, double y, double z, const double *c_rho2, double fr2)
+{
+    const double dx = __dsub_rn(x, c_rho2[0]), dy = __dsub_rn(y, c_rho2[1]), dz = __dsub_rn(z, c_rho2[2]);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return !(d2 > __dmul_rn(fr2, c_rho2[3]));
+}
+// Can a point of the ball (centre, radius) = sphere be near a tet of the tile (header: origin o and the
+// radius rc of its centroids about o; rho_max its largest circumradius)?  No, when the ball is farther
+// than far_ratio rho_max from every centroid, with a margin (0.1% and 1e-5 of the coordinates' scale)
+// that covers the float32 rounding of this test and of the per-pair test: a culled tile holds no pair
+// the per-pair test would call near.
+__device__ __forceinline__ bool tile_culled(float4 sphere, float4 hdr, float rho_max, float far_ratio)
+{
+    const float dx = sphere.x - hdr.x, dy = sphere.y - hdr.y, dz = sphere.z - hdr.z;
+    const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float scale = fabsf(hdr.x) + fabsf(hdr.y) + fabsf(hdr.z) + dist;
+    return dist - sphere.w - hdr.w > far_ratio * rho_max * 1.001f + 1e-5f * scale;
+}
+
 // Everything about a pair that does not depend on the line, in float64.
 struct PairF64 {
     double a[4];           // lambda_i(x); exactly e_k when x is vertex k

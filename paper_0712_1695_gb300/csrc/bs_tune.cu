@@ -1,7 +1,9 @@
 // bs_tune.cu -- the autotuner's cache of chosen kernel variants (host code).
 //
 // An entry maps a tuning key -- GPU name and SM count, precision, tet rule, near rule, number of
-// directions, and the problem's size class (ceil(log2) of the evaluation points and of the tets) -- to
+// directions, the problem's size class (ceil(log2) of the evaluation points and of the tets), and whether
+// the points are the mesh's nodes evaluated by bs_velocity_nodes (where the mesh walk can take the near
+// field) or arbitrary points -- to
 // the variant bs_autotune timed fastest, with that variant's launch shape as a check: an entry whose
 // shape no longer matches the variant table of this build is ignored.  Entries are read from two JSON
 // files: the one shipped beside the package (tune_cache.json next to the library's _build directory)
@@ -150,11 +152,12 @@ std::string variant_shape_string(int precision, int Q, int near_rule, int varian
 }
 
 std::string tune_key(const char *gpu_name, int n_sm, int precision, int Q, int near_rule, int L, int64_t k,
-                     int64_t n_tets)
+                     int64_t n_tets, bool at_nodes)
 {
     char b[256];
-    snprintf(b, sizeof b, "%s/%dsm %s q%d %s L%d k2^%d t2^%d", gpu_name, n_sm, precision == BS_FP32 ? "fp32" : "fp64",
-             Q, near_rule == BS_NEAR_EXACT ? "exact" : "ray", L, ceil_log2(k), ceil_log2(n_tets));
+    snprintf(b, sizeof b, "%s/%dsm %s q%d %s L%d k2^%d t2^%d %s", gpu_name, n_sm,
+             precision == BS_FP32 ? "fp32" : "fp64", Q, near_rule == BS_NEAR_EXACT ? "exact" : "ray", L,
+             ceil_log2(k), ceil_log2(n_tets), at_nodes ? "nodes" : "points");
     return b;
 }
 

@@ -130,7 +130,16 @@ cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cuda
     if (ev_start && (e = cudaEventRecord(ev_start, st)) != cudaSuccess) return e;
     e = vl.v[a.variant].launch(a, n_sm, st, grid_out, false, nullptr);
     if (e != cudaSuccess) return e;
-    if (vl.v[a.variant].s.DR == 3 && a.n_near_warps > 0) {  // the near pass
+    if (ev_stop) e = cudaEventRecord(ev_stop, st);
+    return e;
+}
+
+cudaError_t launch_near_pass(int precision, const VelocityArgs &a, cudaStream_t st)
+{
+    const VariantList vl = velocity_variants(precision, a.Q, a.near_rule);
+    if (vl.n == 0 || a.variant < 0 || a.variant >= vl.n) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    if (vl.v[a.variant].s.DR == 3 && a.n_near_warps > 0) {
         if (!a.near_out || a.tile <= 0 || a.far_stride <= 0) return cudaErrorInvalidValue;
         const size_t sm = a.smem_lines ? sizeof(float4) * a.L : 0;
         const unsigned blocks = (unsigned)((a.n_near_warps + 3) / 4);
@@ -145,9 +154,8 @@ cudaError_t launch_velocity(int precision, const VelocityArgs &a, int n_sm, cuda
                 return e;
             near_pass_kernel<double><<<blocks, 128, sm, st>>>(a);
         }
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = cudaGetLastError();
     }
-    if (ev_stop) e = cudaEventRecord(ev_stop, st);
     return e;
 }
 

@@ -560,37 +560,6 @@ __device__ __forceinline__ void cursor_advance(PairCursor &c, const uint32_t *wm
     c.k0 = k;
 }
 
-// The near/far decision of a (point, tet) pair (Section 1: the tet is far when the point lies beyond
-// far_ratio circumradii of its centroid), with explicit round-to-nearest operations (no contraction), so
-// that every kernel that takes it -- the far sweep, which leaves the near pairs out of its sums, and the
-// near pass, which evaluates them -- decides every pair the same way, bit for bit.  float32: the point
-// x' and the centroid c' in the tile frame (x' = x_hi - o, as the far sweep forms it), c_rho2 = the far
-// record's first float4 (c', rho^2); float64: global coordinates, c_rho2 = the record's first four.
-__device__ __forceinline__ bool pair_is_near_f32(float xp, float yp, float zp, float4 c_rho2, float fr2)
-{
-    const float dx = __fsub_rn(xp, c_rho2.x), dy = __fsub_rn(yp, c_rho2.y), dz = __fsub_rn(zp, c_rho2.z);
-    const float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-    return !(d2 > __fmul_rn(fr2, c_rho2.w));
-}
-__device__ __forceinline__ bool pair_is_near_f64(double x, double y, double z, const double *c_rho2, double fr2)
-{
-    const double dx = __dsub_rn(x, c_rho2[0]), dy = __dsub_rn(y, c_rho2[1]), dz = __dsub_rn(z, c_rho2[2]);
-    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    return !(d2 > __dmul_rn(fr2, c_rho2[3]));
-}
-// Can a point of the ball (centre, radius) = sphere be near a tet of the tile (header: origin o and the
-// radius rc of its centroids about o; rho_max its largest circumradius)?  No, when the ball is farther
-// than far_ratio rho_max from every centroid, with a margin (0.1% and 1e-5 of the coordinates' scale)
-// that covers the float32 rounding of this test and of the per-pair test: a culled tile holds no pair
-// the per-pair test would call near.
-__device__ __forceinline__ bool tile_culled(float4 sphere, float4 hdr, float rho_max, float far_ratio)
-{
-    const float dx = sphere.x - hdr.x, dy = sphere.y - hdr.y, dz = sphere.z - hdr.z;
-    const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
-    const float scale = fabsf(hdr.x) + fabsf(hdr.y) + fabsf(hdr.z) + dist;
-    return dist - sphere.w - hdr.w > far_ratio * rho_max * 1.001f + 1e-5f * scale;
-}
-
 // EXACT: near pairs take the exact integral (tet_exact) instead of the ray rule, the
 // warp's pairs spread over all 32 lanes and each result handed to the lane that owns its point.
 // DR: the near-pair drain's routine is called (0), inlined (1), or inlined in its lean form with the
@@ -1250,7 +1219,7 @@ __global__ void __launch_bounds__(128, 4) near_pass_kernel(const VelocityArgs a)
     __shared__ float spts[128 * 9];                  // the lanes' points as float splits
     __shared__ float4 srec[4][kNearF32Vec4];         // the near record of the current tet, per warp
     extern __shared__ __align__(16) float4 sdir[];   // float32 direction table (a.smem_lines)
-    if (a.skip && *a.skip) return;
+    if ((a.skip && *a.skip) || (a.near_skip && *a.near_skip)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (F32 && a.smem_lines)
         for (int l = threadIdx.x; l < a.L; l += blockDim.x) sdir[l] = a.lines.f32[l];

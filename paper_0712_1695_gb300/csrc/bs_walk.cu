@@ -172,9 +172,9 @@ __device__ __forceinline__ int walk_reenter(const WalkArgs &a, V3<T> x, V3<T> d,
 
 // The integral of omega along one half-line x + t d, t > 0, walking the tets from node `node`.
 // float32: the point as float splits (xh, xm); records from near32.
-template <bool GRAD, bool RE>
+template <bool GRAD, bool RE, bool NEAR>
 __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, const float xh[3],
-                              const float xm[3], V3<float> d, V3<float> e, V3<float> &dI, int &hits)
+                              const float xm[3], V3<float> d, V3<float> e, V3<float> &dI, int &hits, float r_stop)
 {
     V3<float> I = mk(0.f, 0.f, 0.f);
     // start tet: the incident tet whose face planes through x the half-line enters (largest margin)
@@ -274,6 +274,14 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, co
             atomicOr(a.flag, kFlagWalkStuck);
             break;
         }
+        bool take = true;  // near mode: only the tets the far sweep left out (it takes the others)
+        if constexpr (NEAR) {
+            if (fmaxf(lo, 0.f) > r_stop) break;  // this tet and every one beyond are far from the node
+            const float4 o = __ldg(a.tile_hdr + 2 * (T / a.tile));
+            const float4 c = __ldg(reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(a.far) +
+                                                                    (int64_t)T * a.far_stride));
+            take = pair_is_near_f32(xh[0] - o.x, xh[1] - o.y, xh[2] - o.z, c, a.far_ratio2_f);
+        }
         // omega at the vertices (w0 w1 w2 w3, 12 floats)
         const float4 q4 = __ldg(r + 4), q5 = __ldg(r + 5), q6 = __ldg(r + 6);
         float ge[4];  // g_i . e
@@ -283,7 +291,7 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, co
             ge[3] = dot3(g[3], e);
             ge[0] = -(ge[1] + ge[2] + ge[3]);
         }
-        if (!empty && hi - lo > (float)kTau * q0.w) {
+        if (take && !empty && hi - lo > (float)kTau * q0.w) {
             const float l0 = fmaxf(lo, 0.f);
             const float f1 = hi - l0, f2 = 0.5f * (hi * hi - l0 * l0);
             const float c0 = f1 * av[0] + f2 * b[0], c1 = f1 * av[1] + f2 * b[1];
@@ -322,7 +330,7 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, co
         prevT = T;
         if constexpr (RE) {
             tcur = fmaxf(tcur, hx);
-            if (next == -2) {  // left through a face some boundary node lies beyond: does the line come back?
+            if (next == -2 && !(NEAR && tcur > r_stop)) {  // left through a face some boundary node lies beyond: does the line come back?
                 float th;
                 const int f = walk_reenter<float>(a, xf, d, tcur, th);
                 if (f >= 0) {  // a grazing entry may give the tet an empty chord: never find it twice
@@ -340,9 +348,9 @@ __device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, co
 }
 
 // float64 form: records from near64.
-template <bool GRAD, bool RE>
+template <bool GRAD, bool RE, bool NEAR>
 __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3<double> d, V3<double> e,
-                               V3<double> &dI, int &hits)
+                               V3<double> &dI, int &hits, double r_stop)
 {
     V3<double> I = mk(0.0, 0.0, 0.0);
     int T = -1, kk = -1;
@@ -426,6 +434,13 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
             atomicOr(a.flag, kFlagWalkStuck);
             break;
         }
+        bool take = true;  // near mode: only the tets the far sweep left out
+        if constexpr (NEAR) {
+            if (fmax(lo, 0.0) > r_stop) break;
+            take = pair_is_near_f64(x.x, x.y, x.z,
+                                    reinterpret_cast<const double *>(a.far) + (int64_t)T * a.far_stride,
+                                    a.far_ratio2);
+        }
         double ge[4];  // g_i . e
         if constexpr (GRAD) {
             ge[1] = dot3(g[1], e);
@@ -433,7 +448,7 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
             ge[3] = dot3(g[3], e);
             ge[0] = -(ge[1] + ge[2] + ge[3]);
         }
-        if (!empty && hi - lo > kTau * r[nf64::H]) {
+        if (take && !empty && hi - lo > kTau * r[nf64::H]) {
             const double l0 = fmax(lo, 0.0);
             const double f1 = hi - l0, f2 = 0.5 * (hi * hi - l0 * l0);
             for (int i = 0; i < 4; ++i) {
@@ -471,7 +486,7 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
         prevT = T;
         if constexpr (RE) {
             tcur = fmax(tcur, hx);
-            if (next < 0) {
+            if (next < 0 && !(NEAR && tcur > r_stop)) {
                 double th;
                 const int f = walk_reenter<double>(a, x, d, tcur, th);
                 if (f >= 0) {
@@ -490,18 +505,21 @@ __device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3
 
 // RE: the instance for a non-convex domain (mode 2), with the re-entry search; the other one serves convex
 // domains (mode 1).  Both are queued; the one not in charge returns at once.
-template <typename T, bool GRAD, bool RE>
+// NEAR: the near field of the hybrid rule (see WalkArgs::near_mode), else the all-ray rule.
+template <typename T, bool GRAD, bool RE, bool NEAR>
 __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a)
 {
     const int mode = *a.mode;
-    if (!mode) {  // not a conforming mesh: the all-ray kernel takes the nodes
+    if (!mode) {  // not a conforming mesh: the all-ray kernel (or the near pass) takes the nodes
         if (GRAD && !RE && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.flag, kFlagNoWalk);  // no derivative
         return;
     }
     if ((mode == 2) != RE) return;
     const int lane = threadIdx.x & 31;
-    const int64_t node = (int64_t)blockIdx.x * (kWalkThreads / 32) + (threadIdx.x >> 5);
-    if (node >= a.n_nodes) return;  // whole warps
+    const int64_t w = (int64_t)blockIdx.x * (kWalkThreads / 32) + (threadIdx.x >> 5);
+    if (w >= a.n_nodes) return;  // whole warps
+    const int64_t node = NEAR ? (int64_t)a.perm[w] : w;
+    const T r_stop = NEAR ? (T)*a.r_stop : (T)0;
     const V3<double> xd = mk(a.nodes[3 * node], a.nodes[3 * node + 1], a.nodes[3 * node + 2]);
     const double *ep = a.dirs ? a.dirs + 3 * node : a.omega + 3 * node;
     const V3<double> ed = GRAD ? mk(ep[0], ep[1], ep[2]) : mk(0.0, 0.0, 0.0);
@@ -517,8 +535,9 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a)
             const float4 ln = __ldg(a.lines32 + l);
             const V3<float> s = mk(ln.x, ln.y, ln.z);
             V3<float> dp = mk(0.f, 0.f, 0.f), dm = mk(0.f, 0.f, 0.f);
-            const V3<float> Ip = walk_f32<GRAD, RE>(a, node, xd, xh, xm, s, e, dp, hits);
-            const V3<float> Im = walk_f32<GRAD, RE>(a, node, xd, xh, xm, mk(-s.x, -s.y, -s.z), e, dm, hits);
+            const V3<float> Ip = walk_f32<GRAD, RE, NEAR>(a, node, xd, xh, xm, s, e, dp, hits, r_stop);
+            const V3<float> Im = walk_f32<GRAD, RE, NEAR>(a, node, xd, xh, xm, mk(-s.x, -s.y, -s.z), e, dm, hits,
+                                                          r_stop);
             const V3<float> J = mk(Ip.x - Im.x, Ip.y - Im.y, Ip.z - Im.z);
             ax += ln.w * (s.y * J.z - s.z * J.y);
             ay += ln.w * (s.z * J.x - s.x * J.z);
@@ -535,8 +554,8 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a)
             const dbl4 ln = a.lines64[l];
             const V3<double> s = mk(ln.x, ln.y, ln.z);
             V3<double> dp = mk(0.0, 0.0, 0.0), dm = mk(0.0, 0.0, 0.0);
-            const V3<double> Ip = walk_f64<GRAD, RE>(a, node, xd, s, ed, dp, hits);
-            const V3<double> Im = walk_f64<GRAD, RE>(a, node, xd, mk(-s.x, -s.y, -s.z), ed, dm, hits);
+            const V3<double> Ip = walk_f64<GRAD, RE, NEAR>(a, node, xd, s, ed, dp, hits, r_stop);
+            const V3<double> Im = walk_f64<GRAD, RE, NEAR>(a, node, xd, mk(-s.x, -s.y, -s.z), ed, dm, hits, r_stop);
             const V3<double> J = mk(Ip.x - Im.x, Ip.y - Im.y, Ip.z - Im.z);
             ax += ln.w * (s.y * J.z - s.z * J.y);
             ay += ln.w * (s.z * J.x - s.x * J.z);
@@ -558,7 +577,12 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a)
         gy = warp_sum(gy);
         gz = warp_sum(gz);
     }
-    if (lane == 0) {
+    if (NEAR && lane == 0) {  // the near totals by spatial position; the far sweep wrote the other counts
+        a.near_out[3 * w] = (double)ax;
+        a.near_out[3 * w + 1] = (double)ay;
+        a.near_out[3 * w + 2] = (double)az;
+        if (a.counts) a.counts[3 * node + 2] = hits;
+    } else if (lane == 0) {
         a.out[3 * node] = (double)ax;
         a.out[3 * node + 1] = (double)ay;
         a.out[3 * node + 2] = (double)az;
@@ -924,6 +948,32 @@ cudaError_t launch_walk_finalize(const WalkGrid *g, int *mode, cudaStream_t st)
     return cudaGetLastError();
 }
 
+namespace {
+// max over tets of (far_ratio rho + Rb) as float bits (positive floats order as their bit patterns)
+__global__ void near_reach_kernel(const double *__restrict__ rho2, const double *__restrict__ near64, int64_t n_tets,
+                                  double far_ratio, unsigned *bits)
+{
+    float m = 0.f;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tets; t += (int64_t)gridDim.x * blockDim.x) {
+        const double reach = (far_ratio * sqrt(rho2[t]) + sqrt(near64[t * kNearF64 + nf64::RB2])) * (1.0 + 1e-4);
+        m = fmaxf(m, __double2float_ru(reach));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(bits, __float_as_uint(m));
+}
+}  // namespace
+
+cudaError_t launch_near_reach(const double *rho2, const double *near64, int64_t n_tets, double far_ratio,
+                              float *r_stop, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(r_stop, 0, sizeof(float), st);
+    if (e != cudaSuccess || n_tets == 0) return e;
+    const int64_t blocks = std::min<int64_t>((n_tets + 255) / 256, 4096);
+    near_reach_kernel<<<(unsigned)blocks, 256, 0, st>>>(rho2, near64, n_tets, far_ratio,
+                                                        reinterpret_cast<unsigned *>(r_stop));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_walk(int precision, const WalkArgs &a, cudaStream_t st, cudaEvent_t ev_start, cudaEvent_t ev_stop)
 {
     cudaError_t e;
@@ -931,9 +981,19 @@ cudaError_t launch_walk(int precision, const WalkArgs &a, cudaStream_t st, cudaE
     const int64_t blocks = (a.n_nodes + kWalkThreads / 32 - 1) / (kWalkThreads / 32);
     // the convex-domain instance and the one with re-entries (only the one the mode selects does any work)
 #define BS_WALK_PAIR(T_, G_)                                                          \
-    walk_kernel<T_, G_, false><<<(unsigned)blocks, kWalkThreads, 0, st>>>(a);         \
-    walk_kernel<T_, G_, true><<<(unsigned)blocks, kWalkThreads, 0, st>>>(a)
-    if (a.dout) {
+    walk_kernel<T_, G_, false, false><<<(unsigned)blocks, kWalkThreads, 0, st>>>(a);  \
+    walk_kernel<T_, G_, true, false><<<(unsigned)blocks, kWalkThreads, 0, st>>>(a)
+    if (a.near_mode) {
+        if (a.dout || !a.perm || !a.near_out || !a.far || !a.tile_hdr || !a.r_stop || a.tile <= 0)
+            return cudaErrorInvalidValue;
+        if (precision == BS_FP32) {
+            walk_kernel<float, false, false, true><<<(unsigned)blocks, kWalkThreads, 0, st>>>(a);
+            walk_kernel<float, false, true, true><<<(unsigned)blocks, kWalkThreads, 0, st>>>(a);
+        } else {
+            walk_kernel<double, false, false, true><<<(unsigned)blocks, kWalkThreads, 0, st>>>(a);
+            walk_kernel<double, false, true, true><<<(unsigned)blocks, kWalkThreads, 0, st>>>(a);
+        }
+    } else if (a.dout) {
         if (precision == BS_FP32) { BS_WALK_PAIR(float, true); }
         else { BS_WALK_PAIR(double, true); }
     } else {

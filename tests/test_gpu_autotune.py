@@ -41,19 +41,22 @@ def test_cache_miss_times_and_persists_then_hits(orc, c1, precision, monkeypatch
     assert 0 <= v < n
     doc = json.loads(path.read_text())  # a valid JSON document
     entries = doc["entries"]
-    key = [k for k in entries if f"{'fp32' if precision == bs.BS_FP32 else 'fp64'} q4 ray L128" in k]
-    assert len(key) == 1
-    e = entries[key[0]]
-    assert e["variant"] == v and e["candidates"] == n and e["ms"] > 0
-    s = bs.bs_variant_shape(precision, 4, bs.BS_NEAR_RAY, v)
-    assert e["shape"].startswith(f"P{s['points_per_thread']} T{s['tile']} S{s['stages']} B{s['ctas_per_sm']}")
+    tag = f"{'fp32' if precision == bs.BS_FP32 else 'fp64'} q4 ray L128"
+    # two paths, two entries: bs_velocity (points) and bs_velocity_nodes (nodes: the walk can take the near field)
+    for path_tag, vv in (("points", v), ("nodes", h.bs_tuned_variant(precision, 4, at_nodes=True))):
+        key = [k for k in entries if tag in k and k.endswith(path_tag)]
+        assert len(key) == 1, path_tag
+        e = entries[key[0]]
+        assert e["variant"] == vv and e["candidates"] == n and e["ms"] > 0
+        s = bs.bs_variant_shape(precision, 4, bs.BS_NEAR_RAY, vv)
+        assert e["shape"].startswith(f"P{s['points_per_thread']} T{s['tile']} S{s['stages']} B{s['ctas_per_sm']}")
     # a second handle on the same problem: a cache hit, no timing
     monkeypatch.delenv("BS_TUNE_FORCE")
     h2 = bs.Mesh(m.nodes, m.tets, m.omega)
     t0 = time.perf_counter()
     v2 = h2.bs_autotune(precision=precision, **P)
     hit = time.perf_counter() - t0
-    assert v2 == v
+    assert v2 == v and h2.bs_tuned_variant(precision, 4, at_nodes=True) == h.bs_tuned_variant(precision, 4, True)
     assert hit < 0.1 * miss
     # and the variant it runs gives the oracle's velocity
     pts = torch.from_numpy(m.nodes).cuda()
