@@ -165,7 +165,7 @@ struct VelocityArgs {
     // ([n_points][3]; batch: over all meshes), the far records' tile and stride, and its number of warps
     double *near_out = nullptr;
     int tile = 0, far_stride = 0;
-    int64_t n_near_warps = 0;
+    int64_t n_near_warps = 0;  // groups of 32 points (one CTA of the near pass each)
     const int *near_skip = nullptr;  // device flag: when set, the near pass returns at once
 };
 

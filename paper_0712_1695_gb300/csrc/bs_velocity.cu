@@ -142,17 +142,18 @@ cudaError_t launch_near_pass(int precision, const VelocityArgs &a, cudaStream_t 
     if (vl.v[a.variant].s.DR == 3 && a.n_near_warps > 0) {
         if (!a.near_out || a.tile <= 0 || a.far_stride <= 0) return cudaErrorInvalidValue;
         const size_t sm = a.smem_lines ? sizeof(float4) * a.L : 0;
-        const unsigned blocks = (unsigned)((a.n_near_warps + 3) / 4);
+        const unsigned blocks = (unsigned)a.n_near_warps;  // one CTA per 32 points
+        const unsigned threads = 32 * kNearPassWarps;
         if (precision == BS_FP32) {
             if ((e = cudaFuncSetAttribute(near_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)sm)) != cudaSuccess)
                 return e;
-            near_pass_kernel<float><<<blocks, 128, sm, st>>>(a);
+            near_pass_kernel<float><<<blocks, threads, sm, st>>>(a);
         } else {
             if ((e = cudaFuncSetAttribute(near_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)sm)) != cudaSuccess)
                 return e;
-            near_pass_kernel<double><<<blocks, 128, sm, st>>>(a);
+            near_pass_kernel<double><<<blocks, threads, sm, st>>>(a);
         }
         e = cudaGetLastError();
     }

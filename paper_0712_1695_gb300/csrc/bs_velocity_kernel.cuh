@@ -138,10 +138,15 @@ __device__ __noinline__ void line_fallback_f64(V3<double> x, const float *__rest
 //
 // U (the ray bundle): each lane takes U of its lines per iteration (lines l, l + 32, ..., l + 32 (U-1)),
 // unrolled, so that their loads and clipping interleave.
-template <int U>
+//
+// DEFER: the float64 steps are not taken here; *redo_out (warp-uniform) says the pair needs them, *vk_out and
+// *whole_out how, and the caller runs line_fallback_f64_inl for it later (where few registers are live).
+template <int U, bool DEFER = false>
 __device__ __forceinline__ NearOut32 near_pair_f32_body(const float *__restrict__ xs, const float4 *__restrict__ r32,
                                                         const double *__restrict__ r64, const float4 *__restrict__ lines,
-                                                        const dbl4 *__restrict__ lines64, int L, int lane)
+                                                        const dbl4 *__restrict__ lines64, int L, int lane,
+                                                        bool *redo_out = nullptr, int *vk_out = nullptr,
+                                                        bool *whole_out = nullptr)
 {
     // xs: the point as float splits [component][hi, mid, lo]
     const float xh0 = xs[0], xm0 = xs[1], xh1 = xs[3], xm1 = xs[4], xh2 = xs[6], xm2 = xs[7];
@@ -256,7 +261,11 @@ __device__ __forceinline__ NearOut32 near_pair_f32_body(const float *__restrict_
             }
         }
     }
-    if (whole_f64 || any_redo) {
+    if constexpr (DEFER) {
+        *redo_out = whole_f64 || __any_sync(0xffffffffu, any_redo);
+        *vk_out = vk;
+        *whole_out = whole_f64;
+    } else if (whole_f64 || any_redo) {
         // rare: lines (or whole pairs) that need float64; the point's exact coordinates from its splits
         V3<double> acc = mk(0.0, 0.0, 0.0);
         const V3<double> x = mk(join3(xs[0], xs[1], xs[2]), join3(xs[3], xs[4], xs[5]), join3(xs[6], xs[7], xs[8]));
@@ -1203,28 +1212,33 @@ cudaError_t launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
 
 
 // The near field as a pass of its own, after the far sweep of a variant with DR == 3 (which leaves the
-// near pairs out of its sums).  One warp per 32 consecutive points of the spatial order, one point per
-// lane; a batch gives every mesh its own warps (MeshDesc::near_warp_begin).  The warp scans the mesh's
-// tile headers 32 at a time with the far sweep's culling test against its own bounding sphere; in each
-// tile that can hold a near pair it classifies every (point, tet) pair with the far sweep's test
-// (pair_is_near_*, the same decision bit for bit, so the near pass evaluates exactly the pairs the far
-// sweep left out), and evaluates each near pair by the ray rule, the 32 lanes splitting its lines as
-// in the fused drain.  The lane of the pair's point adds the result to its own total (compensated in
-// float32), in ascending tet order (deterministic, independent of how points are grouped), and at the
-// end writes it to near_out (float64, by spatial position) and its ray hits to counts.
+// near pairs out of its sums).  One CTA per 32 consecutive points of the spatial order, one point per
+// lane; its four warps take the same points and split the mesh's tile headers between them (group g of 32
+// tiles to warp g mod 4); a batch gives every mesh its own CTAs (MeshDesc::near_warp_begin).  A warp
+// tests its tiles with the far sweep's culling test against the points' bounding sphere; in each tile that
+// can hold a near pair it classifies every (point, tet) pair with the far sweep's test (pair_is_near_*,
+// the same decision bit for bit, so the near pass evaluates exactly the pairs the far sweep left out), and
+// evaluates each near pair by the ray rule, the 32 lanes splitting its lines as in the fused drain (the
+// float64 steps of the rare pairs that need them after the tet's pairs, where few registers are live).
+// The lane of the pair's point adds the result to its warp's total for that point (compensated in
+// float32), in ascending tet order; the four totals are added in warp order (deterministic, independent of
+// how the points are grouped) and written to near_out (float64, by spatial position), the ray hits to counts.
+constexpr int kNearPassWarps = 4;
 template <typename T>
-__global__ void __launch_bounds__(128, 4) near_pass_kernel(const VelocityArgs a)
+__global__ void __launch_bounds__(32 * kNearPassWarps, 4) near_pass_kernel(const VelocityArgs a)
 {
     constexpr bool F32 = sizeof(T) == 4;
-    __shared__ float spts[128 * 9];                  // the lanes' points as float splits
-    __shared__ float4 srec[4][kNearF32Vec4];         // the near record of the current tet, per warp
+    constexpr int NW = kNearPassWarps;
+    __shared__ float spts[32 * 9];                   // the 32 points as float splits
+    __shared__ float4 srec[NW][kNearF32Vec4];        // the near record of a warp's current tet
+    __shared__ double stot[NW][32][3];               // the warps' totals
+    __shared__ int shits[NW][32];
     extern __shared__ __align__(16) float4 sdir[];   // float32 direction table (a.smem_lines)
     if ((a.skip && *a.skip) || (a.near_skip && *a.near_skip)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (F32 && a.smem_lines)
         for (int l = threadIdx.x; l < a.L; l += blockDim.x) sdir[l] = a.lines.f32[l];
-    __syncthreads();
-    const int64_t wg = (int64_t)blockIdx.x * 4 + warp;  // this warp's index over all meshes
+    const int64_t wg = blockIdx.x;  // this CTA's group of 32 points over all meshes
     const MeshDesc *m = &a.m;
     if (a.meshes) {
         int lo = 0, hi = a.n_meshes - 1;
@@ -1237,16 +1251,18 @@ __global__ void __launch_bounds__(128, 4) near_pass_kernel(const VelocityArgs a)
     }
     const int64_t k = m->k;
     const int64_t w = wg - (a.meshes ? m->near_warp_begin : 0);
-    if (w * 32 >= k || m->n_tets == 0) return;  // warp-uniform
+    if (w * 32 >= k || m->n_tets == 0) return;  // CTA-uniform
     const int64_t gi = w * 32 + lane;
     const int64_t gp = gi < k ? gi : k - 1;  // pad with a real point; its result is not written
-    float *xs = spts + 9 * threadIdx.x;
-    {
+    if (warp == 0) {
         const int64_t src = m->perm[gp];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) split3(m->pts[3 * src + j], xs[3 * j], xs[3 * j + 1], xs[3 * j + 2]);
+        for (int j = 0; j < 3; ++j) split3(m->pts[3 * src + j], spts[9 * lane + 3 * j], spts[9 * lane + 3 * j + 1],
+                                           spts[9 * lane + 3 * j + 2]);
     }
-    // bounding sphere of the warp's points (float, padded), as the far sweep's
+    __syncthreads();
+    const float *xs = spts + 9 * lane;
+    // bounding sphere of the 32 points (float, padded), as the far sweep's
     float4 sphere;
     {
         float mnx = xs[0], mxx = mnx, mny = xs[3], mxy = mny, mnz = xs[6], mxz = mnz;
@@ -1270,8 +1286,18 @@ __global__ void __launch_bounds__(128, 4) near_pass_kernel(const VelocityArgs a)
     float s32[3] = {0.f, 0.f, 0.f}, c32[3] = {0.f, 0.f, 0.f};  // float32: compensated total
     double s64[3] = {0.0, 0.0, 0.0};                            // float64: plain total
     int hits = 0;
+    auto add = [&](float vx, float vy, float vz) {
+        const float v[3] = {vx, vy, vz};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float y = v[q] - c32[q];
+            const float s2 = s32[q] + y;
+            c32[q] = (s2 - s32[q]) - y;
+            s32[q] = s2;
+        }
+    };
 #pragma unroll 1
-    for (int64_t t0 = 0; t0 < n_tiles; t0 += 32) {
+    for (int64_t t0 = 32 * warp; t0 < n_tiles; t0 += 32 * NW) {
         const int64_t tl = t0 + lane;
         bool open = false;
         if (tl < n_tiles) open = a.all_ray || !tile_culled(sphere, m->tile_hdr[2 * tl], m->tile_hdr[2 * tl + 1].x,
@@ -1323,27 +1349,66 @@ __global__ void __launch_bounds__(128, 4) near_pass_kernel(const VelocityArgs a)
                         __syncwarp();
                         if (lane < kNearF32Vec4) srec[warp][lane] = m->near32[tet * kNearF32Vec4 + lane];
                         __syncwarp();
-                    }
+                        unsigned redo = 0u;  // owners whose pair needs the float64 steps
 #pragma unroll 1
-                    while (owners) {
-                        const int owner = __ffs(owners) - 1;
-                        owners &= owners - 1u;
-                        if constexpr (F32) {
-                            const NearOut32 r = near_pair_f32_body<1>(spts + 9 * (warp * 32 + owner), srec[warp],
-                                                                      m->near64 + tet * kNearF64, lines, a.lines.f64,
-                                                                      a.L, lane);
+                        for (unsigned ow = owners; ow; ow &= ow - 1u) {
+                            const int owner = __ffs(ow) - 1;
+                            bool rd = false, whole = false;
+                            int vk = -1;
+                            const NearOut32 r = near_pair_f32_body<1, true>(spts + 9 * owner, srec[warp],
+                                                                            m->near64 + tet * kNearF64, lines,
+                                                                            a.lines.f64, a.L, lane, &rd, &vk, &whole);
                             if (lane == owner) {
-                                const float v[3] = {r.vx, r.vy, r.vz};
-#pragma unroll
-                                for (int q = 0; q < 3; ++q) {
-                                    const float y = v[q] - c32[q];
-                                    const float s2 = s32[q] + y;
-                                    c32[q] = (s2 - s32[q]) - y;
-                                    s32[q] = s2;
-                                }
+                                add(r.vx, r.vy, r.vz);
                                 hits += r.hits;
                             }
-                        } else {
+                            if (rd) redo |= 1u << owner;
+                        }
+#pragma unroll 1
+                        for (; redo; redo &= redo - 1u) {  // rare
+                            const int owner = __ffs(redo) - 1;
+                            const float *xo = spts + 9 * owner;
+                            const V3<double> x = mk(join3(xo[0], xo[1], xo[2]), join3(xo[3], xo[4], xo[5]),
+                                                    join3(xo[6], xo[7], xo[8]));
+                            // vertex index and whole-pair decision again (the same float32 tests)
+                            const float *vh = reinterpret_cast<const float *>(srec[warp] + nf32::VH);
+                            const float *vm = reinterpret_cast<const float *>(srec[warp] + nf32::VM);
+                            int vk = -1;
+#pragma unroll
+                            for (int i = 0; i < 4; ++i)
+                                if (vk < 0 && vh[3 * i] == xo[0] && vm[3 * i] == xo[1] && vh[3 * i + 1] == xo[3] &&
+                                    vm[3 * i + 1] == xo[4] && vh[3 * i + 2] == xo[6] && vm[3 * i + 2] == xo[7])
+                                    vk = i;
+                            bool whole = false;
+                            if (vk < 0) {
+                                const float4 q0 = srec[warp][nf32::G1], q1 = srec[warp][nf32::G2],
+                                             q2 = srec[warp][nf32::G3];
+                                const V3<float> d0 = mk((xo[0] - vh[0]) + (xo[1] - vm[0]), (xo[3] - vh[1]) + (xo[4] - vm[1]),
+                                                        (xo[6] - vh[2]) + (xo[7] - vm[2]));
+                                float av[4];
+                                av[1] = q0.x * d0.x + q0.y * d0.y + q0.z * d0.z;
+                                av[2] = q1.x * d0.x + q1.y * d0.y + q1.z * d0.z;
+                                av[3] = q2.x * d0.x + q2.y * d0.y + q2.z * d0.z;
+                                av[0] = 1.0f - av[1] - av[2] - av[3];
+                                const float amin = fminf(fminf(av[0], av[1]), fminf(av[2], av[3]));
+                                const float aabs = fminf(fminf(fabsf(av[0]), fabsf(av[1])), fminf(fabsf(av[2]), fabsf(av[3])));
+                                whole = amin > -kDegenA && aabs < kDegenA;
+                            }
+                            V3<double> acc = mk(0.0, 0.0, 0.0);
+                            int h2 = 0;
+                            line_fallback_f64_inl(x, xo, srec[warp], m->near64 + tet * kNearF64, lines, a.lines.f64,
+                                                  a.L, lane, vk, whole, acc, h2);
+                            const double vx = warp_sum(acc.x), vy = warp_sum(acc.y), vz = warp_sum(acc.z);
+                            h2 = warp_sum(h2);
+                            if (lane == owner) {
+                                add((float)vx, (float)vy, (float)vz);
+                                hits += h2;
+                            }
+                        }
+                    } else {
+#pragma unroll 1
+                        for (; owners; owners &= owners - 1u) {
+                            const int owner = __ffs(owners) - 1;
                             const V3<double> xo = mk(__shfl_sync(0xffffffffu, xd.x, owner),
                                                      __shfl_sync(0xffffffffu, xd.y, owner),
                                                      __shfl_sync(0xffffffffu, xd.z, owner));
@@ -1360,11 +1425,24 @@ __global__ void __launch_bounds__(128, 4) near_pass_kernel(const VelocityArgs a)
             }
         }
     }
-    if (gi >= k) return;
+    // the four warps' totals, added in warp order
+#pragma unroll
+    for (int q = 0; q < 3; ++q) stot[warp][lane][q] = F32 ? (double)s32[q] - (double)c32[q] : s64[q];
+    shits[warp][lane] = hits;
+    __syncthreads();
+    if (warp != 0 || gi >= k) return;
+    double tot[3] = {0.0, 0.0, 0.0};
+    int th = 0;
+#pragma unroll
+    for (int v = 0; v < NW; ++v) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) tot[q] += stot[v][lane][q];
+        th += shits[v][lane];
+    }
     double *dst = a.near_out + 3 * ((a.meshes ? m->point_begin : 0) + gi);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) dst[q] = F32 ? (double)s32[q] - (double)c32[q] : s64[q];
-    if (a.counts) a.counts[3 * m->perm[gi] + 2] += hits;
+    for (int q = 0; q < 3; ++q) dst[q] = tot[q];
+    if (a.counts) a.counts[3 * m->perm[gi] + 2] += th;
 }
 
 }  // namespace
