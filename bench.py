@@ -655,6 +655,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 path on the 4096 sample nodes")
     ap.add_argument("--variants", default="", help="variants workload: comma-separated variant indices (default all)")
+    ap.add_argument("--grid", type=int, default=64,
+                    help="nodes per side of the Fourier workload (64: the headline; smaller grids are profiling cases)")
     ap.add_argument("--points", type=int, default=0,
                     help="evaluate only this many seeded nodes (small case for profiler captures)")
     args = ap.parse_args()
@@ -698,7 +700,7 @@ def main():
         torch.cuda.synchronize()
 
     bs.load()
-    mesh = config3_fourier()
+    mesh = config3_fourier(args.grid)
     h = bs.Mesh(mesh.nodes, mesh.tets, mesh.omega)
     eval_nodes = mesh.nodes
     if args.points:
@@ -873,7 +875,11 @@ def main():
 
     config = workload_config()
     if args.points:
-        config["workload"] = f"fourier-64^3 mesh (1500282 tets), velocity at the {k} nodes nearest the centre (profiling case)"
+        config["workload"] = (f"fourier-{args.grid}^3 mesh ({mesh.n_tets} tets), velocity at the {k} nodes nearest the "
+                              "centre (profiling case)")
+    elif args.grid != 64:
+        config["workload"] = (f"fourier-{args.grid}^3: {mesh.n_nodes} nodes x {mesh.n_tets} tets, velocity at all nodes "
+                              "(profiling case)")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
