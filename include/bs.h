@@ -268,6 +268,20 @@ BS_API int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, const i
                                const double *omega_dev, const double *eval_pts_dev, int64_t k, const bs_params *p,
                                double *out_dev, void *stream);
 
+/* The error state of the last bs_velocity_noalloc call on the current
+ * device, read from the library's fixed array (no allocation).  The read is
+ * queued on `stream` (a cudaStream_t, NULL = the legacy default stream) and
+ * the call synchronises that stream, so it sees every bs_velocity_noalloc
+ * call queued before it there.  Returns BS_OK if that call found nothing
+ * wrong (or no call has run on this device yet); BS_ERR_MESH for a node index
+ * out of range or a degenerate tet, with *first_bad_tet (optional, may be
+ * NULL; -1 when there is no error) the lowest such tet; BS_ERR_TIMEOUT for a
+ * bulk-copy wait that gave up; BS_ERR_CUDA if the read failed.  The state is
+ * shared by every call on the device: with calls on several unordered
+ * streams it belongs to whichever call wrote it last.  Calling this does
+ * not clear it; the next bs_velocity_noalloc call does. */
+BS_API int bs_noalloc_status(void *stream, int64_t *first_bad_tet);
+
 /* Kernel timing of a handle (for benchmarks).  bs_profile(h, 1) starts
  * recording a CUDA event pair around every velocity-kernel launch of this
  * handle (on the launch stream) and counting every kernel the handle

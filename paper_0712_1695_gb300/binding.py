@@ -25,7 +25,7 @@ EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_sta
             "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read",
             "bs_velocity_noalloc", "bs_tuned_variant", "bs_rk2_step", "bs_nodes", "bs_velocity_nodes",
             "bs_velocity_nodes_dderiv", "bs_rk2_step_stretch", "bs_omega", "bs_rk2_steps",
-            "bs_graph_steps", "bs_set_wait_limits", "bs_num_variants", "bs_variant_shape", "bs_set_variant")
+            "bs_graph_steps", "bs_set_wait_limits", "bs_num_variants", "bs_variant_shape", "bs_set_variant", "bs_noalloc_status")
 
 
 class BSError(RuntimeError):
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         lib.bs_autotune.argtypes = [_P, ctypes.POINTER(bs_params), _P]
         lib.bs_velocity_noalloc.argtypes = [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, ctypes.c_int64,
                                             ctypes.POINTER(bs_params), _P, _P]
+        lib.bs_noalloc_status.argtypes = [_P, ctypes.POINTER(ctypes.c_int64)]
         lib.bs_rk2_step.argtypes = [_P, ctypes.c_double, ctypes.POINTER(bs_params), _P]
         lib.bs_nodes.argtypes = [_P, _P, _P]
         lib.bs_velocity_nodes.argtypes = [_P, ctypes.POINTER(bs_params), _P, _P]
@@ -374,6 +375,21 @@ def bs_velocity_noalloc(nodes_dev, tets_dev, omega_dev, pts_dev, out_dev, counts
                                       omega_dev.data_ptr(), pts_dev.data_ptr(), k, ctypes.byref(p),
                                       out_dev.data_ptr(), _stream_ptr(stream)))
     return out_dev
+
+
+def bs_noalloc_status(stream=None):
+    """Error state of the last bs_velocity_noalloc call on the current device (synchronises the stream).
+
+    Returns None when that call found nothing wrong; raises BSError (code
+    BS_ERR_MESH or BS_ERR_TIMEOUT) otherwise, with the lowest bad tet in the
+    exception's `first_bad_tet` attribute (-1 if not a mesh error).
+    """
+    bad = ctypes.c_int64(-1)
+    rc = load().bs_noalloc_status(_stream_ptr(stream), ctypes.byref(bad))
+    if rc != BS_OK:
+        err = BSError(rc, load().bs_last_error().decode())
+        err.first_bad_tet = bad.value
+        raise err
 
 
 class Batch:

@@ -249,3 +249,48 @@ extern "C" int bs_velocity_noalloc(const double *nodes_dev, int64_t n_nodes, con
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "poison");
     return BS_OK;
 }
+
+extern "C" int bs_noalloc_status(void *stream, int64_t *first_bad_tet)
+{
+    if (first_bad_tet) *first_bad_tet = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        bs_set_last_error(cudaGetErrorString(e));
+        return BS_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= 64) {
+        bs_set_last_error("bs_noalloc_status: device ordinal above 63");
+        return BS_ERR_ARG;
+    }
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        base = g_addr[dev];
+    }
+    if (!base) return BS_OK;  // no bs_velocity_noalloc call on this device yet: nothing to report
+    // the flag word and the lowest bad tet, read in stream order after the calls queued before this one
+    cudaStream_t st = (cudaStream_t)stream;
+    int flag = 0;
+    unsigned long long bad = ~0ULL;
+    if ((e = cudaMemcpyAsync(&flag, base + kFlag, sizeof flag, cudaMemcpyDeviceToHost, st)) == cudaSuccess &&
+        (e = cudaMemcpyAsync(&bad, base + kFirstBad, sizeof bad, cudaMemcpyDeviceToHost, st)) == cudaSuccess)
+        e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        static thread_local std::string m;
+        m = std::string("bs_noalloc_status: ") + cudaGetErrorString(e);
+        bs_set_last_error(m.c_str());
+        return BS_ERR_CUDA;
+    }
+    if (flag & (kFlagMeshIndex | kFlagMeshVolume)) {
+        if (first_bad_tet && bad != ~0ULL) *first_bad_tet = (int64_t)bad;
+        bs_set_last_error((flag & kFlagMeshIndex) ? "bs_velocity_noalloc: node index out of range (or degenerate tet)"
+                                                  : "bs_velocity_noalloc: degenerate tet");
+        return BS_ERR_MESH;
+    }
+    if (flag & kFlagTimeout) {
+        bs_set_last_error("bs_velocity_noalloc: a bounded device wait gave up");
+        return BS_ERR_TIMEOUT;
+    }
+    return BS_OK;
+}

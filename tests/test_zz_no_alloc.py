@@ -26,7 +26,8 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_0712_1695_gb300 as bs  # noqa: E402
-from paper_0712_1695_gb300.binding import BS_ERR_ARG, BS_ERR_ORDER, BSError, bs_velocity_noalloc  # noqa: E402
+from paper_0712_1695_gb300.binding import (  # noqa: E402
+    BS_ERR_ARG, BS_ERR_MESH, BS_ERR_ORDER, BSError, bs_noalloc_status, bs_velocity_noalloc)
 
 PARAMS = dict(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16)
 
@@ -57,7 +58,7 @@ def test_noalloc_matches_bs_velocity_on_two_calls(case, precision):
         counts = torch.full((k, 3), -1, dtype=torch.int32, device="cuda")
         bs_velocity_noalloc(d["nodes"], d["tets"], d["omega"], d["pts"], out, counts_dev=counts, precision=prec,
                             **PARAMS)
-        torch.cuda.synchronize()
+        bs_noalloc_status()  # no error raised on the device
         v = out.cpu().numpy()
         assert np.all(np.isfinite(v)), f"call {call}"
         if prec == bs.BS_FP64:
@@ -154,9 +155,15 @@ def test_noalloc_reports_mesh_errors_in_its_results(case, fault):
                         precision=bs.BS_FP32, **PARAMS)
     torch.cuda.synchronize()
     assert torch.all(torch.isnan(out)) and torch.all(counts == -1)
+    # the flag word itself, read through bs_noalloc_status: a mesh error naming the lowest bad tet
+    with pytest.raises(BSError) as err:
+        bs_noalloc_status()
+    assert err.value.code == BS_ERR_MESH
+    assert err.value.first_bad_tet == (9 if fault == "flat tet" else 17)
     # the next call on a valid mesh starts from a cleared flag
     bs_velocity_noalloc(d["nodes"], d["tets"], d["omega"], d["pts"], out, counts_dev=counts, precision=bs.BS_FP32,
                         **PARAMS)
+    bs_noalloc_status()
     torch.cuda.synchronize()
     assert torch.all(torch.isfinite(out)) and torch.all(counts >= 0)
 
