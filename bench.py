@@ -642,8 +642,10 @@ def main():
     ap.add_argument("--rings-mode", default="hybrid", choices=["hybrid", "allray-stretch"],
                     help="rings workload: the far/near rule with frozen vorticity, or the all-ray method with vortex "
                          "stretching")
-    ap.add_argument("--rings-drift-n", type=int, default=32,
-                    help="rings workload: grid of the FP32-vs-FP64 drift run (20 Heun steps; 0 to skip)")
+    ap.add_argument("--rings-drift-n", type=int, default=56,
+                    help="rings workload: grid of the FP32-vs-FP64 drift run (20 Heun steps; 0 to skip). The default "
+                         "56^3 is the largest grid whose FP64 trajectory takes minutes (about 15 on a GB300); the "
+                         "80^3 one would take about 2.2 hours")
     ap.add_argument("--allray-mesh", default="ring32", choices=["ring32", "fourier64"],
                     help="allray workload: the 32^3 ring mesh (walk, all-ray kernel, dense path) or the 64^3 "
                          "Fourier mesh (the walk alone)")
@@ -880,6 +882,10 @@ def main():
     elif args.grid != 64:
         config["workload"] = (f"fourier-{args.grid}^3: {mesh.n_nodes} nodes x {mesh.n_tets} tets, velocity at all nodes "
                               "(profiling case)")
+    if args.grid != 64:  # far records 176 B and near records 240 B per tet (float32 + float64 copies)
+        far_mb, near_mb = mesh.n_tets * 176 / 1e6, mesh.n_tets * 240 / 1e6
+        config["l2"] = (f"far records {far_mb:.0f} MB, near records {near_mb:.0f} MB: "
+                        + ("larger than L2" if far_mb > 129 else "the far records fit in L2"))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
