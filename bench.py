@@ -43,8 +43,10 @@ FLOPS_PER_HIT = 80
 FP32_LANES_PER_SM = 128
 MAX_SM_MHZ = 2070.0
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "velocity_fp32_fourier64_traffic.json")
+# the device code of the velocity kernel (a stored DRAM-traffic figure applies while these are unchanged and the
+# variant's launch shape is the one it was taken with)
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_0712_1695_gb300", "csrc", f)
-                  for f in ("bs_velocity_kernel.cuh", "bs_vel_f32_q4.cu", "bs_near.cuh", "bs_internal.cuh")]
+                  for f in ("bs_velocity_kernel.cuh", "bs_near.cuh", "bs_exact.cuh")]
 
 
 def workload_config():
@@ -582,6 +584,52 @@ def variants_workload(args):
     return 0
 
 
+def rules_workload(args):
+    """At the nodes of the 24^3 two-ring mesh (bs_velocity_nodes, 8x16 directions), for each precision and tet
+    rule: variant 0 pinned, the first variant that leaves the near pairs to the mesh walk pinned, and the
+    library's own choice without a pin (ms per evaluation, mean of --steps after --warmup) and the RMS
+    difference over max speed of each against variant 0."""
+    import torch
+
+    import paper_0712_1695_gb300 as bs
+
+    bs.load()
+    m = config5_rings(24)
+    h = bs.Mesh(m.nodes, m.tets, m.omega)
+    rows = []
+    with ClockSampler(0) as clk:
+        for prec, pname in ((bs.BS_FP32, "fp32"), (bs.BS_FP64, "fp64")):
+            for q in (1, 4, 8, 27, 64):
+                P = dict(PARAMS, tet_gauss_order=q, precision=prec)
+                nv = bs.bs_num_variants(prec, q)
+                walk = [v for v in range(nv) if bs.bs_variant_shape(prec, q, bs.BS_NEAR_RAY, v)["near_drain"] == 3]
+                ref = None
+                for label, v in (("variant 0", 0), ("near pairs to the walk", walk[0]), ("unpinned", -1)):
+                    h.bs_set_variant(prec, q, bs.BS_NEAR_RAY, v)
+                    for _ in range(max(args.warmup, 1)):
+                        o = h.bs_velocity_nodes(**P)
+                    torch.cuda.synchronize()
+                    h.bs_status()
+                    if ref is None:
+                        ref = o.clone()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(args.steps):
+                        h.bs_velocity_nodes(**P)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    h.bs_status()
+                    d = float(torch.sqrt(((o - ref) ** 2).sum(1).mean()) / ref.norm(dim=1).max())
+                    rows.append({"precision": pname, "tet_rule": q, "choice": label, "variant": v,
+                                 "ms": e0.elapsed_time(e1) / args.steps, "rms_over_max_vs_variant0": d})
+                h.bs_set_variant(prec, q, bs.BS_NEAR_RAY, -1)
+    print(json.dumps({"metric": "ms per evaluation at all nodes by variant choice (two rings 24^3: "
+                                f"{m.n_nodes} nodes x {m.n_tets} tets, far_ratio 2, 8x16 directions)",
+                      "steps": args.steps, "warmup": args.warmup, "rows": rows, "clocks": clk.summary()}),
+          flush=True)
+    return 0
+
+
 def fma_probe():
     """The bench-only fma-chain probe (bench_fma_probe.cu), compiled on demand with the library's nvcc flags."""
     import ctypes
@@ -631,13 +679,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fourier64",
-                    choices=["fourier64", "batch", "rings", "allray", "exact", "peaks", "steps", "variants"],
+                    choices=["fourier64", "batch", "rings", "allray", "exact", "peaks", "steps", "variants", "rules"],
                     help="fourier64: the headline workload; batch: 256 uneven meshes, batched vs separate "
                          "launches; rings: Heun steps of two colliding rings; allray: the ray rule for every "
                          "pair on the 32^3 ring mesh; "
                          "exact: the exact near-field rule against the ray rule on the 64^3 mesh; peaks: measured fma rates; "
                          "steps: Heun steps on small meshes, per-step calls vs a replayed CUDA graph; variants: "
-                         "every float32 kernel variant timed on the headline workload")
+                         "every float32 kernel variant timed on the headline workload; rules: at the nodes of a "
+                         "24^3 mesh, variant 0 against the variant leaving the near pairs to the walk, per precision "
+                         "and tet rule")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
     ap.add_argument("--rings-mode", default="hybrid", choices=["hybrid", "allray-stretch"],
                     help="rings workload: the far/near rule with frozen vorticity, or the all-ray method with vortex "
@@ -684,6 +734,8 @@ def main():
         return steps_workload(args)
     if args.workload == "variants":
         return variants_workload(args)
+    if args.workload == "rules":
+        return rules_workload(args)
 
     import torch
 
@@ -815,7 +867,9 @@ def main():
     if os.path.exists(PROFILE_TRAFFIC):
         with open(PROFILE_TRAFFIC) as f:
             tr = json.load(f)
-        if tr.get("kernel_source_hash") == kernel_source_hash():
+        shape = "P{points_per_thread} T{tile} S{stages} B{ctas_per_sm} D{near_drain} U{ray_bundle} {pk} J{tet_unroll}".format(
+            pk="pp" if variant_shape["point_pairs"] else "qp", **variant_shape)
+        if tr.get("kernel_source_hash") == kernel_source_hash() and tr.get("shape") == shape:
             traffic = tr.get("dram_bytes_per_launch")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic,

@@ -330,11 +330,16 @@ BS_API int bs_batch_destroy(bs_batch b);
  * if set (every call), else the variant pinned by bs_set_variant, else the
  * autotuner's cache entry for this GPU (name and SM count), precision, tet
  * rule, near rule, direction count and size class (ceil(log2) of the point
- * and tet counts), else variant 0 -- except that, for the ray rule, a mesh
- * too small to fill the GPU with variant 0's work items (fewer than 8
- * GPU-fulls) takes the variant with one point per thread.  A batch uses
- * BS_VARIANT, else its first mesh's pinned variant, else the one-point
- * variant when every mesh has at most 80000 tets, else variant 0.
+ * and tet counts, and whether the points are the nodes of bs_velocity_nodes),
+ * else, for the ray rule: at the nodes (at most 4096 directions) the first
+ * variant that leaves the near pairs to the mesh walk -- the one with one
+ * point per thread on a mesh too small to fill the GPU with variant 0's work
+ * items (fewer than 8 GPU-fulls); elsewhere, on such a small mesh, the
+ * variant with one point per thread that drains the near pairs in the far
+ * kernel; else variant 0.  A batch uses BS_VARIANT, else its first mesh's
+ * pinned variant, else (ray rule) variant 0 if it leaves the near pairs to
+ * the near pass, else the one-point variant when every mesh has at most
+ * 80000 tets, else variant 0.
  *
  * The cache is a JSON file: entries are read from tune_cache.json beside the
  * package directory (shipped, written by bs_autotune on this GPU model) and

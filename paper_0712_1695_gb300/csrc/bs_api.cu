@@ -124,6 +124,7 @@ struct bs_ctx {
     int64_t walk_n_bface = 0, walk_n_bnode = 0;
     int *walk_mode = nullptr;      // device: the walk is valid for the current node positions
     float4 *walk_rec = nullptr;    // float32 walk records [n_tets][kWalkRecVec4]
+    float4 *walk_bpos = nullptr;   // convexity check work array [2 n_bnode + 1]
     WalkGridArrays walk_grid;      // boundary faces on a uniform grid (re-entries into a non-convex mesh)
     uint64_t walk_version = 0;     // mesh version when walk_mode was computed
     // bs_rk2_steps: a stream of the handle on which steps are captured and replayed as a CUDA graph, and
@@ -163,7 +164,7 @@ void free_ctx(bs_ctx *h)
                     h->first_bad, h->work_counter, h->rule.bary, h->rule.w, h->far32, h->far64, h->lines.f32,
                     h->lines.f64, h->partial, h->stage, h->rk, h->tile_hdr, h->perm, h->keys,
                     h->cell_count, h->box, h->walk_nbr, h->walk_inc_off, h->walk_inc, h->walk_bface,
-                    h->walk_bnode, h->walk_mode, h->walk_rec, h->rk_w, h->walk_grid.grid,
+                    h->walk_bnode, h->walk_mode, h->walk_rec, h->walk_bpos, h->rk_w, h->walk_grid.grid,
                     h->walk_grid.cell_off, h->walk_grid.cell_cnt, h->walk_grid.cell_face, h->walk_grid.geo,
                     h->walk_grid.geo32, h->near_out, h->r_stop};
     for (void *b : bufs)
@@ -275,8 +276,10 @@ cudaError_t ensure_far(bs_ctx *h, int Q, int tile, int layout, cudaStream_t st)
 
 // The kernel variant of the velocity kernel a call on k points uses: the environment variable
 // BS_VARIANT, else the variant bs_set_variant pinned, else the autotuner's cache entry for this GPU and
-// problem (at_nodes: the mesh's nodes by bs_velocity_nodes, where the walk can take the near field), else
-// (the ray rule) the small-mesh rule, else variant 0.
+// problem (at_nodes: the mesh's nodes by bs_velocity_nodes, where the walk can take the near field), else,
+// for the ray rule: at the nodes (directions within the walk's table) a variant that leaves the near pairs to
+// the walk -- with one point per thread on a small mesh -- and elsewhere, on a small mesh, the one-point
+// variant that drains them in the far kernel; else variant 0.
 int choose_variant(bs_ctx *h, const bs_params *p, int64_t k, bool at_nodes)
 {
     const int prec = p->precision, Q = p->tet_gauss_order, nr = p->near_rule;
@@ -295,17 +298,26 @@ int choose_variant(bs_ctx *h, const bs_params *p, int64_t k, bool at_nodes)
     if (tv >= 0 && tv < nv) return tv;
     if (nr == BS_NEAR_RAY) {
         // a mesh whose default work items would not fill the GPU several times over: 128-point blocks give
-        // its near pairs (each warp drains its own one at a time) three times as many warps
-        const int sv = small_mesh_variant(prec, Q);
-        if (sv > 0) {
+        // it three times as many warps (for the in-kernel drain, three times as many warps draining near pairs)
+        auto small = [&]() {
             const LaunchShape s0 = shape_for(prec, Q, 0, nr);
             int &o0 = h->occ[nr][prec][Q][0];
             if (o0 == 0) o0 = std::max(1, velocity_ctas_per_sm(prec, Q, 0, nr));
             const int64_t b0 = (k + (int64_t)s0.threads * s0.points_per_thread - 1) /
                                ((int64_t)s0.threads * s0.points_per_thread);
             const int64_t t0 = (h->n_tets + s0.tile - 1) / s0.tile;
-            if (b0 * ((t0 + kMinTilesPerItem - 1) / kMinTilesPerItem) < (int64_t)kSmallMeshWaves * h->n_sm * o0)
-                return sv;
+            return b0 * ((t0 + kMinTilesPerItem - 1) / kMinTilesPerItem) < (int64_t)kSmallMeshWaves * h->n_sm * o0;
+        };
+        // at the nodes the walk's cost grows with the chords it integrates, the in-kernel drain's with every
+        // line of every near pair: leave the near pairs to the walk
+        if (at_nodes && p->n_phi * p->n_theta <= kRayLinesSmemMax) {
+            const int sv = small_mesh_variant(prec, Q, true);
+            if (sv >= 0 && small()) return sv;
+            const int dv = near_pass_variant(prec, Q, nr);
+            if (dv >= 0) return dv;
+        } else {
+            const int sv = small_mesh_variant(prec, Q, false);
+            if (sv >= 0 && small()) return sv;
         }
     }
     return 0;
@@ -539,6 +551,7 @@ cudaError_t ensure_walk(bs_ctx *h)
         return e;
     h->walk_n_bface = (int64_t)w.bface.size();
     h->walk_n_bnode = (int64_t)w.bnode.size();
+    if ((e = cudaMalloc((void **)&h->walk_bpos, sizeof(float4) * (2 * h->walk_n_bnode + 1))) != cudaSuccess) return e;
     // face grid: the boundary is a surface, about 6 G^2 of the G^3 cells hold its faces; G for a few faces per
     // surface cell; lists of up to 16 cells per face
     WalkGridArrays &g = h->walk_grid;
@@ -592,8 +605,8 @@ int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *d
     if (h->walk_version != h->version) {  // the mesh changed: walk records, and is the domain still convex?
         BS_CUDA(launch_walk_records(h->near32, h->walk_nbr, h->n_tets, h->walk_rec, st));
         BS_CUDA(launch_convex_check(h->nodes, h->tets, h->walk_nbr, h->n_tets, h->walk_bface, h->walk_n_bface,
-                                    h->walk_bnode, h->walk_n_bnode, h->walk_conforming ? 1 : 0, h->walk_mode,
-                                    h->walk_rec, st));
+                                    h->walk_bnode, h->walk_n_bnode, h->walk_bpos, h->walk_conforming ? 1 : 0,
+                                    h->walk_mode, h->walk_rec, st));
         if (h->walk_conforming) {
             BS_CUDA(launch_walk_grid(h->nodes, h->tets, h->walk_bface, h->walk_n_bface, h->walk_bnode,
                                      h->walk_n_bnode, h->walk_grid, st));
@@ -603,8 +616,7 @@ int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *d
         h->walk_version = h->version;
         if (h->prof)
             h->prof_all += 2 + (h->walk_conforming && h->n_tets > 0 ? 1 : 0) +
-                           (h->walk_conforming && h->walk_n_bface > 0 && h->walk_n_bnode > 0
-                                ? (h->walk_n_bface + 65534) / 65535 : 0);
+                           (h->walk_conforming && h->walk_n_bface > 0 && h->walk_n_bnode > 0 ? 2 : 0);
     }
     WalkArgs w;
     w.nodes = h->nodes;
@@ -1076,8 +1088,9 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     const int prec = p->precision;
     bool changed = false;
 
-    // the variant: BS_VARIANT, else the first mesh's pinned variant (bs_set_variant), else (ray rule) the
-    // one-point-per-thread variant for batches of small meshes, else variant 0
+    // the variant: BS_VARIANT, else the first mesh's pinned variant (bs_set_variant), else (ray rule) variant 0
+    // when it leaves the near pairs to the near pass, else the one-point-per-thread variant for batches of small
+    // meshes, else variant 0
     const int nr = p->near_rule;
     const int nv = num_variants(prec, Q, nr);
     int variant = b->meshes[0]->pinned[nr][prec][Q];
@@ -1088,8 +1101,11 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         if (!variant_env && nr == BS_NEAR_RAY) {
             int64_t largest = 0;
             for (int i = 0; i < n; ++i) largest = std::max(largest, b->meshes[i]->n_tets);
-            const int sv = small_mesh_variant(prec, Q);
-            if (sv >= 0 && largest <= kSmallBatchMeshTets) variant = sv;
+            const int sv = small_mesh_variant(prec, Q, false);
+            // a variant that leaves the near pairs to the near pass, which then covers every mesh's points in
+            // one launch; else, for small meshes, one point per thread with the pairs drained in the kernel
+            if (shape_for(prec, Q, 0, nr).drain == 3) variant = 0;
+            else if (sv >= 0 && largest <= kSmallBatchMeshTets) variant = sv;
         }
     }
     const LaunchShape shape = shape_for(prec, Q, variant, nr);

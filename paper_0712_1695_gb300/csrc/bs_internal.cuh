@@ -222,9 +222,13 @@ VariantList velocity_variants(int precision, int Q, int near_rule);
 
 constexpr int kMaxVariants = 32;  // num_variants() never exceeds this
 int num_variants(int precision, int Q, int near_rule = BS_NEAR_RAY);
-// the variant with one point per thread (128-point blocks), or -1: for meshes too small to fill the GPU with
-// the default blocks, where each warp's near pairs (drained one at a time) set the time
-int small_mesh_variant(int precision, int Q);
+// the variant with one point per thread (128-point blocks) whose near pairs are drained in the far kernel
+// (near_pass false) or left to a pass of their own (near_pass true), or -1: for meshes too small to fill the
+// GPU with the default blocks
+int small_mesh_variant(int precision, int Q, bool near_pass);
+// the first variant that leaves the near pairs to a pass of their own (the near pass, or at the nodes the mesh
+// walk), or -1
+int near_pass_variant(int precision, int Q, int near_rule);
 // a variant the fixed scratch of the no-alloc entry point can hold (quadrature-pair layout, tiles of 8..32
 // tets), preferring one point per thread for the ray rule
 int noalloc_variant(int precision, int Q, int near_rule);
@@ -339,7 +343,7 @@ cudaError_t launch_walk_finalize(const WalkGrid *g, int *mode, cudaStream_t st);
 // then looks for re-entries through the grid)
 cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const int32_t *nbr, int64_t n_tets,
                                 const int32_t *bface, int64_t n_bface, const int32_t *bnode, int64_t n_bnode,
-                                int conforming, int *mode, float4 *wrec, cudaStream_t st);
+                                float4 *bpos, int conforming, int *mode, float4 *wrec, cudaStream_t st);
 cudaError_t launch_walk(int precision, const WalkArgs &a, cudaStream_t st, cudaEvent_t ev_start = nullptr,
                         cudaEvent_t ev_stop = nullptr);
 // *r_stop := (1 + 1e-4) max over tets of (far_ratio * circumradius + bounding radius about the centroid):

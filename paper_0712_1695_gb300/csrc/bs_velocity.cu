@@ -69,12 +69,22 @@ VariantList velocity_variants(int precision, int Q, int near_rule)
 
 int num_variants(int precision, int Q, int near_rule) { return velocity_variants(precision, Q, near_rule).n; }
 
-int small_mesh_variant(int precision, int Q)
+int small_mesh_variant(int precision, int Q, bool near_pass)
 {
     if (precision != BS_FP32 || Q != 4) return -1;
     const VariantList vl = velocity_variants(precision, Q, BS_NEAR_RAY);
+    for (int v = 0; v < vl.n; ++v) {
+        const VariantShape &s = vl.v[v].s;
+        if (s.P == 1 && s.U == 1 && s.TILE == 32 && !s.PK && (s.DR == 3) == near_pass) return v;
+    }
+    return -1;
+}
+
+int near_pass_variant(int precision, int Q, int near_rule)
+{
+    const VariantList vl = velocity_variants(precision, Q, near_rule);
     for (int v = 0; v < vl.n; ++v)
-        if (vl.v[v].s.P == 1 && vl.v[v].s.U == 1 && vl.v[v].s.TILE == 32) return v;
+        if (vl.v[v].s.DR == 3) return v;
     return -1;
 }
 

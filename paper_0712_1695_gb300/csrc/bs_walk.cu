@@ -796,47 +796,118 @@ __global__ void fold_kernel(const double *__restrict__ nodes, const int32_t *__r
     if ((st > 0.0 && su > 0.0) || (st < 0.0 && su < 0.0)) *mode = 0;
 }
 
-__global__ void convex_kernel(const double *__restrict__ nodes, const int32_t *__restrict__ tets,
-                              const int32_t *__restrict__ bface, int64_t n_bface, const int32_t *__restrict__ bnode,
-                              int64_t n_bnode, int *mode, float4 *wrec)
+// Boundary nodes split into float pairs for the convexity screen: hi = (float)q, lo = (float)(q - hi) per
+// coordinate, so that q = hi + lo to within 2^-48 |q|.  bpos[2 n_bnode].x receives (as bits) a float bound on
+// every |coordinate| of the boundary nodes (positive floats order as their bit patterns).
+__global__ void bnode_split_kernel(const double *__restrict__ nodes, const int32_t *__restrict__ bnode, int64_t n_bnode,
+                                   float4 *__restrict__ bpos)
 {
-    const int64_t f = blockIdx.y;  // boundary face of this block row
-    if (f >= n_bface || *mode == 0) return;
-    const int slot = bface[f];
-    const int64_t t = slot >> 2;
-    const int opp = slot & 3;
-    int id[3], j = 0;
-    for (int i = 0; i < 4; ++i)
-        if (i != opp) id[j++] = tets[4 * t + i];
-    const V3<double> p0 = mk(nodes[3 * id[0]], nodes[3 * id[0] + 1], nodes[3 * id[0] + 2]);
-    const V3<double> p1 = mk(nodes[3 * id[1]], nodes[3 * id[1] + 1], nodes[3 * id[1] + 2]);
-    const V3<double> p2 = mk(nodes[3 * id[2]], nodes[3 * id[2] + 1], nodes[3 * id[2] + 2]);
-    const int io = tets[4 * t + opp];
-    const V3<double> po = mk(nodes[3 * io], nodes[3 * io + 1], nodes[3 * io + 2]);
-    const V3<double> e1 = mk(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z), e2 = mk(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z);
-    V3<double> n = mk(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
-    if (n.x * (po.x - p0.x) + n.y * (po.y - p0.y) + n.z * (po.z - p0.z) > 0.0) n = mk(-n.x, -n.y, -n.z);  // outward
-    const double e3 = sqrt(fmax(dot3(e1, e1), fmax(dot3(e2, e2), (p2.x - p1.x) * (p2.x - p1.x) +
-                                                                    (p2.y - p1.y) * (p2.y - p1.y) +
-                                                                    (p2.z - p1.z) * (p2.z - p1.z))));
-    const double tol = 1e-9 * e3 * sqrt(dot3(n, n));
-    // float screen of n . (q - p0) with a margin above its rounding; float64 only near the threshold
-    const float nxf = (float)n.x, nyf = (float)n.y, nzf = (float)n.z;
-    const float pxf = (float)p0.x, pyf = (float)p0.y, pzf = (float)p0.z;
-    const float nn = (float)sqrt(dot3(n, n));
+    float m = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_bnode; i += (int64_t)gridDim.x * blockDim.x) {
         const int q = bnode[i];
-        const float qx = (float)nodes[3 * q], qy = (float)nodes[3 * q + 1], qz = (float)nodes[3 * q + 2];
-        const float dx = qx - pxf, dy = qy - pyf, dz = qz - pzf;
-        const float sf = nxf * dx + nyf * dy + nzf * dz;
-        const float margin = 1e-5f * nn * (fabsf(dx) + fabsf(dy) + fabsf(dz) + fabsf(pxf) + fabsf(pyf) + fabsf(pzf));
-        if (sf < (float)tol - margin) continue;  // inside the plane beyond doubt
-        const double s = n.x * (nodes[3 * q] - p0.x) + n.y * (nodes[3 * q + 1] - p0.y) + n.z * (nodes[3 * q + 2] - p0.z);
-        if (s > tol) {
-            atomicMax(mode, 2);  // not convex: the walk looks for re-entries
-            reinterpret_cast<int *>(wrec + t * kWalkRecVec4 + 7)[opp] = -2;
-            return;
+        float hi[3], lo[3];
+        for (int k = 0; k < 3; ++k) {
+            const double x = nodes[3 * q + k];
+            hi[k] = (float)x;
+            lo[k] = (float)(x - (double)hi[k]);
+            m = fmaxf(m, __double2float_ru(fabs(x)));
         }
+        bpos[2 * i] = make_float4(hi[0], hi[1], hi[2], 0.f);
+        bpos[2 * i + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned *>(bpos + 2 * n_bnode), __float_as_uint(m));
+}
+
+constexpr int kConvexFaces = 128;  // faces per block (one per thread)
+constexpr int kConvexTile = 256;   // boundary nodes per shared-memory tile
+
+// Is every boundary node on the inner side of every boundary face's plane (within 1e-9 of the face's size)?
+// Each thread holds one face; the block's nodes (a chunk of the boundary nodes, blockIdx.y) pass through shared
+// memory in tiles.  The test n . (q - p0) <= tol is screened in float from the split coordinates: with
+// d = (q_hi - p_hi) + (q_lo - p_lo) the screen's error is below 1e-6 sum |n_k d_k| + 2e-13 |n|_1 max|coord|
+// (a few units of 2^-24 relative to the node's offset from the plane, plus the split's 2^-48 |q|), so a node
+// whose screened value clears the threshold by that margin is inside; the rest are decided in float64.  A node
+// that lies on the face's plane (equal coordinates along an axis-aligned face) gives d = 0 exactly and is
+// decided by the screen.
+__global__ void __launch_bounds__(kConvexFaces) convex_kernel(const double *__restrict__ nodes,
+                                                             const int32_t *__restrict__ tets,
+                                                             const int32_t *__restrict__ bface, int64_t n_bface,
+                                                             const int32_t *__restrict__ bnode, int64_t n_bnode,
+                                                             const float4 *__restrict__ bpos, int *mode, float4 *wrec)
+{
+    __shared__ float4 sh[2 * kConvexTile];
+    if (*mode == 0) return;  // block-uniform: not conforming, or folded
+    const int64_t f = blockIdx.x * (int64_t)kConvexFaces + threadIdx.x;
+    const bool active = f < n_bface;
+    V3<double> n = mk(0.0, 0.0, 0.0), p0 = mk(0.0, 0.0, 0.0);
+    double tol = 0.0;
+    int64_t t = 0;
+    int opp = 0;
+    float nxf = 0.f, nyf = 0.f, nzf = 0.f, tolf = 0.f, K = 0.f;
+    float ph[3] = {0.f, 0.f, 0.f}, pl[3] = {0.f, 0.f, 0.f};
+    if (active) {
+        const int slot = bface[f];
+        t = slot >> 2;
+        opp = slot & 3;
+        int id[3], j = 0;
+        for (int i = 0; i < 4; ++i)
+            if (i != opp) id[j++] = tets[4 * t + i];
+        p0 = mk(nodes[3 * id[0]], nodes[3 * id[0] + 1], nodes[3 * id[0] + 2]);
+        const V3<double> p1 = mk(nodes[3 * id[1]], nodes[3 * id[1] + 1], nodes[3 * id[1] + 2]);
+        const V3<double> p2 = mk(nodes[3 * id[2]], nodes[3 * id[2] + 1], nodes[3 * id[2] + 2]);
+        const int io = tets[4 * t + opp];
+        const V3<double> po = mk(nodes[3 * io], nodes[3 * io + 1], nodes[3 * io + 2]);
+        const V3<double> e1 = mk(p1.x - p0.x, p1.y - p0.y, p1.z - p0.z);
+        const V3<double> e2 = mk(p2.x - p0.x, p2.y - p0.y, p2.z - p0.z);
+        n = mk(e1.y * e2.z - e1.z * e2.y, e1.z * e2.x - e1.x * e2.z, e1.x * e2.y - e1.y * e2.x);
+        if (n.x * (po.x - p0.x) + n.y * (po.y - p0.y) + n.z * (po.z - p0.z) > 0.0) n = mk(-n.x, -n.y, -n.z);  // outward
+        const double e3 = sqrt(fmax(dot3(e1, e1), fmax(dot3(e2, e2), (p2.x - p1.x) * (p2.x - p1.x) +
+                                                                        (p2.y - p1.y) * (p2.y - p1.y) +
+                                                                        (p2.z - p1.z) * (p2.z - p1.z))));
+        tol = 1e-9 * e3 * sqrt(dot3(n, n));
+        nxf = (float)n.x;
+        nyf = (float)n.y;
+        nzf = (float)n.z;
+        tolf = __double2float_rd(tol);  // never above tol
+        const double pc[3] = {p0.x, p0.y, p0.z};
+        for (int k = 0; k < 3; ++k) {
+            ph[k] = (float)pc[k];
+            pl[k] = (float)(pc[k] - (double)ph[k]);
+        }
+        const float gmax = __uint_as_float(reinterpret_cast<const unsigned *>(bpos + 2 * n_bnode)[0]);
+        K = 2e-13f * (fabsf(nxf) + fabsf(nyf) + fabsf(nzf)) * gmax;
+    }
+    // this block's chunk of the boundary nodes
+    const int64_t per = (n_bnode + gridDim.y - 1) / gridDim.y;
+    const int64_t b0 = blockIdx.y * per, b1 = min(n_bnode, b0 + per);
+    bool outside = false;
+    for (int64_t base = b0; base < b1; base += kConvexTile) {
+        const int cnt = (int)min((int64_t)kConvexTile, b1 - base);
+        __syncthreads();
+        for (int k = threadIdx.x; k < 2 * cnt; k += kConvexFaces) sh[k] = bpos[2 * base + k];
+        __syncthreads();
+        if (!active || outside) continue;
+        for (int j = 0; j < cnt; ++j) {
+            const float4 qh = sh[2 * j], ql = sh[2 * j + 1];
+            const float dx = (qh.x - ph[0]) + (ql.x - pl[0]);
+            const float dy = (qh.y - ph[1]) + (ql.y - pl[1]);
+            const float dz = (qh.z - ph[2]) + (ql.z - pl[2]);
+            const float sf = fmaf(nxf, dx, fmaf(nyf, dy, nzf * dz));
+            const float ab = fmaf(fabsf(nxf), fabsf(dx), fmaf(fabsf(nyf), fabsf(dy), fabsf(nzf) * fabsf(dz)));
+            if (sf + fmaf(1e-6f, ab, K) <= tolf) continue;  // inside beyond doubt
+            const int q = bnode[base + j];
+            const double s = n.x * (nodes[3 * q] - p0.x) + n.y * (nodes[3 * q + 1] - p0.y) +
+                             n.z * (nodes[3 * q + 2] - p0.z);
+            if (s > tol) {
+                outside = true;
+                break;
+            }
+        }
+    }
+    if (outside) {
+        atomicMax(mode, 2);  // not convex: the walk looks for re-entries
+        reinterpret_cast<int *>(wrec + t * kWalkRecVec4 + 7)[opp] = -2;
     }
 }
 
@@ -897,7 +968,7 @@ bool build_walk_mesh(const int32_t *tets_host, int64_t n_nodes, int64_t n_tets, 
 
 cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const int32_t *nbr, int64_t n_tets,
                                 const int32_t *bface, int64_t n_bface, const int32_t *bnode, int64_t n_bnode,
-                                int conforming, int *mode, float4 *wrec, cudaStream_t st)
+                                float4 *bpos, int conforming, int *mode, float4 *wrec, cudaStream_t st)
 {
     set_int_kernel<<<1, 1, 0, st>>>(mode, conforming ? 1 : 0);
     cudaError_t e = cudaGetLastError();
@@ -907,13 +978,18 @@ cudaError_t launch_convex_check(const double *nodes, const int32_t *tets, const 
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (n_bface == 0 || n_bnode == 0) return e;
-    const int64_t gx = std::min<int64_t>((n_bnode + 255) / 256, 8);
-    for (int64_t f0 = 0; f0 < n_bface; f0 += 65535) {
-        const dim3 grid((unsigned)gx, (unsigned)std::min<int64_t>(65535, n_bface - f0));
-        convex_kernel<<<grid, 256, 0, st>>>(nodes, tets, bface + f0, n_bface - f0, bnode, n_bnode, mode, wrec);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    if ((e = cudaMemsetAsync(bpos + 2 * n_bnode, 0, sizeof(float4), st)) != cudaSuccess) return e;
+    bnode_split_kernel<<<(unsigned)std::min<int64_t>((n_bnode + 255) / 256, 1024), 256, 0, st>>>(nodes, bnode, n_bnode,
+                                                                                                  bpos);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // face blocks x node chunks: about 16 blocks per SM, chunks of at least one tile
+    const int64_t gx = (n_bface + kConvexFaces - 1) / kConvexFaces;
+    const int64_t tiles = (n_bnode + kConvexTile - 1) / kConvexTile;
+    const int64_t gy = std::max<int64_t>(1, std::min<int64_t>({tiles, (2432 + gx - 1) / gx, 65535}));
+    if (gx > INT32_MAX) return cudaErrorInvalidValue;
+    convex_kernel<<<dim3((unsigned)gx, (unsigned)gy), kConvexFaces, 0, st>>>(nodes, tets, bface, n_bface, bnode,
+                                                                             n_bnode, bpos, mode, wrec);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_walk_records(const float4 *near32, const int32_t *nbr, int64_t n_tets, float4 *wrec,
