@@ -872,7 +872,16 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     a.wait_polls = h->copy_wait_polls;
     a.withhold_copies = h->withhold_copies;
     if (!ray && shape.drain == 3) {  // the near pass evaluates the near pairs the far sweep leaves out
-        const size_t need = 3 * (size_t)k;
+        // without the walk, few points split the tiles among several CTAs per group of 32 points (each part at
+        // least one group of 32 tiles per warp), for about kNearPassBlocksPerSm CTAs per SM in all
+        const int64_t groups = (k + 31) / 32;
+        const int64_t tile_groups = (h->n_tets + 32LL * shape.tile - 1) / (32LL * shape.tile);
+        int64_t split = 1;
+        if (!near_walk) {
+            const int64_t want = ((int64_t)kNearPassBlocksPerSm * h->n_sm + groups - 1) / groups;
+            split = std::max<int64_t>(1, std::min<int64_t>({want, tile_groups / kNearPassWarps, 16}));
+        }
+        const size_t need = 3 * (size_t)k * (size_t)split;
         if (need > h->near_cap) {
             if (h->near_out) cudaFreeAsync(h->near_out, st);
             h->near_out = nullptr;
@@ -883,7 +892,9 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
         a.near_out = h->near_out;
         a.tile = shape.tile;
         a.far_stride = p->precision == BS_FP32 ? far_stride<float>(Q, shape.layout) : far_stride<double>(Q);
-        a.n_near_warps = (k + 31) / 32;
+        a.n_near_warps = groups;
+        a.near_split = (int)split;
+        a.near_split_stride = 3 * k;
     }
     int grid = 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1226,7 +1237,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         return BS_OK;
     }
 
-    // the launch sequence {zero counter, persistent velocity kernel, batched reduction} is captured
+    // the launch sequence {zero counter, persistent velocity kernel, near pass, batched reduction} is captured
     // once per (launch arguments, stream) into a CUDA graph and replayed
     const bool graphable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
     const bool same_graph = b->graph && !changed && b->graph_stream == st && b->graph_prec == prec &&
@@ -1240,6 +1251,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         BS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         int grid = 0;
         cudaError_t e1 = launch_velocity(prec, a, b->n_sm, st, &grid);
+        if (e1 == cudaSuccess) e1 = launch_near_pass(prec, a, st);  // no-op unless the variant leaves near pairs
         cudaError_t e2 = e1 == cudaSuccess ? launch_reduce(a, st) : e1;
         cudaError_t e3 = cudaStreamEndCapture(st, &g);
         if (e2 != cudaSuccess) return cuda_fail(e2, "bs_batch_velocity (capture)");
@@ -1256,6 +1268,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     } else {
         int grid = 0;
         BS_CUDA(launch_velocity(prec, a, b->n_sm, st, &grid));
+        BS_CUDA(launch_near_pass(prec, a, st));
         BS_CUDA(launch_reduce(a, st));
     }
     return BS_OK;

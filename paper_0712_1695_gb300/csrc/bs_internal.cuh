@@ -167,7 +167,17 @@ struct VelocityArgs {
     int tile = 0, far_stride = 0;
     int64_t n_near_warps = 0;  // groups of 32 points (one CTA of the near pass each)
     const int *near_skip = nullptr;  // device flag: when set, the near pass returns at once
+    // one mesh (not a batch), no mesh walk: the tiles split into near_split interleaved parts, one CTA per
+    // (group of 32 points, part), part s writing its totals to near_out + s * near_split_stride; the
+    // reduction adds the parts in order
+    int near_split = 1;
+    int64_t near_split_stride = 0;
 };
+
+// the near pass: warps per CTA (one group of 32 points), and the CTAs per SM a launch on few points aims
+// for by splitting the tiles among several CTAs per group
+constexpr int kNearPassWarps = 4;
+constexpr int kNearPassBlocksPerSm = 8;
 
 // far ratio of a launch: its square (+inf for the all-ray rule) in double and float, the ratio in float
 inline void set_far_ratio(VelocityArgs &a, double far_ratio)

@@ -38,11 +38,14 @@ __global__ void reduce_kernel(const VelocityArgs a)
         s1 += q[1];
         s2 += q[2];
     }
-    if (a.near_out && m->n_tets > 0) {  // the near pass's totals
-        const double *q = a.near_out + 3 * ((a.meshes ? m->point_begin : 0) + i);
-        s0 += q[0];
-        s1 += q[1];
-        s2 += q[2];
+    if (a.near_out && m->n_tets > 0) {  // the near pass's totals, its parts in order
+        const int split = a.meshes ? 1 : max(a.near_split, 1);
+        for (int s = 0; s < split; ++s) {
+            const double *q = a.near_out + s * a.near_split_stride + 3 * ((a.meshes ? m->point_begin : 0) + i);
+            s0 += q[0];
+            s1 += q[1];
+            s2 += q[2];
+        }
     }
     const int64_t o = m->perm[i];
     m->out[3 * o + 0] = s0;
@@ -152,7 +155,9 @@ cudaError_t launch_near_pass(int precision, const VelocityArgs &a, cudaStream_t 
     if (vl.v[a.variant].s.DR == 3 && a.n_near_warps > 0) {
         if (!a.near_out || a.tile <= 0 || a.far_stride <= 0) return cudaErrorInvalidValue;
         const size_t sm = a.smem_lines ? sizeof(float4) * a.L : 0;
-        const unsigned blocks = (unsigned)a.n_near_warps;  // one CTA per 32 points
+        const int split = a.meshes ? 1 : std::max(a.near_split, 1);
+        if (a.n_near_warps * split > INT32_MAX) return cudaErrorInvalidValue;
+        const unsigned blocks = (unsigned)(a.n_near_warps * split);  // one CTA per (32 points, part of the tiles)
         const unsigned threads = 32 * kNearPassWarps;
         if (precision == BS_FP32) {
             if ((e = cudaFuncSetAttribute(near_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -1223,7 +1223,9 @@ cudaError_t launch_t(const VelocityArgs &a, int n_sm, cudaStream_t st, int *grid
 // The lane of the pair's point adds the result to its warp's total for that point (compensated in
 // float32), in ascending tet order; the four totals are added in warp order (deterministic, independent of
 // how the points are grouped) and written to near_out (float64, by spatial position), the ray hits to counts.
-constexpr int kNearPassWarps = 4;
+// With a.near_split > 1 each group of 32 points has that many CTAs, CTA part s taking the tile groups
+// s * kNearPassWarps + warp (mod kNearPassWarps * split); each part's totals go to its own slice of near_out
+// and the reduction adds the slices in order.
 template <typename T>
 __global__ void __launch_bounds__(32 * kNearPassWarps, 4) near_pass_kernel(const VelocityArgs a)
 {
@@ -1238,7 +1240,10 @@ __global__ void __launch_bounds__(32 * kNearPassWarps, 4) near_pass_kernel(const
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (F32 && a.smem_lines)
         for (int l = threadIdx.x; l < a.L; l += blockDim.x) sdir[l] = a.lines.f32[l];
-    const int64_t wg = blockIdx.x;  // this CTA's group of 32 points over all meshes
+    // this CTA's group of 32 points over all meshes, and its part of the tiles (one mesh only)
+    const int split = a.meshes ? 1 : max(a.near_split, 1);
+    const int64_t wg = blockIdx.x / split;
+    const int part = (int)(blockIdx.x % split);
     const MeshDesc *m = &a.m;
     if (a.meshes) {
         int lo = 0, hi = a.n_meshes - 1;
@@ -1297,7 +1302,7 @@ __global__ void __launch_bounds__(32 * kNearPassWarps, 4) near_pass_kernel(const
         }
     };
 #pragma unroll 1
-    for (int64_t t0 = 32 * warp; t0 < n_tiles; t0 += 32 * NW) {
+    for (int64_t t0 = 32 * ((int64_t)part * NW + warp); t0 < n_tiles; t0 += 32 * (int64_t)NW * split) {
         const int64_t tl = t0 + lane;
         bool open = false;
         if (tl < n_tiles) open = a.all_ray || !tile_culled(sphere, m->tile_hdr[2 * tl], m->tile_hdr[2 * tl + 1].x,
@@ -1439,10 +1444,13 @@ __global__ void __launch_bounds__(32 * kNearPassWarps, 4) near_pass_kernel(const
         for (int q = 0; q < 3; ++q) tot[q] += stot[v][lane][q];
         th += shits[v][lane];
     }
-    double *dst = a.near_out + 3 * ((a.meshes ? m->point_begin : 0) + gi);
+    double *dst = a.near_out + part * a.near_split_stride + 3 * ((a.meshes ? m->point_begin : 0) + gi);
 #pragma unroll
     for (int q = 0; q < 3; ++q) dst[q] = tot[q];
-    if (a.counts) a.counts[3 * m->perm[gi] + 2] += th;
+    if (a.counts) {
+        if (split == 1) a.counts[3 * m->perm[gi] + 2] += th;
+        else atomicAdd(&a.counts[3 * m->perm[gi] + 2], th);  // integer sum: order-independent
+    }
 }
 
 }  // namespace

@@ -62,6 +62,48 @@ def test_batch_matches_single_mesh_path(meshes, prec):
         assert np.array_equal(a, o.cpu().numpy())
 
 
+def _placements(prec):
+    """A variant that leaves the near pairs to the near pass and one that drains them in the far kernel."""
+    n = bs.bs_num_variants(prec, 4)
+    drain = [bs.bs_variant_shape(prec, 4, bs.BS_NEAR_RAY, v)["near_drain"] for v in range(n)]
+    return [drain.index(3), next(v for v in range(n) if drain[v] != 3)]
+
+
+PLACEMENTS = [(prec, v, graph) for prec in (bs.BS_FP64, bs.BS_FP32) for v in _placements(prec)
+              for graph in (True, False)]
+
+
+@pytest.mark.parametrize("prec,variant,graph", PLACEMENTS,
+                         ids=[f"{'fp64' if p == bs.BS_FP64 else 'fp32'}-v{v}-{'graph' if g else 'direct'}"
+                              for p, v, g in PLACEMENTS])
+def test_batch_near_placements_match_the_single_path(meshes, prec, variant, graph):
+    """The batch with its near pairs in a near pass over every mesh's points, or drained in the far kernel, as
+    a replayed CUDA graph (a side stream) or launched directly (the legacy default stream)."""
+    ms, hs = meshes
+    refs = [_single(h, m, prec) for m, h in zip(ms, hs)]
+    hs[0].bs_set_variant(prec, 4, bs.BS_NEAR_RAY, variant)  # a batch runs its first mesh's pinned variant
+    try:
+        batch = bs.Batch(hs)
+        outs = [torch.full((m.n_nodes, 3), float("nan"), dtype=torch.float64, device="cuda") for m in ms]
+        if graph:
+            stream = torch.cuda.Stream()
+            for _ in range(2):  # capture, then replay
+                with torch.cuda.stream(stream):
+                    batch.bs_batch_velocity(outs, stream=stream, precision=prec, **P)
+            stream.synchronize()
+        else:
+            batch.bs_batch_velocity(outs, stream=0, precision=prec, **P)
+            torch.cuda.synchronize()
+    finally:
+        hs[0].bs_set_variant(prec, 4, bs.BS_NEAR_RAY, -1)
+    for i, (v, ref) in enumerate(zip(outs, refs)):
+        v = v.cpu().numpy()
+        if prec == bs.BS_FP64:
+            assert rel_l2(v, ref) <= TOL_FP64_REL_L2, f"mesh {i}"
+        else:
+            assert rms_over_max(v, ref) <= TOL_FP32_RMS_MAX, f"mesh {i}"
+
+
 def test_batch_against_oracle_and_after_update(orc, meshes):
     ms, hs = meshes
     batch = bs.Batch(hs)

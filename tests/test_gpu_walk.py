@@ -174,8 +174,10 @@ def test_heun_step_all_ray_uses_the_walk(orc, c1):
     assert np.abs(x1 - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
 
 
-def test_hybrid_rule_at_the_nodes_is_bs_velocity(c1):
-    """With a finite far ratio bs_velocity_nodes is bs_velocity at the nodes, bit for bit."""
+def test_hybrid_rule_at_the_nodes_matches_bs_velocity(c1):
+    """With a finite far ratio bs_velocity_nodes computes the rule bs_velocity computes at the nodes (the near
+    field by the walk or in the far kernel, whichever variant each path takes): equal to rounding, with the same
+    near/far split (the same float test decides it) and, to a few grazing lines, the same ray hits."""
     m, h = c1
     p = dict(far_ratio=2.0, tet_gauss_order=4, n_theta=8, n_phi=16)
     for prec in (bs.BS_FP64, bs.BS_FP32):
@@ -183,7 +185,13 @@ def test_hybrid_rule_at_the_nodes_is_bs_velocity(c1):
         cnt = torch.zeros((m.n_nodes, 3), dtype=torch.int32, device="cuda")
         vr = h.bs_velocity(torch.from_numpy(m.nodes).cuda(), counts_dev=cnt, precision=prec, **p).cpu().numpy()
         h.bs_status()
-        assert np.array_equal(v, vr) and np.array_equal(c, cnt.cpu().numpy())
+        cr = cnt.cpu().numpy()
+        if prec == bs.BS_FP64:
+            assert rel_l2(v, vr) <= TOL_FP64_REL_L2
+        else:
+            assert rms_over_max(v, vr) <= TOL_FP32_RMS_MAX
+        assert np.array_equal(c[:, :2], cr[:, :2])
+        assert np.abs(c[:, 2] - cr[:, 2]).sum() <= 1e-3 * cr[:, 2].sum()
 
 
 def test_box_deformed_by_lagrangian_steps(orc):
