@@ -308,7 +308,12 @@ BS_API int bs_tet_rule(int order, double *bary_host, double *w_host);
  * outlive the batch).  bs_batch_velocity: outs[i] is a device [n_nodes_i][3]
  * output for mesh i (host array of n device pointers); p->counts must be NULL.
  * The work queue is built on the device; the launch sequence is captured once
- * into a CUDA graph per (params, stream) and replayed. */
+ * into a CUDA graph per (params, stream) and replayed (on the legacy default
+ * stream it is launched directly).  With a variant that leaves the near pairs
+ * out of the far kernel (the default for the ray rule), each mesh's near field
+ * is taken by its mesh walk, as in bs_velocity_nodes, where the mesh allows it
+ * (the first call builds each mesh's walk tables on the host and synchronises),
+ * else by one near pass over the points of every such mesh. */
 BS_API int bs_batch_create(const bs_handle *meshes, int n, bs_batch *out);
 BS_API int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void *stream);
 BS_API int bs_batch_destroy(bs_batch b);

@@ -190,6 +190,7 @@ struct bs_batch_ctx {
     double *partial = nullptr;
     size_t partial_cap = 0;
     double *near_out = nullptr;  // the near pass's totals over all meshes' points
+    std::vector<WalkArgs> walks;  // per mesh: the near walk of the captured launch sequence (empty: none)
     unsigned long long *work_counter = nullptr;
     int *flag = nullptr;
     LineTables lines;
@@ -578,6 +579,71 @@ cudaError_t ensure_walk(bs_ctx *h)
 
 namespace {
 
+// The walk's tables for the current node positions: face adjacency (first use), then, after every change of
+// the nodes, the walk records, the convexity and fold checks and the boundary-face grid (all queued on st).
+cudaError_t walk_prepare(bs_ctx *h, cudaStream_t st)
+{
+    cudaError_t e = ensure_walk(h);
+    if (e != cudaSuccess || h->walk_version == h->version) return e;
+    if ((e = launch_walk_records(h->near32, h->walk_nbr, h->n_tets, h->walk_rec, st)) != cudaSuccess) return e;
+    if ((e = launch_convex_check(h->nodes, h->tets, h->walk_nbr, h->n_tets, h->walk_bface, h->walk_n_bface,
+                                 h->walk_bnode, h->walk_n_bnode, h->walk_bpos, h->walk_conforming ? 1 : 0,
+                                 h->walk_mode, h->walk_rec, st)) != cudaSuccess)
+        return e;
+    if (h->walk_conforming) {
+        if ((e = launch_walk_grid(h->nodes, h->tets, h->walk_bface, h->walk_n_bface, h->walk_bnode, h->walk_n_bnode,
+                                  h->walk_grid, st)) != cudaSuccess)
+            return e;
+        if ((e = launch_walk_finalize(h->walk_grid.grid, h->walk_mode, st)) != cudaSuccess) return e;
+        if (h->prof) h->prof_all += 5;
+    }
+    h->walk_version = h->version;
+    if (h->prof)
+        h->prof_all += 2 + (h->walk_conforming && h->n_tets > 0 ? 1 : 0) +
+                       (h->walk_conforming && h->walk_n_bface > 0 && h->walk_n_bnode > 0 ? 2 : 0);
+    return cudaSuccess;
+}
+
+// the walk's arguments that come from the mesh handle (tables, flags, step limit)
+void walk_args(bs_ctx *h, WalkArgs &w)
+{
+    w.nodes = h->nodes;
+    w.n_nodes = h->n_nodes;
+    w.n_tets = h->n_tets;
+    w.near32 = h->near32;
+    w.near64 = h->near64;
+    w.wrec = h->walk_rec;
+    w.nbr = h->walk_nbr;
+    w.inc_off = h->walk_inc_off;
+    w.inc = h->walk_inc;
+    w.omega = h->omega;
+    w.mode = h->walk_mode;
+    w.grid = h->walk_grid.grid;
+    w.cell_off = h->walk_grid.cell_off;
+    w.cell_face = h->walk_grid.cell_face;
+    w.bface = h->walk_bface;
+    w.bgeo = h->walk_grid.geo;
+    w.bgeo32 = h->walk_grid.geo32;
+    w.flag = h->flag;
+    // no valid mesh needs more steps than tets; a small cap keeps a broken walk short
+    w.max_steps = (int)std::min<int64_t>(h->n_tets, std::max<int64_t>(4096, 64 * (int64_t)std::cbrt((double)h->n_tets)));
+    if (h->walk_max_steps > 0) w.max_steps = (int)std::min<int64_t>(h->walk_max_steps, INT32_MAX);
+}
+
+// the near walk's stop radius for the mesh's current version and the far ratio
+cudaError_t ensure_rstop(bs_ctx *h, double far_ratio, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    if (!h->r_stop && (e = cudaMallocAsync((void **)&h->r_stop, sizeof(float), st)) != cudaSuccess) return e;
+    if (h->rstop_version != h->version || h->rstop_fr != far_ratio) {
+        if ((e = launch_near_reach(h->rho2, h->near64, h->n_tets, far_ratio, h->r_stop, st)) != cudaSuccess) return e;
+        h->rstop_version = h->version;
+        h->rstop_fr = far_ratio;
+        if (h->prof) h->prof_all += 1;
+    }
+    return cudaSuccess;
+}
+
 // Velocity at the nodes (and, with dout, its derivative along dirs or the nodal vorticity): the mesh walk
 // in all-ray mode, else bs_velocity at the nodes.
 int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *dirs, double *dout, void *stream)
@@ -600,62 +666,20 @@ int nodes_impl(bs_handle h, const bs_params *p, double *out_dev, const double *d
                                      p->near_rule).drain == 3;
     if (!walk && !near_walk) return velocity_impl(h, h->nodes, h->n_nodes, p, out_dev, stream, nullptr);
     cudaStream_t st = (cudaStream_t)stream;
-    BS_CUDA(ensure_walk(h));
+    BS_CUDA(walk_prepare(h, st));
     BS_CUDA(ensure_lines(h, p->n_phi, p->n_theta, st));
-    if (h->walk_version != h->version) {  // the mesh changed: walk records, and is the domain still convex?
-        BS_CUDA(launch_walk_records(h->near32, h->walk_nbr, h->n_tets, h->walk_rec, st));
-        BS_CUDA(launch_convex_check(h->nodes, h->tets, h->walk_nbr, h->n_tets, h->walk_bface, h->walk_n_bface,
-                                    h->walk_bnode, h->walk_n_bnode, h->walk_bpos, h->walk_conforming ? 1 : 0,
-                                    h->walk_mode, h->walk_rec, st));
-        if (h->walk_conforming) {
-            BS_CUDA(launch_walk_grid(h->nodes, h->tets, h->walk_bface, h->walk_n_bface, h->walk_bnode,
-                                     h->walk_n_bnode, h->walk_grid, st));
-            BS_CUDA(launch_walk_finalize(h->walk_grid.grid, h->walk_mode, st));
-            if (h->prof) h->prof_all += 5;
-        }
-        h->walk_version = h->version;
-        if (h->prof)
-            h->prof_all += 2 + (h->walk_conforming && h->n_tets > 0 ? 1 : 0) +
-                           (h->walk_conforming && h->walk_n_bface > 0 && h->walk_n_bnode > 0 ? 2 : 0);
-    }
     WalkArgs w;
-    w.nodes = h->nodes;
-    w.n_nodes = h->n_nodes;
-    w.n_tets = h->n_tets;
-    w.near32 = h->near32;
-    w.near64 = h->near64;
-    w.wrec = h->walk_rec;
-    w.nbr = h->walk_nbr;
-    w.inc_off = h->walk_inc_off;
-    w.inc = h->walk_inc;
+    walk_args(h, w);
     w.lines32 = h->lines.f32;
     w.lines64 = h->lines.f64;
     w.L = L;
     w.out = out_dev;
     w.counts = p->counts;
-    w.omega = h->omega;
     w.dirs = dirs;
     w.dout = dout;
-    w.mode = h->walk_mode;
-    w.grid = h->walk_grid.grid;
-    w.cell_off = h->walk_grid.cell_off;
-    w.cell_face = h->walk_grid.cell_face;
-    w.bface = h->walk_bface;
-    w.bgeo = h->walk_grid.geo;
-    w.bgeo32 = h->walk_grid.geo32;
-    w.flag = h->flag;
-    // no valid mesh needs more steps than tets; a small cap keeps a broken walk short
-    w.max_steps = (int)std::min<int64_t>(h->n_tets, std::max<int64_t>(4096, 64 * (int64_t)std::cbrt((double)h->n_tets)));
-    if (h->walk_max_steps > 0) w.max_steps = (int)std::min<int64_t>(h->walk_max_steps, INT32_MAX);
     if (near_walk) {
         // the stop radius for this mesh version and far ratio; velocity_impl fills in the rest
-        if (!h->r_stop) BS_CUDA(cudaMallocAsync((void **)&h->r_stop, sizeof(float), st));
-        if (h->rstop_version != h->version || h->rstop_fr != p->far_ratio) {
-            BS_CUDA(launch_near_reach(h->rho2, h->near64, h->n_tets, p->far_ratio, h->r_stop, st));
-            h->rstop_version = h->version;
-            h->rstop_fr = p->far_ratio;
-            if (h->prof) h->prof_all += 1;
-        }
+        BS_CUDA(ensure_rstop(h, p->far_ratio, st));
         w.near_mode = 1;
         w.r_stop = h->r_stop;
         w.counts = p->counts;
@@ -1200,6 +1224,53 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         BS_CUDA(cudaMallocAsync((void **)&b->near_out, sizeof(double) * 3 * std::max<int64_t>(b->n_points, 1), st));
         changed = true;
     }
+    // The near field of a variant that leaves it out: at the meshes' nodes, the mesh walk of each mesh (its tables
+    // prepared here, outside any capture) where the mesh allows it; the near pass skips those meshes.
+    const int L = p->n_phi * p->n_theta;
+    const char *walk_env = getenv("BS_WALK");
+    const bool batch_walk = shape.drain == 3 && nr == BS_NEAR_RAY && L <= kRayLinesSmemMax &&
+                            !(walk_env && atoi(walk_env) == 0);
+    std::vector<WalkArgs> walks;
+    if (batch_walk) {
+        double fr2 = 0.0;
+        float fr2f = 0.f;
+        {
+            VelocityArgs t;
+            set_far_ratio(t, p->far_ratio);
+            fr2 = t.far_ratio2;
+            fr2f = t.far_ratio2_f;
+        }
+        for (int i = 0; i < n; ++i) {
+            bs_ctx *h = b->meshes[i];
+            if (h->n_tets == 0) continue;
+            BS_CUDA(walk_prepare(h, st));
+            BS_CUDA(ensure_rstop(h, p->far_ratio, st));
+            WalkArgs w;
+            std::memset(static_cast<void *>(&w), 0, sizeof(w));  // padding too: compared byte for byte
+            walk_args(h, w);
+            w.lines32 = b->lines.f32;
+            w.lines64 = b->lines.f64;
+            w.L = L;
+            w.out = outs[i];
+            w.near_mode = 1;
+            w.perm = md[i].perm;
+            w.near_out = b->near_out + 3 * md[i].point_begin;
+            w.far = md[i].far;
+            w.tile_hdr = h->tile_hdr;
+            w.tile = shape.tile;
+            w.far_stride = prec == BS_FP32 ? far_stride<float>(Q, shape.layout) : far_stride<double>(Q);
+            w.far_ratio2_f = fr2f;
+            w.far_ratio2 = fr2;
+            w.r_stop = h->r_stop;
+            walks.push_back(w);
+            md[i].near_skip = h->walk_mode;  // set on the device when the walk is in charge of this mesh
+        }
+    }
+    if (walks.size() != b->walks.size() ||
+        (!walks.empty() && memcmp(walks.data(), b->walks.data(), sizeof(WalkArgs) * walks.size()) != 0)) {
+        b->walks = walks;
+        changed = true;
+    }
 
     const bool same_desc = b->h_meshes.size() == md.size() &&
                            memcmp(b->h_meshes.data(), md.data(), sizeof(MeshDesc) * md.size()) == 0;
@@ -1237,7 +1308,8 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         return BS_OK;
     }
 
-    // the launch sequence {zero counter, persistent velocity kernel, near pass, batched reduction} is captured
+    // the launch sequence {zero counter, persistent velocity kernel, near walks, near pass, batched reduction} is
+    // captured
     // once per (launch arguments, stream) into a CUDA graph and replayed
     const bool graphable = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
     const bool same_graph = b->graph && !changed && b->graph_stream == st && b->graph_prec == prec &&
@@ -1251,6 +1323,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         BS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         int grid = 0;
         cudaError_t e1 = launch_velocity(prec, a, b->n_sm, st, &grid);
+        for (size_t i = 0; e1 == cudaSuccess && i < b->walks.size(); ++i) e1 = launch_walk(prec, b->walks[i], st);
         if (e1 == cudaSuccess) e1 = launch_near_pass(prec, a, st);  // no-op unless the variant leaves near pairs
         cudaError_t e2 = e1 == cudaSuccess ? launch_reduce(a, st) : e1;
         cudaError_t e3 = cudaStreamEndCapture(st, &g);
@@ -1268,6 +1341,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     } else {
         int grid = 0;
         BS_CUDA(launch_velocity(prec, a, b->n_sm, st, &grid));
+        for (const WalkArgs &w : b->walks) BS_CUDA(launch_walk(prec, w, st));
         BS_CUDA(launch_near_pass(prec, a, st));
         BS_CUDA(launch_reduce(a, st));
     }

@@ -133,6 +133,7 @@ struct MeshDesc {
     int64_t item_begin = 0;   // batch: first work item of this mesh
     int64_t point_begin = 0;  // batch: first point of this mesh in the batched reduction
     int64_t near_warp_begin = 0;  // batch: first warp of this mesh in the near pass
+    const int *near_skip = nullptr;  // batch: device flag, set when the mesh walk took this mesh's near field
 };
 
 struct VelocityArgs {

@@ -1257,6 +1257,7 @@ __global__ void __launch_bounds__(32 * kNearPassWarps, 4) near_pass_kernel(const
     const int64_t k = m->k;
     const int64_t w = wg - (a.meshes ? m->near_warp_begin : 0);
     if (w * 32 >= k || m->n_tets == 0) return;  // CTA-uniform
+    if (m->near_skip && *m->near_skip) return;  // the mesh walk evaluated this mesh's near field
     const int64_t gi = w * 32 + lane;
     const int64_t gp = gi < k ? gi : k - 1;  // pad with a real point; its result is not written
     if (warp == 0) {

@@ -77,8 +77,8 @@ PLACEMENTS = [(prec, v, graph) for prec in (bs.BS_FP64, bs.BS_FP32) for v in _pl
                          ids=[f"{'fp64' if p == bs.BS_FP64 else 'fp32'}-v{v}-{'graph' if g else 'direct'}"
                               for p, v, g in PLACEMENTS])
 def test_batch_near_placements_match_the_single_path(meshes, prec, variant, graph):
-    """The batch with its near pairs in a near pass over every mesh's points, or drained in the far kernel, as
-    a replayed CUDA graph (a side stream) or launched directly (the legacy default stream)."""
+    """The batch with its near pairs left out of the far kernel (the meshes' walks, or the near pass), or drained in
+    the far kernel, as a replayed CUDA graph (a side stream) or launched directly (the legacy default stream)."""
     ms, hs = meshes
     refs = [_single(h, m, prec) for m, h in zip(ms, hs)]
     hs[0].bs_set_variant(prec, 4, bs.BS_NEAR_RAY, variant)  # a batch runs its first mesh's pinned variant
@@ -102,6 +102,35 @@ def test_batch_near_placements_match_the_single_path(meshes, prec, variant, grap
             assert rel_l2(v, ref) <= TOL_FP64_REL_L2, f"mesh {i}"
         else:
             assert rms_over_max(v, ref) <= TOL_FP32_RMS_MAX, f"mesh {i}"
+
+
+@pytest.mark.parametrize("prec", [bs.BS_FP64, bs.BS_FP32], ids=["fp64", "fp32"])
+def test_batch_near_walk_equals_near_pass(meshes, prec, monkeypatch):
+    """At the meshes' nodes the batch's near field comes from each mesh's walk; with the walk switched off
+    (BS_WALK=0) from the near pass over every mesh's points: the same rule, equal to rounding."""
+    ms, hs = meshes
+    v3 = _placements(prec)[0]
+    res = []
+    for walk in ("1", "0"):
+        monkeypatch.setenv("BS_WALK", walk)
+        hs[0].bs_set_variant(prec, 4, bs.BS_NEAR_RAY, v3)
+        try:
+            batch = bs.Batch(hs)
+            outs = [torch.full((m.n_nodes, 3), float("nan"), dtype=torch.float64, device="cuda") for m in ms]
+            stream = torch.cuda.Stream()
+            with torch.cuda.stream(stream):
+                batch.bs_batch_velocity(outs, stream=stream, precision=prec, **P)
+            stream.synchronize()
+        finally:
+            hs[0].bs_set_variant(prec, 4, bs.BS_NEAR_RAY, -1)
+        res.append([o.cpu().numpy() for o in outs])
+    for i, (a, b) in enumerate(zip(*res)):
+        if prec == bs.BS_FP64:
+            assert rel_l2(a, b) <= TOL_FP64_REL_L2, f"mesh {i}"
+        else:
+            assert rms_over_max(a, b) <= TOL_FP32_RMS_MAX, f"mesh {i}"
+    for h in hs:
+        h.bs_status()
 
 
 def test_batch_against_oracle_and_after_update(orc, meshes):
