@@ -170,34 +170,75 @@ __device__ __forceinline__ int walk_reenter(const WalkArgs &a, V3<T> x, V3<T> d,
     return bf;
 }
 
-// The integral of omega along one half-line x + t d, t > 0, walking the tets from node `node`.
-// float32: the point as float splits (xh, xm); records from near32.
+// Start tets of the two half-lines along +s and -s from a node: the incident tet whose face planes through x
+// the half-line enters, by the largest margin min over those faces of (g_i . d) / |g_i| (first in incidence
+// order on a tie).  One pass serves both directions (the margins along -s are the negated products), reading
+// the incident tets' face gradients and their reciprocal norms from the warp's staged copy (count <=
+// kWalkIncCap) or, for a node with more incident tets, from the walk records.
+constexpr int kWalkIncCap = 64;  // incident tets staged in shared memory per node
+// face j (0..2) of the three through vertex k (faces i != k, ascending): its gradient and reciprocal norm,
+// from the walk record's g1..g3 (g0 = -(g1 + g2 + g3)); selects, no indexed register arrays
+__device__ __forceinline__ float4 face_through(float4 q0, float4 q1, float4 q2, int k, int j)
+{
+    const int i = j + (j >= k ? 1 : 0);
+    const V3<float> g = i == 0 ? mk(-(q0.x + q1.x + q2.x), -(q0.y + q1.y + q2.y), -(q0.z + q1.z + q2.z))
+                        : i == 1 ? mk(q0.x, q0.y, q0.z)
+                        : i == 2 ? mk(q1.x, q1.y, q1.z)
+                                 : mk(q2.x, q2.y, q2.z);
+    return make_float4(g.x, g.y, g.z, rsqrtf(dot3(g, g)));
+}
+struct WalkStart {
+    int T = -1, k = -1;
+    float best = -INFINITY;
+};
+__device__ __forceinline__ void walk_start_f32(const WalkArgs &a, int64_t node, const float4 *sg, const int *scode,
+                                               int n_staged, V3<float> s, WalkStart &wp, WalkStart &wm)
+{
+    const int e0 = a.inc_off[node], n = a.inc_off[node + 1] - e0;
+    for (int e = 0; e < n; ++e) {
+        int code;
+        float4 f[3];  // the three faces through x: gradient and reciprocal norm
+        if (n_staged >= 0) {
+            code = scode[e];
+            f[0] = sg[3 * e];
+            f[1] = sg[3 * e + 1];
+            f[2] = sg[3 * e + 2];
+        } else {
+            code = a.inc[e0 + e];
+            const float4 *r = a.wrec + (int64_t)(code >> 2) * kWalkRecVec4;
+            const float4 q0 = __ldg(r), q1 = __ldg(r + 1), q2 = __ldg(r + 2);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) f[j] = face_through(q0, q1, q2, code & 3, j);
+        }
+        float mp = INFINITY, mm = INFINITY;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float p = dot3(mk(f[j].x, f[j].y, f[j].z), s) * f[j].w;
+            mp = fminf(mp, p);
+            mm = fminf(mm, -p);
+        }
+        if (mp > wp.best) {
+            wp.best = mp;
+            wp.T = code >> 2;
+            wp.k = code & 3;
+        }
+        if (mm > wm.best) {
+            wm.best = mm;
+            wm.T = code >> 2;
+            wm.k = code & 3;
+        }
+    }
+}
+
+// The integral of omega along one half-line x + t d, t > 0, walking the tets from node `node`, starting in
+// st.T (x is its vertex st.k).  float32: the point as float splits (xh, xm); records from near32.
 template <bool GRAD, bool RE, bool NEAR>
-__device__ V3<float> walk_f32(const WalkArgs &a, int64_t node, V3<double> xd, const float xh[3],
+__device__ V3<float> walk_f32(const WalkArgs &a, WalkStart st, V3<double> xd, const float xh[3],
                               const float xm[3], V3<float> d, V3<float> e, V3<float> &dI, int &hits, float r_stop)
 {
     V3<float> I = mk(0.f, 0.f, 0.f);
-    // start tet: the incident tet whose face planes through x the half-line enters (largest margin)
-    int T = -1, kk = -1;
-    float best = -INFINITY;
-    for (int e = a.inc_off[node]; e < a.inc_off[node + 1]; ++e) {
-        const int code = a.inc[e];
-        const int t = code >> 2, k = code & 3;
-        const float4 *r = a.wrec + (int64_t)t * kWalkRecVec4;
-        const float4 q0 = __ldg(r), q1 = __ldg(r + 1), q2 = __ldg(r + 2);
-        const V3<float> g1 = mk(q0.x, q0.y, q0.z), g2 = mk(q1.x, q1.y, q1.z), g3 = mk(q2.x, q2.y, q2.z);
-        const V3<float> g0 = mk(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
-        float m = INFINITY;
-        if (k != 0) m = fminf(m, dot3(g0, d) * rsqrtf(dot3(g0, g0)));
-        if (k != 1) m = fminf(m, dot3(g1, d) * rsqrtf(dot3(g1, g1)));
-        if (k != 2) m = fminf(m, dot3(g2, d) * rsqrtf(dot3(g2, g2)));
-        if (k != 3) m = fminf(m, dot3(g3, d) * rsqrtf(dot3(g3, g3)));
-        if (m > best) {
-            best = m;
-            T = t;
-            kk = k;
-        }
-    }
+    int T = st.T, kk = st.k;
+    const float best = st.best;
     bool exact = true;  // x is vertex kk of T
     int entf = -1;      // face of T through which the line came in from outside the mesh
     float tcur = 0.f;  // the farthest point reached: re-entries are looked for beyond it only, so that a line
@@ -531,12 +572,30 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a)
         split3(xd.y, xh[1], xm[1], xl);
         split3(xd.z, xh[2], xm[2], xl);
         const V3<float> e = mk((float)ed.x, (float)ed.y, (float)ed.z);
+        // the node's incident tets, staged once for every line's start search: the gradients of the three faces
+        // through x with their reciprocal norms, and the (tet, vertex) code
+        __shared__ float4 s_inc[kWalkThreads / 32][3 * kWalkIncCap];
+        __shared__ int s_code[kWalkThreads / 32][kWalkIncCap];
+        const int wq = threadIdx.x >> 5;
+        const int e0 = a.inc_off[node], n_inc = a.inc_off[node + 1] - e0;
+        const int n_staged = n_inc <= kWalkIncCap ? n_inc : -1;  // warp-uniform
+        for (int i = lane; i < n_staged; i += 32) {
+            const int code = a.inc[e0 + i];
+            const float4 *r = a.wrec + (int64_t)(code >> 2) * kWalkRecVec4;
+            const float4 q0 = __ldg(r), q1 = __ldg(r + 1), q2 = __ldg(r + 2);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) s_inc[wq][3 * i + j] = face_through(q0, q1, q2, code & 3, j);
+            s_code[wq][i] = code;
+        }
+        __syncwarp();
         for (int l = lane; l < a.L; l += 32) {
             const float4 ln = __ldg(a.lines32 + l);
             const V3<float> s = mk(ln.x, ln.y, ln.z);
             V3<float> dp = mk(0.f, 0.f, 0.f), dm = mk(0.f, 0.f, 0.f);
-            const V3<float> Ip = walk_f32<GRAD, RE, NEAR>(a, node, xd, xh, xm, s, e, dp, hits, r_stop);
-            const V3<float> Im = walk_f32<GRAD, RE, NEAR>(a, node, xd, xh, xm, mk(-s.x, -s.y, -s.z), e, dm, hits,
+            WalkStart sp, sm;
+            walk_start_f32(a, node, s_inc[wq], s_code[wq], n_staged, s, sp, sm);
+            const V3<float> Ip = walk_f32<GRAD, RE, NEAR>(a, sp, xd, xh, xm, s, e, dp, hits, r_stop);
+            const V3<float> Im = walk_f32<GRAD, RE, NEAR>(a, sm, xd, xh, xm, mk(-s.x, -s.y, -s.z), e, dm, hits,
                                                           r_stop);
             const V3<float> J = mk(Ip.x - Im.x, Ip.y - Im.y, Ip.z - Im.z);
             ax += ln.w * (s.y * J.z - s.z * J.y);
