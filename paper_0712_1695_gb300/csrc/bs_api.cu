@@ -191,6 +191,8 @@ struct bs_batch_ctx {
     size_t partial_cap = 0;
     double *near_out = nullptr;  // the near pass's totals over all meshes' points
     std::vector<WalkArgs> walks;  // per mesh: the near walk of the captured launch sequence (empty: none)
+    const int **d_near_skip = nullptr;   // device [n]: per mesh, the walk's mode flag (near pass skips walked meshes)
+    std::vector<const int *> h_near_skip;  // its host copy
     unsigned long long *work_counter = nullptr;
     int *flag = nullptr;
     LineTables lines;
@@ -206,7 +208,7 @@ void free_batch(bs_batch_ctx *b)
 {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     void *bufs[] = {b->perm, b->keys, b->cell_count, b->box, b->d_meshes, b->partial, b->work_counter, b->flag,
-                    b->lines.f32, b->lines.f64, b->near_out};
+                    b->lines.f32, b->lines.f64, b->near_out, (void *)b->d_near_skip};
     for (void *p : bufs)
         if (p) cudaFree(p);
     delete b;
@@ -1263,8 +1265,22 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
             w.far_ratio2 = fr2;
             w.r_stop = h->r_stop;
             walks.push_back(w);
-            md[i].near_skip = h->walk_mode;  // set on the device when the walk is in charge of this mesh
         }
+    }
+    // per mesh, the flag the near pass reads to leave a walked mesh alone (the walk's mode: set when it is in charge)
+    std::vector<const int *> skips(n, nullptr);
+    if (batch_walk)
+        for (int i = 0; i < n; ++i)
+            if (b->meshes[i]->n_tets > 0) skips[i] = b->meshes[i]->walk_mode;
+    if (batch_walk && !b->d_near_skip) {
+        BS_CUDA(cudaMallocAsync((void **)&b->d_near_skip, sizeof(int *) * n, st));
+        changed = true;
+    }
+    if (batch_walk && skips != b->h_near_skip) {
+        BS_CUDA(cudaMemcpyAsync(b->d_near_skip, skips.data(), sizeof(int *) * n, cudaMemcpyHostToDevice, st));
+        BS_CUDA(cudaStreamSynchronize(st));  // skips is a host temporary
+        b->h_near_skip = skips;
+        changed = true;
     }
     if (walks.size() != b->walks.size() ||
         (!walks.empty() && memcmp(walks.data(), b->walks.data(), sizeof(WalkArgs) * walks.size()) != 0)) {
@@ -1302,6 +1318,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         a.tile = shape.tile;
         a.far_stride = prec == BS_FP32 ? far_stride<float>(Q, shape.layout) : far_stride<double>(Q);
         a.n_near_warps = near_warps;
+        if (batch_walk) a.mesh_near_skip = b->d_near_skip;
     }
     if (items == 0) {  // every mesh is empty: the reduction alone writes the zeros
         BS_CUDA(launch_reduce(a, st));

@@ -133,7 +133,6 @@ struct MeshDesc {
     int64_t item_begin = 0;   // batch: first work item of this mesh
     int64_t point_begin = 0;  // batch: first point of this mesh in the batched reduction
     int64_t near_warp_begin = 0;  // batch: first warp of this mesh in the near pass
-    const int *near_skip = nullptr;  // batch: device flag, set when the mesh walk took this mesh's near field
 };
 
 struct VelocityArgs {
@@ -173,6 +172,8 @@ struct VelocityArgs {
     // reduction adds the parts in order
     int near_split = 1;
     int64_t near_split_stride = 0;
+    // batch: per mesh, a device flag set when the mesh walk took that mesh's near field (or null)
+    const int *const *mesh_near_skip = nullptr;
 };
 
 // the near pass: warps per CTA (one group of 32 points), and the CTAs per SM a launch on few points aims

@@ -1253,11 +1253,11 @@ __global__ void __launch_bounds__(32 * kNearPassWarps, 4) near_pass_kernel(const
             else hi = mid - 1;
         }
         m = &a.meshes[lo];
+        if (a.mesh_near_skip && a.mesh_near_skip[lo] && *a.mesh_near_skip[lo]) return;  // the mesh's walk did it
     }
     const int64_t k = m->k;
     const int64_t w = wg - (a.meshes ? m->near_warp_begin : 0);
     if (w * 32 >= k || m->n_tets == 0) return;  // CTA-uniform
-    if (m->near_skip && *m->near_skip) return;  // the mesh walk evaluated this mesh's near field
     const int64_t gi = w * 32 + lane;
     const int64_t gp = gi < k ? gi : k - 1;  // pad with a real point; its result is not written
     if (warp == 0) {
