@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "libbs.so")
 SOURCES = ["bs_tables.cu", "bs_precompute.cu", "bs_order.cu", "bs_velocity.cu", "bs_vel_f32_q4.cu", "bs_vel_f32_rules.cu",
            "bs_vel_f64.cu", "bs_vel_exact.cu", "bs_ray.cu", "bs_walk.cu", "bs_api.cu", "bs_noalloc.cu", "bs_step.cu",
            "bs_tune.cu"]
-HEADERS = ["bs_internal.cuh", "bs_near.cuh", "bs_exact.cuh", "bs_velocity_kernel.cuh"]
+HEADERS = ["bs_internal.cuh", "bs_near.cuh", "bs_exact.cuh", "bs_velocity_kernel.cuh", "bs_near_pass.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 
+#include "bs_near_pass.cuh"
 #include "bs_velocity_kernel.cuh"
 
 namespace bs {

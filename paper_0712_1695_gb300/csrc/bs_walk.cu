@@ -388,30 +388,72 @@ __device__ V3<float> walk_f32(const WalkArgs &a, WalkStart st, V3<double> xd, co
     return I;
 }
 
-// float64 form: records from near64.
+// float64 form: records from near64.  Start tets as walk_start_f32, from float64 face gradients (staged as
+// gradient and reciprocal norm, face j of the three through the node's vertex in ascending face order).
+struct WalkStart64 {
+    int T = -1, k = -1;
+    double best = -INFINITY;
+};
+__device__ __forceinline__ void face_through64(const double *r, int k, int j, double out[4])
+{
+    const int i = j + (j >= k ? 1 : 0);
+    V3<double> g;
+    if (i == 0)
+        g = mk(-(r[nf64::G] + r[nf64::G + 3] + r[nf64::G + 6]), -(r[nf64::G + 1] + r[nf64::G + 4] + r[nf64::G + 7]),
+               -(r[nf64::G + 2] + r[nf64::G + 5] + r[nf64::G + 8]));
+    else
+        g = mk(r[nf64::G + 3 * i - 3], r[nf64::G + 3 * i - 2], r[nf64::G + 3 * i - 1]);
+    out[0] = g.x;
+    out[1] = g.y;
+    out[2] = g.z;
+    out[3] = 1.0 / sqrt(dot3(g, g));
+}
+__device__ __forceinline__ void walk_start_f64(const WalkArgs &a, int64_t node, const double *sg, const int *scode,
+                                               int n_staged, V3<double> s, WalkStart64 &wp, WalkStart64 &wm)
+{
+    const int e0 = a.inc_off[node], n = a.inc_off[node + 1] - e0;
+    for (int e = 0; e < n; ++e) {
+        int code;
+        double f[3][4];
+        if (n_staged >= 0) {
+            code = scode[e];
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) f[j][q] = sg[12 * e + 4 * j + q];
+        } else {
+            code = a.inc[e0 + e];
+            const double *r = a.near64 + (int64_t)(code >> 2) * kNearF64;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) face_through64(r, code & 3, j, f[j]);
+        }
+        double mp = INFINITY, mm = INFINITY;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double p = dot3(mk(f[j][0], f[j][1], f[j][2]), s) * f[j][3];
+            mp = fmin(mp, p);
+            mm = fmin(mm, -p);
+        }
+        if (mp > wp.best) {
+            wp.best = mp;
+            wp.T = code >> 2;
+            wp.k = code & 3;
+        }
+        if (mm > wm.best) {
+            wm.best = mm;
+            wm.T = code >> 2;
+            wm.k = code & 3;
+        }
+    }
+}
+
 template <bool GRAD, bool RE, bool NEAR>
-__device__ V3<double> walk_f64(const WalkArgs &a, int64_t node, V3<double> x, V3<double> d, V3<double> e,
+__device__ V3<double> walk_f64(const WalkArgs &a, WalkStart64 st, V3<double> x, V3<double> d, V3<double> e,
                                V3<double> &dI, int &hits, double r_stop)
 {
     V3<double> I = mk(0.0, 0.0, 0.0);
-    int T = -1, kk = -1;
-    double best = -INFINITY;
-    for (int e = a.inc_off[node]; e < a.inc_off[node + 1]; ++e) {
-        const int code = a.inc[e];
-        const int t = code >> 2, k = code & 3;
-        const double *r = a.near64 + (int64_t)t * kNearF64;
-        V3<double> g[4];
-        for (int i = 1; i < 4; ++i) g[i] = mk(r[nf64::G + 3 * i - 3], r[nf64::G + 3 * i - 2], r[nf64::G + 3 * i - 1]);
-        g[0] = mk(-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z));
-        double m = INFINITY;
-        for (int i = 0; i < 4; ++i)
-            if (i != k) m = fmin(m, dot3(g[i], d) / sqrt(dot3(g[i], g[i])));
-        if (m > best) {
-            best = m;
-            T = t;
-            kk = k;
-        }
-    }
+    int T = st.T, kk = st.k;
+    const double best = st.best;
     bool exact = true;  // x is vertex kk of T
     int entf = -1;      // face of T through which the line came in from outside the mesh
     double tcur = 0.0;  // the farthest point reached (re-entries only beyond it)
@@ -609,12 +651,27 @@ __global__ void __launch_bounds__(kWalkThreads) walk_kernel(const WalkArgs a)
             }
         }
     } else {
+        __shared__ double s_inc64[kWalkThreads / 32][12 * kWalkIncCap];
+        __shared__ int s_code64[kWalkThreads / 32][kWalkIncCap];
+        const int wq = threadIdx.x >> 5;
+        const int e0 = a.inc_off[node], n_inc = a.inc_off[node + 1] - e0;
+        const int n_staged = n_inc <= kWalkIncCap ? n_inc : -1;  // warp-uniform
+        for (int i = lane; i < n_staged; i += 32) {
+            const int code = a.inc[e0 + i];
+            const double *r = a.near64 + (int64_t)(code >> 2) * kNearF64;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) face_through64(r, code & 3, j, &s_inc64[wq][12 * i + 4 * j]);
+            s_code64[wq][i] = code;
+        }
+        __syncwarp();
         for (int l = lane; l < a.L; l += 32) {
             const dbl4 ln = a.lines64[l];
             const V3<double> s = mk(ln.x, ln.y, ln.z);
             V3<double> dp = mk(0.0, 0.0, 0.0), dm = mk(0.0, 0.0, 0.0);
-            const V3<double> Ip = walk_f64<GRAD, RE, NEAR>(a, node, xd, s, ed, dp, hits, r_stop);
-            const V3<double> Im = walk_f64<GRAD, RE, NEAR>(a, node, xd, mk(-s.x, -s.y, -s.z), ed, dm, hits, r_stop);
+            WalkStart64 sp, sm;
+            walk_start_f64(a, node, s_inc64[wq], s_code64[wq], n_staged, s, sp, sm);
+            const V3<double> Ip = walk_f64<GRAD, RE, NEAR>(a, sp, xd, s, ed, dp, hits, r_stop);
+            const V3<double> Im = walk_f64<GRAD, RE, NEAR>(a, sm, xd, mk(-s.x, -s.y, -s.z), ed, dm, hits, r_stop);
             const V3<double> J = mk(Ip.x - Im.x, Ip.y - Im.y, Ip.z - Im.z);
             ax += ln.w * (s.y * J.z - s.z * J.y);
             ay += ln.w * (s.z * J.x - s.x * J.z);
