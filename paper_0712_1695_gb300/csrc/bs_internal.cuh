@@ -176,10 +176,11 @@ struct VelocityArgs {
     const int *const *mesh_near_skip = nullptr;
 };
 
-// the near pass: warps per CTA (one group of 32 points), and the CTAs per SM a launch on few points aims
-// for by splitting the tiles among several CTAs per group
-constexpr int kNearPassWarps = 4;
-constexpr int kNearPassBlocksPerSm = 8;
+// the near pass: warps per CTA (one group of 32 points; one warp scanning every tile beat four warps
+// sharing them, whose barrier waited on the one holding the group's near tiles), and the CTAs per SM a
+// launch on few points aims for by splitting the tiles among several CTAs per group
+constexpr int kNearPassWarps = 1;
+constexpr int kNearPassBlocksPerSm = 32;
 
 // far ratio of a launch: its square (+inf for the all-ray rule) in double and float, the ratio in float
 inline void set_far_ratio(VelocityArgs &a, double far_ratio)

@@ -10,24 +10,22 @@ namespace {
 
 // The near field as a pass of its own, after the far sweep of a variant with DR == 3 (which leaves the
 // near pairs out of its sums).  One CTA per 32 consecutive points of the spatial order, one point per
-// lane; its four warps take the same points and split the mesh's tile headers between them (group g of 32
-// tiles to warp g mod 4); a batch gives every mesh its own CTAs (MeshDesc::near_warp_begin).  A warp
-// tests its tiles with the far sweep's culling test against the points' bounding sphere; in each tile that
-// can hold a near pair it classifies every (point, tet) pair with the far sweep's test (pair_is_near_*,
-// the same decision bit for bit, so the near pass evaluates exactly the pairs the far sweep left out), and
-// evaluates each near pair by the ray rule, the 32 lanes splitting its lines as in the fused drain (the
-// float64 steps of the rare pairs that need them after the tet's pairs, where few registers are live).
-// The lane of the pair's point adds the result to its warp's total for that point (compensated in
-// float32), in ascending tet order; the four totals are added in warp order (deterministic, independent of
-// how the points are grouped) and written to near_out (float64, by spatial position), the ray hits to counts.
-// With a.near_split > 1 each group of 32 points has that many CTAs, CTA part s taking the tile groups
-// s * kNearPassWarps + warp (mod kNearPassWarps * split); each part's totals go to its own slice of near_out
-// and the reduction adds the slices in order.
-template <typename T>
-__global__ void __launch_bounds__(32 * kNearPassWarps, 4) near_pass_kernel(const VelocityArgs a)
+// lane, with NW warps (kNearPassWarps; group g of 32 tiles to warp g mod NW); a batch gives every mesh its
+// own CTAs (MeshDesc::near_warp_begin).  A warp tests its tiles with the far sweep's culling test against the
+// points' bounding sphere; in each tile that can hold a near pair it classifies every (point, tet) pair with
+// the far sweep's test (pair_is_near_*, the same decision bit for bit, so the near pass evaluates exactly the
+// pairs the far sweep left out), and evaluates each near pair by the ray rule, the 32 lanes splitting its
+// lines as in the fused drain (the float64 steps of the rare pairs that need them after the tet's pairs, where
+// few registers are live).  The lane of the pair's point adds the result to its warp's total for that point
+// (compensated in float32), in ascending tet order; the warps' totals are added in warp order (deterministic,
+// independent of how the points are grouped) and written to near_out (float64, by spatial position), the ray
+// hits to counts.  With a.near_split > 1 each group of 32 points has that many CTAs, CTA part s taking the
+// tile groups s * NW + warp (mod NW * split); each part's totals go to its own slice of near_out and the
+// reduction adds the slices in order.
+template <typename T, int NW>
+__global__ void __launch_bounds__(32 * NW, 16 / NW) near_pass_kernel(const VelocityArgs a)
 {
     constexpr bool F32 = sizeof(T) == 4;
-    constexpr int NW = kNearPassWarps;
     __shared__ float spts[32 * 9];                   // the 32 points as float splits
     __shared__ float4 srec[NW][kNearF32Vec4];        // the near record of a warp's current tet
     __shared__ double stot[NW][32][3];               // the warps' totals

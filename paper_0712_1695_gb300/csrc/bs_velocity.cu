@@ -159,19 +159,16 @@ cudaError_t launch_near_pass(int precision, const VelocityArgs &a, cudaStream_t 
         const int split = a.meshes ? 1 : std::max(a.near_split, 1);
         if (a.n_near_warps * split > INT32_MAX) return cudaErrorInvalidValue;
         const unsigned blocks = (unsigned)(a.n_near_warps * split);  // one CTA per (32 points, part of the tiles)
-        const unsigned threads = 32 * kNearPassWarps;
-        if (precision == BS_FP32) {
-            if ((e = cudaFuncSetAttribute(near_pass_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sm)) != cudaSuccess)
-                return e;
-            near_pass_kernel<float><<<blocks, threads, sm, st>>>(a);
-        } else {
-            if ((e = cudaFuncSetAttribute(near_pass_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sm)) != cudaSuccess)
-                return e;
-            near_pass_kernel<double><<<blocks, threads, sm, st>>>(a);
-        }
-        e = cudaGetLastError();
+        auto go = [&](auto kern, int nw) -> cudaError_t {
+            cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (r != cudaSuccess) return r;
+            kern<<<blocks, 32 * nw, sm, st>>>(a);
+            return cudaGetLastError();
+        };
+        if (precision == BS_FP32)
+            e = go(near_pass_kernel<float, kNearPassWarps>, kNearPassWarps);
+        else
+            e = go(near_pass_kernel<double, kNearPassWarps>, kNearPassWarps);
     }
     return e;
 }
