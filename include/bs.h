@@ -316,6 +316,12 @@ BS_API int bs_tet_rule(int order, double *bary_host, double *w_host);
  * else by one near pass over the points of every such mesh. */
 BS_API int bs_batch_create(const bs_handle *meshes, int n, bs_batch *out);
 BS_API int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void *stream);
+/* Synchronise `stream` and report a device error of the batch's launches since
+ * the last call: BS_ERR_TIMEOUT if a bounded wait of the batched far kernel
+ * gave up (the batch follows the wait limits bs_set_wait_limits gave its first
+ * mesh), else the first error bs_status reports for its meshes (their tables
+ * and near walks); every flag read is cleared. */
+BS_API int bs_batch_status(bs_batch b, void *stream);
 BS_API int bs_batch_destroy(bs_batch b);
 
 /* Kernel variants and the autotuner (the paper has no counterpart: launch

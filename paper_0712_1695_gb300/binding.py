@@ -25,7 +25,7 @@ EXPORTED = ("bs_create", "bs_update", "bs_velocity", "bs_velocity_host", "bs_sta
             "bs_batch_velocity", "bs_batch_destroy", "bs_autotune", "bs_profile", "bs_profile_read",
             "bs_velocity_noalloc", "bs_tuned_variant", "bs_rk2_step", "bs_nodes", "bs_velocity_nodes",
             "bs_velocity_nodes_dderiv", "bs_rk2_step_stretch", "bs_omega", "bs_rk2_steps",
-            "bs_graph_steps", "bs_set_wait_limits", "bs_num_variants", "bs_variant_shape", "bs_set_variant", "bs_noalloc_status")
+            "bs_graph_steps", "bs_set_wait_limits", "bs_num_variants", "bs_variant_shape", "bs_set_variant", "bs_noalloc_status", "bs_batch_status")
 
 
 class BSError(RuntimeError):
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
         lib.bs_batch_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)]
         lib.bs_batch_velocity.argtypes = [_P, ctypes.POINTER(bs_params), ctypes.POINTER(_P), _P]
         lib.bs_batch_destroy.argtypes = [_P]
+        lib.bs_batch_status.argtypes = [_P, _P]
         lib.bs_autotune.argtypes = [_P, ctypes.POINTER(bs_params), _P]
         lib.bs_velocity_noalloc.argtypes = [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, ctypes.c_int64,
                                             ctypes.POINTER(bs_params), _P, _P]
@@ -409,6 +410,10 @@ class Batch:
         p = make_params(**params)
         _check(load().bs_batch_velocity(self.handle, ctypes.byref(p), ptrs, _stream_ptr(stream)))
         return outs
+
+    def bs_batch_status(self, stream=None):
+        """Synchronise and raise BSError if a launch of this batch raised a device error (clears the flags)."""
+        _check(load().bs_batch_status(self.handle, _stream_ptr(stream)))
 
     def close(self):
         if self.handle:

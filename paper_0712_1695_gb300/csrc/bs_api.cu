@@ -1313,6 +1313,8 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     a.work_counter = b->work_counter;
     a.variant = variant;
     a.near_rule = p->near_rule;
+    a.wait_polls = b->meshes[0]->copy_wait_polls;  // the batch follows its first mesh's wait limits
+    a.withhold_copies = b->meshes[0]->withhold_copies;
     if (shape.drain == 3) {
         a.near_out = b->near_out;
         a.tile = shape.tile;
@@ -1363,6 +1365,24 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         BS_CUDA(launch_reduce(a, st));
     }
     return BS_OK;
+}
+
+int bs_batch_status(bs_batch b, void *stream)
+{
+    if (!b) return fail(BS_ERR_ARG, "batch is NULL");
+    BS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int flag = 0;
+    BS_CUDA(cudaMemcpy(&flag, b->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    BS_CUDA(cudaMemset(b->flag, 0, sizeof(int)));
+    // the meshes' own flags: their tables (bs_update) and their near walks
+    int rc = BS_OK;
+    for (bs_ctx *h : b->meshes) {
+        const int r = bs_status(h, stream);
+        if (r != BS_OK && rc == BS_OK) rc = r;
+    }
+    if (flag & kFlagTimeout) return fail(BS_ERR_TIMEOUT, "a bounded device wait of the batch gave up");
+    if (flag & (kFlagMeshIndex | kFlagMeshVolume)) return fail(BS_ERR_MESH, "degenerate tet in the batch");
+    return rc;
 }
 
 int bs_batch_destroy(bs_batch b)

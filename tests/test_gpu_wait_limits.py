@@ -88,3 +88,29 @@ def test_wait_limit_arguments(c1):
             h.bs_set_wait_limits(**bad)
         assert ei.value.code == BS_ERR_ARG
     h.bs_set_wait_limits()
+
+
+def test_batch_copy_wait_gives_up(orc, c1):
+    """The batched far kernel follows its first mesh's wait limits: with the copies withheld every CTA gives up,
+    bs_batch_status reports BS_ERR_TIMEOUT, and the next launch with the normal limits matches the oracle."""
+    from workloads import config5_rings
+
+    m, h = c1
+    m2 = config5_rings(10)
+    h2 = bs.Mesh(m2.nodes, m2.tets, m2.omega)
+    batch = bs.Batch([h, h2])
+    outs = [torch.empty((mm.n_nodes, 3), dtype=torch.float64, device="cuda") for mm in (m, m2)]
+    h.bs_set_wait_limits(copy_wait_polls=1 << 12, withhold_copies=True)
+    try:
+        t0 = time.perf_counter()
+        batch.bs_batch_velocity(outs, precision=bs.BS_FP32, **HYBRID)
+        with pytest.raises(BSError) as ei:
+            batch.bs_batch_status()
+        assert ei.value.code == BS_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 30.0
+    finally:
+        h.bs_set_wait_limits()
+    batch.bs_batch_velocity(outs, precision=bs.BS_FP32, **HYBRID)
+    batch.bs_batch_status()
+    for mm, o in zip((m, m2), outs):
+        assert rms_over_max(o.cpu().numpy(), _oracle(orc, mm, mm.nodes, HYBRID)) <= TOL_FP32_RMS_MAX
