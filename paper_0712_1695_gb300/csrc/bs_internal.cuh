@@ -259,7 +259,7 @@ cudaError_t launch_reduce(const VelocityArgs &a, cudaStream_t st);
 // at once when *a.near_skip is set (the mesh walk evaluated the near field)
 cudaError_t launch_near_pass(int precision, const VelocityArgs &a, cudaStream_t st);
 // autotuner cache (bs_tune.cu): key of a (GPU, precision, rule, near rule, directions, size class), the
-// variant stored for it (-1 if none, or if its launch shape does not match this build), and a store that
+// variant stored for it (-1 if none, or if its launch shape does not match the compiled variant table), and a store that
 // also writes the cache file
 std::string variant_shape_string(int precision, int Q, int near_rule, int variant);
 std::string tune_key(const char *gpu_name, int n_sm, int precision, int Q, int near_rule, int L, int64_t k,

@@ -5,7 +5,7 @@
 // the points are the mesh's nodes evaluated by bs_velocity_nodes (where the mesh walk can take the near
 // field) or arbitrary points -- to
 // the variant bs_autotune timed fastest, with that variant's launch shape as a check: an entry whose
-// shape no longer matches the variant table of this build is ignored.  Entries are read from two JSON
+// shape no longer matches the compiled variant table is ignored.  Entries are read from two JSON
 // files: the one shipped beside the package (tune_cache.json next to the library's _build directory)
 // and the file named by the environment variable BS_TUNE_CACHE (its entries take precedence).
 // bs_autotune writes new entries to BS_TUNE_CACHE when it is set, else to the shipped file.
@@ -168,7 +168,7 @@ int tune_lookup(const std::string &key, int precision, int Q, int near_rule)
     const auto it = g_entries.find(key);
     if (it == g_entries.end()) return -1;
     const Entry &e = it->second;
-    if (e.shape != variant_shape_string(precision, Q, near_rule, e.variant)) return -1;  // another build's table
+    if (e.shape != variant_shape_string(precision, Q, near_rule, e.variant)) return -1;  // written by a library with another variant table
     return e.variant;
 }
 
