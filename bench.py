@@ -543,7 +543,9 @@ def steps_workload(args):
 def variants_workload(args):
     """Every variant of the float32 four-point ray rule on the headline workload (the 64^3 Fourier mesh at
     all nodes, or --points nodes nearest the centre), each pinned in turn: ms per evaluation (mean of
-    --steps after --warmup), registers-bound CTAs per SM as launched, and the shape."""
+    --steps after --warmup) and the shape.  The nodes are evaluated as arbitrary points (bs_velocity: far sweep
+    and near pass or in-kernel drain), or with --at-nodes by bs_velocity_nodes (the walk takes the near field of
+    the variants that leave it out)."""
     import torch
 
     import paper_0712_1695_gb300 as bs
@@ -555,6 +557,8 @@ def variants_workload(args):
     if args.points:
         sel = np.sort(np.argsort(np.linalg.norm(mesh.nodes, axis=1), kind="stable")[:args.points])
         nodes = np.ascontiguousarray(mesh.nodes[sel])
+    if args.at_nodes and args.points:
+        raise SystemExit("--at-nodes evaluates all nodes; drop --points")
     pts = torch.from_numpy(nodes).cuda()
     out = torch.empty_like(pts)
     P = dict(PARAMS, precision=bs.BS_FP32)
@@ -564,13 +568,19 @@ def variants_workload(args):
     with ClockSampler(0) as clk:
         for v in only:
             h.bs_set_variant(bs.BS_FP32, 4, bs.BS_NEAR_RAY, v)
+
+            def run():
+                if args.at_nodes:
+                    h.bs_velocity_nodes(out_dev=out, **P)
+                else:
+                    h.bs_velocity(pts, out_dev=out, **P)
             for _ in range(args.warmup):
-                h.bs_velocity(pts, out_dev=out, **P)
+                run()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(args.steps):
-                h.bs_velocity(pts, out_dev=out, **P)
+                run()
             e1.record()
             torch.cuda.synchronize()
             h.bs_status()
@@ -579,6 +589,7 @@ def variants_workload(args):
                              interactions_per_s=len(nodes) * mesh.n_tets / (ms * 1e-3)))
     rows.sort(key=lambda r: r["ms"])
     print(json.dumps({"metric": "ms per evaluation by kernel variant (FP32, 4-point rule, 8x16 directions)",
+                      "path": "bs_velocity_nodes" if args.at_nodes else "bs_velocity",
                       "points": len(nodes), "tets": mesh.n_tets, "steps": args.steps, "warmup": args.warmup,
                       "rows": rows, "clocks": clk.summary()}), flush=True)
     return 0
@@ -688,6 +699,8 @@ def main():
                          "every float32 kernel variant timed on the headline workload; rules: at the nodes of a "
                          "24^3 mesh, variant 0 against the variant leaving the near pairs to the walk, per precision "
                          "and tet rule")
+    ap.add_argument("--at-nodes", action="store_true",
+                    help="variants workload: evaluate through bs_velocity_nodes (all nodes only)")
     ap.add_argument("--rings-n", type=int, default=80, help="nodes per side of the rings workload")
     ap.add_argument("--rings-mode", default="hybrid", choices=["hybrid", "allray-stretch"],
                     help="rings workload: the far/near rule with frozen vorticity, or the all-ray method with vortex "
