@@ -175,6 +175,14 @@ __device__ __forceinline__ int walk_reenter(const WalkArgs &a, V3<T> x, V3<T> d,
 // order on a tie).  One pass serves both directions (the margins along -s are the negated products), reading
 // the incident tets' face gradients and their reciprocal norms from the warp's staged copy (count <=
 // kWalkIncCap) or, for a node with more incident tets, from the walk records.
+// two consecutive float4 of read-only global memory in one 256-bit load (p 32-byte aligned)
+__device__ __forceinline__ void ldg_v8(const float4 *p, float4 &a, float4 &b)
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 constexpr int kWalkIncCap = 64;  // incident tets staged in shared memory per node
 // face j (0..2) of the three through vertex k (faces i != k, ascending): its gradient and reciprocal norm,
 // from the walk record's g1..g3 (g0 = -(g1 + g2 + g3)); selects, no indexed register arrays
@@ -261,7 +269,11 @@ __device__ V3<float> walk_f32(const WalkArgs &a, WalkStart st, V3<double> xd, co
             break;
         }
         const float4 *r = a.wrec + (int64_t)T * kWalkRecVec4;
-        const float4 q0 = __ldg(r), q1 = __ldg(r + 1), q2 = __ldg(r + 2), q3 = __ldg(r + 3);
+        // the record in five loads, 32 bytes where the registers allow (a gather: one L1 wavefront per lane and
+        // load, so the fewer loads the better); the vorticities further down
+        float4 q0, q1, q2, q3;
+        ldg_v8(r, q0, q1);
+        ldg_v8(r + 2, q2, q3);
         const int4 nb = __ldg(reinterpret_cast<const int4 *>(r + 7));  // the face neighbours
         // the face the line came in through (from the previous tet, or from outside): never left through again
         const int inface = prevT >= 0 ? (nb.x == prevT ? 0 : nb.y == prevT ? 1 : nb.z == prevT ? 2 : 3) : entf;
@@ -324,7 +336,9 @@ __device__ V3<float> walk_f32(const WalkArgs &a, WalkStart st, V3<double> xd, co
             take = pair_is_near_f32(xh[0] - o.x, xh[1] - o.y, xh[2] - o.z, c, a.far_ratio2_f);
         }
         // omega at the vertices (w0 w1 w2 w3, 12 floats)
-        const float4 q4 = __ldg(r + 4), q5 = __ldg(r + 5), q6 = __ldg(r + 6);
+        float4 q4, q5;
+        ldg_v8(r + 4, q4, q5);
+        const float4 q6 = __ldg(r + 6);
         float ge[4];  // g_i . e
         if constexpr (GRAD) {
             ge[1] = dot3(g[1], e);
