@@ -30,6 +30,8 @@ const VariantEntry kF32Q4[] = {
     BS_V(4, 32, 2, 3, 1, 1, true, 1), BS_V(1, 32, 4, 5, 2, 1, false, 1),
     // one point per thread with the near pairs left to the near pass (small meshes, batches)
     BS_V(1, 32, 3, 7, 3, 1, false, 2), BS_V(1, 32, 4, 6, 3, 1, false, 2), BS_V(2, 32, 3, 5, 3, 1, false, 2),
+    // the tet loop unrolled by 4 (126 registers, no spills)
+    BS_V(3, 32, 2, 4, 3, 1, false, 4), BS_V(3, 32, 3, 4, 3, 1, false, 4),
 };
 #undef BS_V
 
