@@ -855,14 +855,26 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     const int64_t BP = (int64_t)shape.threads * shape.points_per_thread;
     const int64_t n_blocks = (k + BP - 1) / BP;
     const int64_t n_tiles = (h->n_tets + shape.tile - 1) / shape.tile;
-    const int64_t target = 16LL * h->n_sm * occ;
-    int64_t n_chunks = std::min<int64_t>(std::max<int64_t>((target + n_blocks - 1) / n_blocks, 1), n_tiles);
+    const int64_t slots = (int64_t)h->n_sm * occ;
+    const int64_t target = 16LL * slots;
+    const int64_t c0 = std::min<int64_t>(std::max<int64_t>((target + n_blocks - 1) / n_blocks, 1), n_tiles);
     // at least kMinTilesPerItem tiles per item (shorter items are dominated by their set-up), unless that
     // leaves the GPU with fewer items than it has CTA slots
     const int64_t min_per =
-        n_blocks * ((n_tiles + kMinTilesPerItem - 1) / kMinTilesPerItem) < (int64_t)h->n_sm * occ ? 1 : kMinTilesPerItem;
-    const int64_t per = std::min<int64_t>(std::max<int64_t>((n_tiles + n_chunks - 1) / n_chunks, min_per), n_tiles);
-    n_chunks = (n_tiles + per - 1) / per;
+        n_blocks * ((n_tiles + kMinTilesPerItem - 1) / kMinTilesPerItem) < slots ? 1 : kMinTilesPerItem;
+    // the persistent CTAs pull equal items, so the launch takes about ceil(items / slots) item times: of the chunk
+    // counts c0..2 c0, take the one with the least waves x tiles per item (the last wave as full as it can be)
+    int64_t per = 0, n_chunks = 0, best = 0;
+    for (int64_t c = c0; c <= std::min<int64_t>({2 * c0, c0 + 256, n_tiles}); ++c) {
+        const int64_t pc = std::min<int64_t>(std::max<int64_t>((n_tiles + c - 1) / c, min_per), n_tiles);
+        const int64_t cc = (n_tiles + pc - 1) / pc;
+        const int64_t cost = ((n_blocks * cc + slots - 1) / slots) * pc;
+        if (n_chunks == 0 || cost < best) {
+            best = cost;
+            per = pc;
+            n_chunks = cc;
+        }
+    }
 
     const int bits = order_grid_bits(k);
     BS_CUDA(ensure_order(h, k, bits, st));
