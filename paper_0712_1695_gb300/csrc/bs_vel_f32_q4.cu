@@ -13,8 +13,9 @@ namespace {
 
 // variant 0 is the default; the first variant with one point per thread and tiles of 32 serves small meshes
 const VariantEntry kF32Q4[] = {
-    // near pairs left to the near pass: the far sweep has no drain (no spills at 4 CTAs per SM)
-    BS_V(3, 32, 3, 4, 3, 1, false, 2), BS_V(3, 32, 2, 4, 3, 1, false, 1), BS_V(3, 64, 2, 4, 3, 1, false, 1),
+    // near pairs left to the near pass: the far sweep has no drain (no spills at 4 CTAs per SM); variant 0 unrolls
+    // the tet loop by 4 (the default for sizes the autotuner has not seen)
+    BS_V(3, 32, 2, 4, 3, 1, false, 4), BS_V(3, 32, 2, 4, 3, 1, false, 1), BS_V(3, 64, 2, 4, 3, 1, false, 1),
     BS_V(4, 32, 2, 4, 3, 1, false, 1),
     // one point per thread (small meshes)
     BS_V(1, 32, 4, 5, 0, 1, false, 1),
@@ -30,8 +31,8 @@ const VariantEntry kF32Q4[] = {
     BS_V(4, 32, 2, 3, 1, 1, true, 1), BS_V(1, 32, 4, 5, 2, 1, false, 1),
     // one point per thread with the near pairs left to the near pass (small meshes, batches)
     BS_V(1, 32, 3, 7, 3, 1, false, 2), BS_V(1, 32, 4, 6, 3, 1, false, 2), BS_V(2, 32, 3, 5, 3, 1, false, 2),
-    // the tet loop unrolled by 4 (126 registers, no spills)
-    BS_V(3, 32, 2, 4, 3, 1, false, 4), BS_V(3, 32, 3, 4, 3, 1, false, 4),
+    // three stages, the tet loop unrolled by 2; three stages unrolled by 4
+    BS_V(3, 32, 3, 4, 3, 1, false, 2), BS_V(3, 32, 3, 4, 3, 1, false, 4),
 };
 #undef BS_V
 
