@@ -191,6 +191,9 @@ struct bs_batch_ctx {
     size_t partial_cap = 0;
     double *near_out = nullptr;  // the near pass's totals over all meshes' points
     std::vector<WalkArgs> walks;  // per mesh: the near walk of the captured launch sequence (empty: none)
+    // the near walks run concurrently on side streams, forked from the caller's stream and joined back into it
+    std::vector<cudaStream_t> walk_streams;
+    std::vector<cudaEvent_t> walk_events;  // [0] the fork, [1 + k] the join of side stream k
     const int **d_near_skip = nullptr;   // device [n]: per mesh, the walk's mode flag (near pass skips walked meshes)
     std::vector<const int *> h_near_skip;  // its host copy
     unsigned long long *work_counter = nullptr;
@@ -207,6 +210,8 @@ namespace {
 void free_batch(bs_batch_ctx *b)
 {
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaStream_t s : b->walk_streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->walk_events) cudaEventDestroy(e);
     void *bufs[] = {b->perm, b->keys, b->cell_count, b->box, b->d_meshes, b->partial, b->work_counter, b->flag,
                     b->lines.f32, b->lines.f64, b->near_out, (void *)b->d_near_skip};
     for (void *p : bufs)
@@ -981,6 +986,61 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
     return BS_OK;
 }
 
+// The batch's near walks, one per mesh, spread over side streams so that several meshes' walks share the GPU (a
+// small mesh's walk is about one wave of warps whose gathers wait on one another).  The side streams wait on a
+// fork event of st, take the walks largest mesh first in turn, and st waits on each one's join event; the walks
+// write disjoint outputs, so their order does not change the result.  Inside a stream capture this records the
+// walks as parallel branches of the graph.  Every side stream that waited on the fork is joined back, whatever
+// fails in between, so that a capture can always end.  The side streams and events exist already (made by
+// ensure_walk_streams outside any capture).
+cudaError_t ensure_walk_streams(bs_batch_ctx *b)
+{
+    while ((int)b->walk_streams.size() < kBatchWalkStreams) {
+        cudaStream_t s = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        b->walk_streams.push_back(s);
+    }
+    while ((int)b->walk_events.size() < kBatchWalkStreams + 1) {
+        cudaEvent_t e = nullptr;
+        cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (r != cudaSuccess) return r;
+        b->walk_events.push_back(e);
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_batch_walks(bs_batch_ctx *b, int prec, cudaStream_t st)
+{
+    const int n = (int)b->walks.size();
+    if (n == 0) return cudaSuccess;
+    if ((int)b->walk_streams.size() < kBatchWalkStreams || (int)b->walk_events.size() < kBatchWalkStreams + 1)
+        return cudaErrorNotReady;  // ensure_walk_streams was not called
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return b->walks[x].n_nodes > b->walks[y].n_nodes; });
+    const int K = std::min(n, (int)b->walk_streams.size());
+    cudaError_t first = cudaEventRecord(b->walk_events[0], st);
+    if (first != cudaSuccess) return first;
+    for (int k = 0; k < K; ++k) {
+        cudaStream_t s = b->walk_streams[k];
+        cudaError_t e = cudaStreamWaitEvent(s, b->walk_events[0], 0);
+        if (e != cudaSuccess) {  // not forked: nothing to join
+            if (first == cudaSuccess) first = e;
+            continue;
+        }
+        for (int i = k; first == cudaSuccess && i < n; i += K) {
+            e = launch_walk(prec, b->walks[order[i]], s);
+            if (e != cudaSuccess) first = e;
+        }
+        e = cudaEventRecord(b->walk_events[1 + k], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->walk_events[1 + k], 0);
+        if (e != cudaSuccess && first == cudaSuccess) first = e;
+    }
+    return first;
+}
+
 }  // namespace
 
 int bs_velocity_host(bs_handle h, const double *eval_pts_host, int64_t k, const bs_params *p, double *out_host,
@@ -1294,6 +1354,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         b->h_near_skip = skips;
         changed = true;
     }
+    if (!walks.empty()) BS_CUDA(ensure_walk_streams(b));
     if (walks.size() != b->walks.size() ||
         (!walks.empty() && memcmp(walks.data(), b->walks.data(), sizeof(WalkArgs) * walks.size()) != 0)) {
         b->walks = walks;
@@ -1354,7 +1415,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         BS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         int grid = 0;
         cudaError_t e1 = launch_velocity(prec, a, b->n_sm, st, &grid);
-        for (size_t i = 0; e1 == cudaSuccess && i < b->walks.size(); ++i) e1 = launch_walk(prec, b->walks[i], st);
+        if (e1 == cudaSuccess) e1 = launch_batch_walks(b, prec, st);
         if (e1 == cudaSuccess) e1 = launch_near_pass(prec, a, st);  // no-op unless the variant leaves near pairs
         cudaError_t e2 = e1 == cudaSuccess ? launch_reduce(a, st) : e1;
         cudaError_t e3 = cudaStreamEndCapture(st, &g);
@@ -1372,7 +1433,7 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
     } else {
         int grid = 0;
         BS_CUDA(launch_velocity(prec, a, b->n_sm, st, &grid));
-        for (const WalkArgs &w : b->walks) BS_CUDA(launch_walk(prec, w, st));
+        BS_CUDA(launch_batch_walks(b, prec, st));
         BS_CUDA(launch_near_pass(prec, a, st));
         BS_CUDA(launch_reduce(a, st));
     }

@@ -181,6 +181,8 @@ struct VelocityArgs {
 // launch on few points aims for by splitting the tiles among several CTAs per group
 constexpr int kNearPassWarps = 1;
 constexpr int kNearPassBlocksPerSm = 32;
+// side streams a batch's per-mesh near walks are spread over (graph branches that run concurrently)
+constexpr int kBatchWalkStreams = 8;
 
 // far ratio of a launch: its square (+inf for the all-ray rule) in double and float, the ratio in float
 inline void set_far_ratio(VelocityArgs &a, double far_ratio)
