@@ -315,9 +315,10 @@ BS_API int bs_tet_rule(int order, double *bary_host, double *w_host);
  * (the first call builds each mesh's walk tables on the host and synchronises),
  * else by one near pass over the points of every such mesh.  The meshes' walks
  * run concurrently on 8 non-blocking side streams the batch owns (created by
- * the first call that walks, destroyed by bs_batch_destroy): they wait on an
- * event recorded on `stream` after the far kernel, and `stream` waits on each
- * of them before the near pass, so the call is ordered on `stream` alone. */
+ * the first call that walks, destroyed by bs_batch_destroy), alongside the far
+ * kernel, which they do not depend on: they wait on an event recorded on
+ * `stream` before it, and `stream` waits on each of them before the near pass,
+ * so the call is ordered on `stream` alone. */
 BS_API int bs_batch_create(const bs_handle *meshes, int n, bs_batch *out);
 BS_API int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void *stream);
 /* Synchronise `stream` and report a device error of the batch's launches since

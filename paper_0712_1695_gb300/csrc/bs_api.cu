@@ -987,12 +987,12 @@ int velocity_impl(bs_handle h, const double *eval_pts_dev, int64_t k, const bs_p
 }
 
 // The batch's near walks, one per mesh, spread over side streams so that several meshes' walks share the GPU (a
-// small mesh's walk is about one wave of warps whose gathers wait on one another).  The side streams wait on a
-// fork event of st, take the walks largest mesh first in turn, and st waits on each one's join event; the walks
-// write disjoint outputs, so their order does not change the result.  Inside a stream capture this records the
-// walks as parallel branches of the graph.  Every side stream that waited on the fork is joined back, whatever
-// fails in between, so that a capture can always end.  The side streams and events exist already (made by
-// ensure_walk_streams outside any capture).
+// small mesh's walk is about one wave of warps whose gathers wait on one another) and overlap the far kernel, which
+// they do not depend on (they read the meshes' tables and write their own meshes' near totals).  fork_batch_walks:
+// the side streams wait on an event recorded on st, take the walks largest mesh first in turn, and each records
+// its join event; join_batch_walks: st waits on those.  Their order does not change the result.  Inside a stream
+// capture this records the walks as parallel branches of the graph.  Every side stream that waited on the fork
+// records its join event, whatever fails in between, and *forked marks it, so that a capture can always end.
 cudaError_t ensure_walk_streams(bs_batch_ctx *b)
 {
     while ((int)b->walk_streams.size() < kBatchWalkStreams) {
@@ -1010,12 +1010,13 @@ cudaError_t ensure_walk_streams(bs_batch_ctx *b)
     return cudaSuccess;
 }
 
-cudaError_t launch_batch_walks(bs_batch_ctx *b, int prec, cudaStream_t st)
+cudaError_t fork_batch_walks(bs_batch_ctx *b, int prec, cudaStream_t st, unsigned *forked)
 {
+    *forked = 0;
     const int n = (int)b->walks.size();
     if (n == 0) return cudaSuccess;
     if ((int)b->walk_streams.size() < kBatchWalkStreams || (int)b->walk_events.size() < kBatchWalkStreams + 1)
-        return cudaErrorNotReady;  // ensure_walk_streams was not called
+        return cudaErrorNotReady;  // ensure_walk_streams was not called (it runs outside any capture)
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
@@ -1035,9 +1036,22 @@ cudaError_t launch_batch_walks(bs_batch_ctx *b, int prec, cudaStream_t st)
             if (e != cudaSuccess) first = e;
         }
         e = cudaEventRecord(b->walk_events[1 + k], s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->walk_events[1 + k], 0);
-        if (e != cudaSuccess && first == cudaSuccess) first = e;
+        if (e == cudaSuccess)
+            *forked |= 1u << k;
+        else if (first == cudaSuccess)
+            first = e;
     }
+    return first;
+}
+
+cudaError_t join_batch_walks(bs_batch_ctx *b, cudaStream_t st, unsigned forked)
+{
+    cudaError_t first = cudaSuccess;
+    for (int k = 0; k < (int)b->walk_streams.size(); ++k)
+        if (forked & (1u << k)) {
+            const cudaError_t e = cudaStreamWaitEvent(st, b->walk_events[1 + k], 0);
+            if (e != cudaSuccess && first == cudaSuccess) first = e;
+        }
     return first;
 }
 
@@ -1414,8 +1428,11 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         cudaGraph_t g = nullptr;
         BS_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         int grid = 0;
-        cudaError_t e1 = launch_velocity(prec, a, b->n_sm, st, &grid);
-        if (e1 == cudaSuccess) e1 = launch_batch_walks(b, prec, st);
+        unsigned forked = 0;
+        cudaError_t e1 = fork_batch_walks(b, prec, st, &forked);
+        if (e1 == cudaSuccess) e1 = launch_velocity(prec, a, b->n_sm, st, &grid);
+        const cudaError_t ej = join_batch_walks(b, st, forked);
+        if (e1 == cudaSuccess) e1 = ej;
         if (e1 == cudaSuccess) e1 = launch_near_pass(prec, a, st);  // no-op unless the variant leaves near pairs
         cudaError_t e2 = e1 == cudaSuccess ? launch_reduce(a, st) : e1;
         cudaError_t e3 = cudaStreamEndCapture(st, &g);
@@ -1432,8 +1449,12 @@ int bs_batch_velocity(bs_batch b, const bs_params *p, double *const *outs, void 
         BS_CUDA(cudaGraphLaunch(b->graph, st));
     } else {
         int grid = 0;
-        BS_CUDA(launch_velocity(prec, a, b->n_sm, st, &grid));
-        BS_CUDA(launch_batch_walks(b, prec, st));
+        unsigned forked = 0;
+        cudaError_t e1 = fork_batch_walks(b, prec, st, &forked);
+        if (e1 == cudaSuccess) e1 = launch_velocity(prec, a, b->n_sm, st, &grid);
+        const cudaError_t ej = join_batch_walks(b, st, forked);
+        BS_CUDA(e1);
+        BS_CUDA(ej);
         BS_CUDA(launch_near_pass(prec, a, st));
         BS_CUDA(launch_reduce(a, st));
     }

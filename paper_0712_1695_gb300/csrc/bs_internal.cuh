@@ -183,6 +183,7 @@ constexpr int kNearPassWarps = 1;
 constexpr int kNearPassBlocksPerSm = 32;
 // side streams a batch's per-mesh near walks are spread over (graph branches that run concurrently)
 constexpr int kBatchWalkStreams = 8;
+static_assert(kBatchWalkStreams <= 32, "the forked side streams are a 32-bit mask");
 
 // far ratio of a launch: its square (+inf for the all-ray rule) in double and float, the ratio in float
 inline void set_far_ratio(VelocityArgs &a, double far_ratio)
