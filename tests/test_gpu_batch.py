@@ -38,6 +38,8 @@ def _single(h, m, prec):
 
 @pytest.mark.parametrize("prec", [bs.BS_FP64, bs.BS_FP32], ids=["fp64", "fp32"])
 def test_batch_matches_single_mesh_path(meshes, prec):
+    """The batch on a stream of its own, waited for with that stream's synchronize alone: the meshes' near walks
+    run on the batch's side streams, so this also checks that they are joined back into the caller's stream."""
     ms, hs = meshes
     batch = bs.Batch(hs)
     stream = torch.cuda.Stream()
