@@ -1053,18 +1053,33 @@ bool build_walk_mesh(const int32_t *tets_host, int64_t n_nodes, int64_t n_tets, 
     struct Face {
         int32_t a, b, c, slot;
     };
+    // in (a, b, c, slot) order: a counting sort by the smallest vertex a (the slots ascending within each a), then
+    // each a's few faces sorted by (b, c, slot)
+    auto face_of = [&](int64_t slot) {
+        const int64_t t = slot >> 2;
+        const int i = (int)(slot & 3);
+        int32_t v[3], j = 0;
+        for (int k = 0; k < 4; ++k)
+            if (k != i) v[j++] = tets_host[4 * t + k];
+        std::sort(v, v + 3);
+        return Face{v[0], v[1], v[2], (int32_t)slot};
+    };
+    std::vector<int64_t> a_off((size_t)n_nodes + 1, 0);
+    for (int64_t s = 0; s < 4 * n_tets; ++s) ++a_off[face_of(s).a + 1];
+    for (int64_t q = 0; q < n_nodes; ++q) a_off[q + 1] += a_off[q];
     std::vector<Face> f((size_t)4 * n_tets);
-    for (int64_t t = 0; t < n_tets; ++t)
-        for (int i = 0; i < 4; ++i) {
-            int32_t v[3], j = 0;
-            for (int k = 0; k < 4; ++k)
-                if (k != i) v[j++] = tets_host[4 * t + k];
-            std::sort(v, v + 3);
-            f[4 * t + i] = {v[0], v[1], v[2], (int32_t)(4 * t + i)};
+    {
+        std::vector<int64_t> at(a_off.begin(), a_off.end() - 1);
+        for (int64_t s = 0; s < 4 * n_tets; ++s) {
+            const Face x = face_of(s);
+            f[at[x.a]++] = x;
         }
-    std::sort(f.begin(), f.end(), [](const Face &x, const Face &y) {
-        return std::tie(x.a, x.b, x.c, x.slot) < std::tie(y.a, y.b, y.c, y.slot);
-    });
+    }
+    for (int64_t q = 0; q < n_nodes; ++q)
+        if (a_off[q + 1] - a_off[q] > 1)
+            std::sort(f.begin() + a_off[q], f.begin() + a_off[q + 1], [](const Face &x, const Face &y) {
+                return std::tie(x.b, x.c, x.slot) < std::tie(y.b, y.c, y.slot);
+            });
     w.nbr.assign((size_t)4 * n_tets, -1);
     bool conforming = true;
     std::vector<char> on_boundary((size_t)n_nodes, 0);
